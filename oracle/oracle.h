@@ -1,0 +1,102 @@
+/*
+ * Plain serial FP64 CPU oracle of the Green's-function-corrected Brownian-dynamics step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's CPU-baseline
+ * leg may load or call this library.  It shares no code, header, table or helper with the CUDA
+ * library; it is written from the paper (Sections 2-4) and from the published definitions of the
+ * algorithms it uses (Philox4x32-10, Box-Muller, the erfc continued fraction).
+ *
+ * Units: lengths in the caller's unit (um), times in s.  Inside the Green's-function routines all
+ * lengths are scaled by the contact radius a (R = r/a) and time by a^2/D (tau = D t / a^2), as in
+ * Section 4.1 of the paper.
+ */
+#ifndef RD_ORACLE_H
+#define RD_ORACLE_H
+#include <stdint.h>
+
+#define OR_MAX_SPECIES 16
+#define OR_MAX_PAIRS 32
+#define OR_MAX_DECAYS 16
+
+enum { OR_BC_NONE = 0, OR_BC_ABS = 1, OR_BC_REF = 2, OR_BC_RAD = 3 };
+
+/* Random-stream tags (counter word 3, low byte). */
+enum {
+  OR_TAG_INIT0 = 1, OR_TAG_INIT1 = 2, OR_TAG_UNI = 3, OR_TAG_DISP0 = 4, OR_TAG_DISP1 = 5,
+  OR_TAG_ENC = 6, OR_TAG_RES = 7, OR_TAG_DIR = 8, OR_TAG_DISS0 = 9, OR_TAG_DISS1 = 10,
+  OR_TAG_DISS2 = 11, OR_TAG_DISS3 = 12
+};
+
+typedef struct {
+  int32_t s1, s2, bc, product;
+  double sigma, ka;
+} or_pair;
+
+typedef struct {
+  int32_t parent, n_products, p0, p1;
+  double kd, sigma_place;
+} or_decay;
+
+typedef struct {
+  int32_t dim, n_species, n_pairs, n_decays;
+  double L, dt, c_cut, tau_s;
+  uint64_t seed;
+  uint32_t replica, pad_;
+  double D[OR_MAX_SPECIES];
+  or_pair pairs[OR_MAX_PAIRS];
+  or_decay decays[OR_MAX_DECAYS];
+} or_system;
+
+typedef struct {
+  int64_t n, cap;
+  double* x;          /* cap*3, z ignored in 2D */
+  int32_t* sp;
+  uint32_t* id;
+  uint32_t step, next_id;
+  double t;
+} or_state;
+
+typedef struct {
+  int64_t candidates, fired, matched, reactions, resampled, decays, recombined, near_threshold,
+      overlaps, products;
+} or_stats;
+
+/* Optional per-candidate record (NULL to skip).  One entry per candidate pair. */
+typedef struct {
+  int64_t cap, n;
+  uint32_t *ida, *idb;
+  double *p_enc, *u_enc;
+  int32_t *fired, *matched;
+} or_trace;
+
+/* Philox4x32-10 and the derived uniforms / normals. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double or_u52(uint32_t hi, uint32_t lo);
+
+/* erfcx(x) = exp(x^2) erfc(x) and the scaled repeated integral of erfc. */
+double or_erfcx(double x);
+double or_ierfc_scaled(int n, double z);
+
+/* 3D radial Green's-function quantities (scaled units). */
+double or_p_enc3(double R, double R0, double tau);
+double or_p_reac3(double R, double R0, double tau, double h);
+double or_tail3(double V, double R0, double tau);
+double or_resample3(double U, double R0, double tau);
+double or_S_abs3(double R0, double tau);
+double or_S_rad3(double R0, double tau, double h);
+
+/* 2D radial Green's-function quantities (scaled units). */
+double or_gamma2(int k, int bc, double R, double R0, double h);
+double or_gbc2_series(int bc, double R, double R0, double tau, double h, int nterms);
+double or_gbc2_weber(int bc, double R, double R0, double tau, double h);
+double or_gfree2(double R, double R0, double tau);
+double or_p_enc2(double R, double R0, double tau, double tau_s);
+double or_p_reac2(double R, double R0, double tau, double h, double tau_s);
+double or_tail2(double V, double R0, double tau, double tau_s);
+double or_resample2(double U, double R0, double tau, double tau_s);
+
+/* Whole step and initial condition. */
+int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st);
+int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* stats, or_trace* trace);
+
+#endif

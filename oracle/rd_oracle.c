@@ -1,0 +1,661 @@
+/*
+ * Plain serial FP64 CPU oracle of one Green's-function-corrected Brownian-dynamics step
+ * (Pruestel & Meier-Schellersheim, "Coarse-grained stochastic particle-based reaction-diffusion
+ * simulation algorithm", arXiv:1107.0270).
+ *
+ * TEST INFRASTRUCTURE ONLY: this file is the independent checker of the CUDA library.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.  It is slow on
+ * purpose: an O(N^2) candidate search, a sort-based greedy matching and bisection root finding,
+ * so that each step can be read against the paper.
+ *
+ * Conventions fixed where the paper is silent (they are the library's step specification too):
+ *  - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo, seed hi), counter =
+ *    (step, id_a, id_b, tag | replica << 8), id_b = 0xFFFFFFFF for one-particle streams;
+ *    U = ((x >> 12) + 0.5) 2^-52 from x = (w_hi << 32) | w_lo, exactly representable, in (0,1);
+ *    normals by Box-Muller.
+ *  - candidate pairs: interacting species pairs whose minimum-image start-of-step distance is
+ *    below r_cut = sigma + c sqrt(2 D dt) (Section 3, cut-off radius).
+ *  - conflicts (Section 3, "Details"): key = -ln(U_sel)/p_enc per fired pair; fired pairs are
+ *    accepted greedily in ascending (key, id_a, id_b); an exponential race gives each particle the
+ *    paper's selection probability p_enc,j / sum p_enc among its own fired candidates.
+ *  - unimolecular decays are drawn first from the start-of-step state; decaying particles neither
+ *    move freely nor pair this step.  Products take no part in bimolecular reactions this step.
+ *  - an encountered pair keeps the direction of its free-step separation; only its length is
+ *    resampled from the radial propagator (Section 3, "Details", first item).
+ *  - products: a bimolecular product sits at the centre of diffusion (Eq. Rcoo) of the pair; ids
+ *    are next_id + rank of the event ordered by its lower parent id; survivors keep their order
+ *    and products are appended, so the particle array stays sorted by id.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI 3.14159265358979323846
+#define SQRT_PI 1.77245385090551602730
+#define NEAR_THRESHOLD 1e-9
+
+/* ------------------------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64 multiplies with  */
+/* the published multipliers, key bumped by the two Weyl constants between rounds.              */
+/* ------------------------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double or_u52(uint32_t hi, uint32_t lo) {
+  uint64_t x = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return ((double)(x >> 12) + 0.5) * 0x1p-52;
+}
+
+static void stream(const or_system* sys, uint32_t c0, uint32_t ida, uint32_t idb, uint32_t tag,
+                   uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, ida, idb, tag | (sys->replica << 8)};
+  uint32_t key[2] = {(uint32_t)(sys->seed & 0xFFFFFFFFu), (uint32_t)(sys->seed >> 32)};
+  or_philox4x32_10(ctr, key, out);
+}
+
+/* Box-Muller: two independent unit normals from two uniforms in (0,1). */
+static void box_muller(double u1, double u2, double* n0, double* n1) {
+  double rad = sqrt(-2.0 * log(u1));
+  *n0 = rad * cos(2.0 * PI * u2);
+  *n1 = rad * sin(2.0 * PI * u2);
+}
+
+/* Up to four unit normals from one or two Philox calls with consecutive tags. */
+static void normals(const or_system* sys, uint32_t c0, uint32_t id, uint32_t tag0, int count,
+                    double* n) {
+  uint32_t w[4];
+  stream(sys, c0, id, 0xFFFFFFFFu, tag0, w);
+  box_muller(or_u52(w[0], w[1]), or_u52(w[2], w[3]), &n[0], &n[1]);
+  if (count > 2) {
+    double extra;
+    stream(sys, c0, id, 0xFFFFFFFFu, tag0 + 1, w);
+    box_muller(or_u52(w[0], w[1]), or_u52(w[2], w[3]), &n[2], &extra);
+    if (count > 3) n[3] = extra;
+  }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* erfcx(x) = exp(x^2) erfc(x).  For x < 4 the product of libm's exp and erfc; for x >= 4 the    */
+/* Laplace continued fraction of erfc (Abramowitz & Stegun 7.1.14),                             */
+/*   sqrt(pi) erfcx(x) = 1/(x + (1/2)/(x + 1/(x + (3/2)/(x + 2/(x + ...))))),                   */
+/* evaluated by the modified Lentz method.  cf_tail returns the tail K = (1/2)/(x + 1/(x + ...))  */
+/* so that sqrt(pi) erfcx(x) = 1/(x + K).                                                         */
+/* ------------------------------------------------------------------------------------------ */
+static double cf_tail(double x) {
+  /* Modified Lentz for f = b0 + a1/(b1 + a2/(b2 + ...)) with b0 = 0, a_n = n/2, b_n = x. */
+  const double tiny = 1e-300;
+  double f = tiny, C = f, Dv = 0.0;
+  for (int n = 1; n < 5000; ++n) {
+    double an = 0.5 * n;
+    Dv = x + an * Dv;
+    if (fabs(Dv) < tiny) Dv = tiny;
+    Dv = 1.0 / Dv;
+    C = x + an / C;
+    if (fabs(C) < tiny) C = tiny;
+    double delta = C * Dv;
+    f *= delta;
+    if (fabs(delta - 1.0) < 1e-16) break;
+  }
+  return f;
+}
+
+double or_erfcx(double x) {
+  if (x < 0.0) return 2.0 * exp(x * x) - or_erfcx(-x);
+  if (x < 4.0) return exp(x * x) * erfc(x);
+  return 1.0 / (SQRT_PI * (x + cf_tail(x)));
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 3D, Section 4.1.  With a = 1, tau = D t / a^2, u = R + R0 - 2, s = sqrt(tau):                  */
+/*  g_abs = [exp(-(R-R0)^2/4tau) - exp(-u^2/4tau)] / (8 pi R R0 sqrt(pi tau))                      */
+/*  g_rad = [exp(-(R-R0)^2/4tau) + exp(-u^2/4tau)                                                  */
+/*          - alpha sqrt(4 pi tau) exp(alpha^2 tau + alpha u) erfc(alpha s + u/2s)] / (same)       */
+/*  g_ref = g_rad at kappa_a = 0, alpha = 1 + h (the paper's kappa := (kappa_a+4 pi a D)/(4 pi a D)) */
+/* The radial free function is the angular average of the free Gaussian of Eq. (gaussian):       */
+/*  g_free = [exp(-(R-R0)^2/4tau) - exp(-(R+R0)^2/4tau)] / (8 pi R R0 sqrt(pi tau)).               */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Eq. (bayes1D) with radial Green's functions (Section 2.2.4): p_enc = 1 - g_abs/g_free.
+ * Dividing numerator and denominator by exp(-(R-R0)^2/4tau) and using
+ * (R+R0-2)^2 - (R-R0)^2 = 4 (R-1)(R0-1),  (R+R0)^2 - (R-R0)^2 = 4 R R0:
+ *   g_abs/g_free = (1 - exp(-(R-1)(R0-1)/tau)) / (1 - exp(-R R0/tau)).
+ * An overlapping end point (R <= 1) has certainly met the boundary (Section 3, step 2). */
+double or_p_enc3(double R, double R0, double tau) {
+  if (R <= 1.0) return 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  double ratio = (-expm1(-(R - 1.0) * (R0 - 1.0) / tau)) / (-expm1(-R * R0 / tau));
+  return 1.0 - ratio;
+}
+
+/* Eq. (psurv_radII): p_reac = (g_ref - g_rad) / (g_ref - g_abs).
+ * With E2 = exp(-u^2/4tau) and the identity exp(alpha^2 tau + alpha u) erfc(alpha s + u/2s)
+ * = E2 erfcx(alpha s + u/2s) (because (alpha s + u/2s)^2 = alpha^2 tau + alpha u + u^2/4tau), the
+ * common factor E2/(8 pi R R0 sqrt(pi tau)) cancels and the exp(-(R-R0)^2/4tau) terms drop out:
+ *   g_ref - g_abs ~ 2 - sqrt(4 pi tau) erfcx(s + u/2s)
+ *   g_ref - g_rad ~ sqrt(4 pi tau) [alpha erfcx(alpha s + u/2s) - erfcx(s + u/2s)]. */
+double or_p_reac3(double R, double R0, double tau, double h) {
+  if (R < 1.0) R = 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  double s = sqrt(tau), u = R + R0 - 2.0, alpha = 1.0 + h;
+  double c = sqrt(4.0 * PI * tau);
+  double ref_minus_abs = 2.0 - c * or_erfcx(s + u / (2.0 * s));
+  double ref_minus_rad = c * (alpha * or_erfcx(alpha * s + u / (2.0 * s)) - or_erfcx(s + u / (2.0 * s)));
+  double p = ref_minus_rad / ref_minus_abs;
+  if (p < 0.0) p = 0.0;
+  if (p > 1.0) p = 1.0;
+  return p;
+}
+
+/* Radial propagator of an encountered pair (Section 3, "Details"): density 4 pi R^2 (g_ref - g_abs)
+ * on R > 1.  Its integral over (1+V, inf) is, in closed form (w = R0 - 1, z = (V+w)/2s),
+ *   [erfc(z) + V exp(-z^2) erfcx(s + z)] / R0,
+ * (differentiate: d/dV gives -4 pi R^2 (g_ref - g_abs)), and over (1, inf) it is
+ * 1 - S_abs = erfc(w/2s)/R0.  or_tail3 returns the normalised tail fraction T(V) in [0,1]. */
+double or_tail3(double V, double R0, double tau) {
+  if (R0 < 1.0) R0 = 1.0;
+  double s = sqrt(tau), w = R0 - 1.0;
+  double z = (V + w) / (2.0 * s), z0 = w / (2.0 * s);
+  double num = erfc(z) + V * exp(-z * z) * or_erfcx(s + z);
+  return num / erfc(z0);
+}
+
+/* Inverse of the tail fraction: the R' >= 1 with T(R'-1) = U, by plain bisection to the last bit
+ * (T decreases monotonically from 1 at V = 0 to 0 as V grows). */
+double or_resample3(double U, double R0, double tau) {
+  double s = sqrt(tau);
+  double lo = 0.0, hi = s;
+  while (or_tail3(hi, R0, tau) > U) {
+    lo = hi;
+    hi *= 2.0;
+  }
+  for (int it = 0; it < 2000; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (or_tail3(mid, R0, tau) > U)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 1.0 + 0.5 * (lo + hi);
+}
+
+/* Survival probabilities, Eq. (SurvRad), by integrating the radial g's above over R > 1. */
+double or_S_abs3(double R0, double tau) {
+  double s = sqrt(tau);
+  return 1.0 - erfc((R0 - 1.0) / (2.0 * s)) / R0;
+}
+
+double or_S_rad3(double R0, double tau, double h) {
+  double s = sqrt(tau), w = R0 - 1.0, alpha = 1.0 + h;
+  double z0 = w / (2.0 * s);
+  return 1.0 - (h / alpha) / R0 * (erfc(z0) - exp(-z0 * z0) * or_erfcx(z0 + alpha * s));
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 2D routines are added with the 2D step.                                                       */
+/* ------------------------------------------------------------------------------------------ */
+double or_ierfc_scaled(int n, double z) { (void)n; (void)z; return NAN; }
+double or_gamma2(int k, int bc, double R, double R0, double h) { (void)k; (void)bc; (void)R; (void)R0; (void)h; return NAN; }
+double or_gbc2_series(int bc, double R, double R0, double tau, double h, int nterms) { (void)bc; (void)R; (void)R0; (void)tau; (void)h; (void)nterms; return NAN; }
+double or_gbc2_weber(int bc, double R, double R0, double tau, double h) { (void)bc; (void)R; (void)R0; (void)tau; (void)h; return NAN; }
+double or_gfree2(double R, double R0, double tau) { (void)R; (void)R0; (void)tau; return NAN; }
+double or_p_enc2(double R, double R0, double tau, double tau_s) { (void)R; (void)R0; (void)tau; (void)tau_s; return NAN; }
+double or_p_reac2(double R, double R0, double tau, double h, double tau_s) { (void)R; (void)R0; (void)tau; (void)h; (void)tau_s; return NAN; }
+double or_tail2(double V, double R0, double tau, double tau_s) { (void)V; (void)R0; (void)tau; (void)tau_s; return NAN; }
+double or_resample2(double U, double R0, double tau, double tau_s) { (void)U; (void)R0; (void)tau; (void)tau_s; return NAN; }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Geometry in the periodic box.                                                                  */
+/* ------------------------------------------------------------------------------------------ */
+static double min_image(double d, double L) {
+  if (d > 0.5 * L)
+    d -= L;
+  else if (d < -0.5 * L)
+    d += L;
+  return d;
+}
+
+static double wrap(double x, double L) {
+  if (x >= L) {
+    x -= L;
+  } else if (x < 0.0) {
+    x += L;
+    if (x >= L) x = 0.0;
+  }
+  return x;
+}
+
+/* Squared length summed left to right (the build disables floating-point contraction). */
+static double norm2(const double* v, int dim) {
+  double s = v[0] * v[0];
+  s = s + v[1] * v[1];
+  if (dim == 3) s = s + v[2] * v[2];
+  return s;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Per-pair-type parameters.                                                                      */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int rule;        /* index into sys->pairs, -1: no interaction */
+  double sigma, Drel, tau, h, rcut2;
+} pair_param;
+
+static void pair_params(const or_system* sys, pair_param table[OR_MAX_SPECIES][OR_MAX_SPECIES]) {
+  for (int a = 0; a < OR_MAX_SPECIES; ++a)
+    for (int b = 0; b < OR_MAX_SPECIES; ++b) table[a][b].rule = -1;
+  for (int k = 0; k < sys->n_pairs; ++k) {
+    const or_pair* p = &sys->pairs[k];
+    if (p->bc == OR_BC_NONE) continue;
+    pair_param pp;
+    pp.rule = k;
+    pp.sigma = p->sigma;
+    pp.Drel = sys->D[p->s1] + sys->D[p->s2];                 /* D_eff = D_A + D_B (Section 2.1) */
+    pp.tau = pp.Drel * sys->dt / (p->sigma * p->sigma);
+    if (sys->dim == 3)
+      pp.h = p->ka / (4.0 * PI * p->sigma * pp.Drel);       /* h~3D = kappa_a / (4 pi a D) */
+    else
+      pp.h = p->ka / (2.0 * PI * pp.Drel);                  /* h~2D = kappa_a / (2 pi D) */
+    double rc = p->sigma + sys->c_cut * sqrt(2.0 * pp.Drel * sys->dt);
+    pp.rcut2 = rc * rc;
+    table[p->s1][p->s2] = pp;
+    table[p->s2][p->s1] = pp;
+  }
+}
+
+static double p_enc_dim(const or_system* sys, double R, double R0, double tau) {
+  return sys->dim == 3 ? or_p_enc3(R, R0, tau) : or_p_enc2(R, R0, tau, sys->tau_s);
+}
+static double p_reac_dim(const or_system* sys, double R, double R0, double tau, double h) {
+  return sys->dim == 3 ? or_p_reac3(R, R0, tau, h) : or_p_reac2(R, R0, tau, h, sys->tau_s);
+}
+static double resample_dim(const or_system* sys, double U, double R0, double tau) {
+  return sys->dim == 3 ? or_resample3(U, R0, tau) : or_resample2(U, R0, tau, sys->tau_s);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Initial condition: uniform positions from the INIT streams, species in blocks of n_init.       */
+/* ------------------------------------------------------------------------------------------ */
+int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st) {
+  int64_t n = 0;
+  for (int s = 0; s < sys->n_species; ++s) n += n_init[s];
+  if (n > st->cap) return -1;
+  int64_t i = 0;
+  for (int s = 0; s < sys->n_species; ++s) {
+    for (int64_t k = 0; k < n_init[s]; ++k, ++i) {
+      uint32_t w[4];
+      stream(sys, 0u, (uint32_t)i, 0xFFFFFFFFu, OR_TAG_INIT0, w);
+      double x = or_u52(w[0], w[1]) * sys->L, y = or_u52(w[2], w[3]) * sys->L, z = 0.0;
+      if (sys->dim == 3) {
+        stream(sys, 0u, (uint32_t)i, 0xFFFFFFFFu, OR_TAG_INIT1, w);
+        z = or_u52(w[0], w[1]) * sys->L;
+      }
+      st->x[3 * i + 0] = x < sys->L ? x : 0.0;
+      st->x[3 * i + 1] = y < sys->L ? y : 0.0;
+      st->x[3 * i + 2] = z < sys->L ? z : 0.0;
+      st->sp[i] = s;
+      st->id[i] = (uint32_t)i;
+    }
+  }
+  st->n = n;
+  st->step = 0;
+  st->next_id = (uint32_t)n;
+  st->t = 0.0;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* One step (Section 3, steps 1-5).                                                               */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  int64_t a, b;   /* particle indices, id[a] < id[b] */
+  uint32_t ida, idb;
+  double p, key;
+  int rule;
+  int64_t tidx;   /* trace entry or -1 */
+} fired_pair;
+
+/* total order (key, id_a, id_b) */
+static int cmp_fired(const void* x, const void* y) {
+  const fired_pair* e = (const fired_pair*)x;
+  const fired_pair* f = (const fired_pair*)y;
+  if (e->key != f->key) return e->key < f->key ? -1 : 1;
+  if (e->ida != f->ida) return e->ida < f->ida ? -1 : 1;
+  if (e->idb != f->idb) return e->idb < f->idb ? -1 : 1;
+  return 0;
+}
+
+typedef struct {
+  int n;             /* number of products (0..2) */
+  int species[2];
+  double x[2][3];
+} products_t;
+
+int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* stats,
+            or_trace* trace) {
+  const int dim = sys->dim;
+  const double L = sys->L, dt = sys->dt;
+  const int64_t n = in->n;
+  const uint32_t step = in->step;
+  pair_param pp[OR_MAX_SPECIES][OR_MAX_SPECIES];
+  pair_params(sys, pp);
+  or_stats st;
+  memset(&st, 0, sizeof st);
+  if (trace) trace->n = 0;
+
+  double* x1 = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  int* decayed = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));     /* 0, or channel+1 */
+  int* consumed = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
+  int64_t* partner = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  products_t* prod = (products_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(products_t));
+  for (int64_t i = 0; i < n; ++i) partner[i] = -1;
+
+  /* Step 4 of Section 3, drawn first (start-of-step state): Poisson decay with probability
+   * 1 - exp(-k_d dt), Eq. (rad_prob); with several channels the total rate decides and a second
+   * uniform picks the channel in proportion to its rate. */
+  for (int64_t i = 0; i < n; ++i) {
+    double ktot = 0.0;
+    for (int c = 0; c < sys->n_decays; ++c)
+      if (sys->decays[c].parent == in->sp[i]) ktot += sys->decays[c].kd;
+    if (ktot <= 0.0) continue;
+    uint32_t w[4];
+    stream(sys, step, in->id[i], 0xFFFFFFFFu, OR_TAG_UNI, w);
+    double u = or_u52(w[0], w[1]);
+    double p_uni = -expm1(-ktot * dt);
+    if (fabs(u - p_uni) <= NEAR_THRESHOLD) st.near_threshold++;
+    if (!(u < p_uni)) continue;
+    double target = or_u52(w[2], w[3]) * ktot, acc = 0.0;
+    int chosen = -1, last = -1;
+    for (int c = 0; c < sys->n_decays; ++c) {
+      if (sys->decays[c].parent != in->sp[i]) continue;
+      last = c;
+      acc += sys->decays[c].kd;
+      if (chosen < 0 && target < acc) chosen = c;
+    }
+    if (chosen < 0) chosen = last;
+    decayed[i] = chosen + 1;
+  }
+
+  /* Step 1: free displacement sqrt(2 D dt) N(0,1) of every particle that did not decay. */
+  for (int64_t i = 0; i < n; ++i) {
+    double nrm[4] = {0, 0, 0, 0};
+    if (!decayed[i]) normals(sys, step, in->id[i], OR_TAG_DISP0, dim, nrm);
+    double ell = sqrt(2.0 * sys->D[in->sp[i]] * dt);
+    for (int d = 0; d < 3; ++d) {
+      double v = in->x[3 * i + d];
+      if (d < dim && !decayed[i]) v = wrap(v + ell * nrm[d], L);
+      x1[3 * i + d] = v;
+    }
+  }
+
+  /* Steps 2-3: every interacting pair within the cut-off (start-of-step minimum image distance)
+   * is tested with p_enc (overlap forces p_enc = 1) and a uniform draw. */
+  int64_t fcap = 1024, fn = 0;
+  fired_pair* fired = (fired_pair*)malloc(sizeof(fired_pair) * (size_t)fcap);
+  for (int64_t i = 0; i < n; ++i) {
+    if (decayed[i]) continue;
+    for (int64_t j = i + 1; j < n; ++j) {
+      if (decayed[j]) continue;
+      const pair_param* q = &pp[in->sp[i]][in->sp[j]];
+      if (q->rule < 0) continue;
+      int64_t a = in->id[i] < in->id[j] ? i : j;
+      int64_t b = a == i ? j : i;
+      double r0v[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) {
+        r0v[d] = min_image(in->x[3 * b + d] - in->x[3 * a + d], L);
+        rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
+      }
+      double r02 = norm2(r0v, dim);
+      if (!(r02 < q->rcut2)) continue;
+      double R0 = sqrt(r02) / q->sigma;
+      double R = sqrt(norm2(rv, dim)) / q->sigma;
+      double p = p_enc_dim(sys, R, R0, q->tau);
+      uint32_t w[4];
+      stream(sys, step, in->id[a], in->id[b], OR_TAG_ENC, w);
+      double u_enc = or_u52(w[0], w[1]), u_sel = or_u52(w[2], w[3]);
+      int fires = u_enc < p;
+      st.candidates++;
+      if (R <= 1.0) st.overlaps++;
+      if (fabs(u_enc - p) <= NEAR_THRESHOLD) st.near_threshold++;
+      int64_t tidx = -1;
+      if (trace && trace->n < trace->cap) {
+        tidx = trace->n;
+        trace->ida[trace->n] = in->id[a];
+        trace->idb[trace->n] = in->id[b];
+        trace->p_enc[trace->n] = p;
+        trace->u_enc[trace->n] = u_enc;
+        trace->fired[trace->n] = fires;
+        trace->matched[trace->n] = 0;
+        trace->n++;
+      }
+      if (!fires) continue;
+      if (fn == fcap) {
+        fcap *= 2;
+        fired = (fired_pair*)realloc(fired, sizeof(fired_pair) * (size_t)fcap);
+      }
+      fired[fn].a = a;
+      fired[fn].b = b;
+      fired[fn].ida = in->id[a];
+      fired[fn].idb = in->id[b];
+      fired[fn].tidx = tidx;
+      fired[fn].p = p;
+      fired[fn].key = -log(u_sel) / p;
+      fired[fn].rule = q->rule;
+      fn++;
+    }
+  }
+  st.fired = fn;
+
+  /* Conflict resolution (Section 3, "Details"): greedy in ascending (key, id_a, id_b). */
+  if (fn > 1) qsort(fired, (size_t)fn, sizeof(fired_pair), cmp_fired);
+  for (int64_t e = 0; e < fn; ++e) {
+    if (partner[fired[e].a] >= 0 || partner[fired[e].b] >= 0) continue;
+    partner[fired[e].a] = fired[e].b;
+    partner[fired[e].b] = fired[e].a;
+    st.matched++;
+    if (trace && fired[e].tidx >= 0) trace->matched[fired[e].tidx] = 1;
+  }
+
+  /* Steps 2(a)-(c) for each matched pair, all from their own free end points. */
+  for (int64_t e = 0; e < fn; ++e) {
+    int64_t a = fired[e].a, b = fired[e].b;
+    if (partner[a] != b) continue;
+    const or_pair* rule = &sys->pairs[fired[e].rule];
+    const pair_param* q = &pp[in->sp[a]][in->sp[b]];
+    double Da = sys->D[in->sp[a]], Db = sys->D[in->sp[b]];
+    double wa = Da / q->Drel, wb = Db / q->Drel;
+    double rv[3] = {0, 0, 0}, r0v[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
+      r0v[d] = min_image(in->x[3 * b + d] - in->x[3 * a + d], L);
+    }
+    /* centre of diffusion, Eq. (Rcoo): R = (D_B r_A + D_A r_B)/D_eff = r_A + (D_A/D_eff) r */
+    double c[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) c[d] = x1[3 * a + d] + wa * rv[d];
+    int react = 0;
+    if (rule->bc == OR_BC_ABS) {
+      react = 1;                                                   /* step 2(a) */
+    } else {
+      /* steps 2(b)-(c): new separation length from the radial propagator g_ref - g_abs, kept
+       * along the free-step direction; centre of diffusion unchanged. */
+      uint32_t w[4];
+      stream(sys, step, in->id[a], in->id[b], OR_TAG_RES, w);
+      double u_res = or_u52(w[0], w[1]), u_reac = or_u52(w[2], w[3]);
+      double R0 = sqrt(norm2(r0v, dim)) / q->sigma;
+      if (R0 < 1.0) R0 = 1.0;
+      double Rn = resample_dim(sys, u_res, R0, q->tau);
+      double len = sqrt(norm2(rv, dim));
+      double dir[3] = {0, 0, 0};
+      if (len > 0.0) {
+        for (int d = 0; d < dim; ++d) dir[d] = rv[d] / len;
+      } else {
+        double l0 = sqrt(norm2(r0v, dim));
+        if (l0 > 0.0)
+          for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
+        else
+          dir[0] = 1.0;
+      }
+      for (int d = 0; d < dim; ++d) {
+        double nr = Rn * q->sigma * dir[d];
+        x1[3 * a + d] = wrap(c[d] - wa * nr, L);
+        x1[3 * b + d] = wrap(c[d] + wb * nr, L);
+      }
+      st.resampled++;
+      if (rule->bc == OR_BC_RAD) {
+        double p = p_reac_dim(sys, Rn, R0, q->tau, q->h);
+        if (fabs(u_reac - p) <= NEAR_THRESHOLD) st.near_threshold++;
+        react = u_reac < p;
+      }
+    }
+    if (react) {
+      consumed[a] = consumed[b] = 1;
+      st.reactions++;
+      if (rule->product >= 0) {
+        prod[a].n = 1;
+        prod[a].species[0] = rule->product;
+        for (int d = 0; d < 3; ++d) prod[a].x[0][d] = d < dim ? wrap(c[d], L) : 0.0;
+      }
+    }
+  }
+
+  /* Unimolecular products (Section 2.2.5). */
+  for (int64_t i = 0; i < n; ++i) {
+    if (!decayed[i]) continue;
+    const or_decay* dc = &sys->decays[decayed[i] - 1];
+    consumed[i] = 1;
+    st.decays++;
+    const double* x0 = &in->x[3 * i];
+    if (dc->n_products == 1) {
+      double nrm[4] = {0, 0, 0, 0};
+      normals(sys, step, in->id[i], OR_TAG_DISS0, dim, nrm);
+      double ell = sqrt(2.0 * sys->D[dc->p0] * dt);
+      prod[i].n = 1;
+      prod[i].species[0] = dc->p0;
+      for (int d = 0; d < 3; ++d) prod[i].x[0][d] = d < dim ? wrap(x0[d] + ell * nrm[d], L) : 0.0;
+    } else if (dc->n_products == 2) {
+      int sa = dc->p0, sb = dc->p1;
+      const pair_param* q = &pp[sa][sb];
+      double Drel = sys->D[sa] + sys->D[sb];
+      double wa = sys->D[sa] / Drel, wb = sys->D[sb] / Drel;
+      double DR = sys->D[sa] * sys->D[sb] / Drel;                 /* D_R, Section 2.1 */
+      /* direction of the contact separation, uniform on the sphere / circle */
+      uint32_t w[4];
+      stream(sys, step, in->id[i], 0xFFFFFFFFu, OR_TAG_DIR, w);
+      double dir[3] = {0, 0, 0};
+      if (dim == 3) {
+        double ct = 2.0 * or_u52(w[0], w[1]) - 1.0, ph = 2.0 * PI * or_u52(w[2], w[3]);
+        double st_ = sqrt(fmax(0.0, 1.0 - ct * ct));
+        dir[0] = st_ * cos(ph); dir[1] = st_ * sin(ph); dir[2] = ct;
+      } else {
+        double ph = 2.0 * PI * or_u52(w[0], w[1]);
+        dir[0] = cos(ph); dir[1] = sin(ph);
+      }
+      /* centre of diffusion moves freely with D_R over dt */
+      double nc[4] = {0, 0, 0, 0};
+      normals(sys, step, in->id[i], OR_TAG_DISS0, dim, nc);
+      double ellc = sqrt(2.0 * DR * dt);
+      double c[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) c[d] = x0[d] + ellc * nc[d];
+      int recombine = 0;
+      int product = -1;
+      if (q->rule >= 0) {
+        /* the pair starts at contact, |r0| = a: propagate by g_ref - g_abs with R0 = 1, then
+         * Eq. (psurv_radII) decides escape or recombination (Section 2.2.5) */
+        const or_pair* rule = &sys->pairs[q->rule];
+        stream(sys, step, in->id[i], 0xFFFFFFFFu, OR_TAG_RES, w);
+        double u_res = or_u52(w[0], w[1]), u_reac = or_u52(w[2], w[3]);
+        double Rn = resample_dim(sys, u_res, 1.0, q->tau);
+        for (int d = 0; d < dim; ++d) rv[d] = Rn * q->sigma * dir[d];
+        if (rule->bc == OR_BC_ABS) {
+          recombine = 1;
+        } else if (rule->bc == OR_BC_RAD) {
+          double p = p_reac_dim(sys, Rn, 1.0, q->tau, q->h);
+          if (fabs(u_reac - p) <= NEAR_THRESHOLD) st.near_threshold++;
+          recombine = u_reac < p;
+        }
+        product = rule->product;
+      } else {
+        /* non-interacting products: start sigma_place apart, relative vector diffuses freely */
+        double nr[4] = {0, 0, 0, 0};
+        normals(sys, step, in->id[i], OR_TAG_DISS2, dim, nr);
+        double ellr = sqrt(2.0 * Drel * dt);
+        for (int d = 0; d < dim; ++d) rv[d] = dc->sigma_place * dir[d] + ellr * nr[d];
+      }
+      if (recombine) {
+        st.recombined++;
+        if (product >= 0) {
+          prod[i].n = 1;
+          prod[i].species[0] = product;
+          for (int d = 0; d < 3; ++d) prod[i].x[0][d] = d < dim ? wrap(c[d], L) : 0.0;
+        }
+      } else {
+        prod[i].n = 2;
+        prod[i].species[0] = sa;
+        prod[i].species[1] = sb;
+        for (int d = 0; d < 3; ++d) {
+          prod[i].x[0][d] = d < dim ? wrap(c[d] - wa * rv[d], L) : 0.0;
+          prod[i].x[1][d] = d < dim ? wrap(c[d] + wb * rv[d], L) : 0.0;
+        }
+      }
+    }
+  }
+
+  /* New state: survivors in their order, then products in event order (owner = lower parent id,
+   * and the input is id-sorted, so array order is event order). */
+  int64_t nsurv = 0, nprod = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!consumed[i]) nsurv++;
+    nprod += prod[i].n;
+  }
+  int status = 0;
+  if (nsurv + nprod > out->cap) {
+    status = -2;
+  } else {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (consumed[i]) continue;
+      for (int d = 0; d < 3; ++d) out->x[3 * k + d] = x1[3 * i + d];
+      out->sp[k] = in->sp[i];
+      out->id[k] = in->id[i];
+      k++;
+    }
+    uint32_t next_id = in->next_id;
+    for (int64_t i = 0; i < n; ++i) {
+      for (int m = 0; m < prod[i].n; ++m) {
+        for (int d = 0; d < 3; ++d) out->x[3 * k + d] = prod[i].x[m][d];
+        out->sp[k] = prod[i].species[m];
+        out->id[k] = next_id++;
+        k++;
+      }
+    }
+    out->n = k;
+    out->next_id = next_id;
+    out->step = step + 1;
+    out->t = in->t + dt;
+  }
+  st.products = nprod;
+  if (stats) *stats = st;
+  free(x1); free(decayed); free(consumed); free(partner); free(prod); free(fired);
+  return status;
+}
