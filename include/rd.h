@@ -1,0 +1,194 @@
+/*
+ * rd.h -- C ABI of the GB300 (sm_103a) Green's-function-corrected Brownian-dynamics
+ * reaction-diffusion step of Pruestel & Meier-Schellersheim (arXiv:1107.0270).
+ *
+ * One call of rd_step advances every particle of every replica by one time step dt following the
+ * paper's simulation algorithm (Section 3, steps 1-5):
+ *   free Gaussian displacements (step 1, Eq. oLangevin), encounter detection for every interacting
+ *   pair within the cut-off radius with the encounter probability p_enc = 1 - G_abs/G_free
+ *   (Eq. bayes1D, Section 2.2.4 radial form), conflict resolution among several encounter
+ *   candidates (Section 3, "Details"), propagation of encountered pairs by G_ref - G_abs
+ *   (Eq. passage_prob), the reaction decision p_reac = (G_ref - G_rad)/(G_ref - G_abs)
+ *   (Eq. psurv_radII), unimolecular decays 1 - exp(-k_d dt) (Eq. rad_prob) with reversible
+ *   dissociation products placed at contact (Section 2.2.5), and compaction of the particle arrays.
+ *
+ * Every step runs as hand-written CUDA kernels on the caller's stream; there is no CPU fallback.
+ * All functions return an rd_status code (never throw across the ABI).  Calls on one handle must
+ * not run concurrently from several host threads.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_MAX_SPECIES 16
+#define RD_MAX_PAIRS 32
+#define RD_MAX_DECAYS 16
+
+typedef enum {
+  RD_OK = 0,
+  RD_EINVAL = 1,     /* invalid argument or configuration (nothing was changed) */
+  RD_ENOMEM = 2,     /* device allocation failed */
+  RD_ECAPACITY = 3,  /* a device list or the particle array overflowed; the step was not committed */
+  RD_ETIMEOUT = 4,   /* a bounded device-side iteration (conflict resolution) did not finish */
+  RD_ECUDA = 5,      /* a CUDA runtime call failed; rd_last_cuda_error() gives the code */
+  RD_ENOTREADY = 6   /* entry point not available for this configuration */
+} rd_status;
+
+/* Boundary condition at contact (Section 2.1): absorbing, reflective, radiation (Robin). */
+typedef enum { RD_BC_NONE = 0, RD_BC_ABS = 1, RD_BC_REF = 2, RD_BC_RAD = 3 } rd_bc;
+
+/* Arithmetic of the step.  RD_FP64: every stage in double precision.  RD_MIXED: positions stored
+ * as float4, displacements, binning and the per-candidate p_enc in FP32; conflict resolution,
+ * resampling, p_reac, time and observable sums in FP64. */
+typedef enum { RD_FP64 = 0, RD_MIXED = 1 } rd_precision;
+
+/* Interaction of species s1 and s2 (unordered).  sigma: contact radius a_eff (length unit of the
+ * box).  ka: intrinsic association rate kappa_a (volume/time in 3D, area/time in 2D), used by
+ * RD_BC_RAD only.  product: species of the A+B->C product, or -1 for none. */
+typedef struct {
+  int32_t s1, s2;
+  int32_t bc;
+  int32_t product;
+  double sigma;
+  double ka;
+} rd_pair_rule;
+
+/* Unimolecular reaction parent -> products with rate kd (1/time).  n_products in {0,1,2}.  Two
+ * products that form an interacting pair are placed at that pair's contact radius and propagated
+ * by G_ref - G_abs (geminate recombination by p_reac); otherwise sigma_place apart. */
+typedef struct {
+  int32_t parent;
+  int32_t n_products;
+  int32_t products[2];
+  double kd;
+  double sigma_place;
+} rd_decay;
+
+/* One replica (independent periodic system) of a batched ensemble. */
+typedef struct {
+  double L;                           /* box edge */
+  int64_t n_init[RD_MAX_SPECIES];     /* initial particles per species */
+} rd_replica;
+
+/* Device-memory provider.  When alloc is NULL the library uses cudaMallocAsync/cudaFreeAsync on
+ * the handle's stream.  Bindings pass their framework's caching allocator here. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*release)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} rd_allocator;
+
+typedef struct {
+  int32_t dim;                        /* 2 or 3 */
+  int32_t precision;                  /* rd_precision */
+  int32_t n_species, n_pairs, n_decays;
+  int32_t n_replicas;                 /* >= 1; replicas points to n_replicas entries */
+  double dt;                          /* time step */
+  uint64_t seed;                      /* Philox key */
+  double c_cut;                       /* cut-off r_cut = sigma + c_cut sqrt(2 (D_A+D_B) dt), default 5 */
+  double tau_s;                       /* 2D: small-time series for tau <= tau_s (default 0.01) */
+  double D[RD_MAX_SPECIES];           /* diffusion constants per species */
+  rd_pair_rule pairs[RD_MAX_PAIRS];
+  rd_decay decays[RD_MAX_DECAYS];
+  const rd_replica* replicas;         /* read during rd_init only */
+  double capacity_factor;             /* particle capacity = factor * initial total (default 2) */
+  int64_t pair_capacity;              /* fired-pair list capacity (0: automatic) */
+  int32_t cell_factor_x100;           /* cell edge = r_cut * factor/100 (0: 100); autotuned if < 0 */
+  int32_t block_size;                 /* threads per block of the particle kernels (0: 256) */
+  rd_allocator allocator;
+} rd_config;
+
+typedef struct rd_handle rd_handle;
+
+/* Create a handle: validates cfg, allocates the device state through cfg->allocator on `stream`
+ * (a cudaStream_t, NULL = legacy default stream), draws uniform initial positions from the Philox
+ * INIT streams (ids 0..N-1 per replica, species in blocks of n_init) and enqueues nothing else.
+ * *out receives the handle (NULL on error).  Errors: RD_EINVAL, RD_ENOMEM, RD_ECUDA. */
+int rd_init(const rd_config* cfg, void* stream, rd_handle** out);
+
+/* Advance all replicas by exactly one dt.  Asynchronous on the handle's stream; device-side
+ * errors (RD_ECAPACITY, RD_ETIMEOUT) are latched in a device status word, leave the state of that
+ * step uncommitted, and are returned by the next synchronising call (rd_observables, rd_sync,
+ * rd_get_state). */
+int rd_step(rd_handle* h);
+
+/* Advance by nsteps >= 0 steps through captured CUDA graphs (two steps per graph launch).
+ * Asynchronous like rd_step. */
+int rd_run(rd_handle* h, int64_t nsteps);
+
+/* Synchronise the handle's stream and return the latched device status. */
+int rd_sync(rd_handle* h);
+
+/* Observables after the last completed step; synchronises the stream.  counts: caller-owned
+ * int64[n_replicas * n_species] (may be NULL), current particles per replica and species.
+ * step/t (may be NULL): step index and simulated time (FP64 accumulation).  stats: caller-owned
+ * int64[RD_NSTATS] (may be NULL), cumulative counters since rd_init (see RD_STAT_*). */
+#define RD_NSTATS 12
+enum {
+  RD_STAT_CANDIDATES = 0, RD_STAT_FIRED = 1, RD_STAT_MATCHED = 2, RD_STAT_REACTIONS = 3,
+  RD_STAT_RESAMPLED = 4, RD_STAT_DECAYS = 5, RD_STAT_RECOMBINED = 6, RD_STAT_NEAR_THRESHOLD = 7,
+  RD_STAT_OVERLAPS = 8, RD_STAT_MATCH_ROUNDS = 9, RD_STAT_PARTICLE_STEPS = 10,
+  RD_STAT_FIRED_HWM = 11
+};
+int rd_observables(rd_handle* h, int64_t* counts, int64_t* step, double* t, int64_t* stats);
+
+/* Copy the current state to caller-owned HOST buffers (synchronises).  n_inout: in = capacity of
+ * the buffers (particles), out = particles written; if the capacity is too small nothing is
+ * copied, *n_inout is set to the required count and RD_EINVAL is returned.  x: double[n*3]
+ * (z = 0 in 2D), species: int32[n], id: uint32[n], replica: int32[n] (any may be NULL), ordered by
+ * (replica, id).  next_id: caller-owned uint32[n_replicas] or NULL. */
+int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, uint32_t* id,
+                 int32_t* replica, uint32_t* next_id, int64_t* step);
+
+/* Replace the state from caller-owned HOST buffers (synchronises).  Particles must be grouped by
+ * replica (ascending) and sorted by id inside a replica; positions must lie in [0, L).  step sets
+ * the step counter (the random streams are keyed by it).  Errors: RD_EINVAL, RD_ECAPACITY. */
+int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* species,
+                 const uint32_t* id, const int32_t* replica, const uint32_t* next_id, int64_t step);
+
+/* Per-pair probabilities for separations of species-pair rule `rule` (index into cfg->pairs):
+ * for k < n, p_enc[k] = encounter probability for start separation r0[k] and end separation r[k]
+ * (Eq. bayes1D with radial Green's functions), p_reac[k] = reaction probability for a pair that
+ * met the boundary and ended at r[k] (Eq. psurv_radII).  r0, r, p_enc, p_reac are DEVICE pointers
+ * (double, n entries each; p_enc or p_reac may be NULL), evaluated in the handle's precision
+ * (RD_MIXED: p_enc in FP32, p_reac in FP64).  Asynchronous on the handle's stream. */
+int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r, int64_t n,
+                  double* p_enc, double* p_reac);
+
+/* Resample separations of encountered pairs (Section 3 "Details", radial propagator
+ * 4 pi R^2 (g_ref - g_abs)): for k < n, r_new[k] >= sigma solves T(r_new) = u[k] where T is the
+ * normalised tail of the propagator started at r0[k].  DEVICE pointers, asynchronous. */
+int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n,
+                double* r_new);
+
+/* Diagnostics of the last step (synchronises): the fired (encounter) pairs as ids, their p_enc and
+ * whether the conflict resolution accepted them.  cap: capacity of the caller-owned HOST arrays;
+ * *n_out: pairs in the list (all copied when <= cap).  replica may be NULL. */
+int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uint32_t* id_b,
+                  double* p_enc, int32_t* accepted, int32_t* replica);
+
+/* Number of particles currently alive (synchronises). */
+int rd_num_particles(rd_handle* h, int64_t* n);
+
+/* Name of the kernel-level timing hook: rd_time_kernels enables CUDA-event timing of every kernel
+ * of the next rd_step; rd_kernel_times copies per-kernel (name, ms) pairs of that step. */
+int rd_time_kernels(rd_handle* h, int32_t enable);
+int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* cap*32 */,
+                    float* ms);
+
+/* Release all device memory of the handle (synchronises).  NULL is ignored. */
+void rd_free(rd_handle* h);
+
+const char* rd_strerror(int status);
+int rd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

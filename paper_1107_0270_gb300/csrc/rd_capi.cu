@@ -1,0 +1,683 @@
+// Host runtime behind the C ABI of include/rd.h: configuration checks, derived per-pair
+// parameters, cell grids, device buffers, CUDA-graph capture of two steps, state transfer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rd_kernels.h"
+
+using namespace rd;
+
+namespace {
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return RD_ECUDA;
+}
+}  // namespace
+
+#define RD_CUDA(call)                        \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+struct rd_handle {
+  rd_config cfg;
+  std::vector<rd_replica> reps_host;
+  std::vector<RepDev> reps_init;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevParams hp;
+  StepLaunch L;
+  void* xbuf[2] = {nullptr, nullptr};
+  uint32_t* idbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t vsize = 32;
+  std::vector<std::pair<void*, size_t>> allocs;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  KernelTimer timer;
+  bool time_next = false;
+  std::vector<std::pair<std::string, float>> last_times;
+};
+
+static void* dev_alloc(rd_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (h->cfg.allocator.alloc) {
+    p = h->cfg.allocator.alloc(bytes, (void*)h->stream, h->cfg.allocator.ctx);
+  } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) h->allocs.emplace_back(p, bytes);
+  return p;
+}
+
+static void free_all(rd_handle* h) {
+  for (auto& a : h->allocs) {
+    if (h->cfg.allocator.release)
+      h->cfg.allocator.release(a.first, a.second, (void*)h->stream, h->cfg.allocator.ctx);
+    else if (!h->cfg.allocator.alloc)
+      cudaFreeAsync(a.first, h->stream);
+  }
+  h->allocs.clear();
+}
+
+static StepLaunch launch_for(rd_handle* h, int cur) {
+  StepLaunch L = h->L;
+  L.x_cur = h->xbuf[cur];
+  L.x_next = h->xbuf[1 - cur];
+  L.id_cur = h->idbuf[cur];
+  L.id_next = h->idbuf[1 - cur];
+  return L;
+}
+
+static double max_cutoff(const rd_config& c) {
+  double rc = 0.0;
+  for (int k = 0; k < c.n_pairs; ++k) {
+    const rd_pair_rule& p = c.pairs[k];
+    if (p.bc == RD_BC_NONE) continue;
+    rc = std::max(rc, p.sigma + c.c_cut * std::sqrt(2.0 * (c.D[p.s1] + c.D[p.s2]) * c.dt));
+  }
+  return rc;
+}
+
+static int validate(const rd_config* c) {
+  if (!c || (c->dim != 2 && c->dim != 3)) return RD_EINVAL;
+  if (c->dim == 2) return RD_ENOTREADY;
+  if (c->precision != RD_FP64 && c->precision != RD_MIXED) return RD_EINVAL;
+  if (c->n_species < 1 || c->n_species > RD_MAX_SPECIES) return RD_EINVAL;
+  if (c->n_pairs < 0 || c->n_pairs > RD_MAX_PAIRS || c->n_decays < 0 || c->n_decays > RD_MAX_DECAYS) return RD_EINVAL;
+  if (c->n_replicas < 1 || c->n_replicas >= (1 << 24) || !c->replicas) return RD_EINVAL;
+  if (!(c->dt > 0.0) || !(c->c_cut >= 0.0)) return RD_EINVAL;
+  for (int s = 0; s < c->n_species; ++s)
+    if (!(c->D[s] >= 0.0)) return RD_EINVAL;
+  for (int k = 0; k < c->n_pairs; ++k) {
+    const rd_pair_rule& p = c->pairs[k];
+    if (p.s1 < 0 || p.s1 >= c->n_species || p.s2 < 0 || p.s2 >= c->n_species) return RD_EINVAL;
+    if (p.bc < RD_BC_NONE || p.bc > RD_BC_RAD) return RD_EINVAL;
+    if (p.product < -1 || p.product >= c->n_species) return RD_EINVAL;
+    if (p.bc != RD_BC_NONE && !(p.sigma > 0.0)) return RD_EINVAL;
+    if (p.bc != RD_BC_NONE && !(c->D[p.s1] + c->D[p.s2] > 0.0)) return RD_EINVAL;
+    if (p.bc == RD_BC_RAD && !(p.ka >= 0.0)) return RD_EINVAL;
+    for (int q = 0; q < k; ++q) {
+      const rd_pair_rule& o = c->pairs[q];
+      if ((o.s1 == p.s1 && o.s2 == p.s2) || (o.s1 == p.s2 && o.s2 == p.s1)) return RD_EINVAL;
+    }
+  }
+  for (int k = 0; k < c->n_decays; ++k) {
+    const rd_decay& d = c->decays[k];
+    if (d.parent < 0 || d.parent >= c->n_species || d.n_products < 0 || d.n_products > 2 || !(d.kd >= 0.0))
+      return RD_EINVAL;
+    for (int m = 0; m < d.n_products; ++m)
+      if (d.products[m] < 0 || d.products[m] >= c->n_species) return RD_EINVAL;
+  }
+  const double rc = max_cutoff(*c);
+  for (int r = 0; r < c->n_replicas; ++r) {
+    if (!(c->replicas[r].L > 0.0)) return RD_EINVAL;
+    if (rc > 0.0 && !(rc < 0.5 * c->replicas[r].L)) return RD_EINVAL;  // unique minimum image
+    for (int s = 0; s < c->n_species; ++s)
+      if (c->replicas[r].n_init[s] < 0) return RD_EINVAL;
+  }
+  return RD_OK;
+}
+
+static void derive_params(rd_handle* h) {
+  const rd_config& c = h->cfg;
+  DevParams& P = h->hp;
+  std::memset(&P, 0, sizeof P);
+  P.dim = c.dim;
+  P.n_species = c.n_species;
+  P.precision = c.precision;
+  P.n_replicas = c.n_replicas;
+  P.n_pairs = c.n_pairs;
+  P.n_decays = c.n_decays;
+  P.match_max_rounds = 4096;
+  P.dt = c.dt;
+  P.seed_lo = (uint32_t)(c.seed & 0xFFFFFFFFu);
+  P.seed_hi = (uint32_t)(c.seed >> 32);
+  for (int s = 0; s < c.n_species; ++s) {
+    P.D[s] = c.D[s];
+    P.ell[s] = std::sqrt(2.0 * c.D[s] * c.dt);
+    P.ell_f[s] = (float)P.ell[s];
+  }
+  for (int a = 0; a < kMaxSpecies; ++a)
+    for (int b = 0; b < kMaxSpecies; ++b) P.pair_of[a][b] = -1;
+  for (int k = 0; k < c.n_pairs; ++k) {
+    const rd_pair_rule& p = c.pairs[k];
+    PairDev& q = P.pairs[k];
+    q.bc = p.bc;
+    q.product = p.product;
+    q.s1 = p.s1;
+    q.s2 = p.s2;
+    if (p.bc == RD_BC_NONE) continue;
+    q.sigma = p.sigma;
+    q.Drel = c.D[p.s1] + c.D[p.s2];
+    q.tau = q.Drel * c.dt / (p.sigma * p.sigma);
+    q.inv_tau = 1.0 / q.tau;
+    q.s = std::sqrt(q.tau);
+    q.h = c.dim == 3 ? p.ka / (4.0 * kPi * p.sigma * q.Drel) : p.ka / (2.0 * kPi * q.Drel);
+    q.alpha = 1.0 + q.h;
+    const double rc = p.sigma + c.c_cut * std::sqrt(2.0 * q.Drel * c.dt);
+    q.rcut2 = rc * rc;
+    q.sigma_f = (float)p.sigma;
+    q.inv_sigma_f = (float)(1.0 / p.sigma);
+    q.inv_tau_f = (float)q.inv_tau;
+    q.rcut2_f = (float)q.rcut2;
+    P.pair_of[p.s1][p.s2] = (int8_t)k;
+    P.pair_of[p.s2][p.s1] = (int8_t)k;
+    P.binned_mask |= (1u << p.s1) | (1u << p.s2);
+  }
+  for (int k = 0; k < c.n_decays; ++k) {
+    const rd_decay& d = c.decays[k];
+    DecayDev& q = P.decays[k];
+    q.parent = d.parent;
+    q.n_products = d.n_products;
+    q.p0 = d.n_products > 0 ? d.products[0] : -1;
+    q.p1 = d.n_products > 1 ? d.products[1] : -1;
+    q.kd = d.kd;
+    q.sigma_place = d.sigma_place;
+  }
+  for (int s = 0; s < c.n_species; ++s) {
+    double kt = 0.0;
+    for (int k = 0; k < c.n_decays; ++k)
+      if (c.decays[k].parent == s) kt += c.decays[k].kd;
+    P.ktot[s] = kt;
+    P.p_uni[s] = -std::expm1(-kt * c.dt);
+  }
+}
+
+extern "C" {
+
+const char* rd_strerror(int status) {
+  switch (status) {
+    case RD_OK: return "ok";
+    case RD_EINVAL: return "invalid argument";
+    case RD_ENOMEM: return "device allocation failed";
+    case RD_ECAPACITY: return "device list or particle capacity exceeded; step not committed";
+    case RD_ETIMEOUT: return "conflict resolution did not finish within its iteration bound";
+    case RD_ECUDA: return "CUDA runtime error";
+    case RD_ENOTREADY: return "not available for this configuration";
+    default: return "unknown status";
+  }
+}
+
+int rd_last_cuda_error(void) { return g_last_cuda_error; }
+
+int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
+  if (!out) return RD_EINVAL;
+  *out = nullptr;
+  int v = validate(cfg);
+  if (v != RD_OK) return v;
+  rd_handle* h = new rd_handle();
+  h->cfg = *cfg;
+  if (h->cfg.c_cut == 0.0) h->cfg.c_cut = 5.0;
+  if (h->cfg.tau_s == 0.0) h->cfg.tau_s = 0.01;
+  const rd_config& c = h->cfg;
+  h->reps_host.assign(cfg->replicas, cfg->replicas + cfg->n_replicas);
+  h->cfg.replicas = nullptr;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return cuda_fail(cudaGetLastError());
+    }
+    h->own_stream = true;
+  }
+  derive_params(h);
+  const bool mixed = c.precision == RD_MIXED;
+  h->vsize = mixed ? 16 : 32;
+
+  // cell grids: edge >= the largest cut-off (with a relative margin against rounding)
+  const double rc = max_cutoff(c);
+  const double factor = (c.cell_factor_x100 > 0 ? c.cell_factor_x100 : 100) / 100.0;
+  int64_t total_cells = 0, n_total = 0;
+  h->reps_init.resize(c.n_replicas);
+  for (int r = 0; r < c.n_replicas; ++r) {
+    const rd_replica& rp = h->reps_host[r];
+    RepDev& d = h->reps_init[r];
+    std::memset(&d, 0, sizeof d);
+    d.L = rp.L;
+    d.half_L = 0.5 * rp.L;
+    d.Lf = (float)rp.L;
+    d.half_Lf = 0.5f * d.Lf;
+    for (int a = 0; a < 3; ++a) {
+      int n = 1;
+      if (a < c.dim && rc > 0.0) {
+        const double m = std::floor(rp.L / (rc * factor * (1.0 + 1e-6)));
+        n = m >= 3.0 ? (int)std::min(m, 2048.0) : 1;
+      }
+      d.nc[a] = n;
+      d.inv_edge[a] = n / rp.L;
+      d.inv_edge_f[a] = (float)d.inv_edge[a];
+    }
+    d.cell_base = total_cells;
+    total_cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
+    int64_t nr = 0;
+    for (int s = 0; s < c.n_species; ++s) nr += rp.n_init[s];
+    d.beg = (uint32_t)n_total;
+    d.end = (uint32_t)(n_total + nr);
+    d.next_id = (uint32_t)nr;
+    n_total += nr;
+  }
+  if (total_cells >= (int64_t)0xFFFFFFF0) {
+    delete h;
+    return RD_EINVAL;
+  }
+  const double cf = c.capacity_factor > 0.0 ? c.capacity_factor : 2.0;
+  int64_t cap = (int64_t)std::ceil(cf * (double)n_total) + 1024;
+  if (cap >= (int64_t)0x7FFFFFF0) {
+    delete h;
+    return RD_EINVAL;
+  }
+  int64_t pair_cap = c.pair_capacity > 0 ? c.pair_capacity : std::max<int64_t>(65536, cap);
+  h->hp.cap_particles = cap;
+  h->hp.cap_pairs = pair_cap;
+
+  StepLaunch& L = h->L;
+  std::memset(&L, 0, sizeof L);
+  L.precision = c.precision;
+  L.block = c.block_size > 0 ? c.block_size : 256;
+  L.max_grid = 152 * 16;
+  L.scan_items = 8;
+  L.cap_particles = cap;
+  L.cap_pairs = pair_cap;
+  L.total_cells = total_cells;
+  L.n_counts = c.n_replicas * c.n_species;
+  const int64_t chunk = 256 * (int64_t)L.scan_items;
+  const int64_t nbc = (total_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
+  if (nbc > 1024 * 64 || nbp > 1024 * 64) {
+    delete h;
+    return RD_EINVAL;
+  }
+
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = dev_alloc(h, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  const size_t vs = h->vsize;
+  h->xbuf[0] = A(cap * vs);
+  h->xbuf[1] = A(cap * vs);
+  h->idbuf[0] = (uint32_t*)A(cap * 4);
+  h->idbuf[1] = (uint32_t*)A(cap * 4);
+  L.x1 = A(cap * vs);
+  L.sx0 = A(cap * vs);
+  L.sx1 = A(cap * vs);
+  L.prodpos = A(2 * cap * vs);
+  L.status = (uint32_t*)A(cap * 4);
+  L.matched = (int32_t*)A(cap * 4);
+  L.deg = (uint32_t*)A(cap * 4);
+  L.cell_of = (uint32_t*)A(cap * 4);
+  L.slot = (uint32_t*)A(cap * 4);
+  L.sidx = (uint32_t*)A(cap * 4);
+  L.decay_list = (uint32_t*)A(cap * 4);
+  L.best_key = (unsigned long long*)A(cap * 8);
+  L.best_pid = (unsigned long long*)A(cap * 8);
+  L.scan = (unsigned long long*)A((cap + 1) * 8);
+  L.cell_count = (uint32_t*)A(total_cells * 4);
+  L.cell_start = (uint32_t*)A((total_cells + 1) * 4);
+  L.block_sums32 = (uint32_t*)A((nbc + 1) * 4);
+  L.block_sums64 = (unsigned long long*)A((nbp + 1) * 8);
+  L.fired = (FiredPair*)A(pair_cap * sizeof(FiredPair));
+  L.fstate = (uint32_t*)A(pair_cap * 4);
+  L.conflict = (uint32_t*)A(pair_cap * 4);
+  L.counts = (unsigned long long*)A((size_t)L.n_counts * 8);
+  L.P = (const DevParams*)A(sizeof(DevParams));
+  L.ctl = (DevCtl*)A(sizeof(DevCtl));
+  L.reps = (RepDev*)A(c.n_replicas * sizeof(RepDev));
+  if (!ok) {
+    free_all(h);
+    cudaStreamSynchronize(h->stream);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return RD_ENOMEM;
+  }
+  auto fail = [&](cudaError_t e) {
+    free_all(h);
+    cudaStreamSynchronize(h->stream);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return cuda_fail(e);
+  };
+  cudaError_t e = cudaSuccess;
+  e = cudaMemsetAsync(L.cell_count, 0, total_cells * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.status, 0, cap * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync((void*)L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(L.reps, h->reps_init.data(), c.n_replicas * sizeof(RepDev), cudaMemcpyHostToDevice, h->stream);
+  DevCtl ctl;
+  std::memset(&ctl, 0, sizeof ctl);
+  ctl.n = (uint32_t)n_total;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return fail(e);
+
+  // initial positions: ids 0..N_r-1 per replica, species in blocks of n_init
+  if (n_total > 0) {
+    std::vector<int32_t> rep_of(n_total), sp_of(n_total);
+    std::vector<uint32_t> id_of(n_total);
+    int64_t i = 0;
+    for (int r = 0; r < c.n_replicas; ++r) {
+      uint32_t k = 0;
+      for (int s = 0; s < c.n_species; ++s)
+        for (int64_t m = 0; m < h->reps_host[r].n_init[s]; ++m, ++i, ++k) {
+          rep_of[i] = r;
+          sp_of[i] = s;
+          id_of[i] = k;
+        }
+    }
+    void* tmp = nullptr;
+    const size_t bytes = (size_t)n_total * 12;
+    e = cudaMallocAsync(&tmp, bytes, h->stream);
+    if (e != cudaSuccess) return fail(e);
+    int32_t* d_rep = (int32_t*)tmp;
+    int32_t* d_sp = d_rep + n_total;
+    uint32_t* d_id = (uint32_t*)(d_sp + n_total);
+    e = cudaMemcpyAsync(d_rep, rep_of.data(), n_total * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sp, sp_of.data(), n_total * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_id, id_of.data(), n_total * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+      StepLaunch L0 = launch_for(h, 0);
+      launch_init_positions(L0, d_rep, d_sp, d_id, (uint32_t)n_total, h->stream);
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(tmp, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(e);
+  }
+  launch_count(launch_for(h, 0), h->stream);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(e);
+  *out = h;
+  return RD_OK;
+}
+
+int rd_step(rd_handle* h) {
+  if (!h) return RD_EINVAL;
+  StepLaunch L = launch_for(h, h->cur);
+  if (h->time_next) {
+    h->timer.reset();
+    launch_step(L, h->stream, &h->timer);
+  } else {
+    launch_step(L, h->stream, nullptr);
+  }
+  RD_CUDA(cudaGetLastError());
+  if (h->time_next) {
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    h->last_times.clear();
+    for (size_t k = 1; k < h->timer.used; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, h->timer.events[k - 1], h->timer.events[k]);
+      h->last_times.emplace_back(h->timer.names[k], ms);
+    }
+    h->time_next = false;
+  }
+  h->cur ^= 1;
+  return RD_OK;
+}
+
+static int capture_graph(rd_handle* h, int start) {
+  cudaGraph_t g = nullptr;
+  RD_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  launch_step(launch_for(h, start), h->stream, nullptr);
+  launch_step(launch_for(h, 1 - start), h->stream, nullptr);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(&h->graph[start], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph[start] = nullptr;
+    return cuda_fail(e);
+  }
+  return RD_OK;
+}
+
+int rd_run(rd_handle* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return RD_EINVAL;
+  int64_t pairs = nsteps / 2;
+  if (pairs > 0) {
+    if (!h->graph[h->cur]) {
+      int rc = capture_graph(h, h->cur);
+      if (rc != RD_OK) return rc;
+    }
+    for (int64_t k = 0; k < pairs; ++k) RD_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
+  }
+  if (nsteps & 1) return rd_step(h);
+  return RD_OK;
+}
+
+int rd_sync(rd_handle* h) {
+  if (!h) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  int32_t st = 0;
+  RD_CUDA(cudaMemcpy(&st, &h->L.ctl->status, sizeof st, cudaMemcpyDeviceToHost));
+  return st;
+}
+
+int rd_observables(rd_handle* h, int64_t* counts, int64_t* step, double* t, int64_t* stats) {
+  if (!h) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl ctl;
+  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  if (counts)
+    RD_CUDA(cudaMemcpy(counts, h->L.counts, (size_t)h->L.n_counts * 8, cudaMemcpyDeviceToHost));
+  if (step) *step = ctl.step;
+  if (t) *t = ctl.t;
+  if (stats)
+    for (int k = 0; k < RD_NSTATS; ++k) stats[k] = (int64_t)ctl.stats[k];
+  return ctl.status;
+}
+
+int rd_num_particles(rd_handle* h, int64_t* n) {
+  if (!h || !n) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  uint32_t v = 0;
+  RD_CUDA(cudaMemcpy(&v, &h->L.ctl->n, sizeof v, cudaMemcpyDeviceToHost));
+  *n = v;
+  return RD_OK;
+}
+
+static inline uint32_t wbits_host(const void* rec, size_t vsize) {
+  if (vsize == 32) {
+    uint64_t b;
+    std::memcpy(&b, (const char*)rec + 24, 8);
+    return (uint32_t)b;
+  }
+  uint32_t b;
+  std::memcpy(&b, (const char*)rec + 12, 4);
+  return b;
+}
+
+int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, uint32_t* id, int32_t* replica,
+                 uint32_t* next_id, int64_t* step) {
+  if (!h || !n_inout) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl ctl;
+  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  const int64_t n = ctl.n;
+  if (*n_inout < n) {
+    *n_inout = n;
+    return RD_EINVAL;
+  }
+  *n_inout = n;
+  if (step) *step = ctl.step;
+  std::vector<char> raw((size_t)n * h->vsize);
+  if (n) RD_CUDA(cudaMemcpy(raw.data(), h->xbuf[h->cur], (size_t)n * h->vsize, cudaMemcpyDeviceToHost));
+  if (id && n) RD_CUDA(cudaMemcpy(id, h->idbuf[h->cur], (size_t)n * 4, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < n; ++i) {
+    const char* rec = raw.data() + (size_t)i * h->vsize;
+    const uint32_t wb = wbits_host(rec, h->vsize);
+    if (x) {
+      if (h->vsize == 32) {
+        double v[3];
+        std::memcpy(v, rec, 24);
+        x[3 * i] = v[0]; x[3 * i + 1] = v[1]; x[3 * i + 2] = v[2];
+      } else {
+        float v[3];
+        std::memcpy(v, rec, 12);
+        x[3 * i] = v[0]; x[3 * i + 1] = v[1]; x[3 * i + 2] = v[2];
+      }
+    }
+    if (species) species[i] = (int32_t)(wb & 0xFFu);
+    if (replica) replica[i] = (int32_t)(wb >> 8);
+  }
+  if (next_id) {
+    std::vector<RepDev> reps(h->cfg.n_replicas);
+    RD_CUDA(cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost));
+    for (size_t r = 0; r < reps.size(); ++r) next_id[r] = reps[r].next_id;
+  }
+  return ctl.status;
+}
+
+int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* species, const uint32_t* id,
+                 const int32_t* replica, const uint32_t* next_id, int64_t step) {
+  if (!h || n < 0 || (n > 0 && (!x || !species || !id))) return RD_EINVAL;
+  if (n > h->L.cap_particles) return RD_ECAPACITY;
+  if (step < 0 || step > 0xFFFFFFFFll) return RD_EINVAL;
+  const rd_config& c = h->cfg;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  std::vector<RepDev> reps(c.n_replicas);
+  RD_CUDA(cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> maxid(c.n_replicas, 0);
+  std::vector<int64_t> cnt(c.n_replicas, 0);
+  std::vector<char> raw((size_t)std::max<int64_t>(n, 1) * h->vsize);
+  int prev_r = -1;
+  int64_t prev_id = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    const int r = replica ? replica[i] : 0;
+    if (r < 0 || r >= c.n_replicas || species[i] < 0 || species[i] >= c.n_species) return RD_EINVAL;
+    if (r < prev_r || (r == prev_r && (int64_t)id[i] <= prev_id)) return RD_EINVAL;
+    if (r != prev_r) prev_id = -1;
+    prev_r = r;
+    prev_id = id[i];
+    const double L = reps[r].L;
+    for (int d = 0; d < c.dim; ++d)
+      if (!(x[3 * i + d] >= 0.0 && x[3 * i + d] < L)) return RD_EINVAL;
+    cnt[r]++;
+    maxid[r] = std::max(maxid[r], id[i] + 1);
+    const uint32_t wb = pack_sp((uint32_t)species[i], (uint32_t)r);
+    char* rec = raw.data() + (size_t)i * h->vsize;
+    if (h->vsize == 32) {
+      double v[3] = {x[3 * i], x[3 * i + 1], c.dim == 3 ? x[3 * i + 2] : 0.0};
+      std::memcpy(rec, v, 24);
+      uint64_t b = wb;
+      std::memcpy(rec + 24, &b, 8);
+    } else {
+      float v[3] = {(float)x[3 * i], (float)x[3 * i + 1], c.dim == 3 ? (float)x[3 * i + 2] : 0.0f};
+      for (int d = 0; d < 3; ++d)
+        if (!(v[d] < reps[r].Lf)) v[d] = 0.0f;
+      std::memcpy(rec, v, 12);
+      std::memcpy(rec + 12, &wb, 4);
+    }
+  }
+  int64_t off = 0;
+  for (int r = 0; r < c.n_replicas; ++r) {
+    reps[r].beg = (uint32_t)off;
+    off += cnt[r];
+    reps[r].end = (uint32_t)off;
+    reps[r].next_id = next_id ? std::max(next_id[r], maxid[r]) : maxid[r];
+  }
+  if (n) {
+    RD_CUDA(cudaMemcpy(h->xbuf[h->cur], raw.data(), (size_t)n * h->vsize, cudaMemcpyHostToDevice));
+    RD_CUDA(cudaMemcpy(h->idbuf[h->cur], id, (size_t)n * 4, cudaMemcpyHostToDevice));
+  }
+  RD_CUDA(cudaMemcpy(h->L.reps, reps.data(), reps.size() * sizeof(RepDev), cudaMemcpyHostToDevice));
+  DevCtl ctl;
+  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  ctl.n = (uint32_t)n;
+  ctl.step = (uint32_t)step;
+  ctl.t = (double)step * c.dt;
+  ctl.status = 0;
+  RD_CUDA(cudaMemcpy(h->L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice));
+  launch_count(launch_for(h, h->cur), h->stream);
+  RD_CUDA(cudaGetLastError());
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  return RD_OK;
+}
+
+int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r, int64_t n, double* p_enc,
+                  double* p_reac) {
+  if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || (n > 0 && (!r0 || !r))) return RD_EINVAL;
+  if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
+  if (n == 0) return RD_OK;
+  launch_pair_probs(h->L.P, rule, r0, r, n, p_enc, p_reac, h->L.max_grid, h->stream);
+  RD_CUDA(cudaGetLastError());
+  return RD_OK;
+}
+
+int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n, double* r_new) {
+  if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || (n > 0 && (!r0 || !u || !r_new))) return RD_EINVAL;
+  if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
+  if (n == 0) return RD_OK;
+  launch_resample(h->L.P, rule, r0, u, n, r_new, h->L.max_grid, h->stream);
+  RD_CUDA(cudaGetLastError());
+  return RD_OK;
+}
+
+int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uint32_t* id_b, double* p_enc,
+                  int32_t* accepted, int32_t* replica) {
+  if (!h || !n_out || cap < 0) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl ctl;
+  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  const int64_t n = std::min<int64_t>(ctl.fired, h->L.cap_pairs);
+  *n_out = n;
+  const int64_t m = std::min(n, cap);
+  if (m > 0) {
+    std::vector<FiredPair> f(m);
+    std::vector<uint32_t> fs(m);
+    RD_CUDA(cudaMemcpy(f.data(), h->L.fired, m * sizeof(FiredPair), cudaMemcpyDeviceToHost));
+    RD_CUDA(cudaMemcpy(fs.data(), h->L.fstate, m * 4, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < m; ++k) {
+      if (id_a) id_a[k] = f[k].ida;
+      if (id_b) id_b[k] = f[k].idb;
+      if (p_enc) p_enc[k] = f[k].p;
+      if (accepted) accepted[k] = (fs[k] & 3u) == FS_ACCEPTED;
+      if (replica) replica[k] = (int32_t)(fs[k] >> 8);
+    }
+  }
+  return ctl.status;
+}
+
+int rd_time_kernels(rd_handle* h, int32_t enable) {
+  if (!h) return RD_EINVAL;
+  h->time_next = enable != 0;
+  return RD_OK;
+}
+
+int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names, float* ms) {
+  if (!h || !n_out) return RD_EINVAL;
+  const int n = (int)h->last_times.size();
+  *n_out = n;
+  for (int k = 0; k < n && k < cap; ++k) {
+    if (names) {
+      std::memset(names + 32 * k, 0, 32);
+      std::strncpy(names + 32 * k, h->last_times[k].first.c_str(), 31);
+    }
+    if (ms) ms[k] = h->last_times[k].second;
+  }
+  return RD_OK;
+}
+
+void rd_free(rd_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+  h->timer.destroy();
+  free_all(h);
+  cudaStreamSynchronize(h->stream);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+// Internal definitions of the GB300 GF-BD step: device-side parameter blocks, random streams and
+// the 3D radial Green's-function quantities.  Included by the kernel and host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rd.h"
+
+namespace rd {
+
+constexpr int kMaxSpecies = RD_MAX_SPECIES;
+constexpr int kMaxPairs = RD_MAX_PAIRS;
+constexpr int kMaxDecays = RD_MAX_DECAYS;
+constexpr uint32_t kNoCell = 0xFFFFFFFFu;
+constexpr uint32_t kOneParticle = 0xFFFFFFFFu;   // id_b of one-particle random streams
+
+// Random-stream tags (counter word 3, low byte; replica index in the upper 24 bits).
+enum Tag : uint32_t {
+  TAG_INIT0 = 1, TAG_INIT1 = 2, TAG_UNI = 3, TAG_DISP0 = 4, TAG_DISP1 = 5, TAG_ENC = 6,
+  TAG_RES = 7, TAG_DIR = 8, TAG_DISS0 = 9, TAG_DISS1 = 10, TAG_DISS2 = 11, TAG_DISS3 = 12
+};
+
+// Per-particle status word written every step.
+enum : uint32_t {
+  ST_DECAYED = 1u,         // bit 0: unimolecular decay drawn this step
+  ST_CONSUMED = 2u,        // bit 1: removed at the end of the step (reacted or decayed)
+  ST_NPROD_SHIFT = 2,      // bits 2-3: products owned (0..2)
+  ST_CHANNEL_SHIFT = 4     // bits 4-7: decay channel
+};
+
+// Fired-pair state (low 2 bits), rule index (bits 2-7), replica (bits 8-31).
+enum : uint32_t { FS_LIVE = 0u, FS_ACCEPTED = 1u, FS_DEAD = 2u };
+
+struct __align__(32) d4 {
+  double x, y, z, w;
+};
+
+struct PairDev {
+  int32_t bc, product, s1, s2;
+  double sigma, tau, inv_tau, s, h, alpha, rcut2, Drel;
+  float sigma_f, inv_sigma_f, inv_tau_f, rcut2_f;
+};
+
+struct DecayDev {
+  int32_t parent, n_products, p0, p1;
+  double kd, sigma_place;
+};
+
+struct DevParams {
+  int32_t dim, n_species, precision, n_replicas;
+  int32_t n_pairs, n_decays, match_max_rounds, pad0;
+  double dt;
+  uint32_t seed_lo, seed_hi;
+  uint32_t binned_mask;        // species that appear in an interacting pair rule
+  uint32_t pad1;
+  int64_t cap_particles, cap_pairs;
+  double D[kMaxSpecies];
+  double ell[kMaxSpecies];     // sqrt(2 D dt)
+  float ell_f[kMaxSpecies];
+  double ktot[kMaxSpecies];    // total unimolecular rate per species
+  double p_uni[kMaxSpecies];   // 1 - exp(-ktot dt)
+  int8_t pair_of[kMaxSpecies][kMaxSpecies];   // index into pairs, -1 = no interaction
+  PairDev pairs[kMaxPairs];
+  DecayDev decays[kMaxDecays];
+};
+
+struct RepDev {
+  double L, half_L;
+  double inv_edge[3];
+  float Lf, half_Lf;
+  float inv_edge_f[3];
+  int32_t nc[3];
+  int64_t cell_base;
+  uint32_t beg, end, next_id, pad;
+};
+
+struct DevCtl {
+  uint32_t step;
+  int32_t status;
+  uint32_t n;              // particles alive
+  uint32_t fired;          // fired pairs this step
+  uint32_t n_conflict;     // pairs left to the iterative matching
+  uint32_t n_decay;        // decays this step
+  uint32_t n_binned;
+  uint32_t pad;
+  double t;
+  unsigned long long stats[RD_NSTATS];
+};
+
+struct FiredPair {          // 32 B
+  uint32_t ia, ib;          // particle indices of this step, id[ia] < id[ib]
+  uint32_t ida, idb;        // their ids
+  double p;                 // p_enc
+  double key;               // -ln(U_sel)/p_enc
+};
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon et al., SC'11).
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+#ifdef __CUDA_ARCH__
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+#else
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
+#endif
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 draw(const DevParams& P, uint32_t c0, uint32_t ida, uint32_t idb,
+                                      uint32_t tag, uint32_t replica) {
+  return philox(make_uint4(c0, ida, idb, tag | (replica << 8)), P.seed_lo, P.seed_hi);
+}
+
+// 52-bit uniform in (0,1), exact: ((x >> 12) + 1/2) 2^-52 with x = hi:lo.
+__host__ __device__ __forceinline__ double u52(uint32_t hi, uint32_t lo) {
+  const uint64_t x = ((uint64_t)hi << 32) | lo;
+  return ((double)(x >> 12) + 0.5) * 0x1p-52;
+}
+
+// 23-bit uniform in (0,1) for the FP32 path: ((w >> 9) + 1/2) 2^-23, exact in float.
+__device__ __forceinline__ float u23(uint32_t w) { return ((float)(w >> 9) + 0.5f) * 0x1p-23f; }
+
+__device__ __forceinline__ void box_muller(double u1, double u2, double& n0, double& n1) {
+  const double rad = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  n0 = rad * cs;
+  n1 = rad * sn;
+}
+
+__device__ __forceinline__ void box_muller_f(float u1, float u2, float& n0, float& n1) {
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  n0 = rad * cs;
+  n1 = rad * sn;
+}
+
+// Up to four FP64 unit normals from one (dim 2) or two (dim 3) Philox calls, tags tag0, tag0+1.
+__device__ __forceinline__ void normals64(const DevParams& P, uint32_t c0, uint32_t id, uint32_t tag0,
+                                          uint32_t replica, int count, double n[4]) {
+  uint4 w = draw(P, c0, id, kOneParticle, tag0, replica);
+  box_muller(u52(w.x, w.y), u52(w.z, w.w), n[0], n[1]);
+  n[2] = n[3] = 0.0;
+  if (count > 2) {
+    w = draw(P, c0, id, kOneParticle, tag0 + 1, replica);
+    box_muller(u52(w.x, w.y), u52(w.z, w.w), n[2], n[3]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// periodic geometry
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double min_image(double d, double L, double half_L) {
+  if (d > half_L)
+    d -= L;
+  else if (d < -half_L)
+    d += L;
+  return d;
+}
+
+__device__ __forceinline__ float min_image_f(float d, float L, float half_L) {
+  if (d > half_L)
+    d -= L;
+  else if (d < -half_L)
+    d += L;
+  return d;
+}
+
+__device__ __forceinline__ double wrap(double x, double L) {
+  if (x >= L) {
+    x -= L;
+  } else if (x < 0.0) {
+    x += L;
+    if (x >= L) x = 0.0;
+  }
+  return x;
+}
+
+__device__ __forceinline__ float wrap_f(float x, float L) {
+  if (x >= L) {
+    x -= L;
+  } else if (x < 0.0f) {
+    x += L;
+    if (x >= L) x = 0.0f;
+  }
+  return x;
+}
+
+// squared length with explicit round-to-nearest (no contraction), summed x, y, z.
+__device__ __forceinline__ double norm2_rn(double a, double b, double c, int dim) {
+  double s = __dmul_rn(a, a);
+  s = __dadd_rn(s, __dmul_rn(b, b));
+  if (dim == 3) s = __dadd_rn(s, __dmul_rn(c, c));
+  return s;
+}
+
+__device__ __forceinline__ uint32_t w_bits(double w) { return (uint32_t)__double_as_longlong(w); }
+__device__ __forceinline__ uint32_t w_bits(float w) { return __float_as_uint(w); }
+__device__ __forceinline__ double w_from_bits_d(uint32_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ float w_from_bits_f(uint32_t b) { return __uint_as_float(b); }
+__host__ __device__ __forceinline__ uint32_t pack_sp(uint32_t species, uint32_t replica) {
+  return species | (replica << 8);
+}
+
+// ------------------------------------------------------------------------------------------------
+// 3D radial Green's-function quantities (a = 1, tau = D dt / a^2), Section 4.1 of the paper.
+// ------------------------------------------------------------------------------------------------
+constexpr double kSqrtPi = 1.7724538509055160273;
+constexpr double kPi = 3.14159265358979323846;
+
+// Encounter probability, Eq. (bayes1D) with the radial g_abs of Section 4.1 and the angle-averaged
+// free Gaussian: p_enc = exp(-(R-1)(R0-1)/tau) (1 - exp(-(R+R0-1)/tau)) / (1 - exp(-R R0/tau)).
+__device__ __forceinline__ double p_enc3(double R, double R0, double inv_tau) {
+  if (R <= 1.0) return 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  const double d = R - 1.0, d0 = R0 - 1.0;
+  return exp(-d * d0 * inv_tau) * (expm1(-(R + R0 - 1.0) * inv_tau) / expm1(-R * R0 * inv_tau));
+}
+
+// FP32 form from the contact distances d = R-1, d0 = R0-1 (absolute error <= 2e-6 for the
+// configurations' tau; checked against the FP64 oracle).
+__device__ __forceinline__ float p_enc3_f(float d, float d0, float inv_tau) {
+  if (d <= 0.0f) return 1.0f;
+  if (d0 < 0.0f) d0 = 0.0f;
+  const float num = expm1f(-(d + d0 + 1.0f) * inv_tau);
+  const float den = expm1f(-(d + 1.0f) * (d0 + 1.0f) * inv_tau);
+  return expf(-d * d0 * inv_tau) * (num / den);
+}
+
+// q(y) = 1 - sqrt(pi) y erfcx(y) >= 0: direct below y = 12, asymptotic series
+// sum_{k>=1} (-1)^(k+1) (2k-1)!! / (2 y^2)^k (16 terms) above.
+__device__ __forceinline__ double q_ierfc(double y) {
+  if (y < 12.0) return 1.0 - kSqrtPi * y * erfcx(y);
+  const double x = 1.0 / (2.0 * y * y);
+  double term = x, sum = x;
+#pragma unroll
+  for (int k = 1; k < 16; ++k) {
+    term *= -(2.0 * k + 1.0) * x;
+    sum += term;
+  }
+  return sum;
+}
+
+// Reaction probability, Eq. (psurv_radII), after removing the common factor
+// exp(-u^2/4tau)/(8 pi R R0 sqrt(pi tau)) (u = R+R0-2, s = sqrt(tau), y = s + u/2s):
+//   p_reac = sqrt(pi tau) [alpha erfcx(alpha s + u/2s) - erfcx(y)] / [q(y) + sqrt(pi) (u/2s) erfcx(y)]
+// The denominator, 1 - sqrt(pi tau) erfcx(y), is written as a sum of non-negative terms.
+__device__ __forceinline__ double p_reac3(double R, double R0, double s, double alpha) {
+  if (R < 1.0) R = 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  const double z = (R + R0 - 2.0) / (2.0 * s);
+  const double y = s + z;
+  const double ey = erfcx(y);
+  const double num = kSqrtPi * s * (alpha * erfcx(alpha * s + z) - ey);
+  const double den = q_ierfc(y) + kSqrtPi * z * ey;
+  double p = num / den;
+  return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+}
+
+// Propagator G_ref - G_abs of an encountered pair (radial density 4 pi R^2 (g_ref - g_abs)).
+// With w = R0-1, z = (V+w)/2s, z0 = w/2s, the normalised tail beyond R = 1 + V is
+//   T(V) = exp(z0^2 - z^2) [erfcx(z) + V erfcx(s+z)] / erfcx(z0),
+//   d ln T / dV = -(1+V) [q(s+z) + sqrt(pi) z erfcx(s+z)] / (s sqrt(pi) [erfcx(z) + V erfcx(s+z)]).
+// resample3 solves ln T(V) = ln U by Newton steps kept inside a bisection bracket.
+__device__ __forceinline__ void lnT3(double V, double w, double s, double inv_4tau, double ln_ex0,
+                                     double& f, double& df) {
+  const double z = (V + w) / (2.0 * s);
+  const double ez = erfcx(z), ey = erfcx(s + z);
+  const double body = ez + V * ey;
+  f = -V * (2.0 * w + V) * inv_4tau + log(body) - ln_ex0;
+  df = -(1.0 + V) * (q_ierfc(s + z) + kSqrtPi * z * ey) / (s * kSqrtPi * body);
+}
+
+__device__ __forceinline__ double resample3(double U, double R0, double s) {
+  if (R0 < 1.0) R0 = 1.0;
+  const double w = R0 - 1.0;
+  const double inv_4tau = 1.0 / (4.0 * s * s);
+  const double ln_ex0 = log(erfcx(w / (2.0 * s)));
+  const double lnU = log(U);
+  double lo = 0.0, hi = s, f, df;
+  for (int k = 0; k < 80; ++k) {
+    lnT3(hi, w, s, inv_4tau, ln_ex0, f, df);
+    if (f < lnU) break;
+    lo = hi;
+    hi *= 2.0;
+  }
+  double V = 0.5 * (lo + hi);
+  for (int it = 0; it < 100; ++it) {
+    lnT3(V, w, s, inv_4tau, ln_ex0, f, df);
+    const double g = f - lnU;
+    if (g > 0.0)
+      lo = V;
+    else
+      hi = V;
+    double Vn = V - g / df;
+    if (!(Vn > lo && Vn < hi)) Vn = 0.5 * (lo + hi);
+    if (fabs(Vn - V) <= 4e-16 * (1.0 + V) || hi - lo <= 4e-16 * (1.0 + hi)) {
+      V = Vn;
+      break;
+    }
+    V = Vn;
+  }
+  return 1.0 + V;
+}
+
+}  // namespace rd

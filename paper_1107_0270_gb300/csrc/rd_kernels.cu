@@ -1,0 +1,1027 @@
+// Device kernels of one GF-BD step.  Positions are SoA vectors of 4 components (x, y, z, w) where
+// w carries the bits of (species | replica << 8); T = double for the FP64 step, float for the
+// mixed step.  Every kernel is a grid-stride loop so that CUDA graphs can be captured with grids
+// sized for the capacity while the live particle count stays on the device.
+#include <cuda_runtime.h>
+
+#include "rd_kernels.h"
+
+namespace rd {
+
+template <class T> struct V4;
+template <> struct V4<double> { using type = d4; };
+template <> struct V4<float> { using type = float4; };
+
+__device__ __forceinline__ d4 make_v4(double x, double y, double z, uint32_t wb) {
+  d4 v;
+  v.x = x; v.y = y; v.z = z; v.w = w_from_bits_d(wb);
+  return v;
+}
+__device__ __forceinline__ float4 make_v4f(float x, float y, float z, uint32_t wb) {
+  return make_float4(x, y, z, w_from_bits_f(wb));
+}
+
+__device__ __forceinline__ void set_status(DevCtl* ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+
+// Warp-aggregated add of a per-thread value (all 32 lanes must be active).
+__device__ __forceinline__ void warp_sum_add(unsigned long long* dst, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+__device__ __forceinline__ int cell_coord(double x, double inv_edge, int n) {
+  int c = (int)(x * inv_edge);
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+__device__ __forceinline__ int cell_coord_f(float x, float inv_edge, int n) {
+  int c = (int)(x * inv_edge);
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// ================================================================================================
+// K0: unimolecular decay draws (start-of-step state), free displacement of the other particles,
+// and the first half of the counting sort by cell (start-of-step positions).
+// ================================================================================================
+template <class T>
+__global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          const RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
+                          const uint32_t* __restrict__ id, typename V4<T>::type* __restrict__ x1,
+                          uint32_t* __restrict__ status, int32_t* __restrict__ matched,
+                          uint32_t* __restrict__ deg, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
+                          uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t n = ctl->n, step = ctl->step;
+  const int dim = P.dim;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const auto p = x0[i];
+    const uint32_t wb = w_bits(p.w);
+    const uint32_t sp = wb & 0xFFu, r = wb >> 8;
+    const uint32_t pid = id[i];
+    const RepDev& rep = reps[r];
+    uint32_t st = 0;
+    if (P.ktot[sp] > 0.0) {
+      const uint4 w = draw(P, step, pid, kOneParticle, TAG_UNI, r);
+      const double u = u52(w.x, w.y);
+      if (u < P.p_uni[sp]) {
+        const double target = u52(w.z, w.w) * P.ktot[sp];
+        double acc = 0.0;
+        int chosen = -1, last = -1;
+        for (int c = 0; c < P.n_decays; ++c) {
+          if (P.decays[c].parent != (int)sp) continue;
+          last = c;
+          acc += P.decays[c].kd;
+          if (chosen < 0 && target < acc) chosen = c;
+        }
+        if (chosen < 0) chosen = last;
+        st = ST_DECAYED | ST_CONSUMED | ((uint32_t)chosen << ST_CHANNEL_SHIFT);
+        const unsigned m = __activemask();
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&ctl->n_decay, (uint32_t)__popc(m));
+        base = __shfl_sync(m, base, leader);
+        decay_list[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = i;
+      }
+    }
+    status[i] = st;
+    matched[i] = -1;
+    deg[i] = 0u;
+    typename V4<T>::type q = p;
+    if (!st) {
+      if constexpr (sizeof(T) == 8) {
+        double nr[4];
+        normals64(P, step, pid, TAG_DISP0, r, dim, nr);
+        const double ell = P.ell[sp];
+        q.x = wrap(p.x + ell * nr[0], rep.L);
+        q.y = wrap(p.y + ell * nr[1], rep.L);
+        if (dim == 3) q.z = wrap(p.z + ell * nr[2], rep.L);
+      } else {
+        const uint4 w = draw(P, step, pid, kOneParticle, TAG_DISP0, r);
+        float n0, n1, n2, n3;
+        box_muller_f(u23(w.x), u23(w.y), n0, n1);
+        const float ell = P.ell_f[sp];
+        q.x = wrap_f(p.x + ell * n0, rep.Lf);
+        q.y = wrap_f(p.y + ell * n1, rep.Lf);
+        if (dim == 3) {
+          box_muller_f(u23(w.z), u23(w.w), n2, n3);
+          q.z = wrap_f(p.z + ell * n2, rep.Lf);
+        }
+      }
+    }
+    x1[i] = q;
+    uint32_t cell = kNoCell;
+    if (!st && ((P.binned_mask >> sp) & 1u)) {
+      int cx, cy, cz = 0;
+      if constexpr (sizeof(T) == 8) {
+        cx = cell_coord(p.x, rep.inv_edge[0], rep.nc[0]);
+        cy = cell_coord(p.y, rep.inv_edge[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord(p.z, rep.inv_edge[2], rep.nc[2]);
+      } else {
+        cx = cell_coord_f(p.x, rep.inv_edge_f[0], rep.nc[0]);
+        cy = cell_coord_f(p.y, rep.inv_edge_f[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord_f(p.z, rep.inv_edge_f[2], rep.nc[2]);
+      }
+      cell = (uint32_t)(rep.cell_base + ((int64_t)cz * rep.nc[1] + cy) * rep.nc[0] + cx);
+      slot[i] = atomicAdd(&cell_count[cell], 1u);
+    }
+    cell_of[i] = cell;
+  }
+}
+
+// ================================================================================================
+// Three-phase exclusive scan (block sums -> scan of the sums in one block -> block scans).
+// ================================================================================================
+template <class U, class Load>
+__device__ __forceinline__ U block_exclusive_scan(U v, U* smem, U& total) {
+  // smem: blockDim.x/32 entries
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  U x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const U y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    U s = lane < nw ? smem[lane] : U(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const U y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) smem[lane] = s;
+  }
+  __syncthreads();
+  total = smem[nw - 1];
+  const U warp_off = wid ? smem[wid - 1] : U(0);
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+struct LoadCellCount {
+  const uint32_t* cnt;
+  __device__ uint32_t operator()(int64_t i) const { return cnt[i]; }
+};
+
+struct LoadCompact {
+  const uint32_t* status;
+  __device__ unsigned long long operator()(int64_t i) const {
+    const uint32_t s = status[i];
+    const unsigned long long surv = (s & ST_CONSUMED) ? 0ull : 1ull;
+    const unsigned long long np = (s >> ST_NPROD_SHIFT) & 3u;
+    return (surv << 32) | np;
+  }
+};
+
+template <class U, class Load>
+__global__ void k_scan_reduce(Load load, const int64_t* __restrict__ n_ptr64, const uint32_t* n_ptr32,
+                              int64_t n_const, U* __restrict__ block_sums, int items) {
+  __shared__ U sm[32];
+  const int64_t n = n_ptr32 ? (int64_t)*n_ptr32 : (n_ptr64 ? *n_ptr64 : n_const);
+  const int64_t chunk = (int64_t)blockDim.x * items;
+  const int64_t beg = (int64_t)blockIdx.x * chunk;
+  U acc = 0;
+  for (int k = 0; k < items; ++k) {
+    const int64_t i = beg + (int64_t)k * blockDim.x + threadIdx.x;
+    if (i < n) acc += load(i);
+  }
+  U total;
+  block_exclusive_scan<U, Load>(acc, sm, total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+template <class U>
+__global__ void k_scan_top(U* __restrict__ block_sums, int nblocks) {
+  __shared__ U sm[32];
+  __shared__ U carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nblocks; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const U v = i < nblocks ? block_sums[i] : U(0);
+    U total;
+    const U ex = block_exclusive_scan<U, int>(v, sm, total);
+    if (i < nblocks) block_sums[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[nblocks] = carry;
+}
+
+// Writes out[i] = exclusive prefix, out[n] = total; optionally zeroes the input counts.
+template <class U, class Load>
+__global__ void k_scan_down(Load load, const int64_t* __restrict__ n_ptr64, const uint32_t* n_ptr32,
+                            int64_t n_const, const U* __restrict__ block_sums, U* __restrict__ out,
+                            uint32_t* zero_after, int items, int nblocks) {
+  __shared__ U sm[32];
+  const int64_t n = n_ptr32 ? (int64_t)*n_ptr32 : (n_ptr64 ? *n_ptr64 : n_const);
+  const int64_t chunk = (int64_t)blockDim.x * items;
+  const int64_t beg = (int64_t)blockIdx.x * chunk;
+  U carry = block_sums[blockIdx.x];
+  for (int k = 0; k < items; ++k) {
+    const int64_t i = beg + (int64_t)k * blockDim.x + threadIdx.x;
+    const U v = i < n ? load(i) : U(0);
+    U total;
+    const U ex = block_exclusive_scan<U, Load>(v, sm, total);
+    if (i < n) {
+      out[i] = carry + ex;
+      if (zero_after) zero_after[i] = 0u;
+    }
+    carry += total;
+  }
+  if (blockIdx.x == (unsigned)(nblocks - 1) && threadIdx.x == 0) out[n] = block_sums[nblocks];
+}
+
+// ================================================================================================
+// K2: scatter of the binned particles into cell order: start-of-step position (w = species bits),
+// end-of-free-step position (w = id bits) and the particle index.
+// ================================================================================================
+template <class T>
+__global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V4<T>::type* __restrict__ x0,
+                                const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
+                                const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ slot,
+                                const uint32_t* __restrict__ cell_start,
+                                typename V4<T>::type* __restrict__ sx0, typename V4<T>::type* __restrict__ sx1,
+                                uint32_t* __restrict__ sidx) {
+  if (ctl->status) return;
+  const uint32_t n = ctl->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t c = cell_of[i];
+    if (c == kNoCell) continue;
+    const uint32_t k = cell_start[c] + slot[i];
+    sx0[k] = x0[i];
+    auto q = x1[i];
+    if constexpr (sizeof(T) == 8)
+      q.w = w_from_bits_d(id[i]);
+    else
+      q.w = w_from_bits_f(id[i]);
+    sx1[k] = q;
+    sidx[k] = i;
+  }
+}
+
+// ================================================================================================
+// K3: cell sweep.  One thread per binned particle (cell order) visits the 27 (3D) / 9 (2D)
+// neighbouring cells; every pair (k, j > k) of an interacting species pair whose start-of-step
+// minimum-image distance is below r_cut is a candidate: p_enc from the start and end separations,
+// U_enc < p_enc fires and the pair is appended with a warp-aggregated atomic.
+// ================================================================================================
+template <class T>
+__global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                               const RepDev* __restrict__ reps,
+                                               const typename V4<T>::type* __restrict__ sx0,
+                                               const typename V4<T>::type* __restrict__ sx1,
+                                               const uint32_t* __restrict__ sidx,
+                                               const uint32_t* __restrict__ cell_start,
+                                               const int64_t total_cells, FiredPair* __restrict__ fired,
+                                               uint32_t* __restrict__ fstate, const uint32_t cap_pairs) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t nb = cell_start[total_cells];
+  const uint32_t step = ctl->step;
+  const int dim = P.dim;
+  unsigned long long n_cand = 0, n_near = 0, n_overlap = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (nb + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t k = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nb) {
+      const auto a0 = sx0[k];
+      const auto a1 = sx1[k];
+      const uint32_t wa = w_bits(a0.w);
+      const uint32_t spa = wa & 0xFFu, r = wa >> 8;
+      const uint32_t ida = w_bits(a1.w);
+      const RepDev& rep = reps[r];
+      int cx, cy, cz = 0;
+      if constexpr (sizeof(T) == 8) {
+        cx = cell_coord(a0.x, rep.inv_edge[0], rep.nc[0]);
+        cy = cell_coord(a0.y, rep.inv_edge[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord(a0.z, rep.inv_edge[2], rep.nc[2]);
+      } else {
+        cx = cell_coord_f(a0.x, rep.inv_edge_f[0], rep.nc[0]);
+        cy = cell_coord_f(a0.y, rep.inv_edge_f[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord_f(a0.z, rep.inv_edge_f[2], rep.nc[2]);
+      }
+      const int ox = rep.nc[0] >= 3 ? 1 : 0, oy = rep.nc[1] >= 3 ? 1 : 0;
+      const int oz = (dim == 3 && rep.nc[2] >= 3) ? 1 : 0;
+      for (int dz = -oz; dz <= oz; ++dz) {
+        const int zz = (cz + dz + rep.nc[2]) % rep.nc[2];
+        for (int dy = -oy; dy <= oy; ++dy) {
+          const int yy = (cy + dy + rep.nc[1]) % rep.nc[1];
+          for (int dx = -ox; dx <= ox; ++dx) {
+            const int xx = (cx + dx + rep.nc[0]) % rep.nc[0];
+            const int64_t c = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * rep.nc[0] + xx;
+            const uint32_t jb = cell_start[c], je = cell_start[c + 1];
+            for (uint32_t j = (jb > k ? jb : k + 1); j < je; ++j) {
+              const auto b0 = sx0[j];
+              const uint32_t spb = w_bits(b0.w) & 0xFFu;
+              const int rule = P.pair_of[spa][spb];
+              if (rule < 0) continue;
+              const PairDev& pr = P.pairs[rule];
+              const auto b1 = sx1[j];
+              const uint32_t idb = w_bits(b1.w);
+              // orient the pair from the lower id to the higher id
+              const bool swap = idb < ida;
+              const uint32_t id_lo = swap ? idb : ida, id_hi = swap ? ida : idb;
+              double p;
+              bool overlap;
+              if constexpr (sizeof(T) == 8) {
+                const double sg = swap ? -1.0 : 1.0;
+                const double r0x = min_image(sg * (b0.x - a0.x), rep.L, rep.half_L);
+                const double r0y = min_image(sg * (b0.y - a0.y), rep.L, rep.half_L);
+                const double r0z = dim == 3 ? min_image(sg * (b0.z - a0.z), rep.L, rep.half_L) : 0.0;
+                const double r02 = norm2_rn(r0x, r0y, r0z, dim);
+                if (!(r02 < pr.rcut2)) continue;
+                const double rx = min_image(sg * (b1.x - a1.x), rep.L, rep.half_L);
+                const double ry = min_image(sg * (b1.y - a1.y), rep.L, rep.half_L);
+                const double rz = dim == 3 ? min_image(sg * (b1.z - a1.z), rep.L, rep.half_L) : 0.0;
+                const double R0 = sqrt(r02) / pr.sigma;
+                const double R = sqrt(norm2_rn(rx, ry, rz, dim)) / pr.sigma;
+                overlap = R <= 1.0;
+                p = p_enc3(R, R0, pr.inv_tau);
+              } else {
+                const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf);
+                const float r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
+                const float r0z = dim == 3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
+                const float r02 = r0x * r0x + r0y * r0y + r0z * r0z;
+                if (!(r02 < pr.rcut2_f)) continue;
+                const float rx = min_image_f(b1.x - a1.x, rep.Lf, rep.half_Lf);
+                const float ry = min_image_f(b1.y - a1.y, rep.Lf, rep.half_Lf);
+                const float rz = dim == 3 ? min_image_f(b1.z - a1.z, rep.Lf, rep.half_Lf) : 0.0f;
+                const float d0 = (sqrtf(r02) - pr.sigma_f) * pr.inv_sigma_f;
+                const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
+                overlap = d <= 0.0f;
+                p = (double)p_enc3_f(d, d0, pr.inv_tau_f);
+              }
+              const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
+              const double u_enc = u52(w.x, w.y);
+              ++n_cand;
+              n_overlap += overlap;
+              n_near += fabs(u_enc - p) <= 1e-9;
+              if (u_enc < p) {
+                const unsigned m = __activemask();
+                const int lane = threadIdx.x & 31;
+                const int leader = __ffs(m) - 1;
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(&ctl->fired, (uint32_t)__popc(m));
+                base = __shfl_sync(m, base, leader);
+                const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < cap_pairs) {
+                  FiredPair f;
+                  const uint32_t ia = sidx[k], ib = sidx[j];
+                  f.ia = swap ? ib : ia;
+                  f.ib = swap ? ia : ib;
+                  f.ida = id_lo;
+                  f.idb = id_hi;
+                  f.p = p;
+                  f.key = -log(u52(w.z, w.w)) / p;
+                  fired[pos] = f;
+                  fstate[pos] = FS_LIVE | ((uint32_t)rule << 2) | (r << 8);
+                } else {
+                  set_status(ctl, RD_ECAPACITY);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  warp_sum_add(&ctl->stats[RD_STAT_CANDIDATES], n_cand);
+  warp_sum_add(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
+  warp_sum_add(&ctl->stats[RD_STAT_OVERLAPS], n_overlap);
+}
+
+// ================================================================================================
+// K4: conflict resolution.  Pairs whose two particles fired with nobody else are accepted at once;
+// the rest go through rounds of locally-dominant matching (a pair is accepted when its
+// (key, id_a, id_b) is the smallest at both particles among the live pairs), which reproduces the
+// greedy acceptance in ascending (key, id_a, id_b).
+// ================================================================================================
+__global__ void k_match_degree(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
+                               uint32_t* __restrict__ deg, uint32_t cap_pairs) {
+  if (ctl->status) return;
+  const uint32_t nf = min(ctl->fired, cap_pairs);
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    atomicAdd(&deg[fired[e].ia], 1u);
+    atomicAdd(&deg[fired[e].ib], 1u);
+  }
+}
+
+__global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
+                                uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
+                                int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
+                                unsigned long long* __restrict__ best_key,
+                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs) {
+  if (ctl->status) return;
+  const uint32_t nf = min(ctl->fired, cap_pairs);
+  unsigned long long acc = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (nf + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t e = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nf) {
+      const FiredPair f = fired[e];
+      if (deg[f.ia] == 1u && deg[f.ib] == 1u) {
+        matched[f.ia] = (int32_t)f.ib;
+        matched[f.ib] = (int32_t)f.ia;
+        fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+        ++acc;
+      } else {
+        const unsigned m = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&ctl->n_conflict, (uint32_t)__popc(m));
+        base = __shfl_sync(m, base, leader);
+        conflict[base + __popc(m & ((1u << lane) - 1u))] = e;
+        best_key[f.ia] = ~0ull;
+        best_key[f.ib] = ~0ull;
+        best_pid[f.ia] = ~0ull;
+        best_pid[f.ib] = ~0ull;
+      }
+    }
+  }
+  warp_sum_add(&ctl->stats[RD_STAT_MATCHED], acc);
+}
+
+__global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                       const FiredPair* __restrict__ fired,
+                                                       uint32_t* __restrict__ fstate,
+                                                       int32_t* __restrict__ matched,
+                                                       const uint32_t* __restrict__ conflict,
+                                                       unsigned long long* __restrict__ best_key,
+                                                       unsigned long long* __restrict__ best_pid) {
+  __shared__ uint32_t live;
+  __shared__ unsigned long long acc_s;
+  if (ctl->status) return;
+  const uint32_t nc = ctl->n_conflict;
+  if (nc == 0) return;
+  if (threadIdx.x == 0) acc_s = 0;
+  int rounds = 0;
+  for (;;) {
+    // keys: each live pair offers its key to both particles
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      const uint32_t e = conflict[q];
+      if ((fstate[e] & 3u) != FS_LIVE) continue;
+      const unsigned long long kb = (unsigned long long)__double_as_longlong(fired[e].key);
+      atomicMin(&best_key[fired[e].ia], kb);
+      atomicMin(&best_key[fired[e].ib], kb);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      const uint32_t e = conflict[q];
+      if ((fstate[e] & 3u) != FS_LIVE) continue;
+      const FiredPair f = fired[e];
+      const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
+      const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
+      if (best_key[f.ia] == kb) atomicMin(&best_pid[f.ia], pid);
+      if (best_key[f.ib] == kb) atomicMin(&best_pid[f.ib], pid);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      const uint32_t e = conflict[q];
+      if ((fstate[e] & 3u) != FS_LIVE) continue;
+      const FiredPair f = fired[e];
+      const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
+      const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
+      if (best_key[f.ia] == kb && best_key[f.ib] == kb && best_pid[f.ia] == pid && best_pid[f.ib] == pid) {
+        matched[f.ia] = (int32_t)f.ib;
+        matched[f.ib] = (int32_t)f.ia;
+        fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+        atomicAdd(&acc_s, 1ull);
+      }
+    }
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      const uint32_t e = conflict[q];
+      if ((fstate[e] & 3u) != FS_LIVE) continue;
+      const FiredPair f = fired[e];
+      if (matched[f.ia] >= 0 || matched[f.ib] >= 0) {
+        fstate[e] = (fstate[e] & ~3u) | FS_DEAD;
+      } else {
+        best_key[f.ia] = ~0ull;
+        best_key[f.ib] = ~0ull;
+        best_pid[f.ia] = ~0ull;
+        best_pid[f.ib] = ~0ull;
+        atomicAdd(&live, 1u);
+      }
+    }
+    __syncthreads();
+    ++rounds;
+    if (live == 0) break;
+    if (rounds >= Pp->match_max_rounds) {
+      if (threadIdx.x == 0) set_status(ctl, RD_ETIMEOUT);
+      break;
+    }
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&ctl->stats[RD_STAT_MATCHED], acc_s);
+    atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
+  }
+}
+
+// ================================================================================================
+// K5: accepted pairs (Section 3, steps 2(a)-(c)).  Absorbing: react.  Reflective / radiation:
+// new separation length from the radial propagator G_ref - G_abs (direction of the free step kept,
+// centre of diffusion unchanged); radiation reacts with p_reac (Eq. psurv_radII).  A product sits
+// at the centre of diffusion (Eq. Rcoo).  All in FP64.
+// ================================================================================================
+template <class T>
+__device__ __forceinline__ void load3(const typename V4<T>::type& v, double o[3]) {
+  o[0] = (double)v.x; o[1] = (double)v.y; o[2] = (double)v.z;
+}
+
+template <class T>
+__device__ __forceinline__ typename V4<T>::type store4(const double p[3], uint32_t wb) {
+  if constexpr (sizeof(T) == 8)
+    return make_v4(p[0], p[1], p[2], wb);
+  else
+    return make_v4f((float)p[0], (float)p[1], (float)p[2], wb);
+}
+
+template <class T>
+__global__ void k_resolve(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          const RepDev* __restrict__ reps, const FiredPair* __restrict__ fired,
+                          const uint32_t* __restrict__ fstate, const typename V4<T>::type* __restrict__ x0,
+                          typename V4<T>::type* __restrict__ x1, uint32_t* __restrict__ status,
+                          typename V4<T>::type* __restrict__ prodpos, uint32_t cap_pairs) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t nf = min(ctl->fired, cap_pairs);
+  const uint32_t step = ctl->step;
+  const int dim = P.dim;
+  unsigned long long n_react = 0, n_res = 0, n_near = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (nf + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t e = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nf) continue;
+    const uint32_t fs = fstate[e];
+    if ((fs & 3u) != FS_ACCEPTED) continue;
+    const FiredPair f = fired[e];
+    const int rule = (fs >> 2) & 63u;
+    const uint32_t r = fs >> 8;
+    const PairDev& pr = P.pairs[rule];
+    const RepDev& rep = reps[r];
+    const auto pa1 = x1[f.ia], pb1 = x1[f.ib];
+    const auto pa0 = x0[f.ia], pb0 = x0[f.ib];
+    const uint32_t wa = w_bits(pa1.w), wb = w_bits(pb1.w);
+    const int spa = wa & 0xFF, spb = wb & 0xFF;
+    double a1[3], b1[3], a0[3], b0[3];
+    load3<T>(pa1, a1); load3<T>(pb1, b1); load3<T>(pa0, a0); load3<T>(pb0, b0);
+    const double Drel = P.D[spa] + P.D[spb];
+    const double ca = P.D[spa] / Drel, cb = P.D[spb] / Drel;
+    double rv[3] = {0, 0, 0}, r0v[3] = {0, 0, 0}, c[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+      rv[d] = min_image(b1[d] - a1[d], rep.L, rep.half_L);
+      r0v[d] = min_image(b0[d] - a0[d], rep.L, rep.half_L);
+      c[d] = a1[d] + ca * rv[d];
+    }
+    bool react = false;
+    if (pr.bc == RD_BC_ABS) {
+      react = true;
+    } else {
+      const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
+      const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
+      double R0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim)) / pr.sigma;
+      if (R0 < 1.0) R0 = 1.0;
+      const double Rn = resample3(u_res, R0, pr.s);
+      const double len = sqrt(norm2_rn(rv[0], rv[1], rv[2], dim));
+      double dir[3] = {0, 0, 0};
+      if (len > 0.0) {
+        for (int d = 0; d < dim; ++d) dir[d] = rv[d] / len;
+      } else {
+        const double l0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim));
+        if (l0 > 0.0)
+          for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
+        else
+          dir[0] = 1.0;
+      }
+      for (int d = 0; d < dim; ++d) {
+        const double nr = Rn * pr.sigma * dir[d];
+        a1[d] = wrap(c[d] - ca * nr, rep.L);
+        b1[d] = wrap(c[d] + cb * nr, rep.L);
+      }
+      ++n_res;
+      if (pr.bc == RD_BC_RAD) {
+        const double p = p_reac3(Rn, R0, pr.s, pr.alpha);
+        n_near += fabs(u_reac - p) <= 1e-9;
+        react = u_reac < p;
+      }
+    }
+    if (react) {
+      ++n_react;
+      uint32_t np = 0;
+      if (pr.product >= 0) {
+        double cw[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) cw[d] = wrap(c[d], rep.L);
+        prodpos[2 * (size_t)f.ia] = store4<T>(cw, pack_sp((uint32_t)pr.product, r));
+        np = 1;
+      }
+      status[f.ia] |= ST_CONSUMED | (np << ST_NPROD_SHIFT);
+      status[f.ib] |= ST_CONSUMED;
+    } else {
+      x1[f.ia] = store4<T>(a1, wa);
+      x1[f.ib] = store4<T>(b1, wb);
+    }
+  }
+  // (not all lanes may be active after continue: reduce with atomics directly)
+  if (n_react) atomicAdd(&ctl->stats[RD_STAT_REACTIONS], n_react);
+  if (n_res) atomicAdd(&ctl->stats[RD_STAT_RESAMPLED], n_res);
+  if (n_near) atomicAdd(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
+}
+
+// ================================================================================================
+// K6: unimolecular products (Section 2.2.5).  One product: parent position plus a free step with
+// the product's D.  Two products: centre of diffusion = parent position + free step with D_R;
+// separation a n (n uniform) propagated by G_ref - G_abs from contact, geminate recombination by
+// p_reac(R', 1); non-interacting products start sigma_place apart and separate freely.
+// ================================================================================================
+template <class T>
+__global__ void k_decay(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                        const RepDev* __restrict__ reps, const uint32_t* __restrict__ decay_list,
+                        const typename V4<T>::type* __restrict__ x0, const uint32_t* __restrict__ id,
+                        uint32_t* __restrict__ status, typename V4<T>::type* __restrict__ prodpos) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t nd = ctl->n_decay;
+  const uint32_t step = ctl->step;
+  const int dim = P.dim;
+  unsigned long long n_rec = 0, n_near = 0;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += gridDim.x * blockDim.x) {
+    const uint32_t i = decay_list[q];
+    const uint32_t st = status[i];
+    const DecayDev& dc = P.decays[(st >> ST_CHANNEL_SHIFT) & 15u];
+    const auto p0 = x0[i];
+    const uint32_t r = w_bits(p0.w) >> 8;
+    const RepDev& rep = reps[r];
+    const uint32_t pid = id[i];
+    double xp[3];
+    load3<T>(p0, xp);
+    uint32_t np = 0;
+    if (dc.n_products == 1) {
+      double nr[4];
+      normals64(P, step, pid, TAG_DISS0, r, dim, nr);
+      const double ell = sqrt(2.0 * P.D[dc.p0] * P.dt);
+      double q3[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) q3[d] = wrap(xp[d] + ell * nr[d], rep.L);
+      prodpos[2 * (size_t)i] = store4<T>(q3, pack_sp((uint32_t)dc.p0, r));
+      np = 1;
+    } else if (dc.n_products == 2) {
+      const int sa = dc.p0, sb = dc.p1;
+      const double Drel = P.D[sa] + P.D[sb];
+      const double ca = P.D[sa] / Drel, cb = P.D[sb] / Drel;
+      const double DR = P.D[sa] * P.D[sb] / Drel;
+      uint4 w = draw(P, step, pid, kOneParticle, TAG_DIR, r);
+      double dir[3] = {0, 0, 0};
+      if (dim == 3) {
+        const double ct = 2.0 * u52(w.x, w.y) - 1.0;
+        double sn, cs;
+        sincospi(2.0 * u52(w.z, w.w), &sn, &cs);
+        const double stt = sqrt(fmax(0.0, 1.0 - ct * ct));
+        dir[0] = stt * cs; dir[1] = stt * sn; dir[2] = ct;
+      } else {
+        double sn, cs;
+        sincospi(2.0 * u52(w.x, w.y), &sn, &cs);
+        dir[0] = cs; dir[1] = sn;
+      }
+      double nc[4];
+      normals64(P, step, pid, TAG_DISS0, r, dim, nc);
+      const double ellc = sqrt(2.0 * DR * P.dt);
+      double c[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
+      for (int d = 0; d < dim; ++d) c[d] = xp[d] + ellc * nc[d];
+      const int rule = P.pair_of[sa][sb];
+      bool recombine = false;
+      int product = -1;
+      if (rule >= 0) {
+        const PairDev& pr = P.pairs[rule];
+        w = draw(P, step, pid, kOneParticle, TAG_RES, r);
+        const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
+        const double Rn = resample3(u_res, 1.0, pr.s);
+        for (int d = 0; d < dim; ++d) rv[d] = Rn * pr.sigma * dir[d];
+        if (pr.bc == RD_BC_ABS) {
+          recombine = true;
+        } else if (pr.bc == RD_BC_RAD) {
+          const double p = p_reac3(Rn, 1.0, pr.s, pr.alpha);
+          n_near += fabs(u_reac - p) <= 1e-9;
+          recombine = u_reac < p;
+        }
+        product = pr.product;
+      } else {
+        double nr[4];
+        normals64(P, step, pid, TAG_DISS2, r, dim, nr);
+        const double ellr = sqrt(2.0 * Drel * P.dt);
+        for (int d = 0; d < dim; ++d) rv[d] = dc.sigma_place * dir[d] + ellr * nr[d];
+      }
+      if (recombine) {
+        ++n_rec;
+        if (product >= 0) {
+          double cw[3] = {0, 0, 0};
+          for (int d = 0; d < dim; ++d) cw[d] = wrap(c[d], rep.L);
+          prodpos[2 * (size_t)i] = store4<T>(cw, pack_sp((uint32_t)product, r));
+          np = 1;
+        }
+      } else {
+        double qa[3] = {0, 0, 0}, qb[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+          qa[d] = wrap(c[d] - ca * rv[d], rep.L);
+          qb[d] = wrap(c[d] + cb * rv[d], rep.L);
+        }
+        prodpos[2 * (size_t)i] = store4<T>(qa, pack_sp((uint32_t)sa, r));
+        prodpos[2 * (size_t)i + 1] = store4<T>(qb, pack_sp((uint32_t)sb, r));
+        np = 2;
+      }
+    }
+    status[i] = st | (np << ST_NPROD_SHIFT);
+  }
+  if (n_rec) atomicAdd(&ctl->stats[RD_STAT_RECOMBINED], n_rec);
+  if (n_near) atomicAdd(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
+}
+
+// ================================================================================================
+// K7: compaction.  scan[i] = (survivors before i) << 32 | (products before i).  Survivors keep their
+// order inside their replica, products follow the replica's survivors in owner order with ids
+// next_id + rank.  An error latched during the step turns this into a copy of the unchanged state.
+// ================================================================================================
+template <class T>
+__global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __restrict__ ctl,
+                          const RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
+                          const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
+                          const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
+                          const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
+                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts) {
+  const DevParams& P = *Pp;
+  const uint32_t n = ctl->n;
+  const unsigned long long tot = scan[n];
+  const bool fail = ctl->status != 0 || ((tot >> 32) + (tot & 0xFFFFFFFFull)) > (unsigned long long)P.cap_particles;
+  const int ns = P.n_species;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (fail) {
+      const auto q0 = x0[i];
+      xo[i] = q0;
+      ido[i] = id[i];
+      const uint32_t wb0 = w_bits(q0.w);
+      atomicAdd(&counts[(size_t)(wb0 >> 8) * ns + (wb0 & 0xFFu)], 1ull);
+      continue;
+    }
+    const uint32_t st = status[i];
+    const auto q = x1[i];
+    const uint32_t wb = w_bits(q.w);
+    const uint32_t r = wb >> 8;
+    const RepDev& rep = reps[r];
+    const unsigned long long e = scan[i];
+    const unsigned long long eb = scan[rep.beg], ee = scan[rep.end];
+    const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
+    const uint32_t P_beg = (uint32_t)eb, S_end = (uint32_t)(ee >> 32);
+    if (!(st & ST_CONSUMED)) {
+      const uint32_t o = S_i + P_beg;
+      xo[o] = q;
+      ido[o] = id[i];
+      atomicAdd(&counts[(size_t)r * ns + (wb & 0xFFu)], 1ull);
+    }
+    const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
+    for (uint32_t k = 0; k < np; ++k) {
+      const uint32_t o = S_end + P_i + k;
+      const auto pp = prodpos[2 * (size_t)i + k];
+      xo[o] = pp;
+      ido[o] = rep.next_id + (P_i - P_beg) + k;
+      atomicAdd(&counts[(size_t)r * ns + (w_bits(pp.w) & 0xFFu)], 1ull);
+    }
+  }
+}
+
+// K8: replica segments, next ids, particle count, step and time.
+__global__ void k_finalize(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl, RepDev* __restrict__ reps,
+                           const unsigned long long* __restrict__ scan) {
+  const DevParams& P = *Pp;
+  const uint32_t n = ctl->n;
+  const unsigned long long tot = scan[n];
+  const unsigned long long n_new = (tot >> 32) + (tot & 0xFFFFFFFFull);
+  const bool fail = ctl->status != 0 || n_new > (unsigned long long)P.cap_particles;
+  __syncthreads();
+  if (!fail) {
+    for (int r = threadIdx.x; r < P.n_replicas; r += blockDim.x) {
+      const unsigned long long eb = scan[reps[r].beg], ee = scan[reps[r].end];
+      const uint32_t nb = (uint32_t)(eb >> 32) + (uint32_t)eb;
+      const uint32_t ne = (uint32_t)(ee >> 32) + (uint32_t)ee;
+      reps[r].next_id += (uint32_t)ee - (uint32_t)eb;
+      reps[r].beg = nb;
+      reps[r].end = ne;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!fail) {
+      ctl->stats[RD_STAT_PARTICLE_STEPS] += n;
+      ctl->stats[RD_STAT_DECAYS] += ctl->n_decay;
+      ctl->stats[RD_STAT_FIRED] += ctl->fired;
+      if (ctl->fired > ctl->stats[RD_STAT_FIRED_HWM]) ctl->stats[RD_STAT_FIRED_HWM] = ctl->fired;
+      ctl->n = (uint32_t)n_new;
+      ctl->step += 1;
+      ctl->t += P.dt;
+    } else if (ctl->status == 0) {
+      ctl->status = RD_ECAPACITY;
+    }
+  }
+}
+
+// Per-step reset of the device counters (first kernel of a step).
+__global__ void k_begin_step(DevCtl* __restrict__ ctl, unsigned long long* __restrict__ counts, int n_counts) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->fired = 0;
+    ctl->n_conflict = 0;
+    ctl->n_decay = 0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += gridDim.x * blockDim.x) counts[i] = 0;
+}
+
+// ================================================================================================
+// Initial uniform positions (INIT streams) and helpers.
+// ================================================================================================
+template <class T>
+__global__ void k_init_positions(const DevParams* __restrict__ Pp, const RepDev* __restrict__ reps,
+                                 const int32_t* __restrict__ rep_of, const int32_t* __restrict__ sp_of,
+                                 const uint32_t* __restrict__ id_of, uint32_t n,
+                                 typename V4<T>::type* __restrict__ x, uint32_t* __restrict__ ido) {
+  const DevParams& P = *Pp;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t r = (uint32_t)rep_of[i], pid = id_of[i];
+    const double L = reps[r].L;
+    uint4 w = draw(P, 0u, pid, kOneParticle, TAG_INIT0, r);
+    double p[3];
+    p[0] = u52(w.x, w.y) * L;
+    p[1] = u52(w.z, w.w) * L;
+    p[2] = 0.0;
+    if (P.dim == 3) {
+      w = draw(P, 0u, pid, kOneParticle, TAG_INIT1, r);
+      p[2] = u52(w.x, w.y) * L;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (!(p[d] < L)) p[d] = 0.0;
+    if constexpr (sizeof(T) == 8) {
+      x[i] = make_v4(p[0], p[1], p[2], pack_sp((uint32_t)sp_of[i], r));
+    } else {
+      float f[3];
+      for (int d = 0; d < 3; ++d) {
+        f[d] = (float)p[d];
+        if (!(f[d] < reps[r].Lf)) f[d] = 0.0f;
+      }
+      x[i] = make_v4f(f[0], f[1], f[2], pack_sp((uint32_t)sp_of[i], r));
+    }
+    ido[i] = pid;
+  }
+}
+
+template <class T>
+__global__ void k_count(const DevParams* __restrict__ Pp, const DevCtl* __restrict__ ctl,
+                        const typename V4<T>::type* __restrict__ x, unsigned long long* __restrict__ counts) {
+  const uint32_t n = ctl->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t wb = w_bits(x[i].w);
+    atomicAdd(&counts[(size_t)(wb >> 8) * Pp->n_species + (wb & 0xFFu)], 1ull);
+  }
+}
+
+// Standalone per-pair probabilities (rd_pair_probs).
+__global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const double* __restrict__ r0,
+                             const double* __restrict__ r, int64_t n, double* __restrict__ p_enc,
+                             double* __restrict__ p_reac) {
+  const DevParams& P = *Pp;
+  const PairDev& pr = P.pairs[rule];
+  const double inv_sigma = 1.0 / pr.sigma;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double a = r0[k], b = r[k];
+    if (p_enc) {
+      if (P.precision == RD_MIXED) {
+        const float d0 = (float)((a - pr.sigma) * inv_sigma), d = (float)((b - pr.sigma) * inv_sigma);
+        p_enc[k] = (double)p_enc3_f(d, d0, pr.inv_tau_f);
+      } else {
+        p_enc[k] = p_enc3(b / pr.sigma, a / pr.sigma, pr.inv_tau);
+      }
+    }
+    if (p_reac) p_reac[k] = pr.bc == RD_BC_RAD ? p_reac3(b / pr.sigma, a / pr.sigma, pr.s, pr.alpha)
+                                               : (pr.bc == RD_BC_ABS ? 1.0 : 0.0);
+  }
+}
+
+__global__ void k_resample(const DevParams* __restrict__ Pp, int rule, const double* __restrict__ r0,
+                           const double* __restrict__ u, int64_t n, double* __restrict__ out) {
+  const PairDev& pr = Pp->pairs[rule];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = resample3(u[k], r0[k] / pr.sigma, pr.s) * pr.sigma;
+}
+
+// ================================================================================================
+// host-side launchers
+// ================================================================================================
+static inline int grid_for(int64_t n, int block, int max_grid) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_grid) g = max_grid;
+  return (int)g;
+}
+
+template <class T>
+static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
+  using V = typename V4<T>::type;
+  const int B = L.block;
+  const int Gp = grid_for(L.cap_particles, B, L.max_grid);
+  auto mark = [&](const char* name) {
+    if (timer) timer->mark(name, s);
+  };
+  V* x0 = (V*)L.x_cur;
+  V* xo = (V*)L.x_next;
+  V* x1 = (V*)L.x1;
+  V* sx0 = (V*)L.sx0;
+  V* sx1 = (V*)L.sx1;
+  V* prod = (V*)L.prodpos;
+
+  mark("begin");
+  k_begin_step<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.ctl, L.counts, L.n_counts);
+  mark("k_begin_step");
+  k_prepare<T><<<Gp, B, 0, s>>>(L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg, L.cell_of, L.slot,
+                                 L.cell_count, L.decay_list);
+  mark("k_prepare");
+  // scan of the cell counts -> cell_start (counts zeroed for the next step)
+  const int items = L.scan_items;
+  const int nbc = (int)((L.total_cells + (int64_t)256 * items - 1) / ((int64_t)256 * items));
+  k_scan_reduce<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, nullptr, nullptr,
+                                                             L.total_cells, L.block_sums32, items);
+  k_scan_top<uint32_t><<<1, 1024, 0, s>>>(L.block_sums32, nbc);
+  k_scan_down<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, nullptr, nullptr,
+                                                           L.total_cells, L.block_sums32, L.cell_start,
+                                                           L.cell_count, items, nbc);
+  mark("k_scan_cells");
+  k_scatter_cells<T><<<Gp, B, 0, s>>>(L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1, L.sidx);
+  mark("k_scatter_cells");
+  k_sweep<T><<<Gp, 256, 0, s>>>(L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired,
+                                 L.fstate, (uint32_t)L.cap_pairs);
+  mark("k_sweep");
+  const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
+  k_match_degree<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.deg, (uint32_t)L.cap_pairs);
+  k_match_trivial<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.best_key,
+                                     L.best_pid, (uint32_t)L.cap_pairs);
+  k_match_rounds<<<1, 1024, 0, s>>>(L.P, L.ctl, L.fired, L.fstate, L.matched, L.conflict, L.best_key, L.best_pid);
+  mark("k_match");
+  k_resolve<T><<<Gf, 128, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, x0, x1, L.status, prod,
+                                   (uint32_t)L.cap_pairs);
+  mark("k_resolve");
+  k_decay<T><<<grid_for(L.cap_particles / 8 + 1, 128, L.max_grid), 128, 0, s>>>(L.P, L.ctl, L.reps, L.decay_list,
+                                                                                  x0, L.id_cur, L.status, prod);
+  mark("k_decay");
+  // compaction scan over particles
+  const int nbp = (int)((L.cap_particles + (int64_t)256 * items - 1) / ((int64_t)256 * items));
+  k_scan_reduce<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, nullptr, &L.ctl->n, 0,
+                                                                     L.block_sums64, items);
+  k_scan_top<unsigned long long><<<1, 1024, 0, s>>>(L.block_sums64, nbp);
+  k_scan_down<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, nullptr, &L.ctl->n, 0,
+                                                                   L.block_sums64, L.scan, nullptr, items, nbp);
+  mark("k_scan_compact");
+  k_compact<T><<<Gp, B, 0, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo, L.id_next,
+                                 L.counts);
+  mark("k_compact");
+  k_finalize<<<1, 256, 0, s>>>(L.P, L.ctl, L.reps, L.scan);
+  mark("k_finalize");
+}
+
+void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
+  if (L.precision == RD_MIXED)
+    step_impl<float>(L, s, timer);
+  else
+    step_impl<double>(L, s, timer);
+}
+
+void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int32_t* sp_of, const uint32_t* id_of,
+                           uint32_t n, cudaStream_t s) {
+  const int G = grid_for(n, 256, L.max_grid);
+  if (L.precision == RD_MIXED)
+    k_init_positions<float><<<G, 256, 0, s>>>(L.P, L.reps, rep_of, sp_of, id_of, n, (float4*)L.x_cur, L.id_cur);
+  else
+    k_init_positions<double><<<G, 256, 0, s>>>(L.P, L.reps, rep_of, sp_of, id_of, n, (d4*)L.x_cur, L.id_cur);
+}
+
+void launch_count(const StepLaunch& L, cudaStream_t s) {
+  k_begin_step<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.ctl, L.counts, L.n_counts);
+  const int G = grid_for(L.cap_particles, 256, L.max_grid);
+  if (L.precision == RD_MIXED)
+    k_count<float><<<G, 256, 0, s>>>(L.P, L.ctl, (const float4*)L.x_cur, L.counts);
+  else
+    k_count<double><<<G, 256, 0, s>>>(L.P, L.ctl, (const d4*)L.x_cur, L.counts);
+}
+
+void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,
+                       double* pr, int max_grid, cudaStream_t s) {
+  k_pair_probs<<<grid_for(n, 256, max_grid), 256, 0, s>>>(P, rule, r0, r, n, pe, pr);
+}
+
+void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
+                     int max_grid, cudaStream_t s) {
+  k_resample<<<grid_for(n, 128, max_grid), 128, 0, s>>>(P, rule, r0, u, n, out);
+}
+
+}  // namespace rd

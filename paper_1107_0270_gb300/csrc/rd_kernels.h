@@ -1,0 +1,85 @@
+// Launch interface between the host runtime and the step kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rd_internal.cuh"
+
+namespace rd {
+
+// Device buffers and sizes of one step (pointers are device addresses).
+struct StepLaunch {
+  int precision;
+  int block;
+  int max_grid;
+  int scan_items;
+  int64_t cap_particles, cap_pairs, total_cells;
+  int n_counts;
+  const DevParams* P;
+  DevCtl* ctl;
+  RepDev* reps;
+  void* x_cur;
+  void* x_next;
+  uint32_t* id_cur;
+  uint32_t* id_next;
+  void* x1;
+  void* sx0;
+  void* sx1;
+  void* prodpos;
+  uint32_t* status;
+  int32_t* matched;
+  uint32_t* deg;
+  uint32_t* cell_of;
+  uint32_t* slot;
+  uint32_t* cell_count;
+  uint32_t* cell_start;
+  uint32_t* sidx;
+  uint32_t* decay_list;
+  uint32_t* block_sums32;
+  unsigned long long* block_sums64;
+  unsigned long long* scan;
+  FiredPair* fired;
+  uint32_t* fstate;
+  uint32_t* conflict;
+  unsigned long long* best_key;
+  unsigned long long* best_pid;
+  unsigned long long* counts;
+};
+
+// CUDA-event marks between kernel groups of one (non-graph) step.
+struct KernelTimer {
+  std::vector<cudaEvent_t> events;
+  std::vector<std::string> names;
+  size_t used = 0;
+  void reset() { used = 0; names.clear(); }
+  void mark(const char* name, cudaStream_t s) {
+    if (used == events.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      events.push_back(e);
+    }
+    cudaEventRecord(events[used++], s);
+    names.push_back(name);
+  }
+  void destroy() {
+    for (auto e : events) cudaEventDestroy(e);
+    events.clear();
+    names.clear();
+    used = 0;
+  }
+};
+
+void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer);
+void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int32_t* sp_of, const uint32_t* id_of,
+                           uint32_t n, cudaStream_t s);
+void launch_count(const StepLaunch& L, cudaStream_t s);
+void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,
+                       double* pr, int max_grid, cudaStream_t s);
+void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
+                     int max_grid, cudaStream_t s);
+
+}  // namespace rd
