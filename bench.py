@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the GF-BD reaction-diffusion step on GB300.
+
+Default workload: 3D reversible A+B<->C with a radiation boundary condition, periodic cube
+L = 2.55 um (10 uM), N_A = N_B = 1e5, sigma = 0.005 um, D = 1 (C: 0.5) um^2/s, ka = 0.02 um^3/s,
+kd = 10 /s, dt = 1e-5 s (tau = 0.8), started from the mass-action equilibrium composition.
+One "step" = one pass of the whole step (decays, displacements, binning, cell sweep with p_enc,
+conflict resolution, pair resolution, products, compaction, observables) for every particle.
+
+Timing: W warm-up steps, then K steps as two-step CUDA-graph launches, each bracketed by CUDA
+events on the library's stream; the L2 cache is flushed (512 MiB write) between timed launches,
+outside the events.  Multi-GPU (torchrun): every rank runs an independent replica with its own seed
+("replicas only", weak scaling); value = all ranks' particle-steps / the slowest rank's time.
+
+``--impl reference`` times the plain CPU FP64 oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+KERNELS_PER_STEP = 17          # kernels of one step (begin, prepare, 3 scan, scatter, sweep, 3 match,
+                               # resolve, decay, 3 scan, compact, finalize)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--dt", type=float, default=1e-5)
+    ap.add_argument("--n-each", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, pair-prob batch, e2e")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args, seed=1):
+    return W.reversible_3d(dt=args.dt, seed=seed, n_each=args.n_each, equilibrium_start=True)
+
+
+def workload_name(args):
+    return (f"3D A+B<->C radiation BC, L=2.55 um (10 uM), N_A=N_B={args.n_each:.0e} "
+            f"(mass-action start), sigma=0.005, D=1/1/0.5, ka=0.02, kd=10, dt={args.dt:g}")
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# roofline bookkeeping
+# ------------------------------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kernel, precision, n, n_binned, candidates):
+    """Per-launch algorithmic bytes of the step kernels (minimum traffic the stage needs)."""
+    v = 16 if precision == "mixed" else 32
+    if kernel == "k_prepare":      # read position + id, write end position
+        return n * (2 * v + 4)
+    if kernel == "k_sweep":        # read start + end position of each binned particle once
+        return n_binned * 2 * v
+    if kernel == "k_compact":      # read end position + id + status, write position + id
+        return n * (2 * v + 12)
+    if kernel == "k_scatter_cells":
+        return n_binned * (4 * v + 8)
+    return None
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(args, seconds, seed=1):
+    import oracle as O
+
+    O.build()
+    # Same density, time step and chemistry; a smaller box so that the O(N^2) oracle fits the
+    # time budget.  Rate reported per particle-step.
+    n_each = 4000
+    L = 2.55 * (n_each / args.n_each) ** (1 / 3)
+    system = W.reversible_3d(dt=args.dt, seed=seed, n_each=n_each, L=L, equilibrium_start=True)
+    st = O.init_state(system)
+    ps = 0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        n = st.n
+        st, _ = O.step(system, st)
+        ps += n
+        steps += 1
+        if time.perf_counter() - t0 >= seconds and steps >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": ps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps of the same system in a sub-box L={L:.3f} um with "
+                      f"N_A=N_B={n_each} (same 10 uM density, dt, chemistry); O(N^2) candidate "
+                      f"search, single thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # bounded per-step samples: each timed "step" is one oracle step of the sub-box sample
+    import oracle as O
+
+    O.build()
+    n_each = 4000
+    L = 2.55 * (n_each / args.n_each) ** (1 / 3)
+    system = W.reversible_3d(dt=args.dt, seed=1, n_each=n_each, L=L, equilibrium_start=True)
+    st = O.init_state(system)
+    for _ in range(max(args.warmup, 0) and min(args.warmup, 3)):
+        st, _ = O.step(system, st)
+    steps = min(args.steps, 40)
+    ps = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ps += st.n
+        st, _ = O.step(system, st)
+    el = time.perf_counter() - t0
+    v = ps / el
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": v, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": steps, "warmup": min(args.warmup, 3), "ms_per_step": 1e3 * el / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args) + " -- oracle on a bounded sub-box sample"},
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{steps} steps, sub-box L={L:.3f} um, N_A=N_B={n_each} at the same density"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def timed_graph_run(sim, torch, flush, steps):
+    """K steps as two-step graph launches, each between CUDA events on the library's stream."""
+    launches = steps // 2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(launches)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(launches)]
+    s = sim.stream
+    for k in range(launches):
+        with torch.cuda.stream(s):
+            flush.add_(1)                      # L2 flush, outside the timed events
+            starts[k].record(s)
+        sim.run(2)
+        with torch.cuda.stream(s):
+            ends[k].record(s)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3, 2 * launches
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1107_0270_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    system = workload(args, seed=1 + rank)
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    sim = pkg.Simulation(system, precision=args.precision)
+    sim.run(max(args.warmup, 3))
+    sim.sync()
+    obs0 = sim.observables()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        elapsed, steps_done = timed_graph_run(sim, torch, flush, args.steps)
+    barrier()
+    obs1 = sim.observables()
+    ps_local = obs1["stats"]["particle_steps"] - obs0["stats"]["particle_steps"]
+    cand_local = obs1["stats"]["candidates"] - obs0["stats"]["candidates"]
+    t_max = elapsed
+    ps_total = ps_local
+    if dist is not None:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        pt = torch.tensor([float(ps_local)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pt)
+        ps_total = float(pt.item())
+    value = ps_total / t_max
+
+    extras = {}
+    if rank == 0:
+        # per-kernel times of single (non-graph) steps, CUDA events on the library's stream
+        ker = {}
+        nsamp = 20
+        n_now = sim.num_particles()
+        for _ in range(nsamp):
+            flush.add_(1)
+            torch.cuda.synchronize()
+            for name, ms in sim.timed_step():
+                ker.setdefault(name, []).append(ms)
+        ker_avg = {k: sum(v) / len(v) for k, v in ker.items()}
+        step_ms = sum(ker_avg.values())
+        top = max((k for k in ker_avg if k in ("k_prepare", "k_sweep", "k_compact", "k_scatter_cells")),
+                  key=lambda k: ker_avg[k])
+        st = sim.get_state()
+        binned = int(np.sum(st["species"] < 2))
+        cand_per_step = cand_local / max(steps_done, 1)
+        peak, peak_kind = measured_peaks()
+        ab = algorithmic_bytes(top, args.precision, n_now, binned, cand_per_step)
+        achieved = ab / (ker_avg[top] * 1e-3) / 1e9
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(prof):
+            with open(prof) as f:
+                tj = json.load(f)
+            key = f"{top}:{args.precision}"
+            if key in tj:
+                traffic = tj[key]
+        extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                              "frac": achieved / peak, "traffic": traffic, "kernel": top,
+                              "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
+                              "algorithmic_bytes_per_launch": ab,
+                              "kernel_ms": ker_avg[top]}
+        extras["kernel_ms"] = {k: round(v, 5) for k, v in ker_avg.items()}
+        extras["sweep_pair_prob_evals_per_s"] = cand_per_step / (ker_avg["k_sweep"] * 1e-3)
+        extras["candidates_per_step"] = cand_per_step
+        if not args.no_extras:
+            extras.update(extra_measurements(args, torch, pkg, flush, sim))
+    sim.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": steps_done, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / steps_done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args), "precision": args.precision,
+                   "particles": int(obs1["counts"].sum()), "timing": "2-step CUDA graph launches, events on the library stream",
+                   "l2": "flushed (512 MiB write) between timed graph launches",
+                   "parallelism": f"replicas x{world} (one independent system per GPU)"},
+        "gpu_launches": KERNELS_PER_STEP * steps_done,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+    }
+    line.update(extras)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args, args.cpu_sample_seconds)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def extra_measurements(args, torch, pkg, flush, sim_main):
+    out = {}
+    # FP64 step on the same workload
+    if args.precision == "mixed":
+        sim64 = pkg.Simulation(workload(args), precision="fp64")
+        sim64.run(max(args.warmup, 3))
+        sim64.sync()
+        o0 = sim64.observables()
+        el, nst = timed_graph_run(sim64, torch, flush, min(args.steps, 1000))
+        o1 = sim64.observables()
+        out["fp64"] = {"value": (o1["stats"]["particle_steps"] - o0["stats"]["particle_steps"]) / el,
+                       "unit": "particle-steps/s", "steps": nst, "ms_per_step": 1e3 * el / nst}
+        sim64.close()
+    # standalone pair-probability batch (p_enc only) on 2^25 candidate-shaped pairs (> L2)
+    system = workload(args)
+    pr = system.pairs[0]
+    Drel = system.D[pr.s1] + system.D[pr.s2]
+    r0n, rn = W.pair_samples(1 << 20, pr.sigma, Drel, system.dt, seed=11)
+    reps = 32
+    r0 = torch.tensor(np.tile(r0n, reps), device="cuda")
+    r = torch.tensor(np.tile(rn, reps), device="cuda")
+    res = {}
+    for prec in ("mixed", "fp64"):
+        sim = pkg.Simulation(workload(args, seed=2), precision=prec)
+        pe = torch.empty_like(r0)
+        for _ in range(3):
+            sim.pair_probs(r0, r, out=(pe, None))
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(10):
+            flush.add_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(sim.stream):
+                sim.stream.wait_stream(torch.cuda.current_stream())
+                a.record(sim.stream)
+            sim.pair_probs(r0, r, out=(pe, None))
+            with torch.cuda.stream(sim.stream):
+                b.record(sim.stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(times)
+        res[prec] = {"evals_per_s": r0.numel() / t, "gbs": r0.numel() * 24 / t / 1e9, "pairs": r0.numel()}
+        sim.close()
+    out["pair_prob_evals_per_s"] = res
+    # end to end through the C ABI with host buffers: per step, upload the state from pinned host
+    # memory (rd_set_state), one step, read back the state and the observables (rd_get_state,
+    # rd_observables)
+    sim = pkg.Simulation(workload(args, seed=3), precision=args.precision)
+    sim.run(4)
+    st = sim.get_state()
+    n_e2e = 10
+    t0 = time.perf_counter()
+    ps = 0
+    h2d = d2h = 0
+    for _ in range(n_e2e):
+        n = st["ids"].shape[0]
+        sim.set_state(st["x"], st["species"], st["ids"], st["replica"], st["next_id"], st["step"])
+        sim.step()
+        st = sim.get_state()
+        sim.observables()
+        ps += n
+        h2d += n * (24 + 4 + 4 + 4)
+        d2h += st["ids"].shape[0] * (24 + 4 + 4 + 4) + 8 * 3
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": ps / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // n_e2e,
+                  "d2h_bytes_per_step": d2h // n_e2e,
+                  "path": "rd_set_state(host) + rd_step + rd_get_state(host) + rd_observables per step"}
+    sim.close()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -302,7 +302,7 @@ def step(system, state: State, replica: int = 0, L: float | None = None, trace: 
     tr = None
     arrays = None
     if trace:
-        tcap = max(1024, 64 * n)
+        tcap = n * (n - 1) // 2 + 1024 if n < 4000 else 256 * n
         arrays = dict(ida=np.zeros(tcap, np.uint32), idb=np.zeros(tcap, np.uint32),
                       p_enc=np.zeros(tcap), u_enc=np.zeros(tcap), fired=np.zeros(tcap, np.int32),
                       matched=np.zeros(tcap, np.int32))

@@ -190,6 +190,9 @@ static void derive_params(rd_handle* h) {
       if (c.decays[k].parent == s) kt += c.decays[k].kd;
     P.ktot[s] = kt;
     P.p_uni[s] = -std::expm1(-kt * c.dt);
+    // U = (m + 1/2) 2^-52 < p  <=>  m < ceil(p 2^52 - 1/2); p 2^52 - 1/2 is exact for p < 1
+    const double T = std::ldexp(P.p_uni[s], 52) - 0.5;
+    P.uni_thr[s] = T <= 0.0 ? 0ull : (unsigned long long)std::ceil(T);
   }
 }
 

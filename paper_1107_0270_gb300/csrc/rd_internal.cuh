@@ -14,6 +14,7 @@ constexpr int kMaxPairs = RD_MAX_PAIRS;
 constexpr int kMaxDecays = RD_MAX_DECAYS;
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 constexpr uint32_t kOneParticle = 0xFFFFFFFFu;   // id_b of one-particle random streams
+constexpr int kSmemCounts = 8192;                // per-block histogram of (replica, species) counts
 
 // Random-stream tags (counter word 3, low byte; replica index in the upper 24 bits).
 enum Tag : uint32_t {
@@ -60,6 +61,7 @@ struct DevParams {
   float ell_f[kMaxSpecies];
   double ktot[kMaxSpecies];    // total unimolecular rate per species
   double p_uni[kMaxSpecies];   // 1 - exp(-ktot dt)
+  unsigned long long uni_thr[kMaxSpecies];   // decay iff (52-bit draw m) < uni_thr
   int8_t pair_of[kMaxSpecies][kMaxSpecies];   // index into pairs, -1 = no interaction
   PairDev pairs[kMaxPairs];
   DecayDev decays[kMaxDecays];
@@ -240,10 +242,10 @@ __device__ __forceinline__ float p_enc3_f(float d, float d0, float inv_tau) {
   return expf(-d * d0 * inv_tau) * (num / den);
 }
 
-// q(y) = 1 - sqrt(pi) y erfcx(y) >= 0: direct below y = 12, asymptotic series
+// q(y) = 1 - sqrt(pi) y erfcx(y) >= 0 given ey = erfcx(y): direct below y = 12, asymptotic series
 // sum_{k>=1} (-1)^(k+1) (2k-1)!! / (2 y^2)^k (16 terms) above.
-__device__ __forceinline__ double q_ierfc(double y) {
-  if (y < 12.0) return 1.0 - kSqrtPi * y * erfcx(y);
+__device__ __forceinline__ double q_ierfc(double y, double ey) {
+  if (y < 12.0) return 1.0 - kSqrtPi * y * ey;
   const double x = 1.0 / (2.0 * y * y);
   double term = x, sum = x;
 #pragma unroll
@@ -265,7 +267,7 @@ __device__ __forceinline__ double p_reac3(double R, double R0, double s, double 
   const double y = s + z;
   const double ey = erfcx(y);
   const double num = kSqrtPi * s * (alpha * erfcx(alpha * s + z) - ey);
-  const double den = q_ierfc(y) + kSqrtPi * z * ey;
+  const double den = q_ierfc(y, ey) + kSqrtPi * z * ey;
   double p = num / den;
   return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
 }
@@ -274,44 +276,41 @@ __device__ __forceinline__ double p_reac3(double R, double R0, double s, double 
 // With w = R0-1, z = (V+w)/2s, z0 = w/2s, the normalised tail beyond R = 1 + V is
 //   T(V) = exp(z0^2 - z^2) [erfcx(z) + V erfcx(s+z)] / erfcx(z0),
 //   d ln T / dV = -(1+V) [q(s+z) + sqrt(pi) z erfcx(s+z)] / (s sqrt(pi) [erfcx(z) + V erfcx(s+z)]).
-// resample3 solves ln T(V) = ln U by Newton steps kept inside a bisection bracket.
 __device__ __forceinline__ void lnT3(double V, double w, double s, double inv_4tau, double ln_ex0,
                                      double& f, double& df) {
   const double z = (V + w) / (2.0 * s);
-  const double ez = erfcx(z), ey = erfcx(s + z);
+  const double ez = erfcx(z), y = s + z, ey = erfcx(y);
   const double body = ez + V * ey;
   f = -V * (2.0 * w + V) * inv_4tau + log(body) - ln_ex0;
-  df = -(1.0 + V) * (q_ierfc(s + z) + kSqrtPi * z * ey) / (s * kSqrtPi * body);
+  df = -(1.0 + V) * (q_ierfc(y, ey) + kSqrtPi * z * ey) / (s * kSqrtPi * body);
 }
 
+// Solves ln T(V) = ln U by Newton's method from V = 0, each step kept inside the bracket known so
+// far (bisection / expansion otherwise).  Once a Newton step is below 1e-10 of the length scale
+// max(V, s), quadratic convergence makes the new iterate accurate to rounding.
 __device__ __forceinline__ double resample3(double U, double R0, double s) {
   if (R0 < 1.0) R0 = 1.0;
   const double w = R0 - 1.0;
   const double inv_4tau = 1.0 / (4.0 * s * s);
   const double ln_ex0 = log(erfcx(w / (2.0 * s)));
   const double lnU = log(U);
-  double lo = 0.0, hi = s, f, df;
-  for (int k = 0; k < 80; ++k) {
-    lnT3(hi, w, s, inv_4tau, ln_ex0, f, df);
-    if (f < lnU) break;
-    lo = hi;
-    hi *= 2.0;
-  }
-  double V = 0.5 * (lo + hi);
-  for (int it = 0; it < 100; ++it) {
+  double lo = 0.0, hi = -1.0;          // hi < 0: no upper bound yet
+  double V = 0.0, f = 0.0, df;
+  for (int it = 0; it < 200; ++it) {
     lnT3(V, w, s, inv_4tau, ln_ex0, f, df);
     const double g = f - lnU;
+    if (g == 0.0) break;
     if (g > 0.0)
       lo = V;
     else
       hi = V;
     double Vn = V - g / df;
-    if (!(Vn > lo && Vn < hi)) Vn = 0.5 * (lo + hi);
-    if (fabs(Vn - V) <= 4e-16 * (1.0 + V) || hi - lo <= 4e-16 * (1.0 + hi)) {
-      V = Vn;
-      break;
-    }
+    const bool inside = Vn >= lo && (hi < 0.0 || Vn <= hi);
+    if (!inside) Vn = hi < 0.0 ? lo + fmax(lo, s) : 0.5 * (lo + hi);
+    const double step = fabs(Vn - V);
     V = Vn;
+    if (inside && step <= 1e-10 * fmax(V, s)) break;
+    if (hi >= 0.0 && hi - lo <= 4e-16 * fmax(hi, s)) break;
   }
   return 1.0 + V;
 }

@@ -63,8 +63,9 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
     uint32_t st = 0;
     if (P.ktot[sp] > 0.0) {
       const uint4 w = draw(P, step, pid, kOneParticle, TAG_UNI, r);
-      const double u = u52(w.x, w.y);
-      if (u < P.p_uni[sp]) {
+      // U = (m + 1/2) 2^-52 < p_uni  <=>  m < ceil(p_uni 2^52 - 1/2), an exact integer test
+      const unsigned long long m52 = ((((unsigned long long)w.x) << 32) | w.y) >> 12;
+      if (m52 < P.uni_thr[sp]) {
         const double target = u52(w.z, w.w) * P.ktot[sp];
         double acc = 0.0;
         int chosen = -1, last = -1;
@@ -754,19 +755,31 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __rest
                           const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                           const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
                           const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
-                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts) {
+                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts) {
+  extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
   const DevParams& P = *Pp;
   const uint32_t n = ctl->n;
   const unsigned long long tot = scan[n];
   const bool fail = ctl->status != 0 || ((tot >> 32) + (tot & 0xFFFFFFFFull)) > (unsigned long long)P.cap_particles;
   const int ns = P.n_species;
+  const bool use_smem = n_counts <= kSmemCounts;
+  if (use_smem) {
+    for (int k = threadIdx.x; k < n_counts; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+  }
+  auto count = [&](uint32_t wb) {
+    const uint32_t key = (wb >> 8) * ns + (wb & 0xFFu);
+    if (use_smem)
+      atomicAdd(&hist[key], 1u);
+    else
+      atomicAdd(&counts[key], 1ull);
+  };
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (fail) {
       const auto q0 = x0[i];
       xo[i] = q0;
       ido[i] = id[i];
-      const uint32_t wb0 = w_bits(q0.w);
-      atomicAdd(&counts[(size_t)(wb0 >> 8) * ns + (wb0 & 0xFFu)], 1ull);
+      count(w_bits(q0.w));
       continue;
     }
     const uint32_t st = status[i];
@@ -782,7 +795,7 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __rest
       const uint32_t o = S_i + P_beg;
       xo[o] = q;
       ido[o] = id[i];
-      atomicAdd(&counts[(size_t)r * ns + (wb & 0xFFu)], 1ull);
+      count(wb);
     }
     const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
     for (uint32_t k = 0; k < np; ++k) {
@@ -790,8 +803,13 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __rest
       const auto pp = prodpos[2 * (size_t)i + k];
       xo[o] = pp;
       ido[o] = rep.next_id + (P_i - P_beg) + k;
-      atomicAdd(&counts[(size_t)r * ns + (w_bits(pp.w) & 0xFFu)], 1ull);
+      count(w_bits(pp.w));
     }
+  }
+  if (use_smem) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_counts; k += blockDim.x)
+      if (hist[k]) atomicAdd(&counts[k], (unsigned long long)hist[k]);
   }
 }
 
@@ -982,8 +1000,9 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   k_scan_down<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, nullptr, &L.ctl->n, 0,
                                                                    L.block_sums64, L.scan, nullptr, items, nbp);
   mark("k_scan_compact");
-  k_compact<T><<<Gp, B, 0, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo, L.id_next,
-                                 L.counts);
+  const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
+  k_compact<T><<<Gp, B, hist_bytes, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo,
+                                          L.id_next, L.counts, L.n_counts);
   mark("k_compact");
   k_finalize<<<1, 256, 0, s>>>(L.P, L.ctl, L.reps, L.scan);
   mark("k_finalize");

@@ -49,6 +49,7 @@ def stepwise(system, steps, precision="fp64", check_fired=True):
         g0 = sim.get_state()
         o_in = oracle_state_from(g0)
         o_out, ost, tr = O.step(system, o_in, trace=True)
+        assert len(tr["ida"]) == ost["candidates"], "oracle trace truncated"
         sim.step()
         g1 = sim.get_state()
         if check_fired:
@@ -186,7 +187,7 @@ def test_graph_run_equals_single_steps():
 
 
 def test_replicas_match_oracle_per_replica():
-    base = dense_reversible(n_each=200)
+    base = dense_reversible(n_each=200, dt=2e-5)
     reps = [W.Replica(base.L, [200, 200, 0]), W.Replica(base.L * 1.3, [150, 120, 30]),
             W.Replica(base.L * 0.9, [90, 90, 10])]
     system = W.System(**{**base.__dict__, "replicas": reps})
