@@ -182,6 +182,44 @@ int rd_time_kernels(rd_handle* h, int32_t enable);
 int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* cap*32 */,
                     float* ms);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free single step (the paper has no counterpart; this is a library service).
+ *
+ * Some callers cannot allocate device memory: code running where a cudaMalloc would stall or be
+ * refused (inside a larger application's memory budget, under an allocator that forbids
+ * allocation after start-up, or in a real-time loop that must not synchronise on an allocation).
+ * rd_step_static advances a small single-replica system (cfg->n_replicas == 1, box edge
+ * cfg->replicas[0].L; n_init is ignored) by one dt, exactly as rd_step does, without calling
+ * cudaMalloc, cudaFree or any allocating routine: every scratch buffer of the step lives in one
+ * fixed device array of RD_STATIC_SCRATCH_BYTES that the library reserves on every GPU that loads
+ * it, until the process exits.
+ *
+ * Limits: n <= RD_STATIC_MAX_PARTICLES, at most RD_STATIC_MAX_PAIRS encounter pairs per step (more
+ * latch RD_ECAPACITY in *status_out and leave the state unchanged), the cell grid is coarsened to
+ * RD_STATIC_MAX_CELLS cells.  Larger inputs are rejected with RD_EINVAL before any work.
+ *
+ * Inputs (DEVICE pointers, caller-owned): x_in double[n*3] (z ignored in 2D, positions in [0,L)),
+ * species_in int32[n], id_in uint32[n] sorted ascending; next_id = first id for new products;
+ * step = step index that keys the random streams.  Outputs (DEVICE pointers, caller-owned):
+ * x_out double[out_cap*3], species_out int32[out_cap], id_out uint32[out_cap] with
+ * out_cap >= 2n; n_out int64[1], next_id_out uint32[1], status_out int32[1] (rd_status of the
+ * step; each may be NULL).  Everything is enqueued on `stream`; the host returns without waiting.
+ *
+ * Sharing: all calls use the same scratch array, which keeps the previous call's contents (the
+ * entry point clears what must start at zero).  Calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race on that array and give wrong results: serialise them.
+ * Set-up: the first call on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.
+ * ------------------------------------------------------------------------------------------- */
+#define RD_STATIC_MAX_PARTICLES 16384
+#define RD_STATIC_MAX_CELLS 65536
+#define RD_STATIC_MAX_PAIRS 65536
+#define RD_STATIC_SCRATCH_BYTES (16u << 20)
+int rd_step_static(const rd_config* cfg, void* stream, int64_t n, const double* x_in,
+                   const int32_t* species_in, const uint32_t* id_in, uint32_t next_id, int64_t step,
+                   int64_t out_cap, double* x_out, int32_t* species_out, uint32_t* id_out,
+                   int64_t* n_out, uint32_t* next_id_out, int32_t* status_out);
+
 /* Release all device memory of the handle (synchronises).  NULL is ignored. */
 void rd_free(rd_handle* h);
 

@@ -29,7 +29,7 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
 # exported symbols declared in include/rd.h
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
            "rd_pair_probs", "rd_resample", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
-           "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error"]
+           "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static"]
 
 
 class RDError(RuntimeError):
@@ -100,6 +100,7 @@ def _lib():
         L.rd_num_particles.argtypes = [vp, P(i64)]
         L.rd_time_kernels.argtypes = [vp, i32]
         L.rd_kernel_times.argtypes = [vp, i32, P(i32), C.c_char_p, P(C.c_float)]
+        L.rd_step_static.argtypes = [P(_Config), vp, i64, vp, vp, vp, u32, i64, i64, vp, vp, vp, vp, vp, vp]
         L.rd_free.argtypes = [vp]
         L.rd_free.restype = None
         L.rd_strerror.argtypes = [C.c_int]
@@ -330,3 +331,35 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+def step_static(system, x, species, ids, next_id: int, step: int, precision: Optional[str] = None,
+                stream=None):
+    """One step of a small single-replica system through the allocation-free entry point
+    ``rd_step_static``: its scratch lives in the library's fixed device array, so the library
+    allocates nothing.  Inputs are CUDA tensors (x float64 [n,3], species int32 [n], ids int32 [n]
+    holding uint32 ids); output tensors are created here by the caller side of the ABI.
+    Returns (x, species, ids, next_id, status) with the new particle count."""
+    import torch
+
+    lib = _lib()
+    cfg, rep_arr = make_config(system, precision)
+    n = int(ids.numel())
+    dev = x.device
+    cap = max(2 * n, 1)
+    x_out = torch.empty((cap, 3), dtype=torch.float64, device=dev)
+    sp_out = torch.empty(cap, dtype=torch.int32, device=dev)
+    id_out = torch.empty(cap, dtype=torch.int32, device=dev)
+    meta = torch.zeros(4, dtype=torch.int64, device=dev)      # n_out | next_id | status
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = lib.rd_step_static(C.byref(cfg), C.c_void_p(s.cuda_stream), n, x.contiguous().data_ptr(),
+                            species.contiguous().data_ptr(), ids.contiguous().data_ptr(), int(next_id),
+                            int(step), cap, x_out.data_ptr(), sp_out.data_ptr(), id_out.data_ptr(),
+                            meta.data_ptr(), meta.data_ptr() + 8, meta.data_ptr() + 16)
+    _check(rc, "rd_step_static")
+    s.synchronize()
+    m = meta.cpu()
+    n_new = int(m[0])
+    next_new = int(m[1]) & 0xFFFFFFFF
+    status = int(m[2]) & 0xFFFFFFFF
+    return x_out[:n_new], sp_out[:n_new], id_out[:n_new], next_new, status

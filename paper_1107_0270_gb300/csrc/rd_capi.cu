@@ -684,3 +684,235 @@ void rd_free(rd_handle* h) {
 }
 
 }  // extern "C"
+
+// ================================================================================================
+// Allocation-free single step (rd_step_static).  Every scratch buffer of the step lives in one
+// file-scope device array; the caller passes the state in and receives it out in device buffers.
+// ================================================================================================
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the static scratch for the current device, looked up once per device.
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+struct Bump {
+  unsigned char* base;
+  size_t used = 0;
+  bool ok = true;
+  void* take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > kStaticScratchBytes) {
+      ok = false;
+      return nullptr;
+    }
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+template <class V>
+__global__ void k_static_pack(int64_t n, int dim, double L, const double* __restrict__ x,
+                              const int32_t* __restrict__ sp, const uint32_t* __restrict__ id,
+                              V* __restrict__ xo, uint32_t* __restrict__ ido) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double p0 = x[3 * i], p1 = x[3 * i + 1], p2 = dim == 3 ? x[3 * i + 2] : 0.0;
+    const uint32_t wb = pack_sp((uint32_t)sp[i], 0u);
+    if constexpr (sizeof(V) == 32) {
+      d4 v;
+      v.x = p0; v.y = p1; v.z = p2; v.w = w_from_bits_d(wb);
+      xo[i] = v;
+    } else {
+      float f[3] = {(float)p0, (float)p1, (float)p2};
+      for (int d = 0; d < 3; ++d)
+        if (!(f[d] < (float)L)) f[d] = 0.0f;
+      xo[i] = make_float4(f[0], f[1], f[2], w_from_bits_f(wb));
+    }
+    ido[i] = id[i];
+  }
+}
+
+template <class V>
+__global__ void k_static_unpack(const DevCtl* __restrict__ ctl, const RepDev* __restrict__ rep,
+                                const V* __restrict__ xs, const uint32_t* __restrict__ ids, double* __restrict__ x,
+                                int32_t* __restrict__ sp, uint32_t* __restrict__ id, int64_t* __restrict__ n_out,
+                                uint32_t* __restrict__ next_id_out, int32_t* __restrict__ status_out) {
+  const uint32_t n = ctl->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const V v = xs[i];
+    x[3 * i] = (double)v.x;
+    x[3 * i + 1] = (double)v.y;
+    x[3 * i + 2] = (double)v.z;
+    sp[i] = (int32_t)(w_bits(v.w) & 0xFFu);
+    id[i] = ids[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (n_out) *n_out = (int64_t)n;
+    if (next_id_out) *next_id_out = rep->next_id;
+    if (status_out) *status_out = ctl->status;
+  }
+}
+
+}  // namespace
+
+extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, const double* x_in,
+                              const int32_t* species_in, const uint32_t* id_in, uint32_t next_id, int64_t step,
+                              int64_t out_cap, double* x_out, int32_t* species_out, uint32_t* id_out,
+                              int64_t* n_out, uint32_t* next_id_out, int32_t* status_out) {
+  if (!cfg || cfg->n_replicas != 1 || !cfg->replicas) return RD_EINVAL;
+  if (n < 0 || n > RD_STATIC_MAX_PARTICLES || step < 0 || step > 0xFFFFFFFFll) return RD_EINVAL;
+  if (n > 0 && (!x_in || !species_in || !id_in)) return RD_EINVAL;
+  if (out_cap < 2 * n || !x_out || !species_out || !id_out) return RD_EINVAL;
+  rd_config c = *cfg;
+  if (c.c_cut == 0.0) c.c_cut = 5.0;
+  if (c.tau_s == 0.0) c.tau_s = 0.01;
+  const int v = validate(&c);
+  if (v != RD_OK) return v;
+
+  void* base = nullptr;
+  cudaError_t e = static_scratch_address(&base);
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // derived parameters and the single replica's cell grid (coarsened until it fits the maximum)
+  rd_handle tmp;
+  tmp.cfg = c;
+  tmp.cfg.replicas = nullptr;
+  derive_params(&tmp);
+  const rd_replica& rp = cfg->replicas[0];
+  const double rc = max_cutoff(c);
+  RepDev rep;
+  std::memset(&rep, 0, sizeof rep);
+  rep.L = rp.L;
+  rep.half_L = 0.5 * rp.L;
+  rep.Lf = (float)rp.L;
+  rep.half_Lf = 0.5f * rep.Lf;
+  double factor = (c.cell_factor_x100 > 0 ? c.cell_factor_x100 : 100) / 100.0;
+  int64_t cells = 1;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      int m = 1;
+      if (a < c.dim && rc > 0.0) {
+        const double q = std::floor(rp.L / (rc * factor * (1.0 + 1e-6)));
+        m = q >= 3.0 ? (int)std::min(q, 2048.0) : 1;
+      }
+      rep.nc[a] = m;
+      rep.inv_edge[a] = m / rp.L;
+      rep.inv_edge_f[a] = (float)rep.inv_edge[a];
+      cells *= m;
+    }
+    if (cells <= RD_STATIC_MAX_CELLS) break;
+    factor *= 1.25;
+  }
+  if (cells > RD_STATIC_MAX_CELLS) return RD_EINVAL;
+  rep.cell_base = 0;
+  rep.beg = 0;
+  rep.end = (uint32_t)n;
+  rep.next_id = next_id;
+
+  const int64_t cap = 2 * (int64_t)RD_STATIC_MAX_PARTICLES + 1024;
+  const int64_t pair_cap = RD_STATIC_MAX_PAIRS;
+  tmp.hp.cap_particles = cap;
+  tmp.hp.cap_pairs = pair_cap;
+  const size_t vs = c.precision == RD_MIXED ? 16 : 32;
+
+  StepLaunch L;
+  std::memset(&L, 0, sizeof L);
+  L.precision = c.precision;
+  L.block = 256;
+  L.max_grid = 152 * 16;
+  L.scan_items = 8;
+  L.cap_particles = cap;
+  L.cap_pairs = pair_cap;
+  L.total_cells = cells;
+  L.n_counts = c.n_species;
+  const int64_t chunk = 256 * (int64_t)L.scan_items;
+  const int64_t nbc = (cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
+  Bump b{(unsigned char*)base};
+  void* xb0 = b.take(cap * vs);
+  void* xb1 = b.take(cap * vs);
+  uint32_t* id0 = (uint32_t*)b.take(cap * 4);
+  uint32_t* id1 = (uint32_t*)b.take(cap * 4);
+  L.x1 = b.take(cap * vs);
+  L.sx0 = b.take(cap * vs);
+  L.sx1 = b.take(cap * vs);
+  L.prodpos = b.take(2 * cap * vs);
+  L.status = (uint32_t*)b.take(cap * 4);
+  L.matched = (int32_t*)b.take(cap * 4);
+  L.deg = (uint32_t*)b.take(cap * 4);
+  L.cell_of = (uint32_t*)b.take(cap * 4);
+  L.slot = (uint32_t*)b.take(cap * 4);
+  L.sidx = (uint32_t*)b.take(cap * 4);
+  L.decay_list = (uint32_t*)b.take(cap * 4);
+  L.best_key = (unsigned long long*)b.take(cap * 8);
+  L.best_pid = (unsigned long long*)b.take(cap * 8);
+  L.scan = (unsigned long long*)b.take((cap + 1) * 8);
+  L.cell_count = (uint32_t*)b.take(cells * 4);
+  L.cell_start = (uint32_t*)b.take((cells + 1) * 4);
+  L.block_sums32 = (uint32_t*)b.take((nbc + 1) * 4);
+  L.block_sums64 = (unsigned long long*)b.take((nbp + 1) * 8);
+  L.fired = (FiredPair*)b.take(pair_cap * sizeof(FiredPair));
+  L.fstate = (uint32_t*)b.take(pair_cap * 4);
+  L.conflict = (uint32_t*)b.take(pair_cap * 4);
+  L.counts = (unsigned long long*)b.take((size_t)L.n_counts * 8);
+  L.P = (const DevParams*)b.take(sizeof(DevParams));
+  L.ctl = (DevCtl*)b.take(sizeof(DevCtl));
+  L.reps = (RepDev*)b.take(sizeof(RepDev));
+  if (!b.ok) return RD_EINVAL;
+  L.x_cur = xb0;
+  L.x_next = xb1;
+  L.id_cur = id0;
+  L.id_next = id1;
+
+  DevCtl ctl;
+  std::memset(&ctl, 0, sizeof ctl);
+  ctl.n = (uint32_t)n;
+  ctl.step = (uint32_t)step;
+  ctl.t = (double)step * c.dt;
+  // the array keeps the previous call's contents: reset what the step expects to start at zero
+  RD_CUDA(cudaMemsetAsync(L.cell_count, 0, (size_t)cells * 4, s));
+  RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
+  RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+  RD_CUDA(cudaMemcpyAsync(L.reps, &rep, sizeof rep, cudaMemcpyHostToDevice, s));
+  RD_CUDA(cudaMemcpyAsync(L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, s));
+  const int G = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8);
+  if (n > 0) {
+    if (vs == 32)
+      k_static_pack<d4><<<G, 256, 0, s>>>(n, c.dim, rp.L, x_in, species_in, id_in, (d4*)xb0, id0);
+    else
+      k_static_pack<float4><<<G, 256, 0, s>>>(n, c.dim, rp.L, x_in, species_in, id_in, (float4*)xb0, id0);
+  }
+  launch_step(L, s, nullptr);
+  const int Go = (int)std::min<int64_t>(std::max<int64_t>((2 * n + 255) / 256, 1), 152 * 8);
+  if (vs == 32)
+    k_static_unpack<d4><<<Go, 256, 0, s>>>(L.ctl, L.reps, (const d4*)xb1, id1, x_out, species_out, id_out, n_out,
+                                           next_id_out, status_out);
+  else
+    k_static_unpack<float4><<<Go, 256, 0, s>>>(L.ctl, L.reps, (const float4*)xb1, id1, x_out, species_out, id_out,
+                                               n_out, next_id_out, status_out);
+  RD_CUDA(cudaGetLastError());
+  return RD_OK;
+}
