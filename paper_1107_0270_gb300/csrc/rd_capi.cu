@@ -144,6 +144,7 @@ static void derive_params(rd_handle* h) {
   P.seed_hi = (uint32_t)(c.seed >> 32);
   for (int s = 0; s < c.n_species; ++s) {
     P.D[s] = c.D[s];
+    P.D_f[s] = (float)c.D[s];
     P.ell[s] = std::sqrt(2.0 * c.D[s] * c.dt);
     P.ell_f[s] = (float)P.ell[s];
   }
@@ -170,6 +171,8 @@ static void derive_params(rd_handle* h) {
     q.inv_sigma_f = (float)(1.0 / p.sigma);
     q.inv_tau_f = (float)q.inv_tau;
     q.rcut2_f = (float)q.rcut2;
+    q.s_f = (float)q.s;
+    q.alpha_f = (float)q.alpha;
     P.pair_of[p.s1][p.s2] = (int8_t)k;
     P.pair_of[p.s2][p.s1] = (int8_t)k;
     P.binned_mask |= (1u << p.s1) | (1u << p.s2);
@@ -296,10 +299,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.n_counts = c.n_replicas * c.n_species;
   const int64_t chunk = 256 * (int64_t)L.scan_items;
   const int64_t nbc = (total_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
-  if (nbc > 1024 * 64 || nbp > 1024 * 64) {
-    delete h;
-    return RD_EINVAL;
-  }
+  L.flag_stride = std::max(nbc, nbp) + 1;
 
   bool ok = true;
   auto A = [&](size_t bytes) {
@@ -328,8 +328,12 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.scan = (unsigned long long*)A((cap + 1) * 8);
   L.cell_count = (uint32_t*)A(total_cells * 4);
   L.cell_start = (uint32_t*)A((total_cells + 1) * 4);
-  L.block_sums32 = (uint32_t*)A((nbc + 1) * 4);
-  L.block_sums64 = (unsigned long long*)A((nbp + 1) * 8);
+  L.agg32 = (uint32_t*)A((nbc + 1) * 4);
+  L.incl32 = (uint32_t*)A((nbc + 1) * 4);
+  L.agg64 = (unsigned long long*)A((nbp + 1) * 8);
+  L.incl64 = (unsigned long long*)A((nbp + 1) * 8);
+  L.flags = (uint32_t*)A(2 * L.flag_stride * 4);
+  L.accepted = (uint32_t*)A(pair_cap * 4);
   L.fired = (FiredPair*)A(pair_cap * sizeof(FiredPair));
   L.fstate = (uint32_t*)A(pair_cap * 4);
   L.conflict = (uint32_t*)A(pair_cap * 4);
@@ -353,6 +357,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   };
   cudaError_t e = cudaSuccess;
   e = cudaMemsetAsync(L.cell_count, 0, total_cells * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.flags, 0, 2 * L.flag_stride * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.status, 0, cap * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync((void*)L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
@@ -632,7 +637,7 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
   RD_CUDA(cudaStreamSynchronize(h->stream));
   DevCtl ctl;
   RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
-  const int64_t n = std::min<int64_t>(ctl.fired, h->L.cap_pairs);
+  const int64_t n = std::min<int64_t>(ctl.last_fired, h->L.cap_pairs);
   *n_out = n;
   const int64_t m = std::min(n, cap);
   if (m > 0) {
@@ -872,8 +877,13 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.scan = (unsigned long long*)b.take((cap + 1) * 8);
   L.cell_count = (uint32_t*)b.take(cells * 4);
   L.cell_start = (uint32_t*)b.take((cells + 1) * 4);
-  L.block_sums32 = (uint32_t*)b.take((nbc + 1) * 4);
-  L.block_sums64 = (unsigned long long*)b.take((nbp + 1) * 8);
+  L.flag_stride = std::max(nbc, nbp) + 1;
+  L.agg32 = (uint32_t*)b.take((nbc + 1) * 4);
+  L.incl32 = (uint32_t*)b.take((nbc + 1) * 4);
+  L.agg64 = (unsigned long long*)b.take((nbp + 1) * 8);
+  L.incl64 = (unsigned long long*)b.take((nbp + 1) * 8);
+  L.flags = (uint32_t*)b.take(2 * L.flag_stride * 4);
+  L.accepted = (uint32_t*)b.take(pair_cap * 4);
   L.fired = (FiredPair*)b.take(pair_cap * sizeof(FiredPair));
   L.fstate = (uint32_t*)b.take(pair_cap * 4);
   L.conflict = (uint32_t*)b.take(pair_cap * 4);
@@ -894,6 +904,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   ctl.t = (double)step * c.dt;
   // the array keeps the previous call's contents: reset what the step expects to start at zero
   RD_CUDA(cudaMemsetAsync(L.cell_count, 0, (size_t)cells * 4, s));
+  RD_CUDA(cudaMemsetAsync(L.flags, 0, (size_t)(2 * L.flag_stride) * 4, s));
   RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
   RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemcpyAsync(L.reps, &rep, sizeof rep, cudaMemcpyHostToDevice, s));

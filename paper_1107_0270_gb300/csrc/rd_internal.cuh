@@ -41,6 +41,7 @@ struct PairDev {
   int32_t bc, product, s1, s2;
   double sigma, tau, inv_tau, s, h, alpha, rcut2, Drel;
   float sigma_f, inv_sigma_f, inv_tau_f, rcut2_f;
+  float s_f, alpha_f, pad_f[2];
 };
 
 struct DecayDev {
@@ -57,6 +58,7 @@ struct DevParams {
   uint32_t pad1;
   int64_t cap_particles, cap_pairs;
   double D[kMaxSpecies];
+  float D_f[kMaxSpecies];
   double ell[kMaxSpecies];     // sqrt(2 D dt)
   float ell_f[kMaxSpecies];
   double ktot[kMaxSpecies];    // total unimolecular rate per species
@@ -84,8 +86,11 @@ struct DevCtl {
   uint32_t fired;          // fired pairs this step
   uint32_t n_conflict;     // pairs left to the iterative matching
   uint32_t n_decay;        // decays this step
-  uint32_t n_binned;
-  uint32_t pad;
+  uint32_t n_accept;       // accepted pairs this step
+  uint32_t epoch;          // incremented every step; tags the scan flags
+  uint32_t tile_ctr[2];    // tile tickets of the two scans
+  uint32_t done_blocks;    // blocks of the compaction that finished
+  uint32_t last_fired;     // fired pairs of the last completed step
   double t;
   unsigned long long stats[RD_NSTATS];
 };
@@ -272,6 +277,33 @@ __device__ __forceinline__ double p_reac3(double R, double R0, double s, double 
   return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
 }
 
+// FP32 forms of q and p_reac, used only to pre-screen the FP64 step's reaction decisions: below
+// y = 1.5 q = 1 - sqrt(pi) y erfcx(y) directly, above it through the Laplace continued fraction of
+// erfc (24 terms, q = K/(y+K) with K = (1/2)/(y + 1/(y + (3/2)/(y + ...)))).
+__device__ __forceinline__ float q_ierfc_f(float y, float ey) {
+  if (y < 1.5f) return 1.0f - 1.7724538509f * y * ey;
+  float K = 0.0f;
+#pragma unroll
+  for (int k = 24; k >= 1; --k) K = (0.5f * k) / (y + K);
+  return K / (y + K);
+}
+
+__device__ __forceinline__ float p_reac3_f(float R, float R0, float s, float alpha) {
+  if (R < 1.0f) R = 1.0f;
+  if (R0 < 1.0f) R0 = 1.0f;
+  const float z = ((R - 1.0f) + (R0 - 1.0f)) / (2.0f * s);
+  const float y = s + z;
+  const float ey = erfcxf(y);
+  const float num = 1.7724538509f * s * (alpha * erfcxf(alpha * s + z) - ey);
+  const float den = q_ierfc_f(y, ey) + 1.7724538509f * z * ey;
+  const float p = num / den;
+  return p < 0.0f ? 0.0f : (p > 1.0f ? 1.0f : p);
+}
+
+// Decision U < p evaluated in FP32 first; only draws within kFilter of the FP32 value (whose error
+// stays below a few 1e-6) need the FP64 value, so every decision equals the FP64 one.
+constexpr double kFilter = 1e-4;
+
 // Propagator G_ref - G_abs of an encountered pair (radial density 4 pi R^2 (g_ref - g_abs)).
 // With w = R0-1, z = (V+w)/2s, z0 = w/2s, the normalised tail beyond R = 1 + V is
 //   T(V) = exp(z0^2 - z^2) [erfcx(z) + V erfcx(s+z)] / erfcx(z0),
@@ -285,17 +317,52 @@ __device__ __forceinline__ void lnT3(double V, double w, double s, double inv_4t
   df = -(1.0 + V) * (q_ierfc(y, ey) + kSqrtPi * z * ey) / (s * kSqrtPi * body);
 }
 
-// Solves ln T(V) = ln U by Newton's method from V = 0, each step kept inside the bracket known so
-// far (bisection / expansion otherwise).  Once a Newton step is below 1e-10 of the length scale
-// max(V, s), quadratic convergence makes the new iterate accurate to rounding.
+// FP32 evaluation of ln T and its derivative (seed of the FP64 solve).
+__device__ __forceinline__ void lnT3_f(float V, float w, float s, float inv_4tau, float ln_ex0, float& f, float& df) {
+  const float z = (V + w) / (2.0f * s);
+  const float ez = erfcxf(z), y = s + z, ey = erfcxf(y);
+  const float body = ez + V * ey;
+  const float q = y < 12.0f ? 1.0f - 1.7724538509f * y * ey : 0.5f / (y * y) * (1.0f - 1.5f / (y * y));
+  f = -V * (2.0f * w + V) * inv_4tau + logf(body) - ln_ex0;
+  df = -(1.0f + V) * (q + 1.7724538509f * z * ey) / (s * 1.7724538509f * body);
+}
+
+// Solves ln T(V) = ln U.  A few FP32 Newton steps give a seed good to ~1e-5; FP64 Newton steps,
+// each kept inside the bracket known so far (bisection / expansion otherwise), finish the solve.
+// Once an FP64 Newton step is below 1e-10 of the length scale max(V, s), quadratic convergence
+// makes the new iterate accurate to rounding.
 __device__ __forceinline__ double resample3(double U, double R0, double s) {
   if (R0 < 1.0) R0 = 1.0;
   const double w = R0 - 1.0;
   const double inv_4tau = 1.0 / (4.0 * s * s);
-  const double ln_ex0 = log(erfcx(w / (2.0 * s)));
   const double lnU = log(U);
+  // FP32 seed
+  float Vf = 0.0f;
+  {
+    const float wf = (float)w, sf = (float)s, i4f = (float)inv_4tau, lnUf = (float)lnU;
+    const float lnx0f = logf(erfcxf(wf / (2.0f * sf)));
+    float lo = 0.0f, hi = -1.0f;
+    for (int it = 0; it < 24; ++it) {
+      float f, df;
+      lnT3_f(Vf, wf, sf, i4f, lnx0f, f, df);
+      const float g = f - lnUf;
+      if (g == 0.0f) break;
+      if (g > 0.0f)
+        lo = Vf;
+      else
+        hi = Vf;
+      float Vn = Vf - g / df;
+      const bool inside = Vn >= lo && (hi < 0.0f || Vn <= hi);
+      if (!inside) Vn = hi < 0.0f ? lo + fmaxf(lo, sf) : 0.5f * (lo + hi);
+      const float step = fabsf(Vn - Vf);
+      Vf = Vn;
+      if (inside && step <= 1e-5f * fmaxf(Vf, sf)) break;
+    }
+    if (!(Vf >= 0.0f) || !isfinite(Vf)) Vf = 0.0f;
+  }
+  const double ln_ex0 = log(erfcx(w / (2.0 * s)));
   double lo = 0.0, hi = -1.0;          // hi < 0: no upper bound yet
-  double V = 0.0, f = 0.0, df;
+  double V = (double)Vf, f = 0.0, df;
   for (int it = 0; it < 200; ++it) {
     lnT3(V, w, s, inv_4tau, ln_ex0, f, df);
     const double g = f - lnU;
@@ -313,6 +380,36 @@ __device__ __forceinline__ double resample3(double U, double R0, double s) {
     if (hi >= 0.0 && hi - lo <= 4e-16 * fmax(hi, s)) break;
   }
   return 1.0 + V;
+}
+
+// FP32 propagator sample for the mixed step: the Newton iteration of resample3 in float until the
+// step is below 2e-6 of the length scale.
+__device__ __forceinline__ float resample3_f(float U, float R0, float s) {
+  if (R0 < 1.0f) R0 = 1.0f;
+  const float w = R0 - 1.0f;
+  const float inv_4tau = 1.0f / (4.0f * s * s);
+  const float lnU = logf(U);
+  const float ln_ex0 = logf(erfcxf(w / (2.0f * s)));
+  float lo = 0.0f, hi = -1.0f, V = 0.0f;
+  for (int it = 0; it < 40; ++it) {
+    float f, df;
+    lnT3_f(V, w, s, inv_4tau, ln_ex0, f, df);
+    const float g = f - lnU;
+    if (g == 0.0f) break;
+    if (g > 0.0f)
+      lo = V;
+    else
+      hi = V;
+    float Vn = V - g / df;
+    const bool inside = Vn >= lo && (hi < 0.0f || Vn <= hi);
+    if (!inside) Vn = hi < 0.0f ? lo + fmaxf(lo, s) : 0.5f * (lo + hi);
+    const float step = fabsf(Vn - V);
+    V = Vn;
+    if (inside && step <= 2e-6f * fmaxf(V, s)) break;
+    if (hi >= 0.0f && hi - lo <= 2e-7f * fmaxf(hi, s)) break;
+  }
+  if (!(V >= 0.0f) || !isfinite(V)) V = 0.0f;
+  return 1.0f + V;
 }
 
 }  // namespace rd

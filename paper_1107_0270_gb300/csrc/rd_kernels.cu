@@ -49,8 +49,19 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
                           const uint32_t* __restrict__ id, typename V4<T>::type* __restrict__ x1,
                           uint32_t* __restrict__ status, int32_t* __restrict__ matched,
                           uint32_t* __restrict__ deg, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
-                          uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list) {
+                          uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list,
+                          unsigned long long* __restrict__ counts, int n_counts) {
   const DevParams& P = *Pp;
+  if (blockIdx.x == 0) {
+    // counters of the step's later kernels (the counters used by this kernel were reset at the
+    // end of the previous step)
+    for (int k = threadIdx.x; k < n_counts; k += blockDim.x) counts[k] = 0ull;
+    if (threadIdx.x == 0) {
+      ctl->epoch += 1u;
+      ctl->tile_ctr[0] = 0u;
+      ctl->tile_ctr[1] = 0u;
+    }
+  }
   if (ctl->status) return;
   const uint32_t n = ctl->n, step = ctl->step;
   const int dim = P.dim;
@@ -131,7 +142,7 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
 }
 
 // ================================================================================================
-// Three-phase exclusive scan (block sums -> scan of the sums in one block -> block scans).
+// Block-level exclusive scan and the per-element loaders of the two scans of a step.
 // ================================================================================================
 template <class U, class Load>
 __device__ __forceinline__ U block_exclusive_scan(U v, U* smem, U& total) {
@@ -176,64 +187,94 @@ struct LoadCompact {
   }
 };
 
-template <class U, class Load>
-__global__ void k_scan_reduce(Load load, const int64_t* __restrict__ n_ptr64, const uint32_t* n_ptr32,
-                              int64_t n_const, U* __restrict__ block_sums, int items) {
-  __shared__ U sm[32];
-  const int64_t n = n_ptr32 ? (int64_t)*n_ptr32 : (n_ptr64 ? *n_ptr64 : n_const);
-  const int64_t chunk = (int64_t)blockDim.x * items;
-  const int64_t beg = (int64_t)blockIdx.x * chunk;
-  U acc = 0;
-  for (int k = 0; k < items; ++k) {
-    const int64_t i = beg + (int64_t)k * blockDim.x + threadIdx.x;
-    if (i < n) acc += load(i);
-  }
-  U total;
-  block_exclusive_scan<U, Load>(acc, sm, total);
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
-}
+// Single-pass exclusive scan with decoupled look-back (Merrill & Garland, 2016).  Tiles of
+// blockDim x kScanItems elements take tickets in launch order; each publishes its aggregate, then
+// walks back over its predecessors' published values (bounded wait: a stalled predecessor sets
+// RD_ETIMEOUT).  Flags carry an epoch that changes every scan, so nothing needs clearing.
+// out[i] = exclusive prefix for i < n, out[n] = total; zero_after (optional) is cleared behind.
+constexpr int kScanItems = 8;
+constexpr uint32_t kSpinLimit = 1u << 24;
 
-template <class U>
-__global__ void k_scan_top(U* __restrict__ block_sums, int nblocks) {
+template <class U, class Load>
+__global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const uint32_t* __restrict__ n_ptr,
+                                               U* __restrict__ out, uint32_t* __restrict__ zero_after,
+                                               U* __restrict__ agg, U* __restrict__ incl,
+                                               uint32_t* __restrict__ flag, DevCtl* __restrict__ ctl, int which) {
   __shared__ U sm[32];
-  __shared__ U carry;
-  if (threadIdx.x == 0) carry = 0;
+  __shared__ uint32_t s_tile;
+  __shared__ U s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[which], 1u);
   __syncthreads();
-  for (int base = 0; base < nblocks; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const U v = i < nblocks ? block_sums[i] : U(0);
-    U total;
-    const U ex = block_exclusive_scan<U, int>(v, sm, total);
-    if (i < nblocks) block_sums[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) block_sums[nblocks] = carry;
-}
-
-// Writes out[i] = exclusive prefix, out[n] = total; optionally zeroes the input counts.
-template <class U, class Load>
-__global__ void k_scan_down(Load load, const int64_t* __restrict__ n_ptr64, const uint32_t* n_ptr32,
-                            int64_t n_const, const U* __restrict__ block_sums, U* __restrict__ out,
-                            uint32_t* zero_after, int items, int nblocks) {
-  __shared__ U sm[32];
-  const int64_t n = n_ptr32 ? (int64_t)*n_ptr32 : (n_ptr64 ? *n_ptr64 : n_const);
-  const int64_t chunk = (int64_t)blockDim.x * items;
-  const int64_t beg = (int64_t)blockIdx.x * chunk;
-  U carry = block_sums[blockIdx.x];
-  for (int k = 0; k < items; ++k) {
-    const int64_t i = beg + (int64_t)k * blockDim.x + threadIdx.x;
+  const uint32_t tile = s_tile;
+  const int64_t n = n_ptr ? (int64_t)*n_ptr : n_const;
+  const int64_t tile_elems = (int64_t)blockDim.x * kScanItems;
+  const int64_t ntiles = n > 0 ? (n + tile_elems - 1) / tile_elems : 1;
+  if ((int64_t)tile >= ntiles) return;
+  const uint32_t epoch = (ctl->epoch * 2u + (uint32_t)which) & 0x3FFFFFFFu;
+  const int64_t base = (int64_t)tile * tile_elems;
+  U ex[kScanItems];
+  U tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
     const U v = i < n ? load(i) : U(0);
-    U total;
-    const U ex = block_exclusive_scan<U, Load>(v, sm, total);
+    U t;
+    ex[k] = tot + block_exclusive_scan<U, Load>(v, sm, t);
+    tot += t;
+  }
+  if (threadIdx.x < 32) {
+    // warp 0: publish the aggregate, then look back over windows of 32 predecessors at once
+    const int lane = threadIdx.x;
+    U prefix = 0;
+    if (tile > 0) {
+      if (lane == 0) {
+        agg[tile] = tot;
+        __threadfence();
+        atomicExch(&flag[tile], (epoch << 2) | 1u);
+      }
+      int64_t top = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      for (;;) {
+        const int64_t q = top - lane;
+        const uint32_t f = q >= 0 ? *(volatile uint32_t*)&flag[q] : ((epoch << 2) | 2u);
+        const bool ready = (f >> 2) == epoch && (f & 3u) != 0u;
+        if (!__all_sync(0xFFFFFFFFu, ready)) {
+          if (++spins > kSpinLimit) {
+            if (lane == 0) set_status(ctl, RD_ETIMEOUT);
+            break;
+          }
+          continue;
+        }
+        __threadfence();
+        const unsigned incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (f & 3u) == 2u);
+        const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;   // nearest inclusive predecessor
+        U v = 0;
+        if (q >= 0 && lane <= stop) v = lane == stop ? *(volatile U*)&incl[q] : *(volatile U*)&agg[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        prefix += v;
+        if (incl_mask || top < 32) break;
+        top -= 32;
+      }
+    }
+    if (lane == 0) {
+      incl[tile] = prefix + tot;
+      __threadfence();
+      atomicExch(&flag[tile], (epoch << 2) | 2u);
+      s_prefix = prefix;
+    }
+  }
+  __syncthreads();
+  const U prefix = s_prefix;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
     if (i < n) {
-      out[i] = carry + ex;
+      out[i] = prefix + ex[k];
       if (zero_after) zero_after[i] = 0u;
     }
-    carry += total;
   }
-  if (blockIdx.x == (unsigned)(nblocks - 1) && threadIdx.x == 0) out[n] = block_sums[nblocks];
+  if (threadIdx.x == 0 && (int64_t)tile == ntiles - 1) out[n > 0 ? n : 0] = prefix + tot;
 }
 
 // ================================================================================================
@@ -278,7 +319,8 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                                                const uint32_t* __restrict__ sidx,
                                                const uint32_t* __restrict__ cell_start,
                                                const int64_t total_cells, FiredPair* __restrict__ fired,
-                                               uint32_t* __restrict__ fstate, const uint32_t cap_pairs) {
+                                               uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
+                                               const uint32_t cap_pairs) {
   const DevParams& P = *Pp;
   if (ctl->status) return;
   const uint32_t nb = cell_start[total_cells];
@@ -308,15 +350,22 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
       }
       const int ox = rep.nc[0] >= 3 ? 1 : 0, oy = rep.nc[1] >= 3 ? 1 : 0;
       const int oz = (dim == 3 && rep.nc[2] >= 3) ? 1 : 0;
+      // forward half of the neighbour stencil: every unordered pair of neighbouring cells once,
+      // pairs inside the own cell with j > k
       for (int dz = -oz; dz <= oz; ++dz) {
-        const int zz = (cz + dz + rep.nc[2]) % rep.nc[2];
+        int zz = cz + dz;
+        zz = zz < 0 ? zz + rep.nc[2] : (zz >= rep.nc[2] ? zz - rep.nc[2] : zz);
         for (int dy = -oy; dy <= oy; ++dy) {
-          const int yy = (cy + dy + rep.nc[1]) % rep.nc[1];
+          int yy = cy + dy;
+          yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
           for (int dx = -ox; dx <= ox; ++dx) {
-            const int xx = (cx + dx + rep.nc[0]) % rep.nc[0];
+            const int code = dz * 9 + dy * 3 + dx;
+            if (code < 0) continue;
+            int xx = cx + dx;
+            xx = xx < 0 ? xx + rep.nc[0] : (xx >= rep.nc[0] ? xx - rep.nc[0] : xx);
             const int64_t c = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * rep.nc[0] + xx;
-            const uint32_t jb = cell_start[c], je = cell_start[c + 1];
-            for (uint32_t j = (jb > k ? jb : k + 1); j < je; ++j) {
+            const uint32_t jb = code == 0 ? k + 1 : cell_start[c], je = cell_start[c + 1];
+            for (uint32_t j = jb; j < je; ++j) {
               const auto b0 = sx0[j];
               const uint32_t spb = w_bits(b0.w) & 0xFFu;
               const int rule = P.pair_of[spa][spb];
@@ -381,6 +430,8 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                   f.key = -log(u52(w.z, w.w)) / p;
                   fired[pos] = f;
                   fstate[pos] = FS_LIVE | ((uint32_t)rule << 2) | (r << 8);
+                  atomicAdd(&deg[f.ia], 1u);
+                  atomicAdd(&deg[f.ib], 1u);
                 } else {
                   set_status(ctl, RD_ECAPACITY);
                 }
@@ -402,19 +453,20 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
 // (key, id_a, id_b) is the smallest at both particles among the live pairs), which reproduces the
 // greedy acceptance in ascending (key, id_a, id_b).
 // ================================================================================================
-__global__ void k_match_degree(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
-                               uint32_t* __restrict__ deg, uint32_t cap_pairs) {
-  if (ctl->status) return;
-  const uint32_t nf = min(ctl->fired, cap_pairs);
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
-    atomicAdd(&deg[fired[e].ia], 1u);
-    atomicAdd(&deg[fired[e].ib], 1u);
-  }
+__device__ __forceinline__ void append_accepted(DevCtl* ctl, uint32_t* accepted, uint32_t e) {
+  const unsigned m = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&ctl->n_accept, (uint32_t)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  accepted[base + __popc(m & ((1u << lane) - 1u))] = e;
 }
 
 __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
-                                uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
+                                uint32_t* __restrict__ fstate, const uint32_t* __restrict__ deg,
                                 int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
+                                uint32_t* __restrict__ accepted,
                                 unsigned long long* __restrict__ best_key,
                                 unsigned long long* __restrict__ best_pid, uint32_t cap_pairs) {
   if (ctl->status) return;
@@ -430,6 +482,7 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
         matched[f.ia] = (int32_t)f.ib;
         matched[f.ib] = (int32_t)f.ia;
         fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+        append_accepted(ctl, accepted, e);
         ++acc;
       } else {
         const unsigned m = __activemask();
@@ -454,6 +507,7 @@ __global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restri
                                                        uint32_t* __restrict__ fstate,
                                                        int32_t* __restrict__ matched,
                                                        const uint32_t* __restrict__ conflict,
+                                                       uint32_t* __restrict__ accepted,
                                                        unsigned long long* __restrict__ best_key,
                                                        unsigned long long* __restrict__ best_pid) {
   __shared__ uint32_t live;
@@ -493,6 +547,7 @@ __global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restri
         matched[f.ia] = (int32_t)f.ib;
         matched[f.ib] = (int32_t)f.ia;
         fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+        accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
         atomicAdd(&acc_s, 1ull);
       }
     }
@@ -546,24 +601,14 @@ __device__ __forceinline__ typename V4<T>::type store4(const double p[3], uint32
 }
 
 template <class T>
-__global__ void k_resolve(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                          const RepDev* __restrict__ reps, const FiredPair* __restrict__ fired,
-                          const uint32_t* __restrict__ fstate, const typename V4<T>::type* __restrict__ x0,
-                          typename V4<T>::type* __restrict__ x1, uint32_t* __restrict__ status,
-                          typename V4<T>::type* __restrict__ prodpos, uint32_t cap_pairs) {
-  const DevParams& P = *Pp;
-  if (ctl->status) return;
-  const uint32_t nf = min(ctl->fired, cap_pairs);
-  const uint32_t step = ctl->step;
+__device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* __restrict__ reps,
+                                             const FiredPair* __restrict__ fired, const uint32_t* __restrict__ fstate,
+                                             uint32_t e, uint32_t step, const typename V4<T>::type* __restrict__ x0,
+                                             typename V4<T>::type* __restrict__ x1, uint32_t* __restrict__ status,
+                                             typename V4<T>::type* __restrict__ prodpos, unsigned long long& n_react,
+                                             unsigned long long& n_res, unsigned long long& n_near) {
   const int dim = P.dim;
-  unsigned long long n_react = 0, n_res = 0, n_near = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t n_iter = (nf + stride - 1) / stride;
-  for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t e = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nf) continue;
     const uint32_t fs = fstate[e];
-    if ((fs & 3u) != FS_ACCEPTED) continue;
     const FiredPair f = fired[e];
     const int rule = (fs >> 2) & 63u;
     const uint32_t r = fs >> 8;
@@ -610,9 +655,14 @@ __global__ void k_resolve(const DevParams* __restrict__ Pp, DevCtl* __restrict__
       }
       ++n_res;
       if (pr.bc == RD_BC_RAD) {
-        const double p = p_reac3(Rn, R0, pr.s, pr.alpha);
-        n_near += fabs(u_reac - p) <= 1e-9;
-        react = u_reac < p;
+        const double pf = (double)p_reac3_f((float)Rn, (float)R0, pr.s_f, pr.alpha_f);
+        if (fabs(u_reac - pf) > kFilter) {
+          react = u_reac < pf;
+        } else {
+          const double p = p_reac3(Rn, R0, pr.s, pr.alpha);
+          n_near += fabs(u_reac - p) <= 1e-9;
+          react = u_reac < p;
+        }
       }
     }
     if (react) {
@@ -630,11 +680,6 @@ __global__ void k_resolve(const DevParams* __restrict__ Pp, DevCtl* __restrict__
       x1[f.ia] = store4<T>(a1, wa);
       x1[f.ib] = store4<T>(b1, wb);
     }
-  }
-  // (not all lanes may be active after continue: reduce with atomics directly)
-  if (n_react) atomicAdd(&ctl->stats[RD_STAT_REACTIONS], n_react);
-  if (n_res) atomicAdd(&ctl->stats[RD_STAT_RESAMPLED], n_res);
-  if (n_near) atomicAdd(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
 }
 
 // ================================================================================================
@@ -644,18 +689,12 @@ __global__ void k_resolve(const DevParams* __restrict__ Pp, DevCtl* __restrict__
 // p_reac(R', 1); non-interacting products start sigma_place apart and separate freely.
 // ================================================================================================
 template <class T>
-__global__ void k_decay(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                        const RepDev* __restrict__ reps, const uint32_t* __restrict__ decay_list,
-                        const typename V4<T>::type* __restrict__ x0, const uint32_t* __restrict__ id,
-                        uint32_t* __restrict__ status, typename V4<T>::type* __restrict__ prodpos) {
-  const DevParams& P = *Pp;
-  if (ctl->status) return;
-  const uint32_t nd = ctl->n_decay;
-  const uint32_t step = ctl->step;
+__device__ __forceinline__ void decay_products(const DevParams& P, const RepDev* __restrict__ reps, uint32_t i,
+                                               uint32_t step, const typename V4<T>::type* __restrict__ x0,
+                                               const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
+                                               typename V4<T>::type* __restrict__ prodpos, unsigned long long& n_rec,
+                                               unsigned long long& n_near) {
   const int dim = P.dim;
-  unsigned long long n_rec = 0, n_near = 0;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += gridDim.x * blockDim.x) {
-    const uint32_t i = decay_list[q];
     const uint32_t st = status[i];
     const DecayDev& dc = P.decays[(st >> ST_CHANNEL_SHIFT) & 15u];
     const auto p0 = x0[i];
@@ -708,9 +747,14 @@ __global__ void k_decay(const DevParams* __restrict__ Pp, DevCtl* __restrict__ c
         if (pr.bc == RD_BC_ABS) {
           recombine = true;
         } else if (pr.bc == RD_BC_RAD) {
-          const double p = p_reac3(Rn, 1.0, pr.s, pr.alpha);
-          n_near += fabs(u_reac - p) <= 1e-9;
-          recombine = u_reac < p;
+          const double pf = (double)p_reac3_f((float)Rn, 1.0f, pr.s_f, pr.alpha_f);
+          if (fabs(u_reac - pf) > kFilter) {
+            recombine = u_reac < pf;
+          } else {
+            const double p = p_reac3(Rn, 1.0, pr.s, pr.alpha);
+            n_near += fabs(u_reac - p) <= 1e-9;
+            recombine = u_reac < p;
+          }
         }
         product = pr.product;
       } else {
@@ -739,7 +783,195 @@ __global__ void k_decay(const DevParams* __restrict__ Pp, DevCtl* __restrict__ c
       }
     }
     status[i] = st | (np << ST_NPROD_SHIFT);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Mixed step: positions, displacements and the propagator sample in FP32; p_reac in FP64.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev* __restrict__ reps,
+                                               const FiredPair* __restrict__ fired,
+                                               const uint32_t* __restrict__ fstate, uint32_t e, uint32_t step,
+                                               const float4* __restrict__ x0, float4* __restrict__ x1,
+                                               uint32_t* __restrict__ status, float4* __restrict__ prodpos,
+                                               unsigned long long& n_react, unsigned long long& n_res) {
+  const bool d3 = P.dim == 3;
+  const uint32_t fs = fstate[e];
+  const FiredPair f = fired[e];
+  const int rule = (fs >> 2) & 63u;
+  const uint32_t r = fs >> 8;
+  const PairDev& pr = P.pairs[rule];
+  const RepDev& rep = reps[r];
+  const float4 a1 = x1[f.ia], b1 = x1[f.ib], a0 = x0[f.ia], b0 = x0[f.ib];
+  const uint32_t wa = w_bits(a1.w), wb = w_bits(b1.w);
+  const float Drel = P.D_f[wa & 0xFF] + P.D_f[wb & 0xFF];
+  const float ca = P.D_f[wa & 0xFF] / Drel, cb = P.D_f[wb & 0xFF] / Drel;
+  const float rx = min_image_f(b1.x - a1.x, rep.Lf, rep.half_Lf), ry = min_image_f(b1.y - a1.y, rep.Lf, rep.half_Lf);
+  const float rz = d3 ? min_image_f(b1.z - a1.z, rep.Lf, rep.half_Lf) : 0.0f;
+  const float cx = a1.x + ca * rx, cy = a1.y + ca * ry, cz = a1.z + ca * rz;
+  bool react = true;
+  if (pr.bc != RD_BC_ABS) {
+    const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf), r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
+    const float r0z = d3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
+    const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
+    float R0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z) * pr.inv_sigma_f;
+    R0 = fmaxf(R0, 1.0f);
+    const float Rn = resample3_f(u23(w.x), R0, pr.s_f);
+    const float len = sqrtf(rx * rx + ry * ry + rz * rz);
+    float dx, dy, dz;
+    if (len > 0.0f) {
+      dx = rx / len; dy = ry / len; dz = rz / len;
+    } else {
+      const float l0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z);
+      if (l0 > 0.0f) {
+        dx = r0x / l0; dy = r0y / l0; dz = r0z / l0;
+      } else {
+        dx = 1.0f; dy = 0.0f; dz = 0.0f;
+      }
+    }
+    const float ln = Rn * pr.sigma_f;
+    ++n_res;
+    react = pr.bc == RD_BC_RAD && u52(w.z, w.w) < p_reac3((double)Rn, (double)R0, pr.s, pr.alpha);
+    if (!react) {
+      x1[f.ia] = make_float4(wrap_f(cx - ca * ln * dx, rep.Lf), wrap_f(cy - ca * ln * dy, rep.Lf),
+                             d3 ? wrap_f(cz - ca * ln * dz, rep.Lf) : 0.0f, a1.w);
+      x1[f.ib] = make_float4(wrap_f(cx + cb * ln * dx, rep.Lf), wrap_f(cy + cb * ln * dy, rep.Lf),
+                             d3 ? wrap_f(cz + cb * ln * dz, rep.Lf) : 0.0f, b1.w);
+      return;
+    }
   }
+  ++n_react;
+  uint32_t np = 0;
+  if (pr.product >= 0) {
+    prodpos[2 * (size_t)f.ia] = make_float4(wrap_f(cx, rep.Lf), wrap_f(cy, rep.Lf), d3 ? wrap_f(cz, rep.Lf) : 0.0f,
+                                            w_from_bits_f(pack_sp((uint32_t)pr.product, r)));
+    np = 1;
+  }
+  status[f.ia] |= ST_CONSUMED | (np << ST_NPROD_SHIFT);
+  status[f.ib] |= ST_CONSUMED;
+}
+
+__device__ __forceinline__ void normals_f(const DevParams& P, uint32_t c0, uint32_t id, uint32_t tag0, uint32_t r,
+                                          bool d3, float n[4]) {
+  const uint4 w = draw(P, c0, id, kOneParticle, tag0, r);
+  box_muller_f(u23(w.x), u23(w.y), n[0], n[1]);
+  n[2] = n[3] = 0.0f;
+  if (d3) box_muller_f(u23(w.z), u23(w.w), n[2], n[3]);
+}
+
+__device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDev* __restrict__ reps, uint32_t i,
+                                                 uint32_t step, const float4* __restrict__ x0,
+                                                 const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
+                                                 float4* __restrict__ prodpos, unsigned long long& n_rec) {
+  const bool d3 = P.dim == 3;
+  const uint32_t st = status[i];
+  const DecayDev& dc = P.decays[(st >> ST_CHANNEL_SHIFT) & 15u];
+  const float4 p0 = x0[i];
+  const uint32_t r = w_bits(p0.w) >> 8;
+  const RepDev& rep = reps[r];
+  const uint32_t pid = id[i];
+  const float dt = (float)P.dt;
+  uint32_t np = 0;
+  if (dc.n_products == 1) {
+    float nr[4];
+    normals_f(P, step, pid, TAG_DISS0, r, d3, nr);
+    const float ell = sqrtf(2.0f * P.D_f[dc.p0] * dt);
+    prodpos[2 * (size_t)i] = make_float4(wrap_f(p0.x + ell * nr[0], rep.Lf), wrap_f(p0.y + ell * nr[1], rep.Lf),
+                                         d3 ? wrap_f(p0.z + ell * nr[2], rep.Lf) : 0.0f,
+                                         w_from_bits_f(pack_sp((uint32_t)dc.p0, r)));
+    np = 1;
+  } else if (dc.n_products == 2) {
+    const int sa = dc.p0, sb = dc.p1;
+    const float Drel = P.D_f[sa] + P.D_f[sb];
+    const float ca = P.D_f[sa] / Drel, cb = P.D_f[sb] / Drel;
+    const float DR = P.D_f[sa] * P.D_f[sb] / Drel;
+    uint4 w = draw(P, step, pid, kOneParticle, TAG_DIR, r);
+    float dx, dy, dz = 0.0f;
+    if (d3) {
+      const float ct = 2.0f * u23(w.x) - 1.0f;
+      float sn, cs;
+      sincospif(2.0f * u23(w.y), &sn, &cs);
+      const float stt = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+      dx = stt * cs; dy = stt * sn; dz = ct;
+    } else {
+      sincospif(2.0f * u23(w.x), &dy, &dx);
+    }
+    float nc[4];
+    normals_f(P, step, pid, TAG_DISS0, r, d3, nc);
+    const float ellc = sqrtf(2.0f * DR * dt);
+    const float cx = p0.x + ellc * nc[0], cy = p0.y + ellc * nc[1], cz = p0.z + ellc * nc[2];
+    const int rule = P.pair_of[sa][sb];
+    bool recombine = false;
+    int product = -1;
+    float rx, ry, rz;
+    if (rule >= 0) {
+      const PairDev& pr = P.pairs[rule];
+      w = draw(P, step, pid, kOneParticle, TAG_RES, r);
+      const float Rn = resample3_f(u23(w.x), 1.0f, pr.s_f);
+      const float ln = Rn * pr.sigma_f;
+      rx = ln * dx; ry = ln * dy; rz = ln * dz;
+      if (pr.bc == RD_BC_ABS)
+        recombine = true;
+      else if (pr.bc == RD_BC_RAD)
+        recombine = u52(w.z, w.w) < p_reac3((double)Rn, 1.0, pr.s, pr.alpha);
+      product = pr.product;
+    } else {
+      float nr[4];
+      normals_f(P, step, pid, TAG_DISS2, r, d3, nr);
+      const float ellr = sqrtf(2.0f * Drel * dt);
+      const float sp = (float)dc.sigma_place;
+      rx = sp * dx + ellr * nr[0]; ry = sp * dy + ellr * nr[1]; rz = sp * dz + ellr * nr[2];
+    }
+    if (recombine) {
+      ++n_rec;
+      if (product >= 0) {
+        prodpos[2 * (size_t)i] = make_float4(wrap_f(cx, rep.Lf), wrap_f(cy, rep.Lf), d3 ? wrap_f(cz, rep.Lf) : 0.0f,
+                                             w_from_bits_f(pack_sp((uint32_t)product, r)));
+        np = 1;
+      }
+    } else {
+      prodpos[2 * (size_t)i] = make_float4(wrap_f(cx - ca * rx, rep.Lf), wrap_f(cy - ca * ry, rep.Lf),
+                                           d3 ? wrap_f(cz - ca * rz, rep.Lf) : 0.0f,
+                                           w_from_bits_f(pack_sp((uint32_t)sa, r)));
+      prodpos[2 * (size_t)i + 1] = make_float4(wrap_f(cx + cb * rx, rep.Lf), wrap_f(cy + cb * ry, rep.Lf),
+                                               d3 ? wrap_f(cz + cb * rz, rep.Lf) : 0.0f,
+                                               w_from_bits_f(pack_sp((uint32_t)sb, r)));
+      np = 2;
+    }
+  }
+  status[i] = st | (np << ST_NPROD_SHIFT);
+}
+
+// One work list: accepted pairs first, then decays; one warp per block so that the FP64-bound
+// items spread over all SMs.
+template <class T>
+__global__ void __launch_bounds__(32) k_resolve_all(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                    const RepDev* __restrict__ reps, const FiredPair* __restrict__ fired,
+                                                    const uint32_t* __restrict__ fstate,
+                                                    const uint32_t* __restrict__ accepted,
+                                                    const uint32_t* __restrict__ decay_list,
+                                                    const typename V4<T>::type* __restrict__ x0,
+                                                    typename V4<T>::type* __restrict__ x1,
+                                                    const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
+                                                    typename V4<T>::type* __restrict__ prodpos) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t na = ctl->n_accept, nd = ctl->n_decay, step = ctl->step;
+  unsigned long long n_react = 0, n_res = 0, n_near = 0, n_rec = 0;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < na + nd; q += gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 8) {
+      if (q < na)
+        resolve_pair<T>(P, reps, fired, fstate, accepted[q], step, x0, x1, status, prodpos, n_react, n_res, n_near);
+      else
+        decay_products<T>(P, reps, decay_list[q - na], step, x0, id, status, prodpos, n_rec, n_near);
+    } else {
+      if (q < na)
+        resolve_pair_f(P, reps, fired, fstate, accepted[q], step, x0, x1, status, prodpos, n_react, n_res);
+      else
+        decay_products_f(P, reps, decay_list[q - na], step, x0, id, status, prodpos, n_rec);
+    }
+  }
+  if (n_react) atomicAdd(&ctl->stats[RD_STAT_REACTIONS], n_react);
+  if (n_res) atomicAdd(&ctl->stats[RD_STAT_RESAMPLED], n_res);
   if (n_rec) atomicAdd(&ctl->stats[RD_STAT_RECOMBINED], n_rec);
   if (n_near) atomicAdd(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
 }
@@ -750,8 +982,8 @@ __global__ void k_decay(const DevParams* __restrict__ Pp, DevCtl* __restrict__ c
 // next_id + rank.  An error latched during the step turns this into a copy of the unchanged state.
 // ================================================================================================
 template <class T>
-__global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __restrict__ ctl,
-                          const RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
+__global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
                           const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                           const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
                           const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
@@ -811,25 +1043,21 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, const DevCtl* __rest
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x)
       if (hist[k]) atomicAdd(&counts[k], (unsigned long long)hist[k]);
   }
-}
-
-// K8: replica segments, next ids, particle count, step and time.
-__global__ void k_finalize(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl, RepDev* __restrict__ reps,
-                           const unsigned long long* __restrict__ scan) {
-  const DevParams& P = *Pp;
-  const uint32_t n = ctl->n;
-  const unsigned long long tot = scan[n];
-  const unsigned long long n_new = (tot >> 32) + (tot & 0xFFFFFFFFull);
-  const bool fail = ctl->status != 0 || n_new > (unsigned long long)P.cap_particles;
+  // the last block to finish commits the step: replica segments, ids, count, step, time
+  __shared__ bool s_last;
+  __threadfence();
   __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const unsigned long long n_new = (tot >> 32) + (tot & 0xFFFFFFFFull);
   if (!fail) {
     for (int r = threadIdx.x; r < P.n_replicas; r += blockDim.x) {
       const unsigned long long eb = scan[reps[r].beg], ee = scan[reps[r].end];
-      const uint32_t nb = (uint32_t)(eb >> 32) + (uint32_t)eb;
-      const uint32_t ne = (uint32_t)(ee >> 32) + (uint32_t)ee;
       reps[r].next_id += (uint32_t)ee - (uint32_t)eb;
-      reps[r].beg = nb;
-      reps[r].end = ne;
+      reps[r].beg = (uint32_t)(eb >> 32) + (uint32_t)eb;
+      reps[r].end = (uint32_t)(ee >> 32) + (uint32_t)ee;
     }
   }
   __syncthreads();
@@ -845,17 +1073,13 @@ __global__ void k_finalize(const DevParams* __restrict__ Pp, DevCtl* __restrict_
     } else if (ctl->status == 0) {
       ctl->status = RD_ECAPACITY;
     }
-  }
-}
-
-// Per-step reset of the device counters (first kernel of a step).
-__global__ void k_begin_step(DevCtl* __restrict__ ctl, unsigned long long* __restrict__ counts, int n_counts) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->last_fired = ctl->fired;
     ctl->fired = 0;
     ctl->n_conflict = 0;
+    ctl->n_accept = 0;
     ctl->n_decay = 0;
+    ctl->done_blocks = 0;
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += gridDim.x * blockDim.x) counts[i] = 0;
 }
 
 // ================================================================================================
@@ -922,8 +1146,11 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
         p_enc[k] = p_enc3(b / pr.sigma, a / pr.sigma, pr.inv_tau);
       }
     }
-    if (p_reac) p_reac[k] = pr.bc == RD_BC_RAD ? p_reac3(b / pr.sigma, a / pr.sigma, pr.s, pr.alpha)
-                                               : (pr.bc == RD_BC_ABS ? 1.0 : 0.0);
+    if (p_reac) {
+      double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
+      if (pr.bc == RD_BC_RAD) v = p_reac3(b / pr.sigma, a / pr.sigma, pr.s, pr.alpha);
+      p_reac[k] = v;
+    }
   }
 }
 
@@ -958,54 +1185,39 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   V* sx0 = (V*)L.sx0;
   V* sx1 = (V*)L.sx1;
   V* prod = (V*)L.prodpos;
+  const int64_t tile = 256 * (int64_t)kScanItems;
 
   mark("begin");
-  k_begin_step<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.ctl, L.counts, L.n_counts);
-  mark("k_begin_step");
   k_prepare<T><<<Gp, B, 0, s>>>(L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg, L.cell_of, L.slot,
-                                 L.cell_count, L.decay_list);
+                                 L.cell_count, L.decay_list, L.counts, L.n_counts);
   mark("k_prepare");
-  // scan of the cell counts -> cell_start (counts zeroed for the next step)
-  const int items = L.scan_items;
-  const int nbc = (int)((L.total_cells + (int64_t)256 * items - 1) / ((int64_t)256 * items));
-  k_scan_reduce<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, nullptr, nullptr,
-                                                             L.total_cells, L.block_sums32, items);
-  k_scan_top<uint32_t><<<1, 1024, 0, s>>>(L.block_sums32, nbc);
-  k_scan_down<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, nullptr, nullptr,
-                                                           L.total_cells, L.block_sums32, L.cell_start,
-                                                           L.cell_count, items, nbc);
+  const int nbc = (int)((L.total_cells + tile - 1) / tile);
+  k_scan1<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, L.total_cells, nullptr,
+                                                       L.cell_start, L.cell_count, L.agg32, L.incl32, L.flags,
+                                                       L.ctl, 0);
   mark("k_scan_cells");
   k_scatter_cells<T><<<Gp, B, 0, s>>>(L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1, L.sidx);
   mark("k_scatter_cells");
   k_sweep<T><<<Gp, 256, 0, s>>>(L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired,
-                                 L.fstate, (uint32_t)L.cap_pairs);
+                                 L.fstate, L.deg, (uint32_t)L.cap_pairs);
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
-  k_match_degree<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.deg, (uint32_t)L.cap_pairs);
-  k_match_trivial<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.best_key,
+  k_match_trivial<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted, L.best_key,
                                      L.best_pid, (uint32_t)L.cap_pairs);
-  k_match_rounds<<<1, 1024, 0, s>>>(L.P, L.ctl, L.fired, L.fstate, L.matched, L.conflict, L.best_key, L.best_pid);
+  k_match_rounds<<<1, 1024, 0, s>>>(L.P, L.ctl, L.fired, L.fstate, L.matched, L.conflict, L.accepted, L.best_key,
+                                    L.best_pid);
   mark("k_match");
-  k_resolve<T><<<Gf, 128, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, x0, x1, L.status, prod,
-                                   (uint32_t)L.cap_pairs);
-  mark("k_resolve");
-  k_decay<T><<<grid_for(L.cap_particles / 8 + 1, 128, L.max_grid), 128, 0, s>>>(L.P, L.ctl, L.reps, L.decay_list,
-                                                                                  x0, L.id_cur, L.status, prod);
-  mark("k_decay");
-  // compaction scan over particles
-  const int nbp = (int)((L.cap_particles + (int64_t)256 * items - 1) / ((int64_t)256 * items));
-  k_scan_reduce<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, nullptr, &L.ctl->n, 0,
-                                                                     L.block_sums64, items);
-  k_scan_top<unsigned long long><<<1, 1024, 0, s>>>(L.block_sums64, nbp);
-  k_scan_down<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, nullptr, &L.ctl->n, 0,
-                                                                   L.block_sums64, L.scan, nullptr, items, nbp);
+  k_resolve_all<T><<<152 * 8, 32, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted, L.decay_list, x0, x1,
+                                          L.id_cur, L.status, prod);
+  mark("k_resolve_all");
+  const int nbp = (int)((L.cap_particles + tile - 1) / tile);
+  k_scan1<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, 0, &L.ctl->n, L.scan, nullptr,
+                                                               L.agg64, L.incl64, L.flags + L.flag_stride, L.ctl, 1);
   mark("k_scan_compact");
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
   k_compact<T><<<Gp, B, hist_bytes, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo,
                                           L.id_next, L.counts, L.n_counts);
   mark("k_compact");
-  k_finalize<<<1, 256, 0, s>>>(L.P, L.ctl, L.reps, L.scan);
-  mark("k_finalize");
 }
 
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
@@ -1024,8 +1236,12 @@ void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int
     k_init_positions<double><<<G, 256, 0, s>>>(L.P, L.reps, rep_of, sp_of, id_of, n, (d4*)L.x_cur, L.id_cur);
 }
 
+__global__ void k_zero_counts(unsigned long long* __restrict__ counts, int n_counts) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += gridDim.x * blockDim.x) counts[i] = 0;
+}
+
 void launch_count(const StepLaunch& L, cudaStream_t s) {
-  k_begin_step<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.ctl, L.counts, L.n_counts);
+  k_zero_counts<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.counts, L.n_counts);
   const int G = grid_for(L.cap_particles, 256, L.max_grid);
   if (L.precision == RD_MIXED)
     k_count<float><<<G, 256, 0, s>>>(L.P, L.ctl, (const float4*)L.x_cur, L.counts);

@@ -39,8 +39,13 @@ struct StepLaunch {
   uint32_t* cell_start;
   uint32_t* sidx;
   uint32_t* decay_list;
-  uint32_t* block_sums32;
-  unsigned long long* block_sums64;
+  uint32_t* agg32;             // per-tile aggregates / inclusive prefixes of the cell scan
+  uint32_t* incl32;
+  unsigned long long* agg64;   // ... of the compaction scan
+  unsigned long long* incl64;
+  uint32_t* flags;             // 2 x flag_stride tile flags
+  int64_t flag_stride;
+  uint32_t* accepted;          // accepted pair list
   unsigned long long* scan;
   FiredPair* fired;
   uint32_t* fstate;
