@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-KERNELS_PER_STEP = 17          # kernels of one step (begin, prepare, 3 scan, scatter, sweep, 3 match,
-                               # resolve, decay, 3 scan, compact, finalize)
+KERNELS_PER_STEP = 8           # kernels of one step: prepare, scan (cells), scatter, sweep, 2 match,
+                               # resolve, scan (compaction), compact
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -52,12 +52,17 @@ def parse():
     return ap.parse_args()
 
 
+def box_edge(args):
+    """Box edge keeping the 10 uM concentration of the L = 2.55 um, 1e5 + 1e5 system."""
+    return 2.55 * (args.n_each / 100_000) ** (1.0 / 3.0)
+
+
 def workload(args, seed=1):
-    return W.reversible_3d(dt=args.dt, seed=seed, n_each=args.n_each, equilibrium_start=True)
+    return W.reversible_3d(dt=args.dt, seed=seed, n_each=args.n_each, L=box_edge(args), equilibrium_start=True)
 
 
 def workload_name(args):
-    return (f"3D A+B<->C radiation BC, L=2.55 um (10 uM), N_A=N_B={args.n_each:.0e} "
+    return (f"3D A+B<->C radiation BC, L={box_edge(args):.3g} um (10 uM), N_A=N_B={args.n_each:.0e} "
             f"(mass-action start), sigma=0.005, D=1/1/0.5, ka=0.02, kd=10, dt={args.dt:g}")
 
 
@@ -149,7 +154,7 @@ def oracle_sample(args, seconds, seed=1):
     # Same density, time step and chemistry; a smaller box so that the O(N^2) oracle fits the
     # time budget.  Rate reported per particle-step.
     n_each = 4000
-    L = 2.55 * (n_each / args.n_each) ** (1 / 3)
+    L = box_edge(args) * (n_each / args.n_each) ** (1 / 3)
     system = W.reversible_3d(dt=args.dt, seed=seed, n_each=n_each, L=L, equilibrium_start=True)
     st = O.init_state(system)
     ps = 0
@@ -177,7 +182,7 @@ def run_reference(args, rank, world):
 
     O.build()
     n_each = 4000
-    L = 2.55 * (n_each / args.n_each) ** (1 / 3)
+    L = box_edge(args) * (n_each / args.n_each) ** (1 / 3)
     system = W.reversible_3d(dt=args.dt, seed=1, n_each=n_each, L=L, equilibrium_start=True)
     st = O.init_state(system)
     for _ in range(max(args.warmup, 0) and min(args.warmup, 3)):
@@ -236,7 +241,8 @@ def run_ours(args, rank, world, local_rank):
 
     system = workload(args, seed=1 + rank)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    sim = pkg.Simulation(system, precision=args.precision)
+    sim = pkg.Simulation(system, precision=args.precision, cell_factor="tune")
+    layout = sim.info()
     sim.run(max(args.warmup, 3))
     sim.sync()
     obs0 = sim.observables()
@@ -277,8 +283,9 @@ def run_ours(args, rank, world, local_rank):
                 ker.setdefault(name, []).append(ms)
         ker_avg = {k: sum(v) / len(v) for k, v in ker.items()}
         step_ms = sum(ker_avg.values())
-        top = max((k for k in ker_avg if k in ("k_prepare", "k_sweep", "k_compact", "k_scatter_cells")),
-                  key=lambda k: ker_avg[k])
+        hbm_kernels = ("k_prepare", "k_sweep", "k_compact", "k_scatter_cells")
+        top = max((k for k in ker_avg if k in hbm_kernels), key=lambda k: ker_avg[k])
+        dominant = max(ker_avg, key=lambda k: ker_avg[k])
         st = sim.get_state()
         binned = int(np.sum(st["species"] < 2))
         cand_per_step = cand_local / max(steps_done, 1)
@@ -297,7 +304,8 @@ def run_ours(args, rank, world, local_rank):
                               "frac": achieved / peak, "traffic": traffic, "kernel": top,
                               "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
                               "algorithmic_bytes_per_launch": ab,
-                              "kernel_ms": ker_avg[top]}
+                              "kernel_ms": ker_avg[top], "dominant_kernel": dominant,
+                              "dominant_share": ker_avg[dominant] / step_ms}
         extras["kernel_ms"] = {k: round(v, 5) for k, v in ker_avg.items()}
         extras["sweep_pair_prob_evals_per_s"] = cand_per_step / (ker_avg["k_sweep"] * 1e-3)
         extras["candidates_per_step"] = cand_per_step
@@ -319,6 +327,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed (512 MiB write) between timed graph launches",
                    "parallelism": f"replicas x{world} (one independent system per GPU)"},
         "gpu_launches": KERNELS_PER_STEP * steps_done,
+        "layout": layout,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
     }
     line.update(extras)
@@ -333,7 +342,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     out = {}
     # FP64 step on the same workload
     if args.precision == "mixed":
-        sim64 = pkg.Simulation(workload(args), precision="fp64")
+        sim64 = pkg.Simulation(workload(args), precision="fp64", cell_factor="tune")
         sim64.run(max(args.warmup, 3))
         sim64.sync()
         o0 = sim64.observables()

@@ -99,7 +99,9 @@ typedef struct {
   const rd_replica* replicas;         /* read during rd_init only */
   double capacity_factor;             /* particle capacity = factor * initial total (default 2) */
   int64_t pair_capacity;              /* fired-pair list capacity (0: automatic) */
-  int32_t cell_factor_x100;           /* cell edge = r_cut * factor/100 (0: 100); autotuned if < 0 */
+  int32_t cell_factor_x100;           /* cell edge = largest r_cut x factor/100; 0: density-based
+                                         (about 1.5 interacting particles per cell); < 0: the fastest of
+                                         three factors, timed by rd_init on the initial state */
   int32_t block_size;                 /* threads per block of the particle kernels (0: 256) */
   rd_allocator allocator;
 } rd_config;
@@ -175,6 +177,12 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
 
 /* Number of particles currently alive (synchronises). */
 int rd_num_particles(rd_handle* h, int64_t* n);
+
+/* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge factor (in units of the
+ * largest cut-off), out[1] total cells, out[2] threads per block of the resolution kernel,
+ * out[3] particle capacity, out[4] fired-pair capacity, out[5] autotuned ms per step (0 if not
+ * tuned), out[6] largest cut-off radius.  Writes min(n, 7) values to the caller-owned HOST array. */
+int rd_info(rd_handle* h, double* out, int32_t n);
 
 /* Name of the kernel-level timing hook: rd_time_kernels enables CUDA-event timing of every kernel
  * of the next rd_step; rd_kernel_times copies per-kernel (name, ms) pairs of that step. */

@@ -29,7 +29,8 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
 # exported symbols declared in include/rd.h
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
            "rd_pair_probs", "rd_resample", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
-           "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static"]
+           "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static",
+           "rd_info"]
 
 
 class RDError(RuntimeError):
@@ -101,6 +102,7 @@ def _lib():
         L.rd_time_kernels.argtypes = [vp, i32]
         L.rd_kernel_times.argtypes = [vp, i32, P(i32), C.c_char_p, P(C.c_float)]
         L.rd_step_static.argtypes = [P(_Config), vp, i64, vp, vp, vp, u32, i64, i64, vp, vp, vp, vp, vp, vp]
+        L.rd_info.argtypes = [vp, P(d), i32]
         L.rd_free.argtypes = [vp]
         L.rd_free.restype = None
         L.rd_strerror.argtypes = [C.c_int]
@@ -135,8 +137,10 @@ def _ptr(a, ctype):
 
 
 def make_config(system, precision: Optional[str] = None, capacity_factor: float = 2.0,
-                pair_capacity: int = 0, cell_factor: float = 1.0, block_size: int = 256):
-    """Build the C configuration from a system description (see ``workloads.System``)."""
+                pair_capacity: int = 0, cell_factor=None, block_size: int = 256):
+    """Build the C configuration from a system description (see ``workloads.System``).
+    cell_factor: cell edge in units of the largest cut-off; None = density-based (about 1.5
+    interacting particles per cell), "tune" = timed autotuning at creation."""
     cfg = _Config()
     cfg.dim = int(system.dim)
     cfg.precision = PRECISION[precision or system.precision]
@@ -165,7 +169,12 @@ def make_config(system, precision: Optional[str] = None, capacity_factor: float 
     cfg.replicas = C.cast(rep_arr, C.POINTER(_Replica))
     cfg.capacity_factor = float(capacity_factor)
     cfg.pair_capacity = int(pair_capacity)
-    cfg.cell_factor_x100 = int(round(cell_factor * 100))
+    if cell_factor is None:
+        cfg.cell_factor_x100 = 0
+    elif cell_factor == "tune":
+        cfg.cell_factor_x100 = -1
+    else:
+        cfg.cell_factor_x100 = int(round(float(cell_factor) * 100))
     cfg.block_size = int(block_size)
     return cfg, rep_arr
 
@@ -174,7 +183,7 @@ class Simulation:
     """One handle of the C library: a batch of replicas of a reaction-diffusion system on one GPU."""
 
     def __init__(self, system, precision: Optional[str] = None, device: int = 0, stream=None,
-                 capacity_factor: float = 2.0, pair_capacity: int = 0, cell_factor: float = 1.0,
+                 capacity_factor: float = 2.0, pair_capacity: int = 0, cell_factor=None,
                  block_size: int = 256):
         import torch
 
@@ -229,6 +238,13 @@ class Simulation:
         _check(rc, "rd_observables")
         return {"counts": counts.reshape(self.n_replicas, self.n_species), "step": step.value,
                 "t": t.value, "stats": dict(zip(STAT_NAMES, stats.tolist()))}
+
+    def info(self):
+        v = np.zeros(7)
+        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 7), "rd_info")
+        return {"cell_factor": v[0], "cells": int(v[1]), "resolve_block": int(v[2]),
+                "capacity": int(v[3]), "pair_capacity": int(v[4]), "tuned_ms_per_step": v[5],
+                "r_cut_max": v[6]}
 
     def num_particles(self) -> int:
         n = C.c_int64()

@@ -44,6 +44,9 @@ struct rd_handle {
   KernelTimer timer;
   bool time_next = false;
   std::vector<std::pair<std::string, float>> last_times;
+  std::vector<double> factors;       // cell-edge factors (one, or the autotuner's candidates)
+  double tuned_ms = 0.0;
+  double factor = 1.0;               // cell-edge factor in use
 };
 
 static void* dev_alloc(rd_handle* h, size_t bytes) {
@@ -199,6 +202,157 @@ static void derive_params(rd_handle* h) {
   }
 }
 
+
+// Cell grid of every replica for a cell edge of (factor x largest cut-off), coarsened per replica
+// until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of out[r].
+static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
+                            double rc, double factor, std::vector<RepDev>& out) {
+  int64_t total = 0;
+  for (size_t r = 0; r < reps.size(); ++r) {
+    const rd_replica& rp = reps[r];
+    RepDev& d = out[r];
+    int64_t nb = 0;
+    for (int s = 0; s < c.n_species; ++s)
+      if ((binned_mask >> s) & 1u) nb += rp.n_init[s];
+    double f = factor;
+    int64_t cells = 1;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      cells = 1;
+      for (int a = 0; a < 3; ++a) {
+        int n = 1;
+        if (a < c.dim && rc > 0.0) {
+          const double m = std::floor(rp.L / (rc * f * (1.0 + 1e-6)));
+          n = m >= 3.0 ? (int)std::min(m, 4096.0) : 1;
+        }
+        d.nc[a] = n;
+        d.inv_edge[a] = n / rp.L;
+        d.inv_edge_f[a] = (float)d.inv_edge[a];
+        cells *= n;
+      }
+      if (cells <= 4 * nb + 64) break;
+      f *= 1.25;
+    }
+    d.cell_base = total;
+    total += cells;
+  }
+  return total;
+}
+
+// Cell-edge factor for about 1.5 interacting particles per cell (between 1 and 4 cut-offs).
+static double density_factor(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
+                             double rc) {
+  double nb = 0.0, vol = 0.0;
+  for (const rd_replica& rp : reps) {
+    for (int s = 0; s < c.n_species; ++s)
+      if ((binned_mask >> s) & 1u) nb += (double)rp.n_init[s];
+    vol += std::pow(rp.L, (double)c.dim);
+  }
+  if (nb <= 0.0 || rc <= 0.0) return 1.0;
+  const double per_cell = nb / vol * std::pow(rc, (double)c.dim);
+  const double f = std::pow(1.5 / per_cell, 1.0 / c.dim);
+  return std::min(4.0, std::max(1.0, f));
+}
+
+
+// Autotuner: times a few steps for each candidate cell-edge factor and resolution block size on
+// the initial state, keeps the fastest, and restores the state (the scan epoch stays monotonic).
+static cudaError_t apply_factor(rd_handle* h, double factor) {
+  const rd_config& c = h->cfg;
+  std::vector<RepDev> reps(c.n_replicas);
+  cudaError_t e = cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  h->L.total_cells = layout_cells(c, h->reps_host, h->hp.binned_mask, max_cutoff(c), factor, reps);
+  return cudaMemcpy(h->L.reps, reps.data(), reps.size() * sizeof(RepDev), cudaMemcpyHostToDevice);
+}
+
+static cudaError_t autotune(rd_handle* h) {
+  const size_t xbytes = (size_t)h->L.cap_particles * h->vsize, ibytes = (size_t)h->L.cap_particles * 4;
+  const size_t rbytes = (size_t)h->cfg.n_replicas * sizeof(RepDev);
+  void *sx = nullptr, *si = nullptr;
+  cudaError_t e = cudaMalloc(&sx, xbytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&si, ibytes);
+  if (e != cudaSuccess) {
+    cudaFree(sx);
+    return e;
+  }
+  DevCtl ctl0;
+  std::vector<RepDev> reps0(h->cfg.n_replicas);
+  cudaMemcpy(&ctl0, h->L.ctl, sizeof ctl0, cudaMemcpyDeviceToHost);
+  cudaMemcpy(reps0.data(), h->L.reps, rbytes, cudaMemcpyDeviceToHost);
+  cudaMemcpy(sx, h->xbuf[0], xbytes, cudaMemcpyDeviceToDevice);
+  cudaMemcpy(si, h->idbuf[0], ibytes, cudaMemcpyDeviceToDevice);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto restore = [&]() {
+    DevCtl now;
+    cudaMemcpy(&now, h->L.ctl, sizeof now, cudaMemcpyDeviceToHost);
+    DevCtl back = ctl0;
+    back.epoch = now.epoch;          // flags written by the trial steps must not look current later
+    cudaMemcpy(h->L.ctl, &back, sizeof back, cudaMemcpyHostToDevice);
+    // segments and ids go back to the saved state; the cell grid stays the one being timed, so
+    // that it always matches L.total_cells
+    std::vector<RepDev> cur(reps0.size());
+    cudaMemcpy(cur.data(), h->L.reps, rbytes, cudaMemcpyDeviceToHost);
+    for (size_t r = 0; r < cur.size(); ++r) {
+      cur[r].beg = reps0[r].beg;
+      cur[r].end = reps0[r].end;
+      cur[r].next_id = reps0[r].next_id;
+    }
+    cudaMemcpy(h->L.reps, cur.data(), rbytes, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->xbuf[0], sx, xbytes, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(h->idbuf[0], si, ibytes, cudaMemcpyDeviceToDevice);
+    h->cur = 0;
+  };
+  auto trial = [&]() -> float {
+    StepLaunch L = launch_for(h, 0);
+    launch_step(L, h->stream, nullptr);   // warm-up
+    launch_step(launch_for(h, 1), h->stream, nullptr);
+    cudaEventRecord(a, h->stream);
+    for (int k = 0; k < 3; ++k) {
+      launch_step(launch_for(h, 0), h->stream, nullptr);
+      launch_step(launch_for(h, 1), h->stream, nullptr);
+    }
+    cudaEventRecord(b, h->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    restore();
+    return ms;
+  };
+  double best_f = h->factors[0];
+  float best = 1e30f;
+  h->L.resolve_block = 32;
+  for (double f : h->factors) {
+    apply_factor(h, f);
+    const float ms = std::min(trial(), trial());
+    if (ms < best) {
+      best = ms;
+      best_f = f;
+    }
+  }
+  apply_factor(h, best_f);
+  h->factor = best_f;
+  int best_rb = h->L.resolve_block;
+  for (int rb : {32, 64, 128}) {
+    h->L.resolve_block = rb;
+    const float ms = std::min(trial(), trial());
+    if (ms < best) {
+      best = ms;
+      best_rb = rb;
+    }
+  }
+  h->L.resolve_block = best_rb;
+  h->tuned_ms = best / 6.0;
+  restore();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sx);
+  cudaFree(si);
+  return cudaGetLastError();
+}
+
 extern "C" {
 
 const char* rd_strerror(int status) {
@@ -241,9 +395,21 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   const bool mixed = c.precision == RD_MIXED;
   h->vsize = mixed ? 16 : 32;
 
-  // cell grids: edge >= the largest cut-off (with a relative margin against rounding)
+  // cell grids: edge >= the largest cut-off (with a relative margin against rounding); the edge
+  // factor is explicit (cell_factor_x100 > 0), density-based (0) or autotuned (< 0)
   const double rc = max_cutoff(c);
-  const double factor = (c.cell_factor_x100 > 0 ? c.cell_factor_x100 : 100) / 100.0;
+  const uint32_t bmask = h->hp.binned_mask;
+  const double f_auto = density_factor(c, h->reps_host, bmask, rc);
+  std::vector<double> factors;
+  if (c.cell_factor_x100 > 0) {
+    factors.push_back(c.cell_factor_x100 / 100.0);
+  } else if (c.cell_factor_x100 == 0) {
+    factors.push_back(f_auto);
+  } else {
+    factors.push_back(1.0);
+    for (double m : {0.6, 1.0, 1.5})
+      if (f_auto * m > 1.05) factors.push_back(f_auto * m);
+  }
   int64_t total_cells = 0, n_total = 0;
   h->reps_init.resize(c.n_replicas);
   for (int r = 0; r < c.n_replicas; ++r) {
@@ -254,18 +420,6 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
     d.half_L = 0.5 * rp.L;
     d.Lf = (float)rp.L;
     d.half_Lf = 0.5f * d.Lf;
-    for (int a = 0; a < 3; ++a) {
-      int n = 1;
-      if (a < c.dim && rc > 0.0) {
-        const double m = std::floor(rp.L / (rc * factor * (1.0 + 1e-6)));
-        n = m >= 3.0 ? (int)std::min(m, 2048.0) : 1;
-      }
-      d.nc[a] = n;
-      d.inv_edge[a] = n / rp.L;
-      d.inv_edge_f[a] = (float)d.inv_edge[a];
-    }
-    d.cell_base = total_cells;
-    total_cells += (int64_t)d.nc[0] * d.nc[1] * d.nc[2];
     int64_t nr = 0;
     for (int s = 0; s < c.n_species; ++s) nr += rp.n_init[s];
     d.beg = (uint32_t)n_total;
@@ -273,7 +427,15 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
     d.next_id = (uint32_t)nr;
     n_total += nr;
   }
-  if (total_cells >= (int64_t)0xFFFFFFF0) {
+  int64_t max_cells = 0;
+  {
+    std::vector<RepDev> tmp = h->reps_init;
+    for (double f : factors) max_cells = std::max(max_cells, layout_cells(c, h->reps_host, bmask, rc, f, tmp));
+  }
+  total_cells = layout_cells(c, h->reps_host, bmask, rc, factors[0], h->reps_init);
+  h->factors = factors;
+  h->factor = factors[0];
+  if (max_cells >= (int64_t)0xFFFFFFF0) {
     delete h;
     return RD_EINVAL;
   }
@@ -298,8 +460,9 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.total_cells = total_cells;
   L.n_counts = c.n_replicas * c.n_species;
   const int64_t chunk = 256 * (int64_t)L.scan_items;
-  const int64_t nbc = (total_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
+  const int64_t nbc = (max_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
   L.flag_stride = std::max(nbc, nbp) + 1;
+  L.resolve_block = 32;
 
   bool ok = true;
   auto A = [&](size_t bytes) {
@@ -326,8 +489,8 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.best_key = (unsigned long long*)A(cap * 8);
   L.best_pid = (unsigned long long*)A(cap * 8);
   L.scan = (unsigned long long*)A((cap + 1) * 8);
-  L.cell_count = (uint32_t*)A(total_cells * 4);
-  L.cell_start = (uint32_t*)A((total_cells + 1) * 4);
+  L.cell_count = (uint32_t*)A(max_cells * 4);
+  L.cell_start = (uint32_t*)A((max_cells + 1) * 4);
   L.agg32 = (uint32_t*)A((nbc + 1) * 4);
   L.incl32 = (uint32_t*)A((nbc + 1) * 4);
   L.agg64 = (unsigned long long*)A((nbp + 1) * 8);
@@ -356,7 +519,8 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
     return cuda_fail(e);
   };
   cudaError_t e = cudaSuccess;
-  e = cudaMemsetAsync(L.cell_count, 0, total_cells * 4, h->stream);
+  e = cudaMemsetAsync(L.cell_count, 0, max_cells * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.deg, 0, cap * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.flags, 0, 2 * L.flag_stride * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.status, 0, cap * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync((void*)L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice, h->stream);
@@ -405,6 +569,10 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(e);
+  if (c.cell_factor_x100 < 0 && n_total > 0) {
+    e = autotune(h);
+    if (e != cudaSuccess) return fail(e);
+  }
   *out = h;
   return RD_OK;
 }
@@ -656,6 +824,15 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
   return ctl.status;
 }
 
+int rd_info(rd_handle* h, double* out, int32_t n) {
+  if (!h || !out || n < 0) return RD_EINVAL;
+  const double v[7] = {h->factor, (double)h->L.total_cells, (double)h->L.resolve_block,
+                       (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
+                       max_cutoff(h->cfg)};
+  for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
+  return RD_OK;
+}
+
 int rd_time_kernels(rd_handle* h, int32_t enable) {
   if (!h) return RD_EINVAL;
   h->time_next = enable != 0;
@@ -850,6 +1027,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.block = 256;
   L.max_grid = 152 * 16;
   L.scan_items = 8;
+  L.resolve_block = 32;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;
   L.total_cells = cells;
@@ -905,6 +1083,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   // the array keeps the previous call's contents: reset what the step expects to start at zero
   RD_CUDA(cudaMemsetAsync(L.cell_count, 0, (size_t)cells * 4, s));
   RD_CUDA(cudaMemsetAsync(L.flags, 0, (size_t)(2 * L.flag_stride) * 4, s));
+  RD_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)cap * 4, s));
   RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
   RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemcpyAsync(L.reps, &rep, sizeof rep, cudaMemcpyHostToDevice, s));

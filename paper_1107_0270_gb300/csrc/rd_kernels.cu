@@ -97,8 +97,6 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
       }
     }
     status[i] = st;
-    matched[i] = -1;
-    deg[i] = 0u;
     typename V4<T>::type q = p;
     if (!st) {
       if constexpr (sizeof(T) == 8) {
@@ -320,8 +318,9 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                                                const uint32_t* __restrict__ cell_start,
                                                const int64_t total_cells, FiredPair* __restrict__ fired,
                                                uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
-                                               const uint32_t cap_pairs) {
+                                               int32_t* __restrict__ matched, const uint32_t cap_pairs) {
   const DevParams& P = *Pp;
+  __shared__ uint2 ranges[14][256];
   if (ctl->status) return;
   const uint32_t nb = cell_start[total_cells];
   const uint32_t step = ctl->step;
@@ -351,20 +350,29 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
       const int ox = rep.nc[0] >= 3 ? 1 : 0, oy = rep.nc[1] >= 3 ? 1 : 0;
       const int oz = (dim == 3 && rep.nc[2] >= 3) ? 1 : 0;
       // forward half of the neighbour stencil: every unordered pair of neighbouring cells once,
-      // pairs inside the own cell with j > k
-      for (int dz = -oz; dz <= oz; ++dz) {
-        int zz = cz + dz;
-        zz = zz < 0 ? zz + rep.nc[2] : (zz >= rep.nc[2] ? zz - rep.nc[2] : zz);
-        for (int dy = -oy; dy <= oy; ++dy) {
-          int yy = cy + dy;
+      // pairs inside the own cell with j > k.  All 14 cell ranges are fetched first (independent
+      // loads in flight together), then walked.
+#pragma unroll
+      for (int t = 0; t < 14; ++t) {
+        const int dz = t < 5 ? 0 : 1;
+        const int dy = t < 2 ? 0 : (t < 5 ? 1 : (t - 5) / 3 - 1);
+        const int dx = t < 2 ? t : (t < 5 ? t - 3 : (t - 5) % 3 - 1);
+        uint2 rg = make_uint2(0u, 0u);
+        if ((dx == 0 || ox) && (dy == 0 || oy) && (dz == 0 || oz)) {
+          int xx = cx + dx, yy = cy + dy, zz = cz + dz;
+          xx = xx < 0 ? xx + rep.nc[0] : (xx >= rep.nc[0] ? xx - rep.nc[0] : xx);
           yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
-          for (int dx = -ox; dx <= ox; ++dx) {
-            const int code = dz * 9 + dy * 3 + dx;
-            if (code < 0) continue;
-            int xx = cx + dx;
-            xx = xx < 0 ? xx + rep.nc[0] : (xx >= rep.nc[0] ? xx - rep.nc[0] : xx);
-            const int64_t c = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * rep.nc[0] + xx;
-            const uint32_t jb = code == 0 ? k + 1 : cell_start[c], je = cell_start[c + 1];
+          zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
+          const int64_t c = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * rep.nc[0] + xx;
+          rg = make_uint2(t == 0 ? k + 1 : cell_start[c], cell_start[c + 1]);
+        }
+        ranges[t][threadIdx.x] = rg;
+      }
+      for (int t = 0; t < 14; ++t) {
+        const uint2 rg = ranges[t][threadIdx.x];
+        {
+          {
+            const uint32_t jb = rg.x, je = rg.y;
             for (uint32_t j = jb; j < je; ++j) {
               const auto b0 = sx0[j];
               const uint32_t spb = w_bits(b0.w) & 0xFFu;
@@ -377,6 +385,7 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
               const bool swap = idb < ida;
               const uint32_t id_lo = swap ? idb : ida, id_hi = swap ? ida : idb;
               double p;
+              float pf = 0.0f;
               bool overlap;
               if constexpr (sizeof(T) == 8) {
                 const double sg = swap ? -1.0 : 1.0;
@@ -404,14 +413,21 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                 const float d0 = (sqrtf(r02) - pr.sigma_f) * pr.inv_sigma_f;
                 const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
                 overlap = d <= 0.0f;
-                p = (double)p_enc3_f(d, d0, pr.inv_tau_f);
+                pf = p_enc3_f(d, d0, pr.inv_tau_f);
+                p = (double)pf;
               }
               const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
-              const double u_enc = u52(w.x, w.y);
               ++n_cand;
               n_overlap += overlap;
-              n_near += fabs(u_enc - p) <= 1e-9;
-              if (u_enc < p) {
+              bool fires;
+              if constexpr (sizeof(T) == 8) {
+                const double u_enc = u52(w.x, w.y);
+                n_near += fabs(u_enc - p) <= 1e-9;
+                fires = u_enc < p;
+              } else {
+                fires = u23(w.x) < pf;     // mixed step: FP32 draw and comparison
+              }
+              if (fires) {
                 const unsigned m = __activemask();
                 const int lane = threadIdx.x & 31;
                 const int leader = __ffs(m) - 1;
@@ -427,9 +443,14 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                   f.ida = id_lo;
                   f.idb = id_hi;
                   f.p = p;
-                  f.key = -log(u52(w.z, w.w)) / p;
+                  if constexpr (sizeof(T) == 8)
+                    f.key = -log(u52(w.z, w.w)) / p;
+                  else
+                    f.key = (double)(-logf(u23(w.z)) / pf);
                   fired[pos] = f;
                   fstate[pos] = FS_LIVE | ((uint32_t)rule << 2) | (r << 8);
+                  matched[f.ia] = -1;
+                  matched[f.ib] = -1;
                   atomicAdd(&deg[f.ia], 1u);
                   atomicAdd(&deg[f.ib], 1u);
                 } else {
@@ -944,7 +965,7 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
 // One work list: accepted pairs first, then decays; one warp per block so that the FP64-bound
 // items spread over all SMs.
 template <class T>
-__global__ void __launch_bounds__(32) k_resolve_all(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(128) k_resolve_all(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
                                                     const RepDev* __restrict__ reps, const FiredPair* __restrict__ fired,
                                                     const uint32_t* __restrict__ fstate,
                                                     const uint32_t* __restrict__ accepted,
@@ -952,8 +973,15 @@ __global__ void __launch_bounds__(32) k_resolve_all(const DevParams* __restrict_
                                                     const typename V4<T>::type* __restrict__ x0,
                                                     typename V4<T>::type* __restrict__ x1,
                                                     const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-                                                    typename V4<T>::type* __restrict__ prodpos) {
+                                                    typename V4<T>::type* __restrict__ prodpos,
+                                                    uint32_t* __restrict__ deg, uint32_t cap_pairs) {
   const DevParams& P = *Pp;
+  // the encounter degrees of this step go back to zero for the next one
+  const uint32_t nf = min(ctl->fired, cap_pairs);
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    deg[fired[e].ia] = 0u;
+    deg[fired[e].ib] = 0u;
+  }
   if (ctl->status) return;
   const uint32_t na = ctl->n_accept, nd = ctl->n_decay, step = ctl->step;
   unsigned long long n_react = 0, n_res = 0, n_near = 0, n_rec = 0;
@@ -1199,7 +1227,7 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   k_scatter_cells<T><<<Gp, B, 0, s>>>(L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1, L.sidx);
   mark("k_scatter_cells");
   k_sweep<T><<<Gp, 256, 0, s>>>(L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired,
-                                 L.fstate, L.deg, (uint32_t)L.cap_pairs);
+                                 L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs);
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
   k_match_trivial<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted, L.best_key,
@@ -1207,8 +1235,9 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   k_match_rounds<<<1, 1024, 0, s>>>(L.P, L.ctl, L.fired, L.fstate, L.matched, L.conflict, L.accepted, L.best_key,
                                     L.best_pid);
   mark("k_match");
-  k_resolve_all<T><<<152 * 8, 32, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted, L.decay_list, x0, x1,
-                                          L.id_cur, L.status, prod);
+  const int rb = L.resolve_block > 0 ? L.resolve_block : 32;
+  k_resolve_all<T><<<(152 * 8 * 32) / rb, rb, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted, L.decay_list,
+                                                       x0, x1, L.id_cur, L.status, prod, L.deg, (uint32_t)L.cap_pairs);
   mark("k_resolve_all");
   const int nbp = (int)((L.cap_particles + tile - 1) / tile);
   k_scan1<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, 0, &L.ctl->n, L.scan, nullptr,

@@ -17,6 +17,7 @@ struct StepLaunch {
   int block;
   int max_grid;
   int scan_items;
+  int resolve_block;           // threads per block of the resolution kernel (32..128)
   int64_t cap_particles, cap_pairs, total_cells;
   int n_counts;
   const DevParams* P;

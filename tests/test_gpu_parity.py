@@ -231,3 +231,20 @@ def test_set_state_then_step_matches_oracle():
     sim.step()
     compare_states(sim.get_state(), o2, system.L)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cell_layout_and_autotune_do_not_change_results(precision):
+    # every decision is keyed by particle ids, so the cell edge, the block shapes and the
+    # autotuner's choice must leave the trajectory bit-identical
+    system = dense_reversible(n_each=1500, conc_uM=20.0, dt=2e-5)
+    states = []
+    for cf in (1.0, 2.5, None, "tune"):
+        sim = pkg.Simulation(system, precision=precision, cell_factor=cf)
+        sim.run(9)
+        states.append(sim.get_state())
+        sim.close()
+    for st in states[1:]:
+        assert np.array_equal(st["ids"], states[0]["ids"])
+        assert np.array_equal(st["species"], states[0]["species"])
+        assert np.array_equal(st["x"], states[0]["x"])
