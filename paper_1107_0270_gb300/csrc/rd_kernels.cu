@@ -172,16 +172,36 @@ __device__ __forceinline__ U block_exclusive_scan(U v, U* smem, U& total) {
 
 struct LoadCellCount {
   const uint32_t* cnt;
-  __device__ uint32_t operator()(int64_t i) const { return cnt[i]; }
+  // 8 consecutive elements starting at i (i % 8 == 0); elements >= n read as 0
+  __device__ __forceinline__ void load8(int64_t i, int64_t n, uint32_t v[8]) const {
+    if (i + 8 <= n) {
+      const uint4 a = __ldcg(reinterpret_cast<const uint4*>(cnt + i));
+      const uint4 b = __ldcg(reinterpret_cast<const uint4*>(cnt + i) + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = i + k < n ? cnt[i + k] : 0u;
+    }
+  }
 };
 
 struct LoadCompact {
   const uint32_t* status;
-  __device__ unsigned long long operator()(int64_t i) const {
-    const uint32_t s = status[i];
+  __device__ __forceinline__ static unsigned long long conv(uint32_t s) {
     const unsigned long long surv = (s & ST_CONSUMED) ? 0ull : 1ull;
     const unsigned long long np = (s >> ST_NPROD_SHIFT) & 3u;
     return (surv << 32) | np;
+  }
+  __device__ __forceinline__ void load8(int64_t i, int64_t n, unsigned long long v[8]) const {
+    if (i + 8 <= n) {
+      const uint4 a = __ldcg(reinterpret_cast<const uint4*>(status + i));
+      const uint4 b = __ldcg(reinterpret_cast<const uint4*>(status + i) + 1);
+      v[0] = conv(a.x); v[1] = conv(a.y); v[2] = conv(a.z); v[3] = conv(a.w);
+      v[4] = conv(b.x); v[5] = conv(b.y); v[6] = conv(b.z); v[7] = conv(b.w);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = i + k < n ? conv(status[i + k]) : 0ull;
+    }
   }
 };
 
@@ -209,17 +229,19 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
   const int64_t ntiles = n > 0 ? (n + tile_elems - 1) / tile_elems : 1;
   if ((int64_t)tile >= ntiles) return;
   const uint32_t epoch = (ctl->epoch * 2u + (uint32_t)which) & 0x3FFFFFFFu;
-  const int64_t base = (int64_t)tile * tile_elems;
+  const int64_t base = (int64_t)tile * tile_elems + (int64_t)threadIdx.x * kScanItems;
+  // blocked arrangement: each thread owns kScanItems consecutive elements
+  U v[kScanItems];
+  load.load8(base, n, v);
   U ex[kScanItems];
-  U tot = 0;
+  U run = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
-    const U v = i < n ? load(i) : U(0);
-    U t;
-    ex[k] = tot + block_exclusive_scan<U, Load>(v, sm, t);
-    tot += t;
+    ex[k] = run;
+    run += v[k];
   }
+  U tot;
+  const U toff = block_exclusive_scan<U, Load>(run, sm, tot);
   if (threadIdx.x < 32) {
     // warp 0: publish the aggregate, then look back over windows of 32 predecessors at once
     const int lane = threadIdx.x;
@@ -246,11 +268,11 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
         __threadfence();
         const unsigned incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (f & 3u) == 2u);
         const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;   // nearest inclusive predecessor
-        U v = 0;
-        if (q >= 0 && lane <= stop) v = lane == stop ? *(volatile U*)&incl[q] : *(volatile U*)&agg[q];
+        U vv = 0;
+        if (q >= 0 && lane <= stop) vv = lane == stop ? *(volatile U*)&incl[q] : *(volatile U*)&agg[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        prefix += v;
+        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
+        prefix += vv;
         if (incl_mask || top < 32) break;
         top -= 32;
       }
@@ -263,16 +285,31 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
     }
   }
   __syncthreads();
-  const U prefix = s_prefix;
+  const U prefix = s_prefix + toff;
+  if (base + kScanItems <= n) {
+    U o[kScanItems];
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
-    if (i < n) {
-      out[i] = prefix + ex[k];
-      if (zero_after) zero_after[i] = 0u;
+    for (int k = 0; k < kScanItems; ++k) o[k] = prefix + ex[k];
+    uint4* dst = reinterpret_cast<uint4*>(out + base);
+    const uint4* src = reinterpret_cast<const uint4*>(o);
+#pragma unroll
+    for (int k = 0; k < (int)(kScanItems * sizeof(U) / 16); ++k) dst[k] = src[k];
+    if (zero_after) {
+      uint4* z = reinterpret_cast<uint4*>(zero_after + base);
+      z[0] = make_uint4(0u, 0u, 0u, 0u);
+      z[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int64_t i = base + k;
+      if (i < n) {
+        out[i] = prefix + ex[k];
+        if (zero_after) zero_after[i] = 0u;
+      }
     }
   }
-  if (threadIdx.x == 0 && (int64_t)tile == ntiles - 1) out[n > 0 ? n : 0] = prefix + tot;
+  if (threadIdx.x == 0 && (int64_t)tile == ntiles - 1) out[n > 0 ? n : 0] = s_prefix + tot;
 }
 
 // ================================================================================================
