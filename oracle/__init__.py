@@ -88,7 +88,7 @@ def lib():
                            ("or_erfcx", [d]), ("or_gfree2", [d, d, d]),
                            ("or_p_enc2", [d, d, d, d]), ("or_p_reac2", [d, d, d, d, d]),
                            ("or_tail2", [d, d, d, d]), ("or_resample2", [d, d, d, d]),
-                           ("or_gbc2_weber", [C.c_int, d, d, d, d])]:
+                           ("or_gbc2_weber", [C.c_int, d, d, d, d]), ("or_S_abs2", [d, d])]:
             fn = getattr(L, name)
             fn.restype = d
             fn.argtypes = args
@@ -186,6 +186,10 @@ def p_reac2(R, R0, tau, h, tau_s=0.01):
 
 def tail2(V, R0, tau, tau_s=0.01):
     return lib().or_tail2(V, R0, tau, tau_s)
+
+
+def S_abs2(R0, tau):
+    return lib().or_S_abs2(R0, tau)
 
 
 def resample2(U, R0, tau, tau_s=0.01):

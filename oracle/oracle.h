@@ -94,6 +94,7 @@ double or_p_enc2(double R, double R0, double tau, double tau_s);
 double or_p_reac2(double R, double R0, double tau, double h, double tau_s);
 double or_tail2(double V, double R0, double tau, double tau_s);
 double or_resample2(double U, double R0, double tau, double tau_s);
+double or_S_abs2(double R0, double tau);
 
 /* Whole step and initial condition. */
 int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st);

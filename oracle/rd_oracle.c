@@ -26,6 +26,7 @@
  *    are next_id + rank of the event ordered by its lower parent id; survivors keep their order
  *    and products are appended, so the particle array stays sorted by id.
  */
+#define _DEFAULT_SOURCE
 #include "oracle.h"
 
 #include <math.h>
@@ -213,17 +214,371 @@ double or_S_rad3(double R0, double tau, double h) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
-/* 2D routines are added with the 2D step.                                                       */
+/* Adaptive Gauss-Legendre quadrature.  The 16-point nodes and weights are computed once by       */
+/* Newton's method on the Legendre polynomial (three-term recurrence); an interval is accepted     */
+/* when the rule on it and the rule on its two halves agree within the tolerance.               */
 /* ------------------------------------------------------------------------------------------ */
-double or_ierfc_scaled(int n, double z) { (void)n; (void)z; return NAN; }
-double or_gamma2(int k, int bc, double R, double R0, double h) { (void)k; (void)bc; (void)R; (void)R0; (void)h; return NAN; }
-double or_gbc2_series(int bc, double R, double R0, double tau, double h, int nterms) { (void)bc; (void)R; (void)R0; (void)tau; (void)h; (void)nterms; return NAN; }
-double or_gbc2_weber(int bc, double R, double R0, double tau, double h) { (void)bc; (void)R; (void)R0; (void)tau; (void)h; return NAN; }
-double or_gfree2(double R, double R0, double tau) { (void)R; (void)R0; (void)tau; return NAN; }
-double or_p_enc2(double R, double R0, double tau, double tau_s) { (void)R; (void)R0; (void)tau; (void)tau_s; return NAN; }
-double or_p_reac2(double R, double R0, double tau, double h, double tau_s) { (void)R; (void)R0; (void)tau; (void)h; (void)tau_s; return NAN; }
-double or_tail2(double V, double R0, double tau, double tau_s) { (void)V; (void)R0; (void)tau; (void)tau_s; return NAN; }
-double or_resample2(double U, double R0, double tau, double tau_s) { (void)U; (void)R0; (void)tau; (void)tau_s; return NAN; }
+#define GL_N 16
+static double gl_x[GL_N], gl_w[GL_N];
+static int gl_ready = 0;
+
+static void gl_init(void) {
+  if (gl_ready) return;
+  for (int i = 0; i < GL_N; ++i) {
+    double x = cos(PI * (i + 0.75) / (GL_N + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= GL_N; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = GL_N * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    gl_x[i] = x;
+    gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  gl_ready = 1;
+}
+
+typedef double (*or_fn)(double, const void*);
+
+static double gl_rule(or_fn f, const void* ctx, double a, double b) {
+  double m = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
+  for (int i = 0; i < GL_N; ++i) s += gl_w[i] * f(m + h * gl_x[i], ctx);
+  return s * h;
+}
+
+static double gl_adapt(or_fn f, const void* ctx, double a, double b, double whole, double tol, int depth,
+                       long* budget) {
+  double m = 0.5 * (a + b);
+  double left = gl_rule(f, ctx, a, m), right = gl_rule(f, ctx, m, b);
+  *budget -= 2 * GL_N;
+  if (depth <= 0 || *budget <= 0 || fabs(left + right - whole) <= tol) return left + right;
+  return gl_adapt(f, ctx, a, m, left, 0.5 * tol, depth - 1, budget) +
+         gl_adapt(f, ctx, m, b, right, 0.5 * tol, depth - 1, budget);
+}
+
+/* integral of f over [a,b]: `pieces` equal panels, each refined until halving changes it by less
+ * than its share of rel * |first estimate| (at most 4e6 integrand evaluations in all) */
+static double integrate(or_fn f, const void* ctx, double a, double b, int pieces, double rel) {
+  gl_init();
+  double hstep = (b - a) / pieces, first = 0.0, scale = 0.0;
+  double est[4096];
+  if (pieces > 4096) pieces = 4096;
+  for (int k = 0; k < pieces; ++k) {
+    est[k] = gl_rule(f, ctx, a + k * hstep, a + (k + 1) * hstep);
+    first += est[k];
+    scale += fabs(est[k]);
+  }
+  double tol = rel * (scale > 0.0 ? scale : 1.0) + 1e-300;
+  long budget = 4000000;
+  double s = 0.0;
+  for (int k = 0; k < pieces; ++k)
+    s += gl_adapt(f, ctx, a + k * hstep, a + (k + 1) * hstep, est[k], tol / pieces, 30, &budget);
+  (void)first;
+  return s;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* 2D, Section 4.2.  Scaled units a = 1, tau = D t / a^2, h = kappa_a / (2 pi D) (Eq. 2Dh).        */
+/* ------------------------------------------------------------------------------------------ */
+
+/* e^{z^2} i^n erfc(z) for n >= -1, z >= 0, from the recursion 2n i^n erfc = i^{n-2} erfc -
+ * 2z i^{n-1} erfc (Section 4.2) with i^{-1} erfc = (2/sqrt(pi)) e^{-z^2}, i^0 erfc = erfc.  Each
+ * direction is used where it is stable: upward for z < 1, and for z >= 1 downward on the ratios
+ * r_n = i^n erfc / i^{n-1} erfc, r_{n-1} = 1/(2z + 2n r_n), started at a high order from the
+ * asymptotic ratio (Miller's backward recurrence). */
+double or_ierfc_scaled(int n, double z) {
+  if (n == -1) return 2.0 / SQRT_PI;
+  double f = or_erfcx(z);
+  if (n == 0) return f;
+  if (z < 1.0) {
+    double fm2 = 2.0 / SQRT_PI, fm1 = f;
+    for (int k = 1; k <= n; ++k) {
+      double fk = (fm2 - 2.0 * z * fm1) / (2.0 * k);
+      fm2 = fm1;
+      fm1 = fk;
+    }
+    return fm1;
+  }
+  int M = n + 300;
+  double r = (-z + sqrt(z * z + 2.0 * M)) / (2.0 * M);
+  double ratio[64];
+  for (int k = M; k >= 1; --k) {
+    if (k <= n) ratio[k] = r;
+    r = 1.0 / (2.0 * z + 2.0 * k * r);
+  }
+  for (int k = 1; k <= n; ++k) f *= ratio[k];
+  return f;
+}
+
+/* a_k(nu) of the large-argument expansions of I_nu and K_nu (Eq. coeffDef) */
+static double a_coef(int k, double nu) {
+  double v = 1.0;
+  for (int j = 1; j <= k; ++j) v *= (4.0 * nu * nu - (2.0 * j - 1.0) * (2.0 * j - 1.0)) / (8.0 * j);
+  return v;
+}
+
+/* power-series division c = a / b up to order n */
+static void series_div(const double* a, const double* b, double* c, int n) {
+  for (int k = 0; k <= n; ++k) {
+    double v = a[k];
+    for (int j = 1; j <= k; ++j) v -= b[j] * c[k - j];
+    c[k] = v / b[0];
+  }
+}
+
+static void series_mul(const double* a, const double* b, double* c, int n) {
+  for (int k = 0; k <= n; ++k) {
+    double v = 0.0;
+    for (int j = 0; j <= k; ++j) v += a[j] * b[k - j];
+    c[k] = v;
+  }
+}
+
+/* gamma_k of the expansions (expansionLaplace): with y = 1/q~, the boundary quotient of Eqs.
+ * (absPert), (refPert), (radPert) divided by its leading exponential is I0/K0 (abs), I1/K1 (ref)
+ * or (I1 - h y I0)/(K1 + h y K0) (rad), expanded with the a_k series (I'_0 = I_1, K'_0 = -K_1), and
+ * multiplied by the K_0(q~R0) K_0(q~R) series.  Returns gamma_k, k = 0..24. */
+static void gamma_series(int bc, double R, double R0, double h, int n, double* g) {
+  double A0[32], A0m[32], A1[32], A1m[32], num[32], den[32], ratio[32], k0a[32], k0b[32], kk[32];
+  for (int k = 0; k <= n; ++k) {
+    double sgn = (k & 1) ? -1.0 : 1.0;
+    A0[k] = a_coef(k, 0.0);
+    A0m[k] = sgn * A0[k];
+    A1[k] = a_coef(k, 1.0);
+    A1m[k] = sgn * A1[k];
+    k0a[k] = A0[k] / pow(R0, k);
+    k0b[k] = A0[k] / pow(R, k);
+  }
+  for (int k = 0; k <= n; ++k) {
+    if (bc == OR_BC_ABS) {
+      num[k] = A0m[k];
+      den[k] = A0[k];
+    } else {
+      double hh = bc == OR_BC_RAD ? h : 0.0;
+      num[k] = A1m[k] - (k > 0 ? hh * A0m[k - 1] : 0.0);
+      den[k] = A1[k] + (k > 0 ? hh * A0[k - 1] : 0.0);
+    }
+  }
+  series_div(num, den, ratio, n);
+  series_mul(k0a, k0b, kk, n);
+  series_mul(ratio, kk, g, n);
+}
+
+double or_gamma2(int k, int bc, double R, double R0, double h) {
+  double g[32];
+  if (k < 0 || k > 24) return NAN;
+  gamma_series(bc, R, R0, h, k, g);
+  return g[k];
+}
+
+/* bracket of Eqs. (smallTEabs)/(smallTEabsII) after factoring out e^{-z^2}:
+ * pi^{-1/2} + (1/2) sum_{n=1}^{N} gamma_n e^{z^2} i^{n-1} erfc(z) (2 sqrt(tau))^n */
+static double series_bracket(int bc, double R, double R0, double tau, double h, int N) {
+  double g[32];
+  gamma_series(bc, R, R0, h, N, g);
+  double s = sqrt(tau), z = (R + R0 - 2.0) / (2.0 * s), sum = 1.0 / SQRT_PI, p = 1.0;
+  for (int n = 1; n <= N; ++n) {
+    p *= 2.0 * s;
+    sum += 0.5 * g[n] * or_ierfc_scaled(n - 1, z) * p;
+  }
+  return sum;
+}
+
+/* boundary part g_bc of the radial Green's function, Eqs. (smallTEabs), (smallTEabsII) */
+double or_gbc2_series(int bc, double R, double R0, double tau, double h, int nterms) {
+  double s = sqrt(tau), z = (R + R0 - 2.0) / (2.0 * s);
+  double pref = exp(-z * z) / (4.0 * PI * sqrt(tau * R * R0));
+  double sign = bc == OR_BC_ABS ? -1.0 : 1.0;
+  return sign * pref * series_bracket(bc, R, R0, tau, h, nterms);
+}
+
+/* e^{-x} I0(x): power series below x = 30, large-argument series above */
+static double i0e(double x) {
+  if (x < 30.0) {
+    double t = 1.0, s = 1.0, q = 0.25 * x * x;
+    for (int k = 1; k < 400; ++k) {
+      t *= q / ((double)k * k);
+      s += t;
+      if (t < 1e-17 * s) break;
+    }
+    return s * exp(-x);
+  }
+  double s = 0.0, t = 1.0;
+  for (int k = 0; k < 30; ++k) {
+    if (k > 0) t *= (2.0 * k - 1.0) * (2.0 * k - 1.0) / (8.0 * k * x);
+    s += t;
+  }
+  return s / sqrt(2.0 * PI * x);
+}
+
+/* radial free function: angular average of the free Gaussian of Section 2.1 in 2D */
+double or_gfree2(double R, double R0, double tau) {
+  return exp(-(R - R0) * (R - R0) / (4.0 * tau)) * i0e(R * R0 / (2.0 * tau)) / (4.0 * PI * tau);
+}
+
+/* C_0(R, x) of Eq. (fRad), with J_0' = -J_1, Y_0' = -Y_1:
+ * C_0 = [Y0(Rx) alpha - J0(Rx) beta] / sqrt(alpha^2 + beta^2), alpha = x J1(x) + h J0(x),
+ * beta = x Y1(x) + h Y0(x); absorbing is the h -> infinity limit (alpha = J0, beta = Y0). */
+static void c0_coeffs(int bc, double x, double h, double* al, double* be, double* nrm) {
+  if (bc == OR_BC_ABS) {
+    *al = j0(x);
+    *be = y0(x);
+  } else {
+    double hh = bc == OR_BC_RAD ? h : 0.0;
+    *al = x * j1(x) + hh * j0(x);
+    *be = x * y1(x) + hh * y0(x);
+  }
+  *nrm = sqrt((*al) * (*al) + (*be) * (*be));
+}
+
+typedef struct {
+  double R, R0, tau, h;
+  double coef[4];      /* weights of the abs, ref, rad products */
+  int cdf;             /* 0: g; 1: integral of 2 pi R g over (1, R) */
+} weber_ctx;
+
+/* integrand in t with x = t^2 (dx = 2t dt) */
+static double weber_integrand(double t, const void* vp) {
+  const weber_ctx* c = (const weber_ctx*)vp;
+  double x = t * t;
+  if (x <= 0.0) return 0.0;
+  double w = exp(-c->tau * x * x), s = 0.0;
+  for (int bc = OR_BC_ABS; bc <= OR_BC_RAD; ++bc) {
+    if (c->coef[bc] == 0.0) continue;
+    double al, be, nr;
+    c0_coeffs(bc, x, c->h, &al, &be, &nr);
+    double c0r0 = (y0(c->R0 * x) * al - j0(c->R0 * x) * be) / nr;
+    double other;
+    if (!c->cdf) {
+      other = (y0(c->R * x) * al - j0(c->R * x) * be) / nr;                    /* C_0(R, x) */
+    } else {
+      /* integral of R' C_0(R', x) over (1, R): R' Z_1(R' x) / x is an antiderivative of R' Z_0(R' x) */
+      double hi = c->R * (y1(c->R * x) * al - j1(c->R * x) * be);
+      double lo = y1(x) * al - j1(x) * be;
+      other = (hi - lo) / (x * nr);
+    }
+    s += c->coef[bc] * c0r0 * other;
+  }
+  return w * s * x * 2.0 * t;
+}
+
+static double weber(weber_ctx* c) {
+  double T = pow(60.0 / c->tau, 0.25);
+  double rmax = c->R > c->R0 ? c->R : c->R0;
+  int pieces = 8 + (int)(rmax * T * T / 3.0);
+  double v = integrate(weber_integrand, c, 0.0, T, pieces, 1e-14);
+  return c->cdf ? v : v / (2.0 * PI);
+}
+
+/* the exact radial Green's function from the n = 0 term of Eq. (genericGF):
+ * g = (1/2pi) int_0^inf e^{-tau x^2} C_0(R,x) C_0(R0,x) x dx; returns the boundary part g - g_free */
+double or_gbc2_weber(int bc, double R, double R0, double tau, double h) {
+  weber_ctx c = {R, R0, tau, h, {0, 0, 0, 0}, 0};
+  c.coef[bc] = 1.0;
+  return weber(&c) - or_gfree2(R, R0, tau);
+}
+
+/* Eq. (bayes1D) in 2D: p_enc = 1 - g_abs/g_free = -g_abs^bc/g_free.  In the small-time regime
+ * (tau <= tau_s) both g_abs^bc (Eq. smallTEabs, prefactor e^{-(R+R0-2)^2/4tau}/(4 pi sqrt(tau R R0)))
+ * and g_free (prefactor e^{-(R-R0)^2/4tau}/(4 pi tau)) carry Gaussian factors whose ratio is
+ * e^{-(R-1)(R0-1)/tau}, so p_enc = e^{-(R-1)(R0-1)/tau} sqrt(tau) B_abs / (sqrt(R R0) I0e(R R0/2tau))
+ * with B_abs the bracket of Eq. (smallTEabs); otherwise the Weber integral. */
+double or_p_enc2(double R, double R0, double tau, double tau_s) {
+  if (R <= 1.0) return 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  if (R0 == 1.0) return 1.0;
+  if (tau <= tau_s) {
+    double b = series_bracket(OR_BC_ABS, R, R0, tau, 0.0, 12);
+    return exp(-(R - 1.0) * (R0 - 1.0) / tau) * sqrt(tau) * b / (sqrt(R * R0) * i0e(R * R0 / (2.0 * tau)));
+  }
+  weber_ctx c = {R, R0, tau, 0.0, {0, 0, 0, 0}, 0};
+  c.coef[OR_BC_ABS] = 1.0;
+  return 1.0 - weber(&c) / or_gfree2(R, R0, tau);
+}
+
+/* Eq. (psurv_radII) in 2D; the free parts cancel (Section 4.2), and in the small-time regime so
+ * does the common prefactor of Eqs. (smallTEabs)/(smallTEabsII): p_reac = (B_ref - B_rad)/(B_ref + B_abs)
+ * with B the brackets (g_abs^bc carries the opposite sign). */
+double or_p_reac2(double R, double R0, double tau, double h, double tau_s) {
+  if (R < 1.0) R = 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  if (tau <= tau_s) {
+    double bref = series_bracket(OR_BC_REF, R, R0, tau, h, 12);
+    double brad = series_bracket(OR_BC_RAD, R, R0, tau, h, 12);
+    double babs = series_bracket(OR_BC_ABS, R, R0, tau, h, 12);
+    double p = (bref - brad) / (bref + babs);
+    return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+  }
+  weber_ctx num = {R, R0, tau, h, {0, 0, 0, 0}, 0}, den = {R, R0, tau, h, {0, 0, 0, 0}, 0};
+  num.coef[OR_BC_REF] = 1.0;
+  num.coef[OR_BC_RAD] = -1.0;
+  den.coef[OR_BC_REF] = 1.0;
+  den.coef[OR_BC_ABS] = -1.0;
+  double p = weber(&num) / weber(&den);
+  return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
+}
+
+/* density 2 pi R (g_ref - g_abs) of an encountered pair's new separation (small-time series) */
+typedef struct { double R0, tau; } dens_ctx;
+static double dens2_series(double R, const void* vp) {
+  const dens_ctx* c = (const dens_ctx*)vp;
+  return 2.0 * PI * R *
+         (or_gbc2_series(OR_BC_REF, R, c->R0, c->tau, 0.0, 12) - or_gbc2_series(OR_BC_ABS, R, c->R0, c->tau, 0.0, 12));
+}
+
+/* normalised tail T(V) of the propagator G_ref - G_abs beyond R = 1 + V (Section 3, "Details");
+ * the total over R > 1 is 1 - S_abs */
+/* unnormalised CDF of the new separation over (1, 1 + V): integral of 2 pi R (g_ref - g_abs) */
+static double cdf2(double V, double R0, double tau, double tau_s) {
+  if (tau <= tau_s) {
+    dens_ctx c = {R0, tau};
+    return integrate(dens2_series, &c, 1.0, 1.0 + V, 8, 1e-14);
+  }
+  weber_ctx c = {1.0 + V, R0, tau, 0.0, {0, 0, 0, 0}, 1};
+  c.coef[OR_BC_REF] = 1.0;
+  c.coef[OR_BC_ABS] = -1.0;
+  return weber(&c);
+}
+
+/* beyond 1 + vmax2 the density is below e^{-40} of its peak */
+static double vmax2(double R0, double tau) { return R0 + 13.0 * sqrt(tau); }
+
+double or_tail2(double V, double R0, double tau, double tau_s) {
+  if (R0 < 1.0) R0 = 1.0;
+  const double vmax = vmax2(R0, tau);
+  if (V >= vmax) return 0.0;
+  double t = 1.0 - cdf2(V, R0, tau, tau_s) / cdf2(vmax, R0, tau, tau_s);
+  return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+}
+
+/* encountered fraction 1 - S_abs(tau | R0) = integral of 2 pi R (g_ref - g_abs) over R > 1 */
+double or_S_abs2(double R0, double tau) {
+  if (R0 < 1.0) R0 = 1.0;
+  return 1.0 - cdf2(vmax2(R0, tau), R0, tau, 0.0);
+}
+
+double or_resample2(double U, double R0, double tau, double tau_s) {
+  if (R0 < 1.0) R0 = 1.0;
+  const double vmax = vmax2(R0, tau);
+  const double tot = cdf2(vmax, R0, tau, tau_s);
+  /* T(V) = 1 - cdf(V)/tot decreases from 1 to 0 on (0, vmax): bisection for T(V) = U */
+  double lo = 0.0, hi = vmax;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi || hi - lo < 1e-14 * (1.0 + hi)) break;
+    if (1.0 - cdf2(mid, R0, tau, tau_s) / tot > U)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 1.0 + 0.5 * (lo + hi);
+}
 
 /* ------------------------------------------------------------------------------------------ */
 /* Geometry in the periodic box.                                                                  */
