@@ -197,7 +197,8 @@ int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* ca
  * refused (inside a larger application's memory budget, under an allocator that forbids
  * allocation after start-up, or in a real-time loop that must not synchronise on an allocation).
  * rd_step_static advances a small single-replica system (cfg->n_replicas == 1, box edge
- * cfg->replicas[0].L; n_init is ignored) by one dt, exactly as rd_step does, without calling
+ * cfg->replicas[0].L; n_init is ignored; 3D only, RD_ENOTREADY otherwise) by one dt, exactly as
+ * rd_step does, without calling
  * cudaMalloc, cudaFree or any allocating routine: every scratch buffer of the step lives in one
  * fixed device array of RD_STATIC_SCRATCH_BYTES that the library reserves on every GPU that loads
  * it, until the process exits.

@@ -263,7 +263,7 @@ static double gl_adapt(or_fn f, const void* ctx, double a, double b, double whol
 }
 
 /* integral of f over [a,b]: `pieces` equal panels, each refined until halving changes it by less
- * than its share of rel * |first estimate| (at most 4e6 integrand evaluations in all) */
+ * than its share of rel * |first estimate| (at most 2e5 integrand evaluations in all) */
 static double integrate(or_fn f, const void* ctx, double a, double b, int pieces, double rel) {
   gl_init();
   double hstep = (b - a) / pieces, first = 0.0, scale = 0.0;
@@ -275,7 +275,7 @@ static double integrate(or_fn f, const void* ctx, double a, double b, int pieces
     scale += fabs(est[k]);
   }
   double tol = rel * (scale > 0.0 ? scale : 1.0) + 1e-300;
-  long budget = 4000000;
+  long budget = 200000;
   double s = 0.0;
   for (int k = 0; k < pieces; ++k)
     s += gl_adapt(f, ctx, a + k * hstep, a + (k + 1) * hstep, est[k], tol / pieces, 30, &budget);
@@ -305,7 +305,7 @@ double or_ierfc_scaled(int n, double z) {
     }
     return fm1;
   }
-  int M = n + 300;
+  int M = n + 120;
   double r = (-z + sqrt(z * z + 2.0 * M)) / (2.0 * M);
   double ratio[64];
   for (int k = M; k >= 1; --k) {
@@ -472,7 +472,7 @@ static double weber(weber_ctx* c) {
   double T = pow(60.0 / c->tau, 0.25);
   double rmax = c->R > c->R0 ? c->R : c->R0;
   int pieces = 8 + (int)(rmax * T * T / 3.0);
-  double v = integrate(weber_integrand, c, 0.0, T, pieces, 1e-14);
+  double v = integrate(weber_integrand, c, 0.0, T, pieces, 1e-13);
   return c->cdf ? v : v / (2.0 * PI);
 }
 
@@ -515,12 +515,13 @@ double or_p_reac2(double R, double R0, double tau, double h, double tau_s) {
     double p = (bref - brad) / (bref + babs);
     return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
   }
-  weber_ctx num = {R, R0, tau, h, {0, 0, 0, 0}, 0}, den = {R, R0, tau, h, {0, 0, 0, 0}, 0};
-  num.coef[OR_BC_REF] = 1.0;
-  num.coef[OR_BC_RAD] = -1.0;
-  den.coef[OR_BC_REF] = 1.0;
-  den.coef[OR_BC_ABS] = -1.0;
-  double p = weber(&num) / weber(&den);
+  double g[4];
+  for (int bc = OR_BC_ABS; bc <= OR_BC_RAD; ++bc) {
+    weber_ctx c = {R, R0, tau, h, {0, 0, 0, 0}, 0};
+    c.coef[bc] = 1.0;
+    g[bc] = weber(&c);
+  }
+  double p = (g[OR_BC_REF] - g[OR_BC_RAD]) / (g[OR_BC_REF] - g[OR_BC_ABS]);
   return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
 }
 
@@ -538,7 +539,7 @@ static double dens2_series(double R, const void* vp) {
 static double cdf2(double V, double R0, double tau, double tau_s) {
   if (tau <= tau_s) {
     dens_ctx c = {R0, tau};
-    return integrate(dens2_series, &c, 1.0, 1.0 + V, 8, 1e-14);
+    return integrate(dens2_series, &c, 1.0, 1.0 + V, 8, 1e-12);
   }
   weber_ctx c = {1.0 + V, R0, tau, 0.0, {0, 0, 0, 0}, 1};
   c.coef[OR_BC_REF] = 1.0;

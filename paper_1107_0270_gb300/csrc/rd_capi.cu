@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "rd_gf2d.cuh"
 #include "rd_kernels.h"
 
 using namespace rd;
@@ -93,7 +94,6 @@ static double max_cutoff(const rd_config& c) {
 
 static int validate(const rd_config* c) {
   if (!c || (c->dim != 2 && c->dim != 3)) return RD_EINVAL;
-  if (c->dim == 2) return RD_ENOTREADY;
   if (c->precision != RD_FP64 && c->precision != RD_MIXED) return RD_EINVAL;
   if (c->n_species < 1 || c->n_species > RD_MAX_SPECIES) return RD_EINVAL;
   if (c->n_pairs < 0 || c->n_pairs > RD_MAX_PAIRS || c->n_decays < 0 || c->n_decays > RD_MAX_DECAYS) return RD_EINVAL;
@@ -202,6 +202,132 @@ static void derive_params(rd_handle* h) {
   }
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// 2D tables: Gauss-Legendre nodes (Newton on the Legendre recurrence), the Weber quadrature nodes
+// of each 2D pair type (Bessel values at the abscissas precomputed, as Section 4.1 suggests), and
+// the coefficient series of the small-time expansion.
+// ------------------------------------------------------------------------------------------------
+static void gauss_legendre16(double* x, double* w) {
+  const int n = 16;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), d = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      d = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / d;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * d * d);
+  }
+}
+
+static std::vector<WeberNode> weber_nodes(double tau, double h, double Rmax) {
+  double gx[16], gw[16];
+  gauss_legendre16(gx, gw);
+  const double T = std::pow(60.0 / tau, 0.25);           // e^{-tau x^2} < e^{-60} beyond x = T^2
+  const int panels = 6 + (int)std::ceil(Rmax * T * T / 2.5);
+  std::vector<WeberNode> nodes;
+  nodes.reserve(panels * 16);
+  const double hw = 0.5 * T / panels;
+  for (int p = 0; p < panels; ++p) {
+    const double mid = (2 * p + 1) * hw;
+    for (int i = 0; i < 16; ++i) {
+      const double t = mid + hw * gx[i], x = t * t;
+      WeberNode nd;
+      nd.x = x;
+      nd.w = gw[i] * hw * 2.0 * t * x * std::exp(-tau * x * x) / (2.0 * kPi);
+      const double J0 = ::j0(x), Y0 = ::y0(x), J1 = ::j1(x), Y1 = ::y1(x);
+      const double al[3] = {J0, x * J1, x * J1 + h * J0};
+      const double be[3] = {Y0, x * Y1, x * Y1 + h * Y0};
+      for (int k = 0; k < 3; ++k) {
+        const double nr = std::sqrt(al[k] * al[k] + be[k] * be[k]);
+        nd.a[k] = al[k] / nr;
+        nd.b[k] = be[k] / nr;
+      }
+      nodes.push_back(nd);
+    }
+  }
+  return nodes;
+}
+
+// a_k(nu) of the large-argument expansions of I_nu, K_nu
+static double ak_host(int k, double nu) {
+  double v = 1.0;
+  for (int j = 1; j <= k; ++j) v *= (4.0 * nu * nu - (2.0 * j - 1.0) * (2.0 * j - 1.0)) / (8.0 * j);
+  return v;
+}
+
+static Series2D series_coeffs(double h) {
+  Series2D S;
+  const int n = kSeriesTerms;
+  double A0[kSeriesTerms + 1], A0m[kSeriesTerms + 1], A1[kSeriesTerms + 1], A1m[kSeriesTerms + 1];
+  for (int k = 0; k <= n; ++k) {
+    const double sg = (k % 2) ? -1.0 : 1.0;
+    A0[k] = ak_host(k, 0.0);
+    A0m[k] = sg * A0[k];
+    A1[k] = ak_host(k, 1.0);
+    A1m[k] = sg * A1[k];
+    S.a0[k] = A0[k];
+  }
+  for (int slot = 0; slot < 3; ++slot) {
+    double num[kSeriesTerms + 1], den[kSeriesTerms + 1];
+    for (int k = 0; k <= n; ++k) {
+      if (slot == 0) {            // absorbing: I0/K0
+        num[k] = A0m[k];
+        den[k] = A0[k];
+      } else {                    // reflective (h = 0) / radiation: (I1 - h y I0)/(K1 + h y K0)
+        const double hh = slot == 2 ? h : 0.0;
+        num[k] = A1m[k] - (k ? hh * A0m[k - 1] : 0.0);
+        den[k] = A1[k] + (k ? hh * A0[k - 1] : 0.0);
+      }
+    }
+    for (int k = 0; k <= n; ++k) {    // series division
+      double v = num[k];
+      for (int j = 1; j <= k; ++j) v -= den[j] * S.ratio[slot][k - j];
+      S.ratio[slot][k] = v / den[0];
+    }
+  }
+  return S;
+}
+
+// Builds the 2D data of every 2D pair type into device memory from `alloc`, patching hp.
+template <class Alloc>
+static bool build_2d(const rd_config& c, DevParams& hp, Alloc alloc) {
+  double gx[16], gw[16];
+  gauss_legendre16(gx, gw);
+  for (int i = 0; i < 16; ++i) {
+    hp.gl16[i] = gx[i];
+    hp.gl16[16 + i] = gw[i];
+  }
+  if (c.dim != 2) return true;
+  for (int k = 0; k < c.n_pairs; ++k) {
+    PairDev& q = hp.pairs[k];
+    if (c.pairs[k].bc == RD_BC_NONE) continue;
+    q.series2d = q.tau <= c.tau_s ? 1 : 0;
+    Series2D S = series_coeffs(q.h);
+    void* ds = alloc(sizeof(Series2D));
+    if (!ds || cudaMemcpy(ds, &S, sizeof S, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    q.ser = (const Series2D*)ds;
+    if (!q.series2d) {
+      const double Rmax = std::sqrt(q.rcut2) / q.sigma + 13.0 * q.s + 3.0;
+      std::vector<WeberNode> nodes = weber_nodes(q.tau, q.h, Rmax);
+      void* dn = alloc(nodes.size() * sizeof(WeberNode));
+      if (!dn || cudaMemcpy(dn, nodes.data(), nodes.size() * sizeof(WeberNode), cudaMemcpyHostToDevice) != cudaSuccess)
+        return false;
+      q.nodes = (const WeberNode*)dn;
+      q.n_nodes = (int)nodes.size();
+    }
+  }
+  return true;
+}
 
 // Cell grid of every replica for a cell edge of (factor x largest cut-off), coarsened per replica
 // until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of out[r].
@@ -505,6 +631,13 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.ctl = (DevCtl*)A(sizeof(DevCtl));
   L.reps = (RepDev*)A(c.n_replicas * sizeof(RepDev));
   if (!ok) {
+    free_all(h);
+    cudaStreamSynchronize(h->stream);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return RD_ENOMEM;
+  }
+  if (!build_2d(c, h->hp, [&](size_t bytes) { return dev_alloc(h, bytes); })) {
     free_all(h);
     cudaStreamSynchronize(h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -964,6 +1097,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
                               int64_t out_cap, double* x_out, int32_t* species_out, uint32_t* id_out,
                               int64_t* n_out, uint32_t* next_id_out, int32_t* status_out) {
   if (!cfg || cfg->n_replicas != 1 || !cfg->replicas) return RD_EINVAL;
+  if (cfg->dim != 3) return RD_ENOTREADY;
   if (n < 0 || n > RD_STATIC_MAX_PARTICLES || step < 0 || step > 0xFFFFFFFFll) return RD_EINVAL;
   if (n > 0 && (!x_in || !species_in || !id_in)) return RD_EINVAL;
   if (out_cap < 2 * n || !x_out || !species_out || !id_out) return RD_EINVAL;

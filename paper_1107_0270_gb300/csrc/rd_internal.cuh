@@ -37,11 +37,18 @@ struct __align__(32) d4 {
   double x, y, z, w;
 };
 
+struct WeberNode;
+struct Series2D;
+
 struct PairDev {
   int32_t bc, product, s1, s2;
   double sigma, tau, inv_tau, s, h, alpha, rcut2, Drel;
   float sigma_f, inv_sigma_f, inv_tau_f, rcut2_f;
   float s_f, alpha_f, pad_f[2];
+  // 2D: small-time series (series2d != 0) or Weber quadrature nodes
+  int32_t series2d, n_nodes;
+  const WeberNode* nodes;
+  const Series2D* ser;
 };
 
 struct DecayDev {
@@ -64,6 +71,7 @@ struct DevParams {
   double ktot[kMaxSpecies];    // total unimolecular rate per species
   double p_uni[kMaxSpecies];   // 1 - exp(-ktot dt)
   unsigned long long uni_thr[kMaxSpecies];   // decay iff (52-bit draw m) < uni_thr
+  double gl16[32];             // 16-point Gauss-Legendre nodes then weights on [-1, 1]
   int8_t pair_of[kMaxSpecies][kMaxSpecies];   // index into pairs, -1 = no interaction
   PairDev pairs[kMaxPairs];
   DecayDev decays[kMaxDecays];

@@ -4,6 +4,7 @@
 // sized for the capacity while the live particle count stays on the device.
 #include <cuda_runtime.h>
 
+#include "rd_gf2d.cuh"
 #include "rd_kernels.h"
 
 namespace rd {
@@ -37,6 +38,36 @@ __device__ __forceinline__ int cell_coord(double x, double inv_edge, int n) {
 __device__ __forceinline__ int cell_coord_f(float x, float inv_edge, int n) {
   int c = (int)(x * inv_edge);
   return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// dimension dispatch of the pair quantities (2D evaluations are out-of-line: they are long loops)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ Pair2D pair2d(const PairDev& pr) {
+  Pair2D q;
+  q.series = pr.series2d != 0;
+  q.tau = pr.tau;
+  q.s = pr.s;
+  q.h = pr.h;
+  q.nodes = pr.nodes;
+  q.n_nodes = pr.n_nodes;
+  q.ser = pr.ser;
+  return q;
+}
+__device__ __noinline__ double p_enc2_call(const PairDev& pr, double R, double R0) { return p_enc2(pair2d(pr), R, R0); }
+__device__ __noinline__ double p_reac2_call(const PairDev& pr, double R, double R0) { return p_reac2(pair2d(pr), R, R0); }
+__device__ __noinline__ double resample2_call(const DevParams& P, const PairDev& pr, double U, double R0) {
+  return resample2(pair2d(pr), U, R0, P.gl16);
+}
+__device__ __forceinline__ double p_enc_dim(const DevParams& P, const PairDev& pr, double R, double R0) {
+  return P.dim == 3 ? p_enc3(R, R0, pr.inv_tau) : p_enc2_call(pr, R, R0);
+}
+__device__ __forceinline__ double p_reac_dim(const DevParams& P, const PairDev& pr, double R, double R0) {
+  return P.dim == 3 ? p_reac3(R, R0, pr.s, pr.alpha) : p_reac2_call(pr, R, R0);
+}
+__device__ __forceinline__ double resample_dim(const DevParams& P, const PairDev& pr, double U, double R0) {
+  return P.dim == 3 ? resample3(U, R0, pr.s) : resample2_call(P, pr, U, R0);
 }
 
 // ================================================================================================
@@ -437,7 +468,7 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                 const double R0 = sqrt(r02) / pr.sigma;
                 const double R = sqrt(norm2_rn(rx, ry, rz, dim)) / pr.sigma;
                 overlap = R <= 1.0;
-                p = p_enc3(R, R0, pr.inv_tau);
+                p = p_enc_dim(P, pr, R, R0);
               } else {
                 const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf);
                 const float r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
@@ -450,7 +481,8 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                 const float d0 = (sqrtf(r02) - pr.sigma_f) * pr.inv_sigma_f;
                 const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
                 overlap = d <= 0.0f;
-                pf = p_enc3_f(d, d0, pr.inv_tau_f);
+                pf = dim == 3 ? p_enc3_f(d, d0, pr.inv_tau_f)
+                              : (float)p_enc2_call(pr, 1.0 + (double)d, 1.0 + (double)(d0 > 0.0f ? d0 : 0.0f));
                 p = (double)pf;
               }
               const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
@@ -694,7 +726,7 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
       const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
       double R0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim)) / pr.sigma;
       if (R0 < 1.0) R0 = 1.0;
-      const double Rn = resample3(u_res, R0, pr.s);
+      const double Rn = resample_dim(P, pr, u_res, R0);
       const double len = sqrt(norm2_rn(rv[0], rv[1], rv[2], dim));
       double dir[3] = {0, 0, 0};
       if (len > 0.0) {
@@ -713,11 +745,11 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
       }
       ++n_res;
       if (pr.bc == RD_BC_RAD) {
-        const double pf = (double)p_reac3_f((float)Rn, (float)R0, pr.s_f, pr.alpha_f);
-        if (fabs(u_reac - pf) > kFilter) {
+        const double pf = dim == 3 ? (double)p_reac3_f((float)Rn, (float)R0, pr.s_f, pr.alpha_f) : -1.0;
+        if (dim == 3 && fabs(u_reac - pf) > kFilter) {
           react = u_reac < pf;
         } else {
-          const double p = p_reac3(Rn, R0, pr.s, pr.alpha);
+          const double p = p_reac_dim(P, pr, Rn, R0);
           n_near += fabs(u_reac - p) <= 1e-9;
           react = u_reac < p;
         }
@@ -800,16 +832,16 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
         const PairDev& pr = P.pairs[rule];
         w = draw(P, step, pid, kOneParticle, TAG_RES, r);
         const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
-        const double Rn = resample3(u_res, 1.0, pr.s);
+        const double Rn = resample_dim(P, pr, u_res, 1.0);
         for (int d = 0; d < dim; ++d) rv[d] = Rn * pr.sigma * dir[d];
         if (pr.bc == RD_BC_ABS) {
           recombine = true;
         } else if (pr.bc == RD_BC_RAD) {
-          const double pf = (double)p_reac3_f((float)Rn, 1.0f, pr.s_f, pr.alpha_f);
-          if (fabs(u_reac - pf) > kFilter) {
+          const double pf = dim == 3 ? (double)p_reac3_f((float)Rn, 1.0f, pr.s_f, pr.alpha_f) : -1.0;
+          if (dim == 3 && fabs(u_reac - pf) > kFilter) {
             recombine = u_reac < pf;
           } else {
-            const double p = p_reac3(Rn, 1.0, pr.s, pr.alpha);
+            const double p = p_reac_dim(P, pr, Rn, 1.0);
             n_near += fabs(u_reac - p) <= 1e-9;
             recombine = u_reac < p;
           }
@@ -873,7 +905,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
     float R0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z) * pr.inv_sigma_f;
     R0 = fmaxf(R0, 1.0f);
-    const float Rn = resample3_f(u23(w.x), R0, pr.s_f);
+    const float Rn = d3 ? resample3_f(u23(w.x), R0, pr.s_f) : (float)resample2_call(P, pr, (double)u23(w.x), (double)R0);
     const float len = sqrtf(rx * rx + ry * ry + rz * rz);
     float dx, dy, dz;
     if (len > 0.0f) {
@@ -888,7 +920,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     }
     const float ln = Rn * pr.sigma_f;
     ++n_res;
-    react = pr.bc == RD_BC_RAD && u52(w.z, w.w) < p_reac3((double)Rn, (double)R0, pr.s, pr.alpha);
+    react = pr.bc == RD_BC_RAD && u52(w.z, w.w) < p_reac_dim(P, pr, (double)Rn, (double)R0);
     if (!react) {
       x1[f.ia] = make_float4(wrap_f(cx - ca * ln * dx, rep.Lf), wrap_f(cy - ca * ln * dy, rep.Lf),
                              d3 ? wrap_f(cz - ca * ln * dz, rep.Lf) : 0.0f, a1.w);
@@ -964,13 +996,13 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     if (rule >= 0) {
       const PairDev& pr = P.pairs[rule];
       w = draw(P, step, pid, kOneParticle, TAG_RES, r);
-      const float Rn = resample3_f(u23(w.x), 1.0f, pr.s_f);
+      const float Rn = d3 ? resample3_f(u23(w.x), 1.0f, pr.s_f) : (float)resample2_call(P, pr, (double)u23(w.x), 1.0);
       const float ln = Rn * pr.sigma_f;
       rx = ln * dx; ry = ln * dy; rz = ln * dz;
       if (pr.bc == RD_BC_ABS)
         recombine = true;
       else if (pr.bc == RD_BC_RAD)
-        recombine = u52(w.z, w.w) < p_reac3((double)Rn, 1.0, pr.s, pr.alpha);
+        recombine = u52(w.z, w.w) < p_reac_dim(P, pr, (double)Rn, 1.0);
       product = pr.product;
     } else {
       float nr[4];
@@ -1204,16 +1236,16 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double a = r0[k], b = r[k];
     if (p_enc) {
-      if (P.precision == RD_MIXED) {
+      if (P.precision == RD_MIXED && P.dim == 3) {
         const float d0 = (float)((a - pr.sigma) * inv_sigma), d = (float)((b - pr.sigma) * inv_sigma);
         p_enc[k] = (double)p_enc3_f(d, d0, pr.inv_tau_f);
       } else {
-        p_enc[k] = p_enc3(b / pr.sigma, a / pr.sigma, pr.inv_tau);
+        p_enc[k] = p_enc_dim(P, pr, b / pr.sigma, a / pr.sigma);
       }
     }
     if (p_reac) {
       double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
-      if (pr.bc == RD_BC_RAD) v = p_reac3(b / pr.sigma, a / pr.sigma, pr.s, pr.alpha);
+      if (pr.bc == RD_BC_RAD) v = p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
       p_reac[k] = v;
     }
   }
@@ -1223,7 +1255,7 @@ __global__ void k_resample(const DevParams* __restrict__ Pp, int rule, const dou
                            const double* __restrict__ u, int64_t n, double* __restrict__ out) {
   const PairDev& pr = Pp->pairs[rule];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = resample3(u[k], r0[k] / pr.sigma, pr.s) * pr.sigma;
+    out[k] = resample_dim(*Pp, pr, u[k], r0[k] / pr.sigma) * pr.sigma;
 }
 
 // ================================================================================================
