@@ -329,6 +329,44 @@ static bool build_2d(const rd_config& c, DevParams& hp, Alloc alloc) {
   return true;
 }
 
+// FP32 lookup tables of the mixed step (p_reac in 2D and 3D; F = p_enc e^{d d0/tau} and
+// -ln(tail) in 2D), spacing 0.025 min(sqrt(tau), 1) over d0 up to the cut-off and d up to the propagator's
+// support (d0 + 13 sqrt(tau)), built in FP64 on the device.
+template <class Alloc>
+static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
+  const rd_config& c = h->cfg;
+  if (c.precision != RD_MIXED) return cudaSuccess;
+  for (int k = 0; k < c.n_pairs; ++k) {
+    PairDev& q = h->hp.pairs[k];
+    if (c.pairs[k].bc == RD_BC_NONE) continue;
+    const double hstep = 0.025 * std::min(q.s, 1.0);
+    const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
+    const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
+    const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
+    const size_t bytes = (size_t)n0 * n1 * sizeof(float);
+    auto make = [&](int kind, Tab2& T) -> cudaError_t {
+      float* t = (float*)alloc(bytes);
+      double* tot = (double*)alloc((size_t)n0 * sizeof(double));
+      if (!t || !tot) return cudaErrorMemoryAllocation;
+      launch_build_table(h->L.P, k, kind, t, n0, n1, hstep, tot, h->stream);
+      T.v = t;
+      T.n0 = n0;
+      T.n1 = n1;
+      T.h = (float)hstep;
+      T.inv_h = (float)(1.0 / hstep);
+      return cudaGetLastError();
+    };
+    cudaError_t e = cudaSuccess;
+    if (c.pairs[k].bc == RD_BC_RAD) e = make(0, q.tab_preac);
+    if (e == cudaSuccess && c.dim == 2) e = make(1, q.tab_penc);
+    if (e == cudaSuccess && c.dim == 2) e = make(2, q.tab_tail);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy((void*)h->L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice);
+}
+
 // Cell grid of every replica for a cell edge of (factor x largest cut-off), coarsened per replica
 // until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of out[r].
 static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
@@ -663,6 +701,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   std::memset(&ctl, 0, sizeof ctl);
   ctl.n = (uint32_t)n_total;
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = build_tables(h, [&](size_t bytes) { return dev_alloc(h, bytes); });
   if (e != cudaSuccess) return fail(e);
 
   // initial positions: ids 0..N_r-1 per replica, species in blocks of n_init
@@ -1220,6 +1259,29 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   RD_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)cap * 4, s));
   RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
   RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+  if (c.precision == RD_MIXED) {
+    // the mixed step reads p_reac from an FP32 table: build it into the scratch array as well
+    bool any = false;
+    for (int k = 0; k < c.n_pairs; ++k) {
+      if (c.pairs[k].bc != RD_BC_RAD) continue;
+      PairDev& q = tmp.hp.pairs[k];
+      const double hstep = 0.025 * std::min(q.s, 1.0);
+      const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
+      const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
+      const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
+      float* t = (float*)b.take((size_t)n0 * n1 * sizeof(float));
+      double* tot = (double*)b.take((size_t)n0 * sizeof(double));
+      if (!b.ok) return RD_EINVAL;
+      launch_build_table(L.P, k, 0, t, n0, n1, hstep, tot, s);
+      q.tab_preac.v = t;
+      q.tab_preac.n0 = n0;
+      q.tab_preac.n1 = n1;
+      q.tab_preac.h = (float)hstep;
+      q.tab_preac.inv_h = (float)(1.0 / hstep);
+      any = true;
+    }
+    if (any) RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+  }
   RD_CUDA(cudaMemcpyAsync(L.reps, &rep, sizeof rep, cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemcpyAsync(L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, s));
   const int G = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8);

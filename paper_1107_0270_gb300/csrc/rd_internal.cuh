@@ -40,6 +40,14 @@ struct __align__(32) d4 {
 struct WeberNode;
 struct Series2D;
 
+// Uniform 2D table over (d0, d) with spacing h; row/column 0 is a ghost point at -h and two ghost
+// points follow the last grid point (n0 x n1 stored values).  Catmull-Rom bicubic lookup.
+struct Tab2 {
+  const float* v;
+  int32_t n0, n1;
+  float inv_h, h;
+};
+
 struct PairDev {
   int32_t bc, product, s1, s2;
   double sigma, tau, inv_tau, s, h, alpha, rcut2, Drel;
@@ -49,6 +57,8 @@ struct PairDev {
   int32_t series2d, n_nodes;
   const WeberNode* nodes;
   const Series2D* ser;
+  // mixed step: FP32 tables of p_reac (2D and 3D), F = p_enc e^{d d0/tau} and -ln(tail) (2D)
+  Tab2 tab_preac, tab_penc, tab_tail;
 };
 
 struct DecayDev {
@@ -418,6 +428,38 @@ __device__ __forceinline__ float resample3_f(float U, float R0, float s) {
   }
   if (!(V >= 0.0f) || !isfinite(V)) V = 0.0f;
   return 1.0f + V;
+}
+
+__device__ __forceinline__ void cr_w(float t, float w[4]) {
+  const float t2 = t * t, t3 = t2 * t;
+  w[0] = 0.5f * (-t3 + 2.0f * t2 - t);
+  w[1] = 0.5f * (3.0f * t3 - 5.0f * t2 + 2.0f);
+  w[2] = 0.5f * (-3.0f * t3 + 4.0f * t2 + t);
+  w[3] = 0.5f * (t3 - t2);
+}
+
+// bicubic Catmull-Rom value at (d0, d) >= 0 (clamped to the table)
+__device__ __forceinline__ float tab_eval(const Tab2& T, float d0, float d) {
+  float x = d0 * T.inv_h + 1.0f, y = d * T.inv_h + 1.0f;
+  x = fminf(fmaxf(x, 1.0f), (float)(T.n0 - 3) - 1e-3f);
+  y = fminf(fmaxf(y, 1.0f), (float)(T.n1 - 3) - 1e-3f);
+  const int i = (int)x, j = (int)y;
+  float wx[4], wy[4];
+  cr_w(x - i, wx);
+  cr_w(y - j, wy);
+  float acc = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const float* row = T.v + (size_t)(i - 1 + a) * T.n1 + (j - 1);
+    acc += wx[a] * (wy[0] * __ldg(row) + wy[1] * __ldg(row + 1) + wy[2] * __ldg(row + 2) + wy[3] * __ldg(row + 3));
+  }
+  return acc;
+}
+
+// table p_reac (clamped to [0,1])
+__device__ __forceinline__ float p_reac_tab(const PairDev& pr, float d, float d0) {
+  const float p = tab_eval(pr.tab_preac, fmaxf(d0, 0.0f), fmaxf(d, 0.0f));
+  return fminf(fmaxf(p, 0.0f), 1.0f);
 }
 
 }  // namespace rd

@@ -4,6 +4,8 @@
 // sized for the capacity while the live particle count stays on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "rd_gf2d.cuh"
 #include "rd_kernels.h"
 
@@ -481,8 +483,14 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
                 const float d0 = (sqrtf(r02) - pr.sigma_f) * pr.inv_sigma_f;
                 const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
                 overlap = d <= 0.0f;
-                pf = dim == 3 ? p_enc3_f(d, d0, pr.inv_tau_f)
-                              : (float)p_enc2_call(pr, 1.0 + (double)d, 1.0 + (double)(d0 > 0.0f ? d0 : 0.0f));
+                if (dim == 3) {
+                  pf = p_enc3_f(d, d0, pr.inv_tau_f);
+                } else if (d <= 0.0f || d0 <= 0.0f) {
+                  pf = 1.0f;
+                } else {
+                  const float xx = d * d0 * pr.inv_tau_f;
+                  pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
+                }
                 p = (double)pf;
               }
               const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
@@ -878,6 +886,21 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
 // ------------------------------------------------------------------------------------------------
 // Mixed step: positions, displacements and the propagator sample in FP32; p_reac in FP64.
 // ------------------------------------------------------------------------------------------------
+// 2D propagator sample from the -ln(tail) table: bisection on the interpolant (increasing in v)
+__device__ __forceinline__ float resample2_tab(const PairDev& pr, float U, float R0) {
+  const float d0 = fmaxf(R0 - 1.0f, 0.0f), target = -logf(U);
+  float lo = 0.0f, hi = (float)(pr.tab_tail.n1 - 4) * pr.tab_tail.h;
+#pragma unroll 1
+  for (int it = 0; it < 32; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (tab_eval(pr.tab_tail, d0, mid) < target)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 1.0f + 0.5f * (lo + hi);
+}
+
 __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev* __restrict__ reps,
                                                const FiredPair* __restrict__ fired,
                                                const uint32_t* __restrict__ fstate, uint32_t e, uint32_t step,
@@ -905,7 +928,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
     float R0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z) * pr.inv_sigma_f;
     R0 = fmaxf(R0, 1.0f);
-    const float Rn = d3 ? resample3_f(u23(w.x), R0, pr.s_f) : (float)resample2_call(P, pr, (double)u23(w.x), (double)R0);
+    const float Rn = d3 ? resample3_f(u23(w.x), R0, pr.s_f) : resample2_tab(pr, u23(w.x), R0);
     const float len = sqrtf(rx * rx + ry * ry + rz * rz);
     float dx, dy, dz;
     if (len > 0.0f) {
@@ -920,7 +943,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     }
     const float ln = Rn * pr.sigma_f;
     ++n_res;
-    react = pr.bc == RD_BC_RAD && u52(w.z, w.w) < p_reac_dim(P, pr, (double)Rn, (double)R0);
+    react = pr.bc == RD_BC_RAD && u23(w.z) < p_reac_tab(pr, Rn - 1.0f, R0 - 1.0f);
     if (!react) {
       x1[f.ia] = make_float4(wrap_f(cx - ca * ln * dx, rep.Lf), wrap_f(cy - ca * ln * dy, rep.Lf),
                              d3 ? wrap_f(cz - ca * ln * dz, rep.Lf) : 0.0f, a1.w);
@@ -996,13 +1019,13 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     if (rule >= 0) {
       const PairDev& pr = P.pairs[rule];
       w = draw(P, step, pid, kOneParticle, TAG_RES, r);
-      const float Rn = d3 ? resample3_f(u23(w.x), 1.0f, pr.s_f) : (float)resample2_call(P, pr, (double)u23(w.x), 1.0);
+      const float Rn = d3 ? resample3_f(u23(w.x), 1.0f, pr.s_f) : resample2_tab(pr, u23(w.x), 1.0f);
       const float ln = Rn * pr.sigma_f;
       rx = ln * dx; ry = ln * dy; rz = ln * dz;
       if (pr.bc == RD_BC_ABS)
         recombine = true;
       else if (pr.bc == RD_BC_RAD)
-        recombine = u52(w.z, w.w) < p_reac_dim(P, pr, (double)Rn, 1.0);
+        recombine = u23(w.z) < p_reac_tab(pr, Rn - 1.0f, 0.0f);
       product = pr.product;
     } else {
       float nr[4];
@@ -1236,16 +1259,27 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double a = r0[k], b = r[k];
     if (p_enc) {
-      if (P.precision == RD_MIXED && P.dim == 3) {
+      if (P.precision == RD_MIXED) {
         const float d0 = (float)((a - pr.sigma) * inv_sigma), d = (float)((b - pr.sigma) * inv_sigma);
-        p_enc[k] = (double)p_enc3_f(d, d0, pr.inv_tau_f);
+        float pf;
+        if (P.dim == 3) {
+          pf = p_enc3_f(d, d0, pr.inv_tau_f);
+        } else if (d <= 0.0f || d0 <= 0.0f) {
+          pf = 1.0f;
+        } else {
+          const float xx = d * d0 * pr.inv_tau_f;
+          pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
+        }
+        p_enc[k] = (double)pf;
       } else {
         p_enc[k] = p_enc_dim(P, pr, b / pr.sigma, a / pr.sigma);
       }
     }
     if (p_reac) {
       double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
-      if (pr.bc == RD_BC_RAD) v = p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
+      if (pr.bc == RD_BC_RAD)
+        v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, (float)(b * inv_sigma - 1.0), (float)(a * inv_sigma - 1.0))
+                                    : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
       p_reac[k] = v;
     }
   }
@@ -1255,7 +1289,70 @@ __global__ void k_resample(const DevParams* __restrict__ Pp, int rule, const dou
                            const double* __restrict__ u, int64_t n, double* __restrict__ out) {
   const PairDev& pr = Pp->pairs[rule];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = resample_dim(*Pp, pr, u[k], r0[k] / pr.sigma) * pr.sigma;
+    out[k] = (Pp->precision == RD_MIXED && Pp->dim == 2 ? (double)resample2_tab(pr, (float)u[k], (float)(r0[k] / pr.sigma))
+                                                        : resample_dim(*Pp, pr, u[k], r0[k] / pr.sigma)) * pr.sigma;
+}
+
+
+// ================================================================================================
+// Per-run FP32 tables for the mixed step, built in FP64 from the same pair functions.  Entry
+// (i, j) sits at d0 = (i-1) h, d = (j-1) h; row/column 0 is a ghost filled by extrapolation.
+// kind 0: p_reac; kind 1: F = p_enc e^{d d0/tau} (2D); kind 2: -ln(tail) of the propagator (2D).
+// ================================================================================================
+__global__ void k_tail_totals(const DevParams* __restrict__ Pp, int rule, int n0, double h, double* __restrict__ tot) {
+  const PairDev& pr = Pp->pairs[rule];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
+    const double R0 = 1.0 + fmax((i - 1) * h, 0.0);
+    tot[i] = cdf2(pair2d(pr), R0 + 13.0 * pr.s, R0, Pp->gl16);
+  }
+}
+
+__global__ void k_build_table(const DevParams* __restrict__ Pp, int rule, int kind, float* __restrict__ out, int n0,
+                              int n1, double h, const double* __restrict__ tot) {
+  const DevParams& P = *Pp;
+  const PairDev& pr = P.pairs[rule];
+  const int64_t total = (int64_t)n0 * n1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n1), j = (int)(e % n1);
+    if (i == 0 || j == 0) continue;
+    const double d0 = (i - 1) * h, d = (j - 1) * h;
+    double v;
+    if (kind == 0) {
+      v = p_reac_dim(P, pr, 1.0 + d, 1.0 + d0);
+    } else if (kind == 1) {
+      const double x = d * d0 / pr.tau;
+      v = x > 60.0 ? 1.0 : p_enc_dim(P, pr, 1.0 + d, 1.0 + d0) * exp(x);
+      if (d <= 0.0 || d0 <= 0.0) v = 1.0;
+    } else {
+      const double t = 1.0 - cdf2(pair2d(pr), d, 1.0 + d0, P.gl16) / tot[i];
+      v = t > 1e-30 ? -log(t) : 69.0;
+    }
+    out[e] = (float)v;
+  }
+}
+
+__global__ void k_table_ghosts(float* __restrict__ T, int n0, int n1) {
+  // ghost column 0 of every row, then ghost row 0 (cubic extrapolation)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x) {
+    if (i == 0) continue;
+    float* r = T + (size_t)i * n1;
+    r[0] = 4.0f * r[1] - 6.0f * r[2] + 4.0f * r[3] - r[4];
+  }
+}
+
+__global__ void k_table_ghost_row(float* __restrict__ T, int n1) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n1; j += gridDim.x * blockDim.x)
+    T[j] = 4.0f * T[n1 + j] - 6.0f * T[2 * n1 + j] + 4.0f * T[3 * n1 + j] - T[4 * n1 + j];
+}
+
+void launch_build_table(const DevParams* P, int rule, int kind, float* out, int n0, int n1, double h, double* tot,
+                        cudaStream_t s) {
+  if (kind == 2) k_tail_totals<<<(n0 + 63) / 64, 64, 0, s>>>(P, rule, n0, h, tot);
+  const int64_t total = (int64_t)n0 * n1;
+  const int G = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
+  k_build_table<<<G, 128, 0, s>>>(P, rule, kind, out, n0, n1, h, tot);
+  k_table_ghosts<<<(n0 + 255) / 256, 256, 0, s>>>(out, n0, n1);
+  k_table_ghost_row<<<(n1 + 255) / 256, 256, 0, s>>>(out, n1);
 }
 
 // ================================================================================================

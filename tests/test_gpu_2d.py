@@ -56,6 +56,27 @@ def test_resample_2d_fp64(tau):
     sim.close()
 
 
+@pytest.mark.parametrize("tau", [0.005, 0.08, 0.8])
+def test_pair_probs_2d_mixed_tables_within_2e6(tau):
+    system = pair_system(tau)
+    pr = system.pairs[0]
+    r0, r = W.pair_samples(400, pr.sigma, 0.2, system.dt, dim=2, seed=int(tau * 1e4) + 7)
+    sim = pkg.Simulation(system, precision="mixed")
+    pe, prc = sim.pair_probs(torch.tensor(r0, device="cuda"), torch.tensor(r, device="cuda"))
+    pe_o, pr_o = O.pair_probs(system, r0, r)
+    assert np.max(np.abs(pe.cpu().numpy() - pe_o)) <= 2e-6
+    m = pe_o >= 1e-4
+    assert np.max(np.abs(prc.cpu().numpy()[m] - pr_o[m])) <= 2e-6
+    # propagator samples from the tail table: the sampled separations invert the oracle tail
+    rng = np.random.default_rng(11)
+    r0s = pr.sigma * (1 + rng.uniform(0, 5 * math.sqrt(2 * tau), 24))
+    u = rng.uniform(0.01, 0.99, 24)
+    rn = sim.resample(torch.tensor(r0s, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
+    back = np.array([O.tail2(b / pr.sigma - 1.0, a / pr.sigma, tau) for a, b in zip(r0s, rn)])
+    assert np.max(np.abs(back - u)) <= 2e-5
+    sim.close()
+
+
 def membrane(dt, n_each=60, L=0.3):
     return W.membrane_2d(n_each=n_each, L=L, dt=dt)
 

@@ -115,7 +115,8 @@ def test_pair_probs_mixed_within_2e6(tau):
     pe_o, pr_o = O.pair_probs(system, r0, r)
     err = np.max(np.abs(pe.cpu().numpy() - pe_o))
     assert err <= 2e-6, err
-    assert np.max(np.abs(pr.cpu().numpy() - pr_o)) <= 1e-12
+    err_r = np.max(np.abs(pr.cpu().numpy() - pr_o))      # p_reac from the per-run FP32 table
+    assert err_r <= 2e-6, err_r
     sim.close()
 
 
