@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, pair-prob batch, e2e")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the ensemble, network and membrane context measurements")
     return ap.parse_args()
 
 
@@ -383,6 +385,8 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
         res[prec] = {"evals_per_s": r0.numel() / t, "gbs": r0.numel() * 24 / t / 1e9, "pairs": r0.numel()}
         sim.close()
     out["pair_prob_evals_per_s"] = res
+    if not args.no_workloads:
+        out["workloads"] = other_workloads(torch, pkg, flush)
     # end to end through the C ABI with host buffers: per step, upload the state from pinned host
     # memory (rd_set_state), one step, read back the state and the observables (rd_get_state,
     # rd_observables)
@@ -408,6 +412,37 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
                   "path": "rd_set_state(host) + rd_step + rd_get_state(host) + rd_observables per step"}
     sim.close()
     return out
+
+
+def other_workloads(torch, pkg, flush):
+    """The other experiment shapes at full size (mixed precision), timed like the headline."""
+    cases = [
+        ("ensemble_3d", "4096 independent 3D A+B<->C replicas, N per species log-uniform in [64, 8192], "
+                        "1-20 uM, dt=1e-5", lambda: W.ensemble_3d(), 40),
+        ("network_3d", "5-species 3D network, 1e7 particles in L=20 um, dt=1e-5", lambda: W.network_3d(dt=1e-5), 20),
+        ("membrane_2d", "2D A+B<->C (+C+C reflective), 2e5+2e5 in L=10 um, dt=1e-4 (tau=0.8, Weber tables)",
+         lambda: W.membrane_2d(), 40),
+    ]
+    res = {}
+    for name, desc, make, steps in cases:
+        try:
+            t0 = time.perf_counter()
+            sim = pkg.Simulation(make(), precision="mixed")
+            init_s = time.perf_counter() - t0
+            sim.run(4)
+            sim.sync()
+            o0 = sim.observables()
+            el, nst = timed_graph_run(sim, torch, flush, steps)
+            o1 = sim.observables()
+            ps = o1["stats"]["particle_steps"] - o0["stats"]["particle_steps"]
+            res[name] = {"workload": desc, "value": ps / el, "unit": "particle-steps/s", "steps": nst,
+                         "ms_per_step": 1e3 * el / nst, "particles": int(o1["counts"].sum()),
+                         "init_s": round(init_s, 2)}
+            sim.close()
+        except Exception as exc:  # report, do not hide
+            res[name] = {"workload": desc, "error": str(exc)[:200]}
+        torch.cuda.empty_cache()
+    return res
 
 
 def main():

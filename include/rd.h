@@ -178,6 +178,13 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
 /* Number of particles currently alive (synchronises). */
 int rd_num_particles(rd_handle* h, int64_t* n);
 
+/* Per-step totals over replicas of every species, kept on the device for the last 65536 steps
+ * without host synchronisation during rd_run (the A-count trajectory and, for an irreversible
+ * reaction, the pair-survival histogram -dN_A per step).  Synchronises; out: caller-owned HOST
+ * int64[n_steps * n_species], row k = step first_step + k (0 = initial state).  RD_EINVAL if a
+ * requested step is in the future or no longer kept. */
+int rd_count_history(rd_handle* h, int64_t first_step, int64_t n_steps, int64_t* out);
+
 /* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge factor (in units of the
  * largest cut-off), out[1] total cells, out[2] threads per block of the resolution kernel,
  * out[3] particle capacity, out[4] fired-pair capacity, out[5] autotuned ms per step (0 if not

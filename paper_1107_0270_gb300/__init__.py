@@ -30,7 +30,7 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
            "rd_pair_probs", "rd_resample", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
            "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static",
-           "rd_info"]
+           "rd_info", "rd_count_history"]
 
 
 class RDError(RuntimeError):
@@ -103,6 +103,7 @@ def _lib():
         L.rd_kernel_times.argtypes = [vp, i32, P(i32), C.c_char_p, P(C.c_float)]
         L.rd_step_static.argtypes = [P(_Config), vp, i64, vp, vp, vp, u32, i64, i64, vp, vp, vp, vp, vp, vp]
         L.rd_info.argtypes = [vp, P(d), i32]
+        L.rd_count_history.argtypes = [vp, i64, i64, P(i64)]
         L.rd_free.argtypes = [vp]
         L.rd_free.restype = None
         L.rd_strerror.argtypes = [C.c_int]
@@ -238,6 +239,15 @@ class Simulation:
         _check(rc, "rd_observables")
         return {"counts": counts.reshape(self.n_replicas, self.n_species), "step": step.value,
                 "t": t.value, "stats": dict(zip(STAT_NAMES, stats.tolist()))}
+
+    def count_history(self, first_step: int = 0, n_steps: Optional[int] = None):
+        """Totals per species (summed over replicas) for steps first_step .. first_step+n_steps-1."""
+        if n_steps is None:
+            n_steps = self.observables()["step"] - first_step + 1
+        out = np.zeros((max(n_steps, 1), self.n_species), np.int64)
+        _check(_lib().rd_count_history(self._h, int(first_step), int(n_steps), _ptr(out, C.c_int64)),
+               "rd_count_history")
+        return out[:n_steps]
 
     def info(self):
         v = np.zeros(7)

@@ -28,6 +28,8 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
+constexpr int kHistoryLen = 1 << 16;   // steps kept by the per-step count history
+
 struct rd_handle {
   rd_config cfg;
   std::vector<rd_replica> reps_host;
@@ -665,6 +667,8 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.fstate = (uint32_t*)A(pair_cap * 4);
   L.conflict = (uint32_t*)A(pair_cap * 4);
   L.counts = (unsigned long long*)A((size_t)L.n_counts * 8);
+  L.history_len = kHistoryLen;
+  L.history = (long long*)A((size_t)kHistoryLen * c.n_species * 8);
   L.P = (const DevParams*)A(sizeof(DevParams));
   L.ctl = (DevCtl*)A(sizeof(DevCtl));
   L.reps = (RepDev*)A(c.n_replicas * sizeof(RepDev));
@@ -1002,6 +1006,23 @@ int rd_info(rd_handle* h, double* out, int32_t n) {
                        (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
                        max_cutoff(h->cfg)};
   for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
+  return RD_OK;
+}
+
+int rd_count_history(rd_handle* h, int64_t first_step, int64_t n_steps, int64_t* out) {
+  if (!h || !out || first_step < 0 || n_steps < 0) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl ctl;
+  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  const int64_t last = ctl.step;
+  if (first_step + n_steps - 1 > last || (n_steps > 0 && last - first_step >= h->L.history_len)) return RD_EINVAL;
+  const int ns = h->cfg.n_species;
+  std::vector<long long> ring((size_t)h->L.history_len * ns);
+  RD_CUDA(cudaMemcpy(ring.data(), h->L.history, ring.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < n_steps; ++k) {
+    const int64_t slot = (first_step + k) % h->L.history_len;
+    for (int sp = 0; sp < ns; ++sp) out[k * ns + sp] = ring[(size_t)slot * ns + sp];
+  }
   return RD_OK;
 }
 

@@ -1107,7 +1107,8 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__
                           const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                           const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
                           const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
-                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts) {
+                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts,
+                          long long* __restrict__ history, int history_len) {
   extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
   const DevParams& P = *Pp;
   const uint32_t n = ctl->n;
@@ -1178,6 +1179,16 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__
       reps[r].next_id += (uint32_t)ee - (uint32_t)eb;
       reps[r].beg = (uint32_t)(eb >> 32) + (uint32_t)eb;
       reps[r].end = (uint32_t)(ee >> 32) + (uint32_t)ee;
+    }
+  }
+  __syncthreads();
+  // per-step totals over replicas of every species (ring buffer indexed by the new step)
+  if (!fail && history_len > 0) {
+    const int slot = (int)((ctl->step + 1u) % (uint32_t)history_len);
+    for (int sp = threadIdx.x; sp < ns; sp += blockDim.x) {
+      long long tot_sp = 0;
+      for (int r = 0; r < P.n_replicas; ++r) tot_sp += (long long)counts[(size_t)r * ns + sp];
+      history[(size_t)slot * ns + sp] = tot_sp;
     }
   }
   __syncthreads();
@@ -1411,7 +1422,7 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_scan_compact");
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
   k_compact<T><<<Gp, B, hist_bytes, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo,
-                                          L.id_next, L.counts, L.n_counts);
+                                          L.id_next, L.counts, L.n_counts, L.history, L.history_len);
   mark("k_compact");
 }
 
@@ -1435,6 +1446,19 @@ __global__ void k_zero_counts(unsigned long long* __restrict__ counts, int n_cou
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_counts; i += gridDim.x * blockDim.x) counts[i] = 0;
 }
 
+// history entry of the current step from the counts (after initialisation or a state upload)
+__global__ void k_history_now(const DevParams* __restrict__ Pp, const DevCtl* __restrict__ ctl,
+                              const unsigned long long* __restrict__ counts, long long* __restrict__ history,
+                              int history_len) {
+  const int ns = Pp->n_species;
+  const int slot = (int)(ctl->step % (uint32_t)history_len);
+  for (int sp = threadIdx.x; sp < ns; sp += blockDim.x) {
+    long long t = 0;
+    for (int r = 0; r < Pp->n_replicas; ++r) t += (long long)counts[(size_t)r * ns + sp];
+    history[(size_t)slot * ns + sp] = t;
+  }
+}
+
 void launch_count(const StepLaunch& L, cudaStream_t s) {
   k_zero_counts<<<grid_for(L.n_counts, 256, 64), 256, 0, s>>>(L.counts, L.n_counts);
   const int G = grid_for(L.cap_particles, 256, L.max_grid);
@@ -1442,6 +1466,7 @@ void launch_count(const StepLaunch& L, cudaStream_t s) {
     k_count<float><<<G, 256, 0, s>>>(L.P, L.ctl, (const float4*)L.x_cur, L.counts);
   else
     k_count<double><<<G, 256, 0, s>>>(L.P, L.ctl, (const d4*)L.x_cur, L.counts);
+  if (L.history && L.history_len > 0) k_history_now<<<1, 32, 0, s>>>(L.P, L.ctl, L.counts, L.history, L.history_len);
 }
 
 void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,

@@ -54,6 +54,8 @@ struct StepLaunch {
   unsigned long long* best_key;
   unsigned long long* best_pid;
   unsigned long long* counts;
+  long long* history;          // history_len x n_species totals per step (ring), may be null
+  int history_len;
 };
 
 // CUDA-event marks between kernel groups of one (non-graph) step.
