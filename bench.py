@@ -434,10 +434,15 @@ def other_workloads(torch, pkg, flush):
             o0 = sim.observables()
             el, nst = timed_graph_run(sim, torch, flush, steps)
             o1 = sim.observables()
+            ker = {}
+            for _ in range(4):
+                for kname, ms in sim.timed_step():
+                    ker[kname] = ker.get(kname, 0.0) + ms / 4
             ps = o1["stats"]["particle_steps"] - o0["stats"]["particle_steps"]
             res[name] = {"workload": desc, "value": ps / el, "unit": "particle-steps/s", "steps": nst,
                          "ms_per_step": 1e3 * el / nst, "particles": int(o1["counts"].sum()),
-                         "init_s": round(init_s, 2)}
+                         "init_s": round(init_s, 2), "layout": sim.info(),
+                         "kernel_ms": {k: round(v, 5) for k, v in ker.items()}}
             sim.close()
         except Exception as exc:  # report, do not hide
             res[name] = {"workload": desc, "error": str(exc)[:200]}

@@ -99,9 +99,11 @@ typedef struct {
   const rd_replica* replicas;         /* read during rd_init only */
   double capacity_factor;             /* particle capacity = factor * initial total (default 2) */
   int64_t pair_capacity;              /* fired-pair list capacity (0: automatic) */
-  int32_t cell_factor_x100;           /* cell edge = largest r_cut x factor/100; 0: density-based
-                                         (about 1.5 interacting particles per cell); < 0: the fastest of
-                                         three factors, timed by rd_init on the initial state */
+  int32_t cell_factor_x100;           /* cell edge = largest r_cut x factor/100; 0: density-based per
+                                         replica (about 0.25 interacting particles per cell, edge between
+                                         1 and 4 cut-offs); < 0: the fastest of four choices (fixed
+                                         1.0, density rule x 0.7 / 1 / 1.5), timed by rd_init on the
+                                         initial state */
   int32_t block_size;                 /* threads per block of the particle kernels (0: 256) */
   rd_allocator allocator;
 } rd_config;
@@ -169,11 +171,13 @@ int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r,
 int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n,
                 double* r_new);
 
-/* Diagnostics of the last step (synchronises): the fired (encounter) pairs as ids, their p_enc and
- * whether the conflict resolution accepted them.  cap: capacity of the caller-owned HOST arrays;
- * *n_out: pairs in the list (all copied when <= cap).  replica may be NULL. */
+/* Diagnostics of the last step (synchronises): the fired (encounter) pairs as ids, their p_enc,
+ * their selection key -ln(U_sel)/p_enc and whether the conflict resolution accepted them (the
+ * accepted set is the greedy matching in ascending (key, id_a, id_b)).  cap: capacity of the
+ * caller-owned HOST arrays; *n_out: pairs in the list (all copied when <= cap).  Any output array
+ * may be NULL. */
 int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uint32_t* id_b,
-                  double* p_enc, int32_t* accepted, int32_t* replica);
+                  double* p_enc, int32_t* accepted, int32_t* replica, double* key);
 
 /* Number of particles currently alive (synchronises). */
 int rd_num_particles(rd_handle* h, int64_t* n);
@@ -185,8 +189,8 @@ int rd_num_particles(rd_handle* h, int64_t* n);
  * requested step is in the future or no longer kept. */
 int rd_count_history(rd_handle* h, int64_t first_step, int64_t n_steps, int64_t* out);
 
-/* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge factor (in units of the
- * largest cut-off), out[1] total cells, out[2] threads per block of the resolution kernel,
+/* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge choice (> 0: fixed factor
+ * in units of the largest cut-off; < 0: per-replica density rule times -out[0]), out[1] total cells, out[2] threads per block of the resolution kernel,
  * out[3] particle capacity, out[4] fired-pair capacity, out[5] autotuned ms per step (0 if not
  * tuned), out[6] largest cut-off radius.  Writes min(n, 7) values to the caller-owned HOST array. */
 int rd_info(rd_handle* h, double* out, int32_t n);

@@ -97,7 +97,7 @@ def _lib():
         L.rd_set_state.argtypes = [vp, i64, P(d), P(i32), P(u32), P(i32), P(u32), i64]
         L.rd_pair_probs.argtypes = [vp, i32, vp, vp, i64, vp, vp]
         L.rd_resample.argtypes = [vp, i32, vp, vp, i64, vp]
-        L.rd_last_fired.argtypes = [vp, i64, P(i64), P(u32), P(u32), P(d), P(i32), P(i32)]
+        L.rd_last_fired.argtypes = [vp, i64, P(i64), P(u32), P(u32), P(d), P(i32), P(i32), P(d)]
         L.rd_num_particles.argtypes = [vp, P(i64)]
         L.rd_time_kernels.argtypes = [vp, i32]
         L.rd_kernel_times.argtypes = [vp, i32, P(i32), C.c_char_p, P(C.c_float)]
@@ -252,7 +252,8 @@ class Simulation:
     def info(self):
         v = np.zeros(7)
         _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 7), "rd_info")
-        return {"cell_factor": v[0], "cells": int(v[1]), "resolve_block": int(v[2]),
+        return {"cell_factor": abs(v[0]), "cell_rule": "density" if v[0] < 0 else "fixed",
+                "cells": int(v[1]), "resolve_block": int(v[2]),
                 "capacity": int(v[3]), "pair_capacity": int(v[4]), "tuned_ms_per_step": v[5],
                 "r_cut_max": v[6]}
 
@@ -291,18 +292,21 @@ class Simulation:
 
     def last_fired(self, cap: int = 1 << 22):
         n = C.c_int64()
-        _check(_lib().rd_last_fired(self._h, 0, C.byref(n), None, None, None, None, None), "rd_last_fired")
+        _check(_lib().rd_last_fired(self._h, 0, C.byref(n), None, None, None, None, None, None),
+               "rd_last_fired")
         m = min(n.value, cap)
         ida = np.zeros(max(m, 1), np.uint32)
         idb = np.zeros(max(m, 1), np.uint32)
         p = np.zeros(max(m, 1))
         acc = np.zeros(max(m, 1), np.int32)
         rep = np.zeros(max(m, 1), np.int32)
+        key = np.zeros(max(m, 1))
         _check(_lib().rd_last_fired(self._h, m, C.byref(n), _ptr(ida, C.c_uint32), _ptr(idb, C.c_uint32),
-                                    _ptr(p, C.c_double), _ptr(acc, C.c_int32), _ptr(rep, C.c_int32)),
+                                    _ptr(p, C.c_double), _ptr(acc, C.c_int32), _ptr(rep, C.c_int32),
+                                    _ptr(key, C.c_double)),
                "rd_last_fired")
         return {"id_a": ida[:m], "id_b": idb[:m], "p_enc": p[:m], "accepted": acc[:m].astype(bool),
-                "replica": rep[:m]}
+                "replica": rep[:m], "key": key[:m]}
 
     # -- per-pair probability and propagator batches (device tensors) ------------------------
     def pair_probs(self, r0, r, rule: int = 0, out=None):

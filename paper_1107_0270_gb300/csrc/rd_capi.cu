@@ -1,5 +1,7 @@
 // Host runtime behind the C ABI of include/rd.h: configuration checks, derived per-pair
 // parameters, cell grids, device buffers, CUDA-graph capture of two steps, state transfer.
+#include <map>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -176,6 +178,8 @@ static void derive_params(rd_handle* h) {
     q.inv_sigma_f = (float)(1.0 / p.sigma);
     q.inv_tau_f = (float)q.inv_tau;
     q.rcut2_f = (float)q.rcut2;
+    P.rcut2_max = std::max(P.rcut2_max, q.rcut2);
+    P.rcut2_max_f = std::max(P.rcut2_max_f, q.rcut2_f);
     q.s_f = (float)q.s;
     q.alpha_f = (float)q.alpha;
     P.pair_of[p.s1][p.s2] = (int8_t)k;
@@ -348,10 +352,12 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
     const size_t bytes = (size_t)n0 * n1 * sizeof(float);
     auto make = [&](int kind, Tab2& T) -> cudaError_t {
       float* t = (float*)alloc(bytes);
+      float4* q4 = (float4*)alloc(4 * bytes);
       double* tot = (double*)alloc((size_t)n0 * sizeof(double));
-      if (!t || !tot) return cudaErrorMemoryAllocation;
-      launch_build_table(h->L.P, k, kind, t, n0, n1, hstep, tot, h->stream);
+      if (!t || !q4 || !tot) return cudaErrorMemoryAllocation;
+      launch_build_table(h->L.P, k, kind, t, q4, n0, n1, hstep, tot, h->stream);
       T.v = t;
+      T.q = q4;
       T.n0 = n0;
       T.n1 = n1;
       T.h = (float)hstep;
@@ -369,8 +375,38 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
   return cudaMemcpy((void*)h->L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice);
 }
 
-// Cell grid of every replica for a cell edge of (factor x largest cut-off), coarsened per replica
-// until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of out[r].
+// Blocks of the cooperative matching launch for the current device, cached per device.
+static int match_grid_for_current_device() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  const int g = match_grid_size(sms);
+  cache[dev] = g;
+  return g;
+}
+
+// Cell-edge factor for about 0.25 interacting particles per cell (between 1 and 4 cut-offs) at the
+// given number density of binned particles.  The sweep walks five contiguous row ranges per
+// particle whatever the cell size, so its cost grows with the particles those rows hold (15 cells
+// x density) while the cell scan grows with the number of cells; 0.25 per cell balances the two.
+static double density_edge_factor(double nb, double volume, int dim, double rc) {
+  if (nb <= 0.0 || rc <= 0.0 || volume <= 0.0) return 1.0;
+  const double per_cell = nb / volume * std::pow(rc, (double)dim);
+  const double f = std::pow(0.25 / per_cell, 1.0 / dim);
+  return std::min(4.0, std::max(1.0, f));
+}
+
+// Cell grid of every replica.  factor > 0: cell edge = factor x the largest cut-off in every
+// replica; factor < 0: each replica's own density-based edge factor times -factor (never below one
+// cut-off), so that replicas of very different concentrations each get a suitable grid.  A grid is
+// coarsened until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of
+// out[r].
 static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
                             double rc, double factor, std::vector<RepDev>& out) {
   int64_t total = 0;
@@ -380,7 +416,9 @@ static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& r
     int64_t nb = 0;
     for (int s = 0; s < c.n_species; ++s)
       if ((binned_mask >> s) & 1u) nb += rp.n_init[s];
-    double f = factor;
+    double f = factor > 0.0 ? factor
+                            : std::max(1.0, -factor * density_edge_factor((double)nb, std::pow(rp.L, (double)c.dim),
+                                                                          c.dim, rc));
     int64_t cells = 1;
     for (int attempt = 0; attempt < 64; ++attempt) {
       cells = 1;
@@ -404,24 +442,7 @@ static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& r
   return total;
 }
 
-// Cell-edge factor for about 1.5 interacting particles per cell (between 1 and 4 cut-offs).
-static double density_factor(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
-                             double rc) {
-  double nb = 0.0, vol = 0.0;
-  for (const rd_replica& rp : reps) {
-    for (int s = 0; s < c.n_species; ++s)
-      if ((binned_mask >> s) & 1u) nb += (double)rp.n_init[s];
-    vol += std::pow(rp.L, (double)c.dim);
-  }
-  if (nb <= 0.0 || rc <= 0.0) return 1.0;
-  const double per_cell = nb / vol * std::pow(rc, (double)c.dim);
-  const double f = std::pow(1.5 / per_cell, 1.0 / c.dim);
-  return std::min(4.0, std::max(1.0, f));
-}
-
-
-// Autotuner: times a few steps for each candidate cell-edge factor and resolution block size on
-// the initial state, keeps the fastest, and restores the state (the scan epoch stays monotonic).
+// Cell-edge choice: a fixed factor (> 0) or the per-replica density rule with a multiplier (< 0).
 static cudaError_t apply_factor(rd_handle* h, double factor) {
   const rd_config& c = h->cfg;
   std::vector<RepDev> reps(c.n_replicas);
@@ -431,6 +452,8 @@ static cudaError_t apply_factor(rd_handle* h, double factor) {
   return cudaMemcpy(h->L.reps, reps.data(), reps.size() * sizeof(RepDev), cudaMemcpyHostToDevice);
 }
 
+// Autotuner: times a few steps for each candidate cell-edge choice and resolution block size on
+// the initial state, keeps the fastest, and restores the state (the scan epoch stays monotonic).
 static cudaError_t autotune(rd_handle* h) {
   const size_t xbytes = (size_t)h->L.cap_particles * h->vsize, ibytes = (size_t)h->L.cap_particles * 4;
   const size_t rbytes = (size_t)h->cfg.n_replicas * sizeof(RepDev);
@@ -565,16 +588,14 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   // factor is explicit (cell_factor_x100 > 0), density-based (0) or autotuned (< 0)
   const double rc = max_cutoff(c);
   const uint32_t bmask = h->hp.binned_mask;
-  const double f_auto = density_factor(c, h->reps_host, bmask, rc);
+  // cell-edge choices: > 0 a fixed factor, < 0 the per-replica density rule times -value
   std::vector<double> factors;
   if (c.cell_factor_x100 > 0) {
     factors.push_back(c.cell_factor_x100 / 100.0);
   } else if (c.cell_factor_x100 == 0) {
-    factors.push_back(f_auto);
+    factors.push_back(-1.0);
   } else {
-    factors.push_back(1.0);
-    for (double m : {0.6, 1.0, 1.5})
-      if (f_auto * m > 1.05) factors.push_back(f_auto * m);
+    for (double f : {-1.0, 1.0, -0.7, -1.5}) factors.push_back(f);
   }
   int64_t total_cells = 0, n_total = 0;
   h->reps_init.resize(c.n_replicas);
@@ -617,6 +638,8 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
 
   StepLaunch& L = h->L;
   std::memset(&L, 0, sizeof L);
+  L.pdl = true;
+  L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
   L.max_grid = 152 * 16;
@@ -976,7 +999,7 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
 }
 
 int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uint32_t* id_b, double* p_enc,
-                  int32_t* accepted, int32_t* replica) {
+                  int32_t* accepted, int32_t* replica, double* key) {
   if (!h || !n_out || cap < 0) return RD_EINVAL;
   RD_CUDA(cudaStreamSynchronize(h->stream));
   DevCtl ctl;
@@ -995,6 +1018,7 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
       if (p_enc) p_enc[k] = f[k].p;
       if (accepted) accepted[k] = (fs[k] & 3u) == FS_ACCEPTED;
       if (replica) replica[k] = (int32_t)(fs[k] >> 8);
+      if (key) key[k] = f[k].key;
     }
   }
   return ctl.status;
@@ -1064,7 +1088,6 @@ void rd_free(rd_handle* h) {
 // Allocation-free single step (rd_step_static).  Every scratch buffer of the step lives in one
 // file-scope device array; the caller passes the state in and receives it out in device buffers.
 // ================================================================================================
-#include <mutex>
 
 namespace {
 
@@ -1217,6 +1240,8 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
 
   StepLaunch L;
   std::memset(&L, 0, sizeof L);
+  L.pdl = true;
+  L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = 256;
   L.max_grid = 152 * 16;
@@ -1291,10 +1316,12 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
       const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
       const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
       float* t = (float*)b.take((size_t)n0 * n1 * sizeof(float));
+      float4* q4 = (float4*)b.take((size_t)n0 * n1 * sizeof(float4));
       double* tot = (double*)b.take((size_t)n0 * sizeof(double));
       if (!b.ok) return RD_EINVAL;
-      launch_build_table(L.P, k, 0, t, n0, n1, hstep, tot, s);
+      launch_build_table(L.P, k, 0, t, q4, n0, n1, hstep, tot, s);
       q.tab_preac.v = t;
+      q.tab_preac.q = q4;
       q.tab_preac.n0 = n0;
       q.tab_preac.n1 = n1;
       q.tab_preac.h = (float)hstep;

@@ -43,7 +43,8 @@ struct Series2D;
 // Uniform 2D table over (d0, d) with spacing h; row/column 0 is a ghost point at -h and two ghost
 // points follow the last grid point (n0 x n1 stored values).  Catmull-Rom bicubic lookup.
 struct Tab2 {
-  const float* v;
+  const float* v;             // n0 x n1 values on the grid (d0, d) = (h (i-1), h (j-1))
+  const float4* q;            // q[i n1 + j] = v[i n1 + j-1 .. j+2]: one aligned load per stencil row
   int32_t n0, n1;
   float inv_h, h;
 };
@@ -85,6 +86,8 @@ struct DevParams {
   int8_t pair_of[kMaxSpecies][kMaxSpecies];   // index into pairs, -1 = no interaction
   PairDev pairs[kMaxPairs];
   DecayDev decays[kMaxDecays];
+  double rcut2_max;            // largest squared cut-off over the pair rules
+  float rcut2_max_f, pad2;
 };
 
 struct RepDev {
@@ -109,6 +112,10 @@ struct DevCtl {
   uint32_t tile_ctr[2];    // tile tickets of the two scans
   uint32_t done_blocks;    // blocks of the compaction that finished
   uint32_t last_fired;     // fired pairs of the last completed step
+  uint32_t bar_count;      // grid barrier of the cooperative matching: arrivals, generation
+  uint32_t bar_gen;
+  uint32_t live[2];        // live conflict pairs after a matching round (by round parity)
+  uint32_t pad_ctl;
   double t;
   unsigned long long stats[RD_NSTATS];
 };
@@ -447,12 +454,12 @@ __device__ __forceinline__ float tab_eval(const Tab2& T, float d0, float d) {
   float wx[4], wy[4];
   cr_w(x - i, wx);
   cr_w(y - j, wy);
+  float4 v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = __ldg(T.q + (size_t)(i - 1 + a) * T.n1 + j);
   float acc = 0.0f;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const float* row = T.v + (size_t)(i - 1 + a) * T.n1 + (j - 1);
-    acc += wx[a] * (wy[0] * __ldg(row) + wy[1] * __ldg(row + 1) + wy[2] * __ldg(row + 2) + wy[3] * __ldg(row + 3));
-  }
+  for (int a = 0; a < 4; ++a) acc += wx[a] * (wy[0] * v[a].x + wy[1] * v[a].y + wy[2] * v[a].z + wy[3] * v[a].w);
   return acc;
 }
 

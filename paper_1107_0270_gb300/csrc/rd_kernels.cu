@@ -2,6 +2,7 @@
 // w carries the bits of (species | replica << 8); T = double for the FP64 step, float for the
 // mixed step.  Every kernel is a grid-stride loop so that CUDA graphs can be captured with grids
 // sized for the capacity while the live particle count stays on the device.
+#include <utility>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +11,15 @@
 #include "rd_kernels.h"
 
 namespace rd {
+
+// Programmatic dependent launch: a step kernel waits for the whole previous kernel (completion and
+// memory visibility) before it touches memory, then lets the next kernel's blocks be scheduled while
+// its own blocks run.  Both are no-ops for a launch without a programmatic dependency.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 
 template <class T> struct V4;
 template <> struct V4<double> { using type = d4; };
@@ -84,6 +94,7 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
                           uint32_t* __restrict__ deg, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
                           uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list,
                           unsigned long long* __restrict__ counts, int n_counts) {
+  pdl_enter();
   const DevParams& P = *Pp;
   if (blockIdx.x == 0) {
     // counters of the step's later kernels (the counters used by this kernel were reset at the
@@ -251,6 +262,7 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
                                                U* __restrict__ out, uint32_t* __restrict__ zero_after,
                                                U* __restrict__ agg, U* __restrict__ incl,
                                                uint32_t* __restrict__ flag, DevCtl* __restrict__ ctl, int which) {
+  pdl_enter();
   __shared__ U sm[32];
   __shared__ uint32_t s_tile;
   __shared__ U s_prefix;
@@ -356,6 +368,7 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
                                 const uint32_t* __restrict__ cell_start,
                                 typename V4<T>::type* __restrict__ sx0, typename V4<T>::type* __restrict__ sx1,
                                 uint32_t* __restrict__ sidx) {
+  pdl_enter();
   if (ctl->status) return;
   const uint32_t n = ctl->n;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -374,23 +387,29 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
 }
 
 // ================================================================================================
-// K3: cell sweep.  One thread per binned particle (cell order) visits the 27 (3D) / 9 (2D)
-// neighbouring cells; every pair (k, j > k) of an interacting species pair whose start-of-step
-// minimum-image distance is below r_cut is a candidate: p_enc from the start and end separations,
-// U_enc < p_enc fires and the pair is appended with a warp-aggregated atomic.
+// K3: cell sweep.  One thread per binned particle (cell order) walks the forward half of the
+// 27-cell (3D) / 9-cell (2D) neighbourhood; every pair (k, j > k) of an interacting species pair
+// whose start-of-step minimum-image distance is below r_cut is a candidate: p_enc from the start and
+// end separations, U_enc < p_enc fires and the pair is appended with a warp-aggregated atomic.
+// In cell order the three cells x-1..x+1 of a row are one contiguous particle range, so the half
+// stencil is five row ranges (3D: own row from k+1 through x+1, row y+1, the three rows of layer
+// z+1; 2D: the first two), each split in two where the row wraps around x.
 // ================================================================================================
+constexpr int kSweepRanges = 10;
+
 template <class T>
-__global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                                               const RepDev* __restrict__ reps,
-                                               const typename V4<T>::type* __restrict__ sx0,
-                                               const typename V4<T>::type* __restrict__ sx1,
-                                               const uint32_t* __restrict__ sidx,
-                                               const uint32_t* __restrict__ cell_start,
-                                               const int64_t total_cells, FiredPair* __restrict__ fired,
-                                               uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
-                                               int32_t* __restrict__ matched, const uint32_t cap_pairs) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                  const RepDev* __restrict__ reps,
+                                                  const typename V4<T>::type* __restrict__ sx0,
+                                                  const typename V4<T>::type* __restrict__ sx1,
+                                                  const uint32_t* __restrict__ sidx,
+                                                  const uint32_t* __restrict__ cell_start,
+                                                  const int64_t total_cells, FiredPair* __restrict__ fired,
+                                                  uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
+                                                  int32_t* __restrict__ matched, const uint32_t cap_pairs) {
+  pdl_enter();
   const DevParams& P = *Pp;
-  __shared__ uint2 ranges[14][256];
+  __shared__ uint2 ranges[kSweepRanges][256];
   if (ctl->status) return;
   const uint32_t nb = cell_start[total_cells];
   const uint32_t step = ctl->step;
@@ -417,124 +436,144 @@ __global__ void __launch_bounds__(256) k_sweep(const DevParams* __restrict__ Pp,
         cy = cell_coord_f(a0.y, rep.inv_edge_f[1], rep.nc[1]);
         if (dim == 3) cz = cell_coord_f(a0.z, rep.inv_edge_f[2], rep.nc[2]);
       }
-      const int ox = rep.nc[0] >= 3 ? 1 : 0, oy = rep.nc[1] >= 3 ? 1 : 0;
-      const int oz = (dim == 3 && rep.nc[2] >= 3) ? 1 : 0;
-      // forward half of the neighbour stencil: every unordered pair of neighbouring cells once,
-      // pairs inside the own cell with j > k.  All 14 cell ranges are fetched first (independent
-      // loads in flight together), then walked.
+      const int nc0 = rep.nc[0];
+      // the grid has 1 or >= 3 cells along each axis; with 1 only the own cell counts
+      const bool ox = nc0 >= 3, oy = rep.nc[1] >= 3, oz = dim == 3 && rep.nc[2] >= 3;
+      // all row ranges first (independent loads in flight together), the non-empty ones kept in
+      // order, then one flattened walk over them
+      int nr = 0;
 #pragma unroll
-      for (int t = 0; t < 14; ++t) {
-        const int dz = t < 5 ? 0 : 1;
-        const int dy = t < 2 ? 0 : (t < 5 ? 1 : (t - 5) / 3 - 1);
-        const int dx = t < 2 ? t : (t < 5 ? t - 3 : (t - 5) % 3 - 1);
-        uint2 rg = make_uint2(0u, 0u);
-        if ((dx == 0 || ox) && (dy == 0 || oy) && (dz == 0 || oz)) {
-          int xx = cx + dx, yy = cy + dy, zz = cz + dz;
-          xx = xx < 0 ? xx + rep.nc[0] : (xx >= rep.nc[0] ? xx - rep.nc[0] : xx);
+      for (int row = 0; row < kSweepRanges / 2; ++row) {
+        const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
+        const int dz = row < 2 ? 0 : 1;
+        if ((dy == 0 || oy) && (dz == 0 || oz)) {
+          int yy = cy + dy, zz = cz + dz;
           yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
           zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
-          const int64_t c = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * rep.nc[0] + xx;
-          rg = make_uint2(t == 0 ? k + 1 : cell_start[c], cell_start[c + 1]);
+          const int64_t rowc = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * nc0;
+          const int xl = (row == 0 || !ox) ? cx : max(cx - 1, 0);
+          const int xh = ox ? min(cx + 1, nc0 - 1) : cx;
+          const uint2 main_rg = make_uint2(row == 0 ? k + 1 : cell_start[rowc + xl], cell_start[rowc + xh + 1]);
+          uint2 wrap_rg = make_uint2(0u, 0u);
+          if (ox && row != 0 && cx == 0)
+            wrap_rg = make_uint2(cell_start[rowc + nc0 - 1], cell_start[rowc + nc0]);
+          else if (ox && cx == nc0 - 1)
+            wrap_rg = make_uint2(cell_start[rowc], cell_start[rowc + 1]);
+          if (main_rg.y > main_rg.x) ranges[nr++][threadIdx.x] = main_rg;
+          if (wrap_rg.y > wrap_rg.x) ranges[nr++][threadIdx.x] = wrap_rg;
         }
-        ranges[t][threadIdx.x] = rg;
       }
-      for (int t = 0; t < 14; ++t) {
-        const uint2 rg = ranges[t][threadIdx.x];
-        {
-          {
-            const uint32_t jb = rg.x, je = rg.y;
-            for (uint32_t j = jb; j < je; ++j) {
-              const auto b0 = sx0[j];
-              const uint32_t spb = w_bits(b0.w) & 0xFFu;
-              const int rule = P.pair_of[spa][spb];
-              if (rule < 0) continue;
-              const PairDev& pr = P.pairs[rule];
-              const auto b1 = sx1[j];
-              const uint32_t idb = w_bits(b1.w);
-              // orient the pair from the lower id to the higher id
-              const bool swap = idb < ida;
-              const uint32_t id_lo = swap ? idb : ida, id_hi = swap ? ida : idb;
-              double p;
-              float pf = 0.0f;
-              bool overlap;
-              if constexpr (sizeof(T) == 8) {
-                const double sg = swap ? -1.0 : 1.0;
-                const double r0x = min_image(sg * (b0.x - a0.x), rep.L, rep.half_L);
-                const double r0y = min_image(sg * (b0.y - a0.y), rep.L, rep.half_L);
-                const double r0z = dim == 3 ? min_image(sg * (b0.z - a0.z), rep.L, rep.half_L) : 0.0;
-                const double r02 = norm2_rn(r0x, r0y, r0z, dim);
-                if (!(r02 < pr.rcut2)) continue;
-                const double rx = min_image(sg * (b1.x - a1.x), rep.L, rep.half_L);
-                const double ry = min_image(sg * (b1.y - a1.y), rep.L, rep.half_L);
-                const double rz = dim == 3 ? min_image(sg * (b1.z - a1.z), rep.L, rep.half_L) : 0.0;
-                const double R0 = sqrt(r02) / pr.sigma;
-                const double R = sqrt(norm2_rn(rx, ry, rz, dim)) / pr.sigma;
-                overlap = R <= 1.0;
-                p = p_enc_dim(P, pr, R, R0);
-              } else {
-                const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf);
-                const float r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
-                const float r0z = dim == 3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
-                const float r02 = r0x * r0x + r0y * r0y + r0z * r0z;
-                if (!(r02 < pr.rcut2_f)) continue;
-                const float rx = min_image_f(b1.x - a1.x, rep.Lf, rep.half_Lf);
-                const float ry = min_image_f(b1.y - a1.y, rep.Lf, rep.half_Lf);
-                const float rz = dim == 3 ? min_image_f(b1.z - a1.z, rep.Lf, rep.half_Lf) : 0.0f;
-                const float d0 = (sqrtf(r02) - pr.sigma_f) * pr.inv_sigma_f;
-                const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
-                overlap = d <= 0.0f;
-                if (dim == 3) {
-                  pf = p_enc3_f(d, d0, pr.inv_tau_f);
-                } else if (d <= 0.0f || d0 <= 0.0f) {
-                  pf = 1.0f;
-                } else {
-                  const float xx = d * d0 * pr.inv_tau_f;
-                  pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
-                }
-                p = (double)pf;
-              }
-              const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
-              ++n_cand;
-              n_overlap += overlap;
-              bool fires;
-              if constexpr (sizeof(T) == 8) {
-                const double u_enc = u52(w.x, w.y);
-                n_near += fabs(u_enc - p) <= 1e-9;
-                fires = u_enc < p;
-              } else {
-                fires = u23(w.x) < pf;     // mixed step: FP32 draw and comparison
-              }
-              if (fires) {
-                const unsigned m = __activemask();
-                const int lane = threadIdx.x & 31;
-                const int leader = __ffs(m) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(&ctl->fired, (uint32_t)__popc(m));
-                base = __shfl_sync(m, base, leader);
-                const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < cap_pairs) {
-                  FiredPair f;
-                  const uint32_t ia = sidx[k], ib = sidx[j];
-                  f.ia = swap ? ib : ia;
-                  f.ib = swap ? ia : ib;
-                  f.ida = id_lo;
-                  f.idb = id_hi;
-                  f.p = p;
-                  if constexpr (sizeof(T) == 8)
-                    f.key = -log(u52(w.z, w.w)) / p;
-                  else
-                    f.key = (double)(-logf(u23(w.z)) / pf);
-                  fired[pos] = f;
-                  fstate[pos] = FS_LIVE | ((uint32_t)rule << 2) | (r << 8);
-                  matched[f.ia] = -1;
-                  matched[f.ib] = -1;
-                  atomicAdd(&deg[f.ia], 1u);
-                  atomicAdd(&deg[f.ib], 1u);
-                } else {
-                  set_status(ctl, RD_ECAPACITY);
-                }
-              }
-            }
+      int rr = 0;
+      uint2 rg = nr > 0 ? ranges[0][threadIdx.x] : make_uint2(0u, 0u);
+      uint32_t j = rg.x;
+      while (rr < nr) {
+        const uint32_t jj = j++;
+        if (j >= rg.y && ++rr < nr) {
+          rg = ranges[rr][threadIdx.x];
+          j = rg.x;
+        }
+        const auto b0 = sx0[jj];
+        // start-of-step separation first (the norm does not depend on the pair's orientation),
+        // against the largest cut-off; the species pair and its own cut-off after that
+        double p, r02;
+        float pf = 0.0f, r02f = 0.0f;
+        if constexpr (sizeof(T) == 8) {
+          const double r0x = min_image(b0.x - a0.x, rep.L, rep.half_L);
+          const double r0y = min_image(b0.y - a0.y, rep.L, rep.half_L);
+          const double r0z = dim == 3 ? min_image(b0.z - a0.z, rep.L, rep.half_L) : 0.0;
+          r02 = norm2_rn(r0x, r0y, r0z, dim);
+          if (!(r02 < P.rcut2_max)) continue;
+        } else {
+          const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf);
+          const float r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
+          const float r0z = dim == 3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
+          r02f = r0x * r0x + r0y * r0y + r0z * r0z;
+          if (!(r02f < P.rcut2_max_f)) continue;
+        }
+        const uint32_t spb = w_bits(b0.w) & 0xFFu;
+        const int rule = P.pair_of[spa][spb];
+        if (rule < 0) continue;
+        const PairDev& pr = P.pairs[rule];
+        if constexpr (sizeof(T) == 8) {
+          if (!(r02 < pr.rcut2)) continue;
+        } else {
+          if (!(r02f < pr.rcut2_f)) continue;
+        }
+        const auto b1 = sx1[jj];
+        const uint32_t idb = w_bits(b1.w);
+        // orient the pair from the lower id to the higher id
+        const bool swap = idb < ida;
+        const uint32_t id_lo = swap ? idb : ida, id_hi = swap ? ida : idb;
+        bool overlap;
+        if constexpr (sizeof(T) == 8) {
+          const double rx = min_image(b1.x - a1.x, rep.L, rep.half_L);
+          const double ry = min_image(b1.y - a1.y, rep.L, rep.half_L);
+          const double rz = dim == 3 ? min_image(b1.z - a1.z, rep.L, rep.half_L) : 0.0;
+          const double R0 = sqrt(r02) / pr.sigma;
+          const double R = sqrt(norm2_rn(rx, ry, rz, dim)) / pr.sigma;
+          overlap = R <= 1.0;
+          p = p_enc_dim(P, pr, R, R0);
+        } else {
+          const float rx = min_image_f(b1.x - a1.x, rep.Lf, rep.half_Lf);
+          const float ry = min_image_f(b1.y - a1.y, rep.Lf, rep.half_Lf);
+          const float rz = dim == 3 ? min_image_f(b1.z - a1.z, rep.Lf, rep.half_Lf) : 0.0f;
+          const float d0 = (sqrtf(r02f) - pr.sigma_f) * pr.inv_sigma_f;
+          const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - pr.sigma_f) * pr.inv_sigma_f;
+          overlap = d <= 0.0f;
+          if (dim == 3) {
+            pf = p_enc3_f(d, d0, pr.inv_tau_f);
+          } else if (d <= 0.0f || d0 <= 0.0f) {
+            pf = 1.0f;
+          } else {
+            const float xx = d * d0 * pr.inv_tau_f;
+            pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
+          }
+          p = (double)pf;
+        }
+        ++n_cand;
+        n_overlap += overlap;
+        // mixed step: FP32 draw and comparison; the smallest FP32 uniform is 2^-24, so a smaller
+        // p_enc cannot fire and needs no draw
+        if constexpr (sizeof(T) == 4) {
+          if (!(pf > 0x1p-24f)) continue;
+        }
+        const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
+        bool fires;
+        if constexpr (sizeof(T) == 8) {
+          const double u_enc = u52(w.x, w.y);
+          n_near += fabs(u_enc - p) <= 1e-9;
+          fires = u_enc < p;
+        } else {
+          fires = u23(w.x) < pf;
+        }
+        if (fires) {
+          const unsigned m = __activemask();
+          const int lane = threadIdx.x & 31;
+          const int leader = __ffs(m) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(&ctl->fired, (uint32_t)__popc(m));
+          base = __shfl_sync(m, base, leader);
+          const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+          if (pos < cap_pairs) {
+            FiredPair f;
+            const uint32_t ia = sidx[k], ib = sidx[jj];
+            f.ia = swap ? ib : ia;
+            f.ib = swap ? ia : ib;
+            f.ida = id_lo;
+            f.idb = id_hi;
+            f.p = p;
+            if constexpr (sizeof(T) == 8)
+              f.key = -log(u52(w.z, w.w)) / p;
+            else
+              f.key = (double)(-logf(u23(w.z)) / pf);
+            fired[pos] = f;
+            fstate[pos] = FS_LIVE | ((uint32_t)rule << 2) | (r << 8);
+            matched[f.ia] = -1;
+            matched[f.ib] = -1;
+            atomicAdd(&deg[f.ia], 1u);
+            atomicAdd(&deg[f.ib], 1u);
+          } else {
+            set_status(ctl, RD_ECAPACITY);
           }
         }
       }
@@ -567,6 +606,7 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
                                 uint32_t* __restrict__ accepted,
                                 unsigned long long* __restrict__ best_key,
                                 unsigned long long* __restrict__ best_pid, uint32_t cap_pairs) {
+  pdl_enter();
   if (ctl->status) return;
   const uint32_t nf = min(ctl->fired, cap_pairs);
   unsigned long long acc = 0;
@@ -600,32 +640,86 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
   warp_sum_add(&ctl->stats[RD_STAT_MATCHED], acc);
 }
 
-__global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                                                       const FiredPair* __restrict__ fired,
-                                                       uint32_t* __restrict__ fstate,
-                                                       int32_t* __restrict__ matched,
-                                                       const uint32_t* __restrict__ conflict,
-                                                       uint32_t* __restrict__ accepted,
-                                                       unsigned long long* __restrict__ best_key,
-                                                       unsigned long long* __restrict__ best_pid) {
-  __shared__ uint32_t live;
+// Grid-wide barrier of the cooperative matching launch (every block resident).  Bounded: a block
+// that waits longer than kBarrierSpin polls sets RD_ETIMEOUT and leaves; the caller then stops.
+constexpr uint32_t kBarrierSpin = 1u << 22;
+constexpr uint32_t kMatchSingleMax = 2048;   // conflict pairs handled by one block without barriers
+
+__device__ __forceinline__ bool grid_barrier(DevCtl* ctl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = &ctl->bar_gen;
+    const uint32_t g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
+      ctl->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      uint32_t spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpin) {
+          set_status(ctl, RD_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok && *(volatile int32_t*)&ctl->status == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Rounds of locally-dominant matching over the conflict list.  A short list is handled by block 0
+// alone (block barriers); a long one by the whole cooperative grid (grid barriers between the
+// phases of a round).  Each round: every live pair offers its key to both particles (atomic min),
+// then its (id_a, id_b) among equal keys; a pair that is the minimum at both particles is
+// accepted; pairs touching an accepted particle die, the rest stay live.
+__global__ void __launch_bounds__(256) k_match_rounds(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                      const FiredPair* __restrict__ fired,
+                                                      uint32_t* __restrict__ fstate,
+                                                      int32_t* __restrict__ matched,
+                                                      const uint32_t* __restrict__ conflict,
+                                                      uint32_t* __restrict__ accepted,
+                                                      unsigned long long* __restrict__ best_key,
+                                                      unsigned long long* __restrict__ best_pid) {
+  pdl_enter();
   __shared__ unsigned long long acc_s;
+  __shared__ uint32_t live_s;
   if (ctl->status) return;
   const uint32_t nc = ctl->n_conflict;
   if (nc == 0) return;
+  const bool multi = nc > kMatchSingleMax && gridDim.x > 1;
+  if (!multi && blockIdx.x != 0) return;
+  const uint32_t nthr = multi ? gridDim.x * blockDim.x : blockDim.x;
+  const uint32_t tid = multi ? blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
+  auto sync = [&]() -> bool {
+    if (multi) return grid_barrier(ctl);
+    __syncthreads();
+    return true;
+  };
   if (threadIdx.x == 0) acc_s = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->live[0] = 0u;
+    ctl->live[1] = 0u;
+  }
   int rounds = 0;
-  for (;;) {
-    // keys: each live pair offers its key to both particles
-    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+  bool ok = sync();
+  while (ok) {
+    for (uint32_t q = tid; q < nc; q += nthr) {
       const uint32_t e = conflict[q];
       if ((fstate[e] & 3u) != FS_LIVE) continue;
       const unsigned long long kb = (unsigned long long)__double_as_longlong(fired[e].key);
       atomicMin(&best_key[fired[e].ia], kb);
       atomicMin(&best_key[fired[e].ib], kb);
     }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+    if (!(ok = sync())) break;
+    for (uint32_t q = tid; q < nc; q += nthr) {
       const uint32_t e = conflict[q];
       if ((fstate[e] & 3u) != FS_LIVE) continue;
       const FiredPair f = fired[e];
@@ -634,8 +728,8 @@ __global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restri
       if (best_key[f.ia] == kb) atomicMin(&best_pid[f.ia], pid);
       if (best_key[f.ib] == kb) atomicMin(&best_pid[f.ib], pid);
     }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+    if (!(ok = sync())) break;
+    for (uint32_t q = tid; q < nc; q += nthr) {
       const uint32_t e = conflict[q];
       if ((fstate[e] & 3u) != FS_LIVE) continue;
       const FiredPair f = fired[e];
@@ -649,9 +743,9 @@ __global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restri
         atomicAdd(&acc_s, 1ull);
       }
     }
-    if (threadIdx.x == 0) live = 0;
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+    if (threadIdx.x == 0) live_s = 0u;
+    if (!(ok = sync())) break;
+    for (uint32_t q = tid; q < nc; q += nthr) {
       const uint32_t e = conflict[q];
       if ((fstate[e] & 3u) != FS_LIVE) continue;
       const FiredPair f = fired[e];
@@ -662,20 +756,26 @@ __global__ void __launch_bounds__(1024) k_match_rounds(const DevParams* __restri
         best_key[f.ib] = ~0ull;
         best_pid[f.ia] = ~0ull;
         best_pid[f.ib] = ~0ull;
-        atomicAdd(&live, 1u);
+        atomicAdd(&live_s, 1u);
       }
     }
     __syncthreads();
+    const int par = rounds & 1;
+    if (threadIdx.x == 0 && live_s) atomicAdd(&ctl->live[par], live_s);
+    if (!(ok = sync())) break;
     ++rounds;
+    const uint32_t live = *(volatile uint32_t*)&ctl->live[par];
     if (live == 0) break;
+    // the other parity was last read before this round's first barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->live[par ^ 1] = 0u;
     if (rounds >= Pp->match_max_rounds) {
-      if (threadIdx.x == 0) set_status(ctl, RD_ETIMEOUT);
+      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, RD_ETIMEOUT);
       break;
     }
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&ctl->stats[RD_STAT_MATCHED], acc_s);
-    atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
+    if (acc_s) atomicAdd(&ctl->stats[RD_STAT_MATCHED], acc_s);
+    if (blockIdx.x == 0) atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
   }
 }
 
@@ -1067,6 +1167,7 @@ __global__ void __launch_bounds__(128) k_resolve_all(const DevParams* __restrict
                                                     const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
                                                     typename V4<T>::type* __restrict__ prodpos,
                                                     uint32_t* __restrict__ deg, uint32_t cap_pairs) {
+  pdl_enter();
   const DevParams& P = *Pp;
   // the encounter degrees of this step go back to zero for the next one
   const uint32_t nf = min(ctl->fired, cap_pairs);
@@ -1101,14 +1202,46 @@ __global__ void __launch_bounds__(128) k_resolve_all(const DevParams* __restrict
 // order inside their replica, products follow the replica's survivors in owner order with ids
 // next_id + rank.  An error latched during the step turns this into a copy of the unchanged state.
 // ================================================================================================
+// Per-warp aggregated count: lanes holding the same (replica, species) key add once.  Called by all
+// 32 lanes of a converged warp; key kNoKey is skipped.
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+__device__ __forceinline__ void count_key(uint32_t key, bool smem, uint32_t* hist, unsigned long long* counts) {
+  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  if (key != kNoKey && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    if (smem)
+      atomicAdd(&hist[key], (uint32_t)__popc(peers));
+    else
+      atomicAdd(&counts[key], (unsigned long long)__popc(peers));
+  }
+}
+
+// Species totals over all replicas of the (replica, species) counts, by one whole block.
+__device__ __forceinline__ void species_totals(const unsigned long long* __restrict__ counts, int n_replicas, int ns,
+                                               long long* __restrict__ out) {
+  __shared__ unsigned long long tot[RD_MAX_SPECIES];
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) tot[k] = 0ull;
+  __syncthreads();
+  for (int k = 0; k < ns; ++k) {
+    unsigned long long v = 0ull;
+#pragma unroll 4
+    for (int r = threadIdx.x; r < n_replicas; r += blockDim.x) v += counts[(size_t)r * ns + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[k], v);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) out[k] = (long long)tot[k];
+}
+
 template <class T>
-__global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256) k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
                           RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
                           const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                           const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
                           const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
                           uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts,
                           long long* __restrict__ history, int history_len) {
+  pdl_enter();
   extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
   const DevParams& P = *Pp;
   const uint32_t n = ctl->n;
@@ -1120,44 +1253,47 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
   }
-  auto count = [&](uint32_t wb) {
-    const uint32_t key = (wb >> 8) * ns + (wb & 0xFFu);
-    if (use_smem)
-      atomicAdd(&hist[key], 1u);
-    else
-      atomicAdd(&counts[key], 1ull);
-  };
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (fail) {
-      const auto q0 = x0[i];
-      xo[i] = q0;
-      ido[i] = id[i];
-      count(w_bits(q0.w));
-      continue;
+  auto key_of = [&](uint32_t wb) { return (wb >> 8) * ns + (wb & 0xFFu); };
+  // every lane runs the same number of iterations so that the counting stays warp-converged
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (n + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey;
+    if (i < n) {
+      if (fail) {
+        const auto q0 = x0[i];
+        xo[i] = q0;
+        ido[i] = id[i];
+        k0 = key_of(w_bits(q0.w));
+      } else {
+        const uint32_t st = status[i];
+        const auto q = x1[i];
+        const uint32_t wb = w_bits(q.w);
+        const RepDev& rep = reps[wb >> 8];
+        const unsigned long long e = scan[i];
+        const unsigned long long eb = scan[rep.beg], ee = scan[rep.end];
+        const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
+        const uint32_t P_beg = (uint32_t)eb, S_end = (uint32_t)(ee >> 32);
+        if (!(st & ST_CONSUMED)) {
+          const uint32_t o = S_i + P_beg;
+          xo[o] = q;
+          ido[o] = id[i];
+          k0 = key_of(wb);
+        }
+        const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
+        for (uint32_t k = 0; k < np; ++k) {
+          const uint32_t o = S_end + P_i + k;
+          const auto pp = prodpos[2 * (size_t)i + k];
+          xo[o] = pp;
+          ido[o] = rep.next_id + (P_i - P_beg) + k;
+          (k == 0 ? k1 : k2) = key_of(w_bits(pp.w));
+        }
+      }
     }
-    const uint32_t st = status[i];
-    const auto q = x1[i];
-    const uint32_t wb = w_bits(q.w);
-    const uint32_t r = wb >> 8;
-    const RepDev& rep = reps[r];
-    const unsigned long long e = scan[i];
-    const unsigned long long eb = scan[rep.beg], ee = scan[rep.end];
-    const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
-    const uint32_t P_beg = (uint32_t)eb, S_end = (uint32_t)(ee >> 32);
-    if (!(st & ST_CONSUMED)) {
-      const uint32_t o = S_i + P_beg;
-      xo[o] = q;
-      ido[o] = id[i];
-      count(wb);
-    }
-    const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
-    for (uint32_t k = 0; k < np; ++k) {
-      const uint32_t o = S_end + P_i + k;
-      const auto pp = prodpos[2 * (size_t)i + k];
-      xo[o] = pp;
-      ido[o] = rep.next_id + (P_i - P_beg) + k;
-      count(w_bits(pp.w));
-    }
+    count_key(k0, use_smem, hist, counts);
+    if (__any_sync(0xFFFFFFFFu, k1 != kNoKey)) count_key(k1, use_smem, hist, counts);
+    if (__any_sync(0xFFFFFFFFu, k2 != kNoKey)) count_key(k2, use_smem, hist, counts);
   }
   if (use_smem) {
     __syncthreads();
@@ -1181,16 +1317,9 @@ __global__ void k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__
       reps[r].end = (uint32_t)(ee >> 32) + (uint32_t)ee;
     }
   }
-  __syncthreads();
   // per-step totals over replicas of every species (ring buffer indexed by the new step)
-  if (!fail && history_len > 0) {
-    const int slot = (int)((ctl->step + 1u) % (uint32_t)history_len);
-    for (int sp = threadIdx.x; sp < ns; sp += blockDim.x) {
-      long long tot_sp = 0;
-      for (int r = 0; r < P.n_replicas; ++r) tot_sp += (long long)counts[(size_t)r * ns + sp];
-      history[(size_t)slot * ns + sp] = tot_sp;
-    }
-  }
+  if (!fail && history_len > 0)
+    species_totals(counts, P.n_replicas, ns, history + (size_t)((ctl->step + 1u) % (uint32_t)history_len) * ns);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (!fail) {
@@ -1254,9 +1383,16 @@ template <class T>
 __global__ void k_count(const DevParams* __restrict__ Pp, const DevCtl* __restrict__ ctl,
                         const typename V4<T>::type* __restrict__ x, unsigned long long* __restrict__ counts) {
   const uint32_t n = ctl->n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t wb = w_bits(x[i].w);
-    atomicAdd(&counts[(size_t)(wb >> 8) * Pp->n_species + (wb & 0xFFu)], 1ull);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = (n + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t key = kNoKey;
+    if (i < n) {
+      const uint32_t wb = w_bits(x[i].w);
+      key = (wb >> 8) * Pp->n_species + (wb & 0xFFu);
+    }
+    count_key(key, false, nullptr, counts);
   }
 }
 
@@ -1356,14 +1492,26 @@ __global__ void k_table_ghost_row(float* __restrict__ T, int n1) {
     T[j] = 4.0f * T[n1 + j] - 6.0f * T[2 * n1 + j] + 4.0f * T[3 * n1 + j] - T[4 * n1 + j];
 }
 
-void launch_build_table(const DevParams* P, int rule, int kind, float* out, int n0, int n1, double h, double* tot,
-                        cudaStream_t s) {
+// quad layout of a finished table: q[i n1 + j] = (v[i n1 + j-1], .., v[i n1 + j+2]), zero off the ends
+__global__ void k_table_quads(const float* __restrict__ T, int n0, int n1, float4* __restrict__ Q) {
+  const int64_t total = (int64_t)n0 * n1;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(k % n1);
+    float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (j >= 1 && j + 2 < n1) q = make_float4(T[k - 1], T[k], T[k + 1], T[k + 2]);
+    Q[k] = q;
+  }
+}
+
+void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
+                        double* tot, cudaStream_t s) {
   if (kind == 2) k_tail_totals<<<(n0 + 63) / 64, 64, 0, s>>>(P, rule, n0, h, tot);
   const int64_t total = (int64_t)n0 * n1;
   const int G = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
   k_build_table<<<G, 128, 0, s>>>(P, rule, kind, out, n0, n1, h, tot);
   k_table_ghosts<<<(n0 + 255) / 256, 256, 0, s>>>(out, n0, n1);
   k_table_ghost_row<<<(n1 + 255) / 256, 256, 0, s>>>(out, n1);
+  k_table_quads<<<G, 128, 0, s>>>(out, n0, n1, quad);
 }
 
 // ================================================================================================
@@ -1374,6 +1522,47 @@ static inline int grid_for(int64_t n, int block, int max_grid) {
   if (g < 1) g = 1;
   if (g > max_grid) g = max_grid;
   return (int)g;
+}
+
+// Kernel launch with the programmatic-stream-serialization attribute (see pdl_enter).
+template <typename... KArgs, typename... Args>
+static void launch_k(bool pdl, void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Cooperative launch (all blocks resident at once, as the grid barrier requires; a grid larger
+// than the device can hold is refused by the runtime).
+template <typename... KArgs, typename... Args>
+static void launch_coop(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+int match_grid_size(int device_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_rounds, 256, 0) != cudaSuccess || per_sm < 1)
+    return 1;
+  return device_sms * std::min(per_sm, 2);
 }
 
 template <class T>
@@ -1393,36 +1582,38 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   const int64_t tile = 256 * (int64_t)kScanItems;
 
   mark("begin");
-  k_prepare<T><<<Gp, B, 0, s>>>(L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg, L.cell_of, L.slot,
-                                 L.cell_count, L.decay_list, L.counts, L.n_counts);
+  const bool pdl = L.pdl;
+  launch_k(pdl, k_prepare<T>, Gp, B, 0, s, L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg,
+           L.cell_of, L.slot, L.cell_count, L.decay_list, L.counts, L.n_counts);
   mark("k_prepare");
   const int nbc = (int)((L.total_cells + tile - 1) / tile);
-  k_scan1<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, L.total_cells, nullptr,
-                                                       L.cell_start, L.cell_count, L.agg32, L.incl32, L.flags,
-                                                       L.ctl, 0);
+  launch_k(pdl, k_scan1<uint32_t, LoadCellCount>, nbc, 256, 0, s, LoadCellCount{L.cell_count}, L.total_cells,
+           (const uint32_t*)nullptr, L.cell_start, L.cell_count, L.agg32, L.incl32, L.flags, L.ctl, 0);
   mark("k_scan_cells");
-  k_scatter_cells<T><<<Gp, B, 0, s>>>(L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1, L.sidx);
+  launch_k(pdl, k_scatter_cells<T>, Gp, B, 0, s, L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1,
+           L.sidx);
   mark("k_scatter_cells");
-  k_sweep<T><<<Gp, 256, 0, s>>>(L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired,
-                                 L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs);
+  launch_k(pdl, k_sweep<T>, Gp, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells,
+           L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs);
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
-  k_match_trivial<<<Gf, 256, 0, s>>>(L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted, L.best_key,
-                                     L.best_pid, (uint32_t)L.cap_pairs);
-  k_match_rounds<<<1, 1024, 0, s>>>(L.P, L.ctl, L.fired, L.fstate, L.matched, L.conflict, L.accepted, L.best_key,
-                                    L.best_pid);
+  launch_k(pdl, k_match_trivial, Gf, 256, 0, s, L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted,
+           L.best_key, L.best_pid, (uint32_t)L.cap_pairs);
+  launch_coop(k_match_rounds, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.fired, L.fstate, L.matched,
+              L.conflict, L.accepted, L.best_key, L.best_pid);
   mark("k_match");
   const int rb = L.resolve_block > 0 ? L.resolve_block : 32;
-  k_resolve_all<T><<<(152 * 8 * 32) / rb, rb, 0, s>>>(L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted, L.decay_list,
-                                                       x0, x1, L.id_cur, L.status, prod, L.deg, (uint32_t)L.cap_pairs);
+  launch_k(pdl, k_resolve_all<T>, (152 * 8 * 32) / rb, rb, 0, s, L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted,
+           L.decay_list, x0, x1, L.id_cur, L.status, prod, L.deg, (uint32_t)L.cap_pairs);
   mark("k_resolve_all");
   const int nbp = (int)((L.cap_particles + tile - 1) / tile);
-  k_scan1<unsigned long long, LoadCompact><<<nbp, 256, 0, s>>>(LoadCompact{L.status}, 0, &L.ctl->n, L.scan, nullptr,
-                                                               L.agg64, L.incl64, L.flags + L.flag_stride, L.ctl, 1);
+  launch_k(pdl, k_scan1<unsigned long long, LoadCompact>, nbp, 256, 0, s, LoadCompact{L.status}, (int64_t)0,
+           (const uint32_t*)&L.ctl->n, L.scan, (uint32_t*)nullptr, L.agg64, L.incl64, L.flags + L.flag_stride, L.ctl,
+           1);
   mark("k_scan_compact");
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
-  k_compact<T><<<Gp, B, hist_bytes, s>>>(L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan, xo,
-                                          L.id_next, L.counts, L.n_counts, L.history, L.history_len);
+  launch_k(pdl, k_compact<T>, Gp, B, hist_bytes, s, L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan,
+           xo, L.id_next, L.counts, L.n_counts, L.history, L.history_len);
   mark("k_compact");
 }
 
@@ -1451,12 +1642,7 @@ __global__ void k_history_now(const DevParams* __restrict__ Pp, const DevCtl* __
                               const unsigned long long* __restrict__ counts, long long* __restrict__ history,
                               int history_len) {
   const int ns = Pp->n_species;
-  const int slot = (int)(ctl->step % (uint32_t)history_len);
-  for (int sp = threadIdx.x; sp < ns; sp += blockDim.x) {
-    long long t = 0;
-    for (int r = 0; r < Pp->n_replicas; ++r) t += (long long)counts[(size_t)r * ns + sp];
-    history[(size_t)slot * ns + sp] = t;
-  }
+  species_totals(counts, Pp->n_replicas, ns, history + (size_t)(ctl->step % (uint32_t)history_len) * ns);
 }
 
 void launch_count(const StepLaunch& L, cudaStream_t s) {
@@ -1466,7 +1652,7 @@ void launch_count(const StepLaunch& L, cudaStream_t s) {
     k_count<float><<<G, 256, 0, s>>>(L.P, L.ctl, (const float4*)L.x_cur, L.counts);
   else
     k_count<double><<<G, 256, 0, s>>>(L.P, L.ctl, (const d4*)L.x_cur, L.counts);
-  if (L.history && L.history_len > 0) k_history_now<<<1, 32, 0, s>>>(L.P, L.ctl, L.counts, L.history, L.history_len);
+  if (L.history && L.history_len > 0) k_history_now<<<1, 256, 0, s>>>(L.P, L.ctl, L.counts, L.history, L.history_len);
 }
 
 void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,

@@ -18,6 +18,8 @@ struct StepLaunch {
   int max_grid;
   int scan_items;
   int resolve_block;           // threads per block of the resolution kernel (32..128)
+  bool pdl;                    // programmatic dependent launch between the step kernels
+  int match_grid;              // blocks of the cooperative matching launch (all resident)
   int64_t cap_particles, cap_pairs, total_cells;
   int n_counts;
   const DevParams* P;
@@ -81,14 +83,16 @@ struct KernelTimer {
   }
 };
 
+// blocks of the cooperative matching launch that fit on the device at once (>= 1)
+int match_grid_size(int device_sms);
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer);
 void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int32_t* sp_of, const uint32_t* id_of,
                            uint32_t n, cudaStream_t s);
 void launch_count(const StepLaunch& L, cudaStream_t s);
 void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,
                        double* pr, int max_grid, cudaStream_t s);
-void launch_build_table(const DevParams* P, int rule, int kind, float* out, int n0, int n1, double h, double* tot,
-                        cudaStream_t s);
+void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
+                        double* tot, cudaStream_t s);
 void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
                      int max_grid, cudaStream_t s);
 
