@@ -32,12 +32,12 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-KERNELS_PER_STEP = 8           # kernels of one step: prepare, scan (cells), scatter, sweep, 2 match,
-                               # resolve, scan (compaction), compact
+KERNELS_PER_STEP = 8           # kernels of one step: prepare, scan (cells), scatter, sweep, trivial
+                               # matching, matching rounds + resolution, scan (compaction), compact
 L2_FLUSH_BYTES = 512 << 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the ensemble, network and membrane context measurements")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def box_edge(args):
@@ -132,18 +132,35 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def algorithmic_bytes(kernel, precision, n, n_binned, candidates):
-    """Per-launch algorithmic bytes of the step kernels (minimum traffic the stage needs)."""
+def algorithmic_bytes(kernel, precision, w):
+    """Per-launch algorithmic bytes of a step kernel: the data the stage must read and write once
+    (w: particles n, binned particles nb, cells, fired pairs, accepted pairs, decays per step).
+    v = bytes of one position record (x, y, z, species/id bits)."""
     v = 16 if precision == "mixed" else 32
-    if kernel == "k_prepare":      # read position + id, write end position
-        return n * (2 * v + 4)
-    if kernel == "k_sweep":        # read start + end position of each binned particle once
-        return n_binned * 2 * v
-    if kernel == "k_compact":      # read end position + id + status, write position + id
-        return n * (2 * v + 12)
-    if kernel == "k_scatter_cells":
-        return n_binned * (4 * v + 8)
-    return None
+    n, nb, cells = w["n"], w["nb"], w["cells"]
+    fired, acc, dec = w["fired"], w["accepted"], w["decays"]
+    table = {
+        # read position + id; write end position, status, cell, slot; one cell counter per binned
+        "k_prepare": n * (2 * v + 16) + 4 * nb,
+        # read the cell counts, write the cell starts, clear the counts
+        "k_scan_cells": 12 * cells,
+        # read cell, slot, both positions, id, cell start; write both sorted positions + index
+        "k_scatter_cells": nb * (4 * v + 20),
+        # both positions of every binned particle once, the cell starts once, the fired records
+        "k_sweep": nb * 2 * v + 4 * cells + fired * 52,
+        # fired records and both degrees; accepted / conflict lists
+        "k_match_trivial": fired * 48,
+        # degrees cleared; per accepted pair or decay: record, state, 2x2 positions read, 2
+        # positions + statuses written (conflict rounds add re-reads of the conflict pairs)
+        "k_match_resolve": fired * 16 + (acc + dec) * (48 + 6 * v),
+        # read status, write the 64-bit scan
+        "k_scan_compact": 12 * n,
+        # read end position, id, status, scan; write position + id
+        "k_compact": n * (2 * v + 20),
+    }
+    if kernel not in table:
+        raise KeyError(f"no algorithmic byte count for step kernel {kernel}")
+    return table[kernel]
 
 
 # ------------------------------------------------------------------------------------------------
@@ -228,6 +245,18 @@ def timed_graph_run(sim, torch, flush, steps):
     return sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3, 2 * launches
 
 
+def reduce_over_ranks(dist, torch, elapsed, ps_local, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time and the particle-steps of
+    all ranks (each rank runs its own independent system)."""
+    if dist is None:
+        return elapsed, float(ps_local)
+    tt = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([float(ps_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(pt)
+    return float(tt.item()), float(pt.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -261,15 +290,7 @@ def run_ours(args, rank, world, local_rank):
     obs1 = sim.observables()
     ps_local = obs1["stats"]["particle_steps"] - obs0["stats"]["particle_steps"]
     cand_local = obs1["stats"]["candidates"] - obs0["stats"]["candidates"]
-    t_max = elapsed
-    ps_total = ps_local
-    if dist is not None:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        pt = torch.tensor([float(ps_local)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pt)
-        ps_total = float(pt.item())
+    t_max, ps_total = reduce_over_ranks(dist, torch, elapsed, ps_local, "cuda")
     value = ps_total / t_max
 
     extras = {}
@@ -285,29 +306,38 @@ def run_ours(args, rank, world, local_rank):
                 ker.setdefault(name, []).append(ms)
         ker_avg = {k: sum(v) / len(v) for k, v in ker.items()}
         step_ms = sum(ker_avg.values())
-        hbm_kernels = ("k_prepare", "k_sweep", "k_compact", "k_scatter_cells")
-        top = max((k for k in ker_avg if k in hbm_kernels), key=lambda k: ker_avg[k])
         dominant = max(ker_avg, key=lambda k: ker_avg[k])
         st = sim.get_state()
-        binned = int(np.sum(st["species"] < 2))
-        cand_per_step = cand_local / max(steps_done, 1)
+        d_stats = {k: obs1["stats"][k] - obs0["stats"][k] for k in obs1["stats"]}
+        per = max(steps_done, 1)
+        work = {"n": n_now, "nb": int(np.sum(np.isin(st["species"], [0, 1]))), "cells": layout["cells"],
+                "fired": d_stats["fired"] / per, "accepted": d_stats["matched"] / per,
+                "decays": d_stats["decays"] / per}
+        cand_per_step = cand_local / per
         peak, peak_kind = measured_peaks()
-        ab = algorithmic_bytes(top, args.precision, n_now, binned, cand_per_step)
-        achieved = ab / (ker_avg[top] * 1e-3) / 1e9
+        ab = algorithmic_bytes(dominant, args.precision, work)
+        achieved = ab / (ker_avg[dominant] * 1e-3) / 1e9
         traffic = None
         prof = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(prof):
             with open(prof) as f:
                 tj = json.load(f)
-            key = f"{top}:{args.precision}"
+            key = f"{dominant}:{args.precision}"
             if key in tj:
                 traffic = tj[key]
         extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                              "frac": achieved / peak, "traffic": traffic, "kernel": top,
+                              "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
                               "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
-                              "algorithmic_bytes_per_launch": ab,
-                              "kernel_ms": ker_avg[top], "dominant_kernel": dominant,
-                              "dominant_share": ker_avg[dominant] / step_ms}
+                              "algorithmic_bytes_per_launch": ab, "kernel_ms": ker_avg[dominant],
+                              "share": ker_avg[dominant] / step_ms}
+        step_bytes = sum(algorithmic_bytes(k, args.precision, work) for k in ker_avg)
+        step_graph_ms = 1e3 * t_max / per
+        extras["step_roofline"] = {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
+                                   "ms_per_step": step_graph_ms,
+                                   "achieved": step_bytes / (step_graph_ms * 1e-3) / 1e9, "peak": peak,
+                                   "unit": "GB/s",
+                                   "frac": step_bytes / (step_graph_ms * 1e-3) / 1e9 / peak,
+                                   "work_per_step": {k: round(float(v), 1) for k, v in work.items()}}
         extras["kernel_ms"] = {k: round(v, 5) for k, v in ker_avg.items()}
         extras["sweep_pair_prob_evals_per_s"] = cand_per_step / (ker_avg["k_sweep"] * 1e-3)
         extras["candidates_per_step"] = cand_per_step

@@ -104,7 +104,12 @@ typedef struct {
                                          1 and 4 cut-offs); < 0: the fastest of four choices (fixed
                                          1.0, density rule x 0.7 / 1 / 1.5), timed by rd_init on the
                                          initial state */
-  int32_t block_size;                 /* threads per block of the particle kernels (0: 256) */
+  int32_t block_size;                 /* threads per block of the particle kernels: 0 (256) or a
+                                         multiple of 32 in [32, 256]; RD_EINVAL otherwise */
+  int32_t sweep_split;                /* cell sweep: 0 automatic (one thread per particle, or one per
+                                         stencil row when the autotuner finds it faster), 1 one
+                                         thread per particle, 2 one thread per (particle, row) */
+  int32_t pad_cfg;
   rd_allocator allocator;
 } rd_config;
 
@@ -190,9 +195,11 @@ int rd_num_particles(rd_handle* h, int64_t* n);
 int rd_count_history(rd_handle* h, int64_t first_step, int64_t n_steps, int64_t* out);
 
 /* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge choice (> 0: fixed factor
- * in units of the largest cut-off; < 0: per-replica density rule times -out[0]), out[1] total cells, out[2] threads per block of the resolution kernel,
- * out[3] particle capacity, out[4] fired-pair capacity, out[5] autotuned ms per step (0 if not
- * tuned), out[6] largest cut-off radius.  Writes min(n, 7) values to the caller-owned HOST array. */
+ * in units of the largest cut-off; < 0: per-replica density rule times -out[0]), out[1] total cells,
+ * out[2] threads per block of the particle kernels, out[3] particle capacity, out[4] fired-pair
+ * capacity, out[5] autotuned ms per step (0 if not tuned), out[6] largest cut-off radius, out[7]
+ * threads per binned particle in the cell sweep (1, or one per stencil row).  Writes min(n, 8)
+ * values to the caller-owned HOST array. */
 int rd_info(rd_handle* h, double* out, int32_t n);
 
 /* Name of the kernel-level timing hook: rd_time_kernels enables CUDA-event timing of every kernel

@@ -74,6 +74,7 @@ class _Config(C.Structure):
                 ("decays", _Decay * MAX_DECAYS), ("replicas", C.POINTER(_Replica)),
                 ("capacity_factor", C.c_double), ("pair_capacity", C.c_int64),
                 ("cell_factor_x100", C.c_int32), ("block_size", C.c_int32),
+                ("sweep_split", C.c_int32), ("pad_cfg", C.c_int32),
                 ("allocator", _Allocator)]
 
 
@@ -138,10 +139,11 @@ def _ptr(a, ctype):
 
 
 def make_config(system, precision: Optional[str] = None, capacity_factor: float = 2.0,
-                pair_capacity: int = 0, cell_factor=None, block_size: int = 256):
+                pair_capacity: int = 0, cell_factor=None, block_size: int = 256, sweep_split: int = 0):
     """Build the C configuration from a system description (see ``workloads.System``).
-    cell_factor: cell edge in units of the largest cut-off; None = density-based (about 1.5
-    interacting particles per cell), "tune" = timed autotuning at creation."""
+    cell_factor: cell edge in units of the largest cut-off; None = density-based per replica
+    (about 0.25 interacting particles per cell), "tune" = timed autotuning at creation.
+    sweep_split: 0 automatic, 1 one sweep thread per particle, 2 one per (particle, stencil row)."""
     cfg = _Config()
     cfg.dim = int(system.dim)
     cfg.precision = PRECISION[precision or system.precision]
@@ -177,6 +179,7 @@ def make_config(system, precision: Optional[str] = None, capacity_factor: float 
     else:
         cfg.cell_factor_x100 = int(round(float(cell_factor) * 100))
     cfg.block_size = int(block_size)
+    cfg.sweep_split = int(sweep_split)
     return cfg, rep_arr
 
 
@@ -185,7 +188,7 @@ class Simulation:
 
     def __init__(self, system, precision: Optional[str] = None, device: int = 0, stream=None,
                  capacity_factor: float = 2.0, pair_capacity: int = 0, cell_factor=None,
-                 block_size: int = 256):
+                 block_size: int = 256, sweep_split: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -198,7 +201,7 @@ class Simulation:
         self.n_replicas = len(system.replica_list())
         self.precision = precision or system.precision
         cfg, self._rep_arr = make_config(system, self.precision, capacity_factor, pair_capacity,
-                                         cell_factor, block_size)
+                                         cell_factor, block_size, sweep_split)
         dev = self.device.index
 
         def _alloc(nbytes, stream_ptr, ctx):
@@ -250,12 +253,12 @@ class Simulation:
         return out[:n_steps]
 
     def info(self):
-        v = np.zeros(7)
-        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 7), "rd_info")
+        v = np.zeros(8)
+        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 8), "rd_info")
         return {"cell_factor": abs(v[0]), "cell_rule": "density" if v[0] < 0 else "fixed",
-                "cells": int(v[1]), "resolve_block": int(v[2]),
+                "cells": int(v[1]), "block": int(v[2]),
                 "capacity": int(v[3]), "pair_capacity": int(v[4]), "tuned_ms_per_step": v[5],
-                "r_cut_max": v[6]}
+                "r_cut_max": v[6], "sweep_split": int(v[7])}
 
     def num_particles(self) -> int:
         n = C.c_int64()

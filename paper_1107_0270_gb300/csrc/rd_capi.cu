@@ -103,6 +103,8 @@ static int validate(const rd_config* c) {
   if (c->n_pairs < 0 || c->n_pairs > RD_MAX_PAIRS || c->n_decays < 0 || c->n_decays > RD_MAX_DECAYS) return RD_EINVAL;
   if (c->n_replicas < 1 || c->n_replicas >= (1 << 24) || !c->replicas) return RD_EINVAL;
   if (!(c->dt > 0.0) || !(c->c_cut >= 0.0)) return RD_EINVAL;
+  if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32 != 0)) return RD_EINVAL;
+  if (c->sweep_split < 0 || c->sweep_split > 2) return RD_EINVAL;
   for (int s = 0; s < c->n_species; ++s)
     if (!(c->D[s] >= 0.0)) return RD_EINVAL;
   for (int k = 0; k < c->n_pairs; ++k) {
@@ -512,7 +514,7 @@ static cudaError_t autotune(rd_handle* h) {
   };
   double best_f = h->factors[0];
   float best = 1e30f;
-  h->L.resolve_block = 32;
+  const int block0 = h->L.block;
   for (double f : h->factors) {
     apply_factor(h, f);
     const float ms = std::min(trial(), trial());
@@ -523,16 +525,28 @@ static cudaError_t autotune(rd_handle* h) {
   }
   apply_factor(h, best_f);
   h->factor = best_f;
-  int best_rb = h->L.resolve_block;
-  for (int rb : {32, 64, 128}) {
-    h->L.resolve_block = rb;
+  // threads per block of the particle-parallel kernels (prepare, scatter, compaction)
+  int best_block = block0;
+  for (int bs : {128, 256}) {
+    if (bs == block0) continue;
+    h->L.block = bs;
     const float ms = std::min(trial(), trial());
     if (ms < best) {
       best = ms;
-      best_rb = rb;
+      best_block = bs;
     }
   }
-  h->L.resolve_block = best_rb;
+  h->L.block = best_block;
+  // one thread per (particle, stencil row) in the sweep, for small systems
+  const int rows = h->cfg.dim == 3 ? 5 : 2;
+  if (h->cfg.sweep_split == 0 && (double)h->L.cap_particles * rows < 4.0e9) {
+    h->L.sweep_split = rows;
+    const float ms = std::min(trial(), trial());
+    if (ms < best)
+      best = ms;
+    else
+      h->L.sweep_split = 1;
+  }
   h->tuned_ms = best / 6.0;
   restore();
   cudaEventDestroy(a);
@@ -639,6 +653,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   StepLaunch& L = h->L;
   std::memset(&L, 0, sizeof L);
   L.pdl = true;
+  L.sweep_split = c.sweep_split == 2 && (double)cap * (c.dim == 3 ? 5 : 2) < 4.0e9 ? (c.dim == 3 ? 5 : 2) : 1;
   L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
@@ -651,7 +666,6 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   const int64_t chunk = 256 * (int64_t)L.scan_items;
   const int64_t nbc = (max_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
   L.flag_stride = std::max(nbc, nbp) + 1;
-  L.resolve_block = 32;
 
   bool ok = true;
   auto A = [&](size_t bytes) {
@@ -1026,10 +1040,10 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
 
 int rd_info(rd_handle* h, double* out, int32_t n) {
   if (!h || !out || n < 0) return RD_EINVAL;
-  const double v[7] = {h->factor, (double)h->L.total_cells, (double)h->L.resolve_block,
+  const double v[8] = {h->factor, (double)h->L.total_cells, (double)h->L.block,
                        (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
-                       max_cutoff(h->cfg)};
-  for (int k = 0; k < n && k < 7; ++k) out[k] = v[k];
+                       max_cutoff(h->cfg), (double)h->L.sweep_split};
+  for (int k = 0; k < n && k < 8; ++k) out[k] = v[k];
   return RD_OK;
 }
 
@@ -1241,12 +1255,12 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   StepLaunch L;
   std::memset(&L, 0, sizeof L);
   L.pdl = true;
+  L.sweep_split = 1;
   L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = 256;
   L.max_grid = 152 * 16;
   L.scan_items = 8;
-  L.resolve_block = 32;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;
   L.total_cells = cells;

@@ -397,7 +397,7 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
 // ================================================================================================
 constexpr int kSweepRanges = 10;
 
-template <class T>
+template <class T, bool kSplit>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
                                                   const RepDev* __restrict__ reps,
                                                   const typename V4<T>::type* __restrict__ sx0,
@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
                                                   const uint32_t* __restrict__ cell_start,
                                                   const int64_t total_cells, FiredPair* __restrict__ fired,
                                                   uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
-                                                  int32_t* __restrict__ matched, const uint32_t cap_pairs) {
+                                                  int32_t* __restrict__ matched, const uint32_t cap_pairs,
+                                                  const uint32_t split) {
   pdl_enter();
   const DevParams& P = *Pp;
   __shared__ uint2 ranges[kSweepRanges][256];
@@ -415,11 +416,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
   const uint32_t step = ctl->step;
   const int dim = P.dim;
   unsigned long long n_cand = 0, n_near = 0, n_overlap = 0;
+  // split = 1: one thread walks all rows of a particle; split = number of rows: one thread per
+  // (particle, row), more independent chains for small systems (the host keeps nb * split < 2^32)
+  const uint32_t work = kSplit ? nb * split : nb;
   const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t n_iter = (nb + stride - 1) / stride;
+  const uint32_t n_iter = (work + stride - 1) / stride;
   for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t k = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nb) {
+    const uint32_t t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < work) {
+      const uint32_t k = kSplit ? t / split : t;
+      const int row_lo = kSplit ? (int)(t - k * split) : 0;
+      const int row_hi = kSplit ? row_lo + 1 : kSweepRanges / 2;
       const auto a0 = sx0[k];
       const auto a1 = sx1[k];
       const uint32_t wa = w_bits(a0.w);
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
       for (int row = 0; row < kSweepRanges / 2; ++row) {
         const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
         const int dz = row < 2 ? 0 : 1;
-        if ((dy == 0 || oy) && (dz == 0 || oz)) {
+        if (row >= row_lo && row < row_hi && (dy == 0 || oy) && (dz == 0 || oz)) {
           int yy = cy + dy, zz = cz + dz;
           yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
           zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
@@ -675,111 +682,26 @@ __device__ __forceinline__ bool grid_barrier(DevCtl* ctl) {
   return s_ok != 0;
 }
 
-// Rounds of locally-dominant matching over the conflict list.  A short list is handled by block 0
-// alone (block barriers); a long one by the whole cooperative grid (grid barriers between the
-// phases of a round).  Each round: every live pair offers its key to both particles (atomic min),
-// then its (id_a, id_b) among equal keys; a pair that is the minimum at both particles is
-// accepted; pairs touching an accepted particle die, the rest stay live.
-__global__ void __launch_bounds__(256) k_match_rounds(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                                                      const FiredPair* __restrict__ fired,
-                                                      uint32_t* __restrict__ fstate,
-                                                      int32_t* __restrict__ matched,
-                                                      const uint32_t* __restrict__ conflict,
-                                                      uint32_t* __restrict__ accepted,
-                                                      unsigned long long* __restrict__ best_key,
-                                                      unsigned long long* __restrict__ best_pid) {
-  pdl_enter();
-  __shared__ unsigned long long acc_s;
-  __shared__ uint32_t live_s;
-  if (ctl->status) return;
-  const uint32_t nc = ctl->n_conflict;
-  if (nc == 0) return;
-  const bool multi = nc > kMatchSingleMax && gridDim.x > 1;
-  if (!multi && blockIdx.x != 0) return;
-  const uint32_t nthr = multi ? gridDim.x * blockDim.x : blockDim.x;
-  const uint32_t tid = multi ? blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
-  auto sync = [&]() -> bool {
-    if (multi) return grid_barrier(ctl);
-    __syncthreads();
-    return true;
-  };
-  if (threadIdx.x == 0) acc_s = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->live[0] = 0u;
-    ctl->live[1] = 0u;
-  }
-  int rounds = 0;
-  bool ok = sync();
-  while (ok) {
-    for (uint32_t q = tid; q < nc; q += nthr) {
-      const uint32_t e = conflict[q];
-      if ((fstate[e] & 3u) != FS_LIVE) continue;
-      const unsigned long long kb = (unsigned long long)__double_as_longlong(fired[e].key);
-      atomicMin(&best_key[fired[e].ia], kb);
-      atomicMin(&best_key[fired[e].ib], kb);
-    }
-    if (!(ok = sync())) break;
-    for (uint32_t q = tid; q < nc; q += nthr) {
-      const uint32_t e = conflict[q];
-      if ((fstate[e] & 3u) != FS_LIVE) continue;
-      const FiredPair f = fired[e];
-      const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
-      const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
-      if (best_key[f.ia] == kb) atomicMin(&best_pid[f.ia], pid);
-      if (best_key[f.ib] == kb) atomicMin(&best_pid[f.ib], pid);
-    }
-    if (!(ok = sync())) break;
-    for (uint32_t q = tid; q < nc; q += nthr) {
-      const uint32_t e = conflict[q];
-      if ((fstate[e] & 3u) != FS_LIVE) continue;
-      const FiredPair f = fired[e];
-      const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
-      const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
-      if (best_key[f.ia] == kb && best_key[f.ib] == kb && best_pid[f.ia] == pid && best_pid[f.ib] == pid) {
-        matched[f.ia] = (int32_t)f.ib;
-        matched[f.ib] = (int32_t)f.ia;
-        fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
-        accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
-        atomicAdd(&acc_s, 1ull);
-      }
-    }
-    if (threadIdx.x == 0) live_s = 0u;
-    if (!(ok = sync())) break;
-    for (uint32_t q = tid; q < nc; q += nthr) {
-      const uint32_t e = conflict[q];
-      if ((fstate[e] & 3u) != FS_LIVE) continue;
-      const FiredPair f = fired[e];
-      if (matched[f.ia] >= 0 || matched[f.ib] >= 0) {
-        fstate[e] = (fstate[e] & ~3u) | FS_DEAD;
-      } else {
-        best_key[f.ia] = ~0ull;
-        best_key[f.ib] = ~0ull;
-        best_pid[f.ia] = ~0ull;
-        best_pid[f.ib] = ~0ull;
-        atomicAdd(&live_s, 1u);
-      }
-    }
-    __syncthreads();
-    const int par = rounds & 1;
-    if (threadIdx.x == 0 && live_s) atomicAdd(&ctl->live[par], live_s);
-    if (!(ok = sync())) break;
-    ++rounds;
-    const uint32_t live = *(volatile uint32_t*)&ctl->live[par];
-    if (live == 0) break;
-    // the other parity was last read before this round's first barrier
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->live[par ^ 1] = 0u;
-    if (rounds >= Pp->match_max_rounds) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, RD_ETIMEOUT);
-      break;
-    }
-  }
-  if (threadIdx.x == 0) {
-    if (acc_s) atomicAdd(&ctl->stats[RD_STAT_MATCHED], acc_s);
-    if (blockIdx.x == 0) atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
-  }
+// ================================================================================================
+
+// Out-of-line copies of the random draw, the propagator samples, the normals and the p_reac
+// table for the resolution path: its items are few and each runs a long straight code path once,
+// so one shared copy of each keeps the instruction footprint small.  (The cell sweep keeps the
+// inlined forms.)
+__device__ __noinline__ uint4 draw_ni(const DevParams& P, uint32_t c0, uint32_t ida, uint32_t idb, uint32_t tag,
+                                      uint32_t replica) {
+  return draw(P, c0, ida, idb, tag, replica);
+}
+__device__ __noinline__ float resample3_f_ni(float U, float R0, float s) { return resample3_f(U, R0, s); }
+__device__ __noinline__ double resample_dim_ni(const DevParams& P, const PairDev& pr, double U, double R0) {
+  return resample_dim(P, pr, U, R0);
+}
+__device__ __noinline__ float p_reac_tab_ni(const PairDev& pr, float d, float d0) { return p_reac_tab(pr, d, d0); }
+__device__ __noinline__ void normals64_ni(const DevParams& P, uint32_t c0, uint32_t id, uint32_t tag0, uint32_t r,
+                                          int dim, double n[4]) {
+  normals64(P, c0, id, tag0, r, dim, n);
 }
 
-// ================================================================================================
 // K5: accepted pairs (Section 3, steps 2(a)-(c)).  Absorbing: react.  Reflective / radiation:
 // new separation length from the radial propagator G_ref - G_abs (direction of the free step kept,
 // centre of diffusion unchanged); radiation reacts with p_reac (Eq. psurv_radII).  A product sits
@@ -830,11 +752,11 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
     if (pr.bc == RD_BC_ABS) {
       react = true;
     } else {
-      const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
+      const uint4 w = draw_ni(P, step, f.ida, f.idb, TAG_RES, r);
       const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
       double R0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim)) / pr.sigma;
       if (R0 < 1.0) R0 = 1.0;
-      const double Rn = resample_dim(P, pr, u_res, R0);
+      const double Rn = resample_dim_ni(P, pr, u_res, R0);
       const double len = sqrt(norm2_rn(rv[0], rv[1], rv[2], dim));
       double dir[3] = {0, 0, 0};
       if (len > 0.0) {
@@ -904,7 +826,7 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
     uint32_t np = 0;
     if (dc.n_products == 1) {
       double nr[4];
-      normals64(P, step, pid, TAG_DISS0, r, dim, nr);
+      normals64_ni(P, step, pid, TAG_DISS0, r, dim, nr);
       const double ell = sqrt(2.0 * P.D[dc.p0] * P.dt);
       double q3[3] = {0, 0, 0};
       for (int d = 0; d < dim; ++d) q3[d] = wrap(xp[d] + ell * nr[d], rep.L);
@@ -915,7 +837,7 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
       const double Drel = P.D[sa] + P.D[sb];
       const double ca = P.D[sa] / Drel, cb = P.D[sb] / Drel;
       const double DR = P.D[sa] * P.D[sb] / Drel;
-      uint4 w = draw(P, step, pid, kOneParticle, TAG_DIR, r);
+      uint4 w = draw_ni(P, step, pid, kOneParticle, TAG_DIR, r);
       double dir[3] = {0, 0, 0};
       if (dim == 3) {
         const double ct = 2.0 * u52(w.x, w.y) - 1.0;
@@ -929,7 +851,7 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
         dir[0] = cs; dir[1] = sn;
       }
       double nc[4];
-      normals64(P, step, pid, TAG_DISS0, r, dim, nc);
+      normals64_ni(P, step, pid, TAG_DISS0, r, dim, nc);
       const double ellc = sqrt(2.0 * DR * P.dt);
       double c[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
       for (int d = 0; d < dim; ++d) c[d] = xp[d] + ellc * nc[d];
@@ -938,9 +860,9 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
       int product = -1;
       if (rule >= 0) {
         const PairDev& pr = P.pairs[rule];
-        w = draw(P, step, pid, kOneParticle, TAG_RES, r);
+        w = draw_ni(P, step, pid, kOneParticle, TAG_RES, r);
         const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
-        const double Rn = resample_dim(P, pr, u_res, 1.0);
+        const double Rn = resample_dim_ni(P, pr, u_res, 1.0);
         for (int d = 0; d < dim; ++d) rv[d] = Rn * pr.sigma * dir[d];
         if (pr.bc == RD_BC_ABS) {
           recombine = true;
@@ -957,7 +879,7 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
         product = pr.product;
       } else {
         double nr[4];
-        normals64(P, step, pid, TAG_DISS2, r, dim, nr);
+        normals64_ni(P, step, pid, TAG_DISS2, r, dim, nr);
         const double ellr = sqrt(2.0 * Drel * P.dt);
         for (int d = 0; d < dim; ++d) rv[d] = dc.sigma_place * dir[d] + ellr * nr[d];
       }
@@ -1025,10 +947,10 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
   if (pr.bc != RD_BC_ABS) {
     const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf), r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
     const float r0z = d3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
-    const uint4 w = draw(P, step, f.ida, f.idb, TAG_RES, r);
+    const uint4 w = draw_ni(P, step, f.ida, f.idb, TAG_RES, r);
     float R0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z) * pr.inv_sigma_f;
     R0 = fmaxf(R0, 1.0f);
-    const float Rn = d3 ? resample3_f(u23(w.x), R0, pr.s_f) : resample2_tab(pr, u23(w.x), R0);
+    const float Rn = d3 ? resample3_f_ni(u23(w.x), R0, pr.s_f) : resample2_tab(pr, u23(w.x), R0);
     const float len = sqrtf(rx * rx + ry * ry + rz * rz);
     float dx, dy, dz;
     if (len > 0.0f) {
@@ -1043,7 +965,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     }
     const float ln = Rn * pr.sigma_f;
     ++n_res;
-    react = pr.bc == RD_BC_RAD && u23(w.z) < p_reac_tab(pr, Rn - 1.0f, R0 - 1.0f);
+    react = pr.bc == RD_BC_RAD && u23(w.z) < p_reac_tab_ni(pr, Rn - 1.0f, R0 - 1.0f);
     if (!react) {
       x1[f.ia] = make_float4(wrap_f(cx - ca * ln * dx, rep.Lf), wrap_f(cy - ca * ln * dy, rep.Lf),
                              d3 ? wrap_f(cz - ca * ln * dz, rep.Lf) : 0.0f, a1.w);
@@ -1065,7 +987,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
 
 __device__ __forceinline__ void normals_f(const DevParams& P, uint32_t c0, uint32_t id, uint32_t tag0, uint32_t r,
                                           bool d3, float n[4]) {
-  const uint4 w = draw(P, c0, id, kOneParticle, tag0, r);
+  const uint4 w = draw_ni(P, c0, id, kOneParticle, tag0, r);
   box_muller_f(u23(w.x), u23(w.y), n[0], n[1]);
   n[2] = n[3] = 0.0f;
   if (d3) box_muller_f(u23(w.z), u23(w.w), n[2], n[3]);
@@ -1097,7 +1019,7 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     const float Drel = P.D_f[sa] + P.D_f[sb];
     const float ca = P.D_f[sa] / Drel, cb = P.D_f[sb] / Drel;
     const float DR = P.D_f[sa] * P.D_f[sb] / Drel;
-    uint4 w = draw(P, step, pid, kOneParticle, TAG_DIR, r);
+    uint4 w = draw_ni(P, step, pid, kOneParticle, TAG_DIR, r);
     float dx, dy, dz = 0.0f;
     if (d3) {
       const float ct = 2.0f * u23(w.x) - 1.0f;
@@ -1118,14 +1040,14 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     float rx, ry, rz;
     if (rule >= 0) {
       const PairDev& pr = P.pairs[rule];
-      w = draw(P, step, pid, kOneParticle, TAG_RES, r);
-      const float Rn = d3 ? resample3_f(u23(w.x), 1.0f, pr.s_f) : resample2_tab(pr, u23(w.x), 1.0f);
+      w = draw_ni(P, step, pid, kOneParticle, TAG_RES, r);
+      const float Rn = d3 ? resample3_f_ni(u23(w.x), 1.0f, pr.s_f) : resample2_tab(pr, u23(w.x), 1.0f);
       const float ln = Rn * pr.sigma_f;
       rx = ln * dx; ry = ln * dy; rz = ln * dz;
       if (pr.bc == RD_BC_ABS)
         recombine = true;
       else if (pr.bc == RD_BC_RAD)
-        recombine = u23(w.z) < p_reac_tab(pr, Rn - 1.0f, 0.0f);
+        recombine = u23(w.z) < p_reac_tab_ni(pr, Rn - 1.0f, 0.0f);
       product = pr.product;
     } else {
       float nr[4];
@@ -1154,41 +1076,170 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
   status[i] = st | (np << ST_NPROD_SHIFT);
 }
 
-// One work list: accepted pairs first, then decays; one warp per block so that the FP64-bound
-// items spread over all SMs.
+// One accepted pair or one decay of this step (item q of the combined list).
 template <class T>
-__global__ void __launch_bounds__(128) k_resolve_all(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                                                    const RepDev* __restrict__ reps, const FiredPair* __restrict__ fired,
-                                                    const uint32_t* __restrict__ fstate,
-                                                    const uint32_t* __restrict__ accepted,
-                                                    const uint32_t* __restrict__ decay_list,
-                                                    const typename V4<T>::type* __restrict__ x0,
-                                                    typename V4<T>::type* __restrict__ x1,
-                                                    const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-                                                    typename V4<T>::type* __restrict__ prodpos,
-                                                    uint32_t* __restrict__ deg, uint32_t cap_pairs) {
+__device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __restrict__ reps,
+                                             const FiredPair* __restrict__ fired, const uint32_t* __restrict__ fstate,
+                                             bool pair, uint32_t idx, uint32_t step,
+                                             const typename V4<T>::type* __restrict__ x0,
+                                             typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
+                                             uint32_t* __restrict__ status, typename V4<T>::type* __restrict__ prodpos,
+                                             unsigned long long& n_react, unsigned long long& n_res,
+                                             unsigned long long& n_rec, unsigned long long& n_near) {
+  if constexpr (sizeof(T) == 8) {
+    if (pair)
+      resolve_pair<T>(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res, n_near);
+    else
+      decay_products<T>(P, reps, idx, step, x0, id, status, prodpos, n_rec, n_near);
+  } else {
+    if (pair)
+      resolve_pair_f(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res);
+    else
+      decay_products_f(P, reps, idx, step, x0, id, status, prodpos, n_rec);
+  }
+}
+
+// K5: rounds of locally-dominant matching over the conflict list, and the resolution of every
+// accepted pair and every decay of the step (one cooperative launch).
+//  - A short conflict list is matched by block 0 alone (block barriers); trivially accepted pairs
+//    and decays involve no conflict pair, so blocks 1.. resolve them meanwhile.  A long list is
+//    matched by the whole grid (grid barriers between the phases of a round), and everything is
+//    resolved after the last round.
+//  - Each round: every live pair offers its key to both particles (atomic min), then its
+//    (id_a, id_b) among equal keys; a pair that is the minimum at both particles is accepted;
+//    pairs touching an accepted particle die, the rest stay live.  The pairs accepted in the
+//    rounds are resolved after the last round.
+template <class T>
+__global__ void __launch_bounds__(256, 2) k_match_resolve(
+    const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl, const RepDev* __restrict__ reps,
+    const FiredPair* __restrict__ fired, uint32_t* __restrict__ fstate, int32_t* __restrict__ matched,
+    const uint32_t* __restrict__ conflict, uint32_t* __restrict__ accepted,
+    unsigned long long* __restrict__ best_key, unsigned long long* __restrict__ best_pid,
+    const uint32_t* __restrict__ decay_list, const typename V4<T>::type* __restrict__ x0,
+    typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
+    typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs) {
   pdl_enter();
+  __shared__ unsigned long long acc_s;
+  __shared__ uint32_t live_s;
   const DevParams& P = *Pp;
-  // the encounter degrees of this step go back to zero for the next one
+  // the encounter degrees of this step go back to zero for the next one (the previous kernel made
+  // the last reads of them)
   const uint32_t nf = min(ctl->fired, cap_pairs);
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
     deg[fired[e].ia] = 0u;
     deg[fired[e].ib] = 0u;
   }
   if (ctl->status) return;
-  const uint32_t na = ctl->n_accept, nd = ctl->n_decay, step = ctl->step;
+  const uint32_t nc = ctl->n_conflict, n_triv = ctl->n_accept, nd = ctl->n_decay, step = ctl->step;
+  const bool multi = nc > kMatchSingleMax && gridDim.x > 1;
   unsigned long long n_react = 0, n_res = 0, n_near = 0, n_rec = 0;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < na + nd; q += gridDim.x * blockDim.x) {
-    if constexpr (sizeof(T) == 8) {
-      if (q < na)
-        resolve_pair<T>(P, reps, fired, fstate, accepted[q], step, x0, x1, status, prodpos, n_react, n_res, n_near);
-      else
-        decay_products<T>(P, reps, decay_list[q - na], step, x0, id, status, prodpos, n_rec, n_near);
-    } else {
-      if (q < na)
-        resolve_pair_f(P, reps, fired, fstate, accepted[q], step, x0, x1, status, prodpos, n_react, n_res);
-      else
-        decay_products_f(P, reps, decay_list[q - na], step, x0, id, status, prodpos, n_rec);
+  if (!multi) {
+    // block 0 runs the (short) rounds alone, the other blocks resolve meanwhile
+    const bool skip0 = gridDim.x > 1 && nc > 0;
+    const uint32_t nblk = skip0 ? gridDim.x - 1 : gridDim.x;
+    if (!(skip0 && blockIdx.x == 0)) {
+      const uint32_t b = skip0 ? blockIdx.x - 1 : blockIdx.x;
+      for (uint32_t q = b * blockDim.x + threadIdx.x; q < n_triv + nd; q += nblk * blockDim.x) {
+        const bool pair = q < n_triv;
+        resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_triv], step, x0, x1, id,
+                        status, prodpos, n_react, n_res, n_rec, n_near);
+      }
+    }
+  }
+  if (nc > 0 && (multi || blockIdx.x == 0)) {
+    const uint32_t nthr = multi ? gridDim.x * blockDim.x : blockDim.x;
+    const uint32_t tid = multi ? blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
+    auto sync = [&]() -> bool {
+      if (multi) return grid_barrier(ctl);
+      __syncthreads();
+      return true;
+    };
+    if (threadIdx.x == 0) acc_s = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->live[0] = 0u;
+      ctl->live[1] = 0u;
+    }
+    int rounds = 0;
+    bool ok = sync();
+    while (ok) {
+      for (uint32_t q = tid; q < nc; q += nthr) {
+        const uint32_t e = conflict[q];
+        if ((fstate[e] & 3u) != FS_LIVE) continue;
+        const unsigned long long kb = (unsigned long long)__double_as_longlong(fired[e].key);
+        atomicMin(&best_key[fired[e].ia], kb);
+        atomicMin(&best_key[fired[e].ib], kb);
+      }
+      if (!(ok = sync())) break;
+      for (uint32_t q = tid; q < nc; q += nthr) {
+        const uint32_t e = conflict[q];
+        if ((fstate[e] & 3u) != FS_LIVE) continue;
+        const FiredPair f = fired[e];
+        const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
+        const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
+        if (best_key[f.ia] == kb) atomicMin(&best_pid[f.ia], pid);
+        if (best_key[f.ib] == kb) atomicMin(&best_pid[f.ib], pid);
+      }
+      if (!(ok = sync())) break;
+      for (uint32_t q = tid; q < nc; q += nthr) {
+        const uint32_t e = conflict[q];
+        if ((fstate[e] & 3u) != FS_LIVE) continue;
+        const FiredPair f = fired[e];
+        const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
+        const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
+        if (best_key[f.ia] == kb && best_key[f.ib] == kb && best_pid[f.ia] == pid && best_pid[f.ib] == pid) {
+          matched[f.ia] = (int32_t)f.ib;
+          matched[f.ib] = (int32_t)f.ia;
+          fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+          accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
+          atomicAdd(&acc_s, 1ull);
+        }
+      }
+      if (threadIdx.x == 0) live_s = 0u;
+      if (!(ok = sync())) break;
+      for (uint32_t q = tid; q < nc; q += nthr) {
+        const uint32_t e = conflict[q];
+        if ((fstate[e] & 3u) != FS_LIVE) continue;
+        const FiredPair f = fired[e];
+        if (matched[f.ia] >= 0 || matched[f.ib] >= 0) {
+          fstate[e] = (fstate[e] & ~3u) | FS_DEAD;
+        } else {
+          best_key[f.ia] = ~0ull;
+          best_key[f.ib] = ~0ull;
+          best_pid[f.ia] = ~0ull;
+          best_pid[f.ib] = ~0ull;
+          atomicAdd(&live_s, 1u);
+        }
+      }
+      __syncthreads();
+      const int par = rounds & 1;
+      if (threadIdx.x == 0 && live_s) atomicAdd(&ctl->live[par], live_s);
+      if (!(ok = sync())) break;
+      ++rounds;
+      const uint32_t live = *(volatile uint32_t*)&ctl->live[par];
+      if (live == 0) break;
+      // the other parity was last read before this round's first barrier
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->live[par ^ 1] = 0u;
+      if (rounds >= P.match_max_rounds) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(ctl, RD_ETIMEOUT);
+        ok = false;
+        break;
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (acc_s) atomicAdd(&ctl->stats[RD_STAT_MATCHED], acc_s);
+      if (blockIdx.x == 0) atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
+    }
+    // after the last barrier (all blocks of the rounds have passed it): the pairs accepted in the
+    // rounds; with the whole grid in the rounds also the trivially accepted pairs and the decays,
+    // kept out of the barrier-separated phases because a resolution can take long (FP64 2D)
+    if (ok) {
+      const uint32_t n_acc = *(volatile uint32_t*)&ctl->n_accept;
+      const uint32_t first = multi ? 0u : n_triv, last = multi ? n_acc + nd : n_acc;
+      for (uint32_t q = first + tid; q < last; q += nthr) {
+        const bool pair = q < n_acc;
+        resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_acc], step, x0, x1, id,
+                        status, prodpos, n_react, n_res, n_rec, n_near);
+      }
     }
   }
   if (n_react) atomicAdd(&ctl->stats[RD_STAT_REACTIONS], n_react);
@@ -1559,10 +1610,12 @@ static void launch_coop(void (*kernel)(KArgs...), int grid, int block, cudaStrea
 }
 
 int match_grid_size(int device_sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_rounds, 256, 0) != cudaSuccess || per_sm < 1)
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_match_resolve<float>, 256, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_match_resolve<double>, 256, 0) != cudaSuccess)
     return 1;
-  return device_sms * std::min(per_sm, 2);
+  const int per_sm = std::min(std::min(a, b), 2);
+  return per_sm >= 1 ? device_sms * per_sm : 1;
 }
 
 template <class T>
@@ -1593,19 +1646,23 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   launch_k(pdl, k_scatter_cells<T>, Gp, B, 0, s, L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1,
            L.sidx);
   mark("k_scatter_cells");
-  launch_k(pdl, k_sweep<T>, Gp, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells,
-           L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs);
+  const uint32_t split = L.sweep_split > 1 ? (uint32_t)L.sweep_split : 1u;
+  const int Gs = grid_for(L.cap_particles * (int64_t)split, 256, L.max_grid);
+  if (split > 1)
+    launch_k(pdl, k_sweep<T, true>, Gs, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start,
+             L.total_cells, L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs, split);
+  else
+    launch_k(pdl, k_sweep<T, false>, Gs, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start,
+             L.total_cells, L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs, split);
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
   launch_k(pdl, k_match_trivial, Gf, 256, 0, s, L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted,
            L.best_key, L.best_pid, (uint32_t)L.cap_pairs);
-  launch_coop(k_match_rounds, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.fired, L.fstate, L.matched,
-              L.conflict, L.accepted, L.best_key, L.best_pid);
-  mark("k_match");
-  const int rb = L.resolve_block > 0 ? L.resolve_block : 32;
-  launch_k(pdl, k_resolve_all<T>, (152 * 8 * 32) / rb, rb, 0, s, L.P, L.ctl, L.reps, L.fired, L.fstate, L.accepted,
-           L.decay_list, x0, x1, L.id_cur, L.status, prod, L.deg, (uint32_t)L.cap_pairs);
-  mark("k_resolve_all");
+  mark("k_match_trivial");
+  launch_coop(k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
+              L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0, x1, L.id_cur, L.status,
+              prod, L.deg, (uint32_t)L.cap_pairs);
+  mark("k_match_resolve");
   const int nbp = (int)((L.cap_particles + tile - 1) / tile);
   launch_k(pdl, k_scan1<unsigned long long, LoadCompact>, nbp, 256, 0, s, LoadCompact{L.status}, (int64_t)0,
            (const uint32_t*)&L.ctl->n, L.scan, (uint32_t*)nullptr, L.agg64, L.incl64, L.flags + L.flag_stride, L.ctl,

@@ -17,9 +17,9 @@ struct StepLaunch {
   int block;
   int max_grid;
   int scan_items;
-  int resolve_block;           // threads per block of the resolution kernel (32..128)
   bool pdl;                    // programmatic dependent launch between the step kernels
   int match_grid;              // blocks of the cooperative matching launch (all resident)
+  int sweep_split;             // threads per binned particle in the sweep: 1 or the stencil rows
   int64_t cap_particles, cap_pairs, total_cells;
   int n_counts;
   const DevParams* P;

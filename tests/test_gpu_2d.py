@@ -81,10 +81,10 @@ def membrane(dt, n_each=60, L=0.3):
     return W.membrane_2d(n_each=n_each, L=L, dt=dt)
 
 
-@pytest.mark.parametrize("dt", [1e-4, 1e-6])
-def test_stepwise_parity_2d(dt):
+@pytest.mark.parametrize("dt,split", [(1e-4, 1), (1e-6, 1), (1e-4, 2)])
+def test_stepwise_parity_2d(dt, split):
     system = membrane(dt)
-    sim = pkg.Simulation(system, precision="fp64")
+    sim = pkg.Simulation(system, precision="fp64", sweep_split=split)
     totals = {"fired": 0, "resampled": 0}
     for k in range(4):
         g0 = sim.get_state()

@@ -240,8 +240,10 @@ def test_cell_layout_and_autotune_do_not_change_results(precision):
     # autotuner's choice must leave the trajectory bit-identical
     system = dense_reversible(n_each=1500, conc_uM=20.0, dt=2e-5)
     states = []
-    for cf in (1.0, 2.5, None, "tune"):
-        sim = pkg.Simulation(system, precision=precision, cell_factor=cf)
+    for cf, split in ((1.0, 1), (2.5, 1), (None, 0), ("tune", 0), (1.0, 2), (2.5, 2), (None, 2)):
+        sim = pkg.Simulation(system, precision=precision, cell_factor=cf, sweep_split=split)
+        if split == 2:
+            assert sim.info()["sweep_split"] == 5
         sim.run(9)
         states.append(sim.get_state())
         sim.close()

@@ -115,10 +115,14 @@ def reversible_3d(dt: float = 1e-5, seed: int = 1, n_each: int = 100_000, L: flo
                   decays=[Decay(2, 10.0, (0, 1))])
 
 
-def membrane_2d(seed: int = 1, n_each: int = 200_000, L: float = 10.0, dt: float = 1e-4) -> System:
+def membrane_2d(seed: int = 1, n_each: int = 200_000, L: float = 10.0, dt: float = 1e-4,
+                equilibrium_start: bool = False) -> System:
     """2D A+B<->C on a membrane: square L=10, 2e5 A + 2e5 B, sigma 0.005, D=0.1, ka=0.01 um^2/s,
-    kd=1, dt=1e-4.  A+B carries the radiation BC; C+C is reflective (excluded volume)."""
-    return System(dim=2, L=L, dt=dt, seed=seed, D=[0.1, 0.1, 0.1], n_init=[n_each, n_each, 0],
+    kd=1, dt=1e-4.  A+B carries the radiation BC; C+C is reflective (excluded volume).
+    ``equilibrium_start`` seeds the mass-action composition (bound fraction 0.8) instead of
+    all-unbound."""
+    n_c = int(round(0.8 * n_each)) if equilibrium_start else 0
+    return System(dim=2, L=L, dt=dt, seed=seed, D=[0.1, 0.1, 0.1], n_init=[n_each - n_c, n_each - n_c, n_c],
                   names=["A", "B", "C"],
                   pairs=[PairRule(0, 1, 0.005, "rad", 0.01, 2),
                          PairRule(2, 2, 0.005, "ref")],
