@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-KERNELS_PER_STEP = 8           # kernels of one step: prepare, scan (cells), scatter, sweep, trivial
-                               # matching, matching rounds + resolution, scan (compaction), compact
+KERNELS_PER_STEP = 7           # kernels of one step: prepare, scan (cells), scatter, sweep, trivial
+                               # matching, matching rounds + resolution, compaction (scan + placement)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -153,10 +153,8 @@ def algorithmic_bytes(kernel, precision, w):
         # degrees cleared; per accepted pair or decay: record, state, 2x2 positions read, 2
         # positions + statuses written (conflict rounds add re-reads of the conflict pairs)
         "k_match_resolve": fired * 16 + (acc + dec) * (48 + 6 * v),
-        # read status, write the 64-bit scan
-        "k_scan_compact": 12 * n,
-        # read end position, id, status, scan; write position + id
-        "k_compact": n * (2 * v + 20),
+        # read status, end position, id; write position + id (the scan stays on chip)
+        "k_compact": n * (2 * v + 12),
     }
     if kernel not in table:
         raise KeyError(f"no algorithmic byte count for step kernel {kernel}")

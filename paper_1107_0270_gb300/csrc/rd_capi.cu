@@ -691,7 +691,9 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.decay_list = (uint32_t*)A(cap * 4);
   L.best_key = (unsigned long long*)A(cap * 8);
   L.best_pid = (unsigned long long*)A(cap * 8);
-  L.scan = (unsigned long long*)A((cap + 1) * 8);
+  L.repx = (RepX*)A((size_t)c.n_replicas * sizeof(RepX));
+  L.rep_cons = (uint32_t*)A((size_t)c.n_replicas * 4);
+  L.rep_prod = (uint32_t*)A((size_t)c.n_replicas * 4);
   L.cell_count = (uint32_t*)A(max_cells * 4);
   L.cell_start = (uint32_t*)A((max_cells + 1) * 4);
   L.agg32 = (uint32_t*)A((nbc + 1) * 4);
@@ -735,6 +737,8 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(L.deg, 0, cap * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.flags, 0, 2 * L.flag_stride * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.status, 0, cap * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.rep_cons, 0, (size_t)c.n_replicas * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.rep_prod, 0, (size_t)c.n_replicas * 4, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync((void*)L.P, &h->hp, sizeof(DevParams), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L.reps, h->reps_init.data(), c.n_replicas * sizeof(RepDev), cudaMemcpyHostToDevice, h->stream);
@@ -1285,7 +1289,9 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.decay_list = (uint32_t*)b.take(cap * 4);
   L.best_key = (unsigned long long*)b.take(cap * 8);
   L.best_pid = (unsigned long long*)b.take(cap * 8);
-  L.scan = (unsigned long long*)b.take((cap + 1) * 8);
+  L.repx = (RepX*)b.take(sizeof(RepX));
+  L.rep_cons = (uint32_t*)b.take(4);
+  L.rep_prod = (uint32_t*)b.take(4);
   L.cell_count = (uint32_t*)b.take(cells * 4);
   L.cell_start = (uint32_t*)b.take((cells + 1) * 4);
   L.flag_stride = std::max(nbc, nbp) + 1;
@@ -1318,6 +1324,8 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   RD_CUDA(cudaMemsetAsync(L.flags, 0, (size_t)(2 * L.flag_stride) * 4, s));
   RD_CUDA(cudaMemsetAsync(L.deg, 0, (size_t)cap * 4, s));
   RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
+  RD_CUDA(cudaMemsetAsync(L.rep_cons, 0, 4, s));
+  RD_CUDA(cudaMemsetAsync(L.rep_prod, 0, 4, s));
   RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
   if (c.precision == RD_MIXED) {
     // the mixed step reads p_reac from an FP32 table: build it into the scratch array as well

@@ -14,7 +14,7 @@ constexpr int kMaxPairs = RD_MAX_PAIRS;
 constexpr int kMaxDecays = RD_MAX_DECAYS;
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 constexpr uint32_t kOneParticle = 0xFFFFFFFFu;   // id_b of one-particle random streams
-constexpr int kSmemCounts = 8192;                // per-block histogram of (replica, species) counts
+constexpr int kSmemCounts = 6144;                // per-block histogram of (replica, species) counts
 
 // Random-stream tags (counter word 3, low byte; replica index in the upper 24 bits).
 enum Tag : uint32_t {
@@ -115,9 +115,18 @@ struct DevCtl {
   uint32_t bar_count;      // grid barrier of the cooperative matching: arrivals, generation
   uint32_t bar_gen;
   uint32_t live[2];        // live conflict pairs after a matching round (by round parity)
+  uint32_t done_res;       // blocks of the matching / resolution kernel that finished
+  uint32_t n_new;          // particles after this step (set with the replica table)
   uint32_t pad_ctl;
   double t;
   unsigned long long stats[RD_NSTATS];
+};
+
+// Per-replica placement of this step's compaction (built once the resolution is complete):
+// products before the replica's first particle, survivors up to and including the replica, and
+// the replica's survivors and products.
+struct RepX {
+  uint32_t p_beg, s_end, surv, prod;
 };
 
 struct FiredPair {          // 32 B

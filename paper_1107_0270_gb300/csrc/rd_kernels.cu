@@ -249,13 +249,63 @@ struct LoadCompact {
   }
 };
 
+constexpr int kScanItems = 8;
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Decoupled look-back of one tile, run by warp 0 of its block: publishes the tile's aggregate, sums
+// the predecessors' published values back to the nearest inclusive prefix (windows of 32 tiles at
+// once; a predecessor that does not publish within kSpinLimit polls sets RD_ETIMEOUT), publishes
+// the tile's inclusive prefix and returns the exclusive prefix (in every lane).  Flags carry an
+// epoch that changes every scan, so nothing needs clearing.
+template <class U>
+__device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch, U* __restrict__ agg,
+                                           U* __restrict__ incl, uint32_t* __restrict__ flag, DevCtl* ctl) {
+  const int lane = threadIdx.x & 31;
+  U prefix = 0;
+  if (tile > 0) {
+    if (lane == 0) {
+      agg[tile] = tot;
+      __threadfence();
+      atomicExch(&flag[tile], (epoch << 2) | 1u);
+    }
+    int64_t top = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    for (;;) {
+      const int64_t q = top - lane;
+      const uint32_t f = q >= 0 ? *(volatile uint32_t*)&flag[q] : ((epoch << 2) | 2u);
+      const bool ready = (f >> 2) == epoch && (f & 3u) != 0u;
+      if (!__all_sync(0xFFFFFFFFu, ready)) {
+        if (++spins > kSpinLimit) {
+          if (lane == 0) set_status(ctl, RD_ETIMEOUT);
+          break;
+        }
+        continue;
+      }
+      __threadfence();
+      const unsigned incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (f & 3u) == 2u);
+      const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;   // nearest inclusive predecessor
+      U vv = 0;
+      if (q >= 0 && lane <= stop) vv = lane == stop ? *(volatile U*)&incl[q] : *(volatile U*)&agg[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
+      prefix += vv;
+      if (incl_mask || top < 32) break;
+      top -= 32;
+    }
+  }
+  if (lane == 0) {
+    incl[tile] = prefix + tot;
+    __threadfence();
+    atomicExch(&flag[tile], (epoch << 2) | 2u);
+  }
+  return prefix;
+}
+
 // Single-pass exclusive scan with decoupled look-back (Merrill & Garland, 2016).  Tiles of
 // blockDim x kScanItems elements take tickets in launch order; each publishes its aggregate, then
 // walks back over its predecessors' published values (bounded wait: a stalled predecessor sets
 // RD_ETIMEOUT).  Flags carry an epoch that changes every scan, so nothing needs clearing.
 // out[i] = exclusive prefix for i < n, out[n] = total; zero_after (optional) is cleared behind.
-constexpr int kScanItems = 8;
-constexpr uint32_t kSpinLimit = 1u << 24;
 
 template <class U, class Load>
 __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const uint32_t* __restrict__ n_ptr,
@@ -288,46 +338,8 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
   U tot;
   const U toff = block_exclusive_scan<U, Load>(run, sm, tot);
   if (threadIdx.x < 32) {
-    // warp 0: publish the aggregate, then look back over windows of 32 predecessors at once
-    const int lane = threadIdx.x;
-    U prefix = 0;
-    if (tile > 0) {
-      if (lane == 0) {
-        agg[tile] = tot;
-        __threadfence();
-        atomicExch(&flag[tile], (epoch << 2) | 1u);
-      }
-      int64_t top = (int64_t)tile - 1;
-      uint32_t spins = 0;
-      for (;;) {
-        const int64_t q = top - lane;
-        const uint32_t f = q >= 0 ? *(volatile uint32_t*)&flag[q] : ((epoch << 2) | 2u);
-        const bool ready = (f >> 2) == epoch && (f & 3u) != 0u;
-        if (!__all_sync(0xFFFFFFFFu, ready)) {
-          if (++spins > kSpinLimit) {
-            if (lane == 0) set_status(ctl, RD_ETIMEOUT);
-            break;
-          }
-          continue;
-        }
-        __threadfence();
-        const unsigned incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (f & 3u) == 2u);
-        const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;   // nearest inclusive predecessor
-        U vv = 0;
-        if (q >= 0 && lane <= stop) vv = lane == stop ? *(volatile U*)&incl[q] : *(volatile U*)&agg[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xFFFFFFFFu, vv, o);
-        prefix += vv;
-        if (incl_mask || top < 32) break;
-        top -= 32;
-      }
-    }
-    if (lane == 0) {
-      incl[tile] = prefix + tot;
-      __threadfence();
-      atomicExch(&flag[tile], (epoch << 2) | 2u);
-      s_prefix = prefix;
-    }
+    const U prefix = tile_lookback<U>(tot, tile, epoch, agg, incl, flag, ctl);
+    if (threadIdx.x == 0) s_prefix = prefix;
   }
   __syncthreads();
   const U prefix = s_prefix + toff;
@@ -1076,6 +1088,38 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
   status[i] = st | (np << ST_NPROD_SHIFT);
 }
 
+// Compaction table over replicas, by one block: survivors = particles - consumed; exclusive
+// prefixes of products and inclusive prefixes of survivors over the replicas; the new particle
+// count.
+__device__ __forceinline__ void replica_table(int n_replicas, const RepDev* __restrict__ reps,
+                                              const uint32_t* __restrict__ rep_cons,
+                                              const uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx,
+                                              DevCtl* __restrict__ ctl) {
+  __shared__ unsigned long long sm[32];
+  unsigned long long carry = 0;      // survivors << 32 | products of the replicas done so far
+  for (int base = 0; base < n_replicas; base += blockDim.x) {
+    const int r = base + (int)threadIdx.x;
+    uint32_t surv = 0, prod = 0;
+    if (r < n_replicas) {
+      surv = reps[r].end - reps[r].beg - __ldcg(&rep_cons[r]);
+      prod = __ldcg(&rep_prod[r]);
+    }
+    const unsigned long long v = ((unsigned long long)surv << 32) | prod;
+    unsigned long long tot;
+    const unsigned long long ex = carry + block_exclusive_scan<unsigned long long, int>(v, sm, tot);
+    if (r < n_replicas) {
+      RepX x;
+      x.p_beg = (uint32_t)ex;
+      x.s_end = (uint32_t)(ex >> 32) + surv;
+      x.surv = surv;
+      x.prod = prod;
+      repx[r] = x;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) ctl->n_new = (uint32_t)(carry >> 32) + (uint32_t)carry;
+}
+
 // One accepted pair or one decay of this step (item q of the combined list).
 template <class T>
 __device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __restrict__ reps,
@@ -1084,6 +1128,7 @@ __device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __re
                                              const typename V4<T>::type* __restrict__ x0,
                                              typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                                              uint32_t* __restrict__ status, typename V4<T>::type* __restrict__ prodpos,
+                                             uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod,
                                              unsigned long long& n_react, unsigned long long& n_res,
                                              unsigned long long& n_rec, unsigned long long& n_near) {
   if constexpr (sizeof(T) == 8) {
@@ -1096,6 +1141,16 @@ __device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __re
       resolve_pair_f(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res);
     else
       decay_products_f(P, reps, idx, step, x0, id, status, prodpos, n_rec);
+  }
+  // per-replica tallies for the compaction: a reacting pair consumes both particles, a decay its
+  // parent; the owner's status carries the number of products
+  const uint32_t owner = pair ? fired[idx].ia : idx;
+  const uint32_t st = status[owner];
+  if (st & ST_CONSUMED) {
+    const uint32_t r = pair ? (fstate[idx] >> 8) : (w_bits(x0[idx].w) >> 8);
+    atomicAdd(&rep_cons[r], pair ? 2u : 1u);
+    const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
+    if (np) atomicAdd(&rep_prod[r], np);
   }
 }
 
@@ -1117,7 +1172,8 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
     unsigned long long* __restrict__ best_key, unsigned long long* __restrict__ best_pid,
     const uint32_t* __restrict__ decay_list, const typename V4<T>::type* __restrict__ x0,
     typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-    typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs) {
+    typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs,
+    uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx) {
   pdl_enter();
   __shared__ unsigned long long acc_s;
   __shared__ uint32_t live_s;
@@ -1142,7 +1198,7 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
       for (uint32_t q = b * blockDim.x + threadIdx.x; q < n_triv + nd; q += nblk * blockDim.x) {
         const bool pair = q < n_triv;
         resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_triv], step, x0, x1, id,
-                        status, prodpos, n_react, n_res, n_rec, n_near);
+                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near);
       }
     }
   }
@@ -1238,7 +1294,7 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
       for (uint32_t q = first + tid; q < last; q += nthr) {
         const bool pair = q < n_acc;
         resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_acc], step, x0, x1, id,
-                        status, prodpos, n_react, n_res, n_rec, n_near);
+                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near);
       }
     }
   }
@@ -1246,13 +1302,19 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
   if (n_res) atomicAdd(&ctl->stats[RD_STAT_RESAMPLED], n_res);
   if (n_rec) atomicAdd(&ctl->stats[RD_STAT_RECOMBINED], n_rec);
   if (n_near) atomicAdd(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
+  // with several replicas, the last block to finish (no block waits for it) builds the
+  // compaction's replica table; a single replica needs none (the compaction reads its tallies)
+  if (P.n_replicas == 1) return;
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctl->done_res, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  replica_table(P.n_replicas, reps, rep_cons, rep_prod, repx, ctl);
 }
 
-// ================================================================================================
-// K7: compaction.  scan[i] = (survivors before i) << 32 | (products before i).  Survivors keep their
-// order inside their replica, products follow the replica's survivors in owner order with ids
-// next_id + rank.  An error latched during the step turns this into a copy of the unchanged state.
-// ================================================================================================
 // Per-warp aggregated count: lanes holding the same (replica, species) key add once.  Called by all
 // 32 lanes of a converged warp; key kNoKey is skipped.
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
@@ -1284,67 +1346,124 @@ __device__ __forceinline__ void species_totals(const unsigned long long* __restr
   for (int k = threadIdx.x; k < ns; k += blockDim.x) out[k] = (long long)tot[k];
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                          RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
+// ================================================================================================
+// K7: compaction, one pass.  Tiles of 2048 particles scan (survivor, products) counts
+// with a decoupled look-back, then place their own particles: survivors keep their order inside
+// their replica, products follow the replica's survivors in owner order with ids next_id + rank
+// (the per-replica offsets come from the table built at the end of the resolution).  An error
+// latched during the step, or a particle count above capacity, turns this into a copy of the
+// unchanged state.  The last block to finish commits the step.
+// ================================================================================================
+constexpr int kCompactTile = 2048;   // particles per tile (the look-back buffers are sized for it)
+
+template <class T, int kCompactThreads>
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          RepDev* __restrict__ reps, const RepX* __restrict__ repx,
+                          uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod,
+                          const typename V4<T>::type* __restrict__ x0,
                           const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
                           const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
-                          const unsigned long long* __restrict__ scan, typename V4<T>::type* __restrict__ xo,
+                          unsigned long long* __restrict__ agg, unsigned long long* __restrict__ incl,
+                          uint32_t* __restrict__ flag, typename V4<T>::type* __restrict__ xo,
                           uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts,
                           long long* __restrict__ history, int history_len) {
   pdl_enter();
   extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
+  constexpr int kTile = kCompactTile, kCompactItems = kCompactTile / kCompactThreads;
+  __shared__ unsigned long long s_pre[kTile];
+  __shared__ unsigned long long sm[32];
+  __shared__ uint32_t s_tile;
+  __shared__ unsigned long long s_prefix;
+  __shared__ bool s_last;
   const DevParams& P = *Pp;
-  const uint32_t n = ctl->n;
-  const unsigned long long tot = scan[n];
-  const bool fail = ctl->status != 0 || ((tot >> 32) + (tot & 0xFFFFFFFFull)) > (unsigned long long)P.cap_particles;
   const int ns = P.n_species;
   const bool use_smem = n_counts <= kSmemCounts;
-  if (use_smem) {
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[1], 1u);
+  if (use_smem)
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x) hist[k] = 0u;
-    __syncthreads();
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t n = ctl->n;
+  // a single replica: its placement follows from the step's tallies directly
+  const bool one = P.n_replicas == 1;
+  RepX rx1 = {0u, 0u, 0u, 0u};
+  if (one) {
+    rx1.surv = n - __ldcg(&rep_cons[0]);
+    rx1.prod = __ldcg(&rep_prod[0]);
+    rx1.s_end = rx1.surv;
   }
+  const uint32_t n_new = one ? rx1.surv + rx1.prod : ctl->n_new;
+  const bool fail = ctl->status != 0 || (unsigned long long)n_new > (unsigned long long)P.cap_particles;
+  const uint32_t ntiles = (uint32_t)(((int64_t)n + kTile - 1) / kTile);
   auto key_of = [&](uint32_t wb) { return (wb >> 8) * ns + (wb & 0xFFu); };
-  // every lane runs the same number of iterations so that the counting stays warp-converged
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t n_iter = (n + stride - 1) / stride;
-  for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey;
-    if (i < n) {
-      if (fail) {
-        const auto q0 = x0[i];
-        xo[i] = q0;
-        ido[i] = id[i];
-        k0 = key_of(w_bits(q0.w));
+  if (tile < ntiles) {
+    const int64_t t0 = (int64_t)tile * kTile;
+    if (!fail) {
+      // blocked arrangement for the scan: each thread owns kCompactItems consecutive particles
+      const int64_t base = t0 + (int64_t)threadIdx.x * kCompactItems;
+      unsigned long long v[kCompactItems], ex[kCompactItems], run = 0;
+      if constexpr (kCompactItems == 8) {
+        LoadCompact{status}.load8(base, n, v);
       } else {
-        const uint32_t st = status[i];
-        const auto q = x1[i];
-        const uint32_t wb = w_bits(q.w);
-        const RepDev& rep = reps[wb >> 8];
-        const unsigned long long e = scan[i];
-        const unsigned long long eb = scan[rep.beg], ee = scan[rep.end];
-        const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
-        const uint32_t P_beg = (uint32_t)eb, S_end = (uint32_t)(ee >> 32);
-        if (!(st & ST_CONSUMED)) {
-          const uint32_t o = S_i + P_beg;
-          xo[o] = q;
-          ido[o] = id[i];
-          k0 = key_of(wb);
-        }
-        const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
-        for (uint32_t k = 0; k < np; ++k) {
-          const uint32_t o = S_end + P_i + k;
-          const auto pp = prodpos[2 * (size_t)i + k];
-          xo[o] = pp;
-          ido[o] = rep.next_id + (P_i - P_beg) + k;
-          (k == 0 ? k1 : k2) = key_of(w_bits(pp.w));
+#pragma unroll
+        for (int k = 0; k < kCompactItems; ++k) v[k] = base + k < (int64_t)n ? LoadCompact::conv(__ldcg(status + base + k)) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < kCompactItems; ++k) {
+        ex[k] = run;
+        run += v[k];
+      }
+      unsigned long long tot;
+      const unsigned long long toff = block_exclusive_scan<unsigned long long, int>(run, sm, tot);
+      if (threadIdx.x < 32) {
+        const uint32_t epoch = (ctl->epoch * 2u + 1u) & 0x3FFFFFFFu;
+        const unsigned long long prefix = tile_lookback<unsigned long long>(tot, tile, epoch, agg, incl, flag, ctl);
+        if (threadIdx.x == 0) s_prefix = prefix;
+      }
+      __syncthreads();
+      const unsigned long long pre = s_prefix + toff;
+#pragma unroll
+      for (int k = 0; k < kCompactItems; ++k) s_pre[threadIdx.x * kCompactItems + k] = pre + ex[k];
+      __syncthreads();
+    }
+    // striped placement (coalesced), one particle per thread per pass, warp-converged counting
+    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+      const int64_t i = t0 + j;
+      uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey;
+      if (i < (int64_t)n) {
+        if (fail) {
+          const auto q0 = x0[i];
+          xo[i] = q0;
+          ido[i] = id[i];
+          k0 = key_of(w_bits(q0.w));
+        } else {
+          const unsigned long long e = s_pre[j];
+          const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
+          const uint32_t st = status[i];
+          const auto q = x1[i];
+          const uint32_t wb = w_bits(q.w);
+          const uint32_t r = wb >> 8;
+          const RepX rx = one ? rx1 : repx[r];
+          if (!(st & ST_CONSUMED)) {
+            const uint32_t o = S_i + rx.p_beg;
+            xo[o] = q;
+            ido[o] = id[i];
+            k0 = key_of(wb);
+          }
+          const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
+          for (uint32_t k = 0; k < np; ++k) {
+            const uint32_t o = rx.s_end + P_i + k;
+            const auto pp = prodpos[2 * (size_t)i + k];
+            xo[o] = pp;
+            ido[o] = reps[r].next_id + (P_i - rx.p_beg) + k;
+            (k == 0 ? k1 : k2) = key_of(w_bits(pp.w));
+          }
         }
       }
+      count_key(k0, use_smem, hist, counts);
+      if (__any_sync(0xFFFFFFFFu, k1 != kNoKey)) count_key(k1, use_smem, hist, counts);
+      if (__any_sync(0xFFFFFFFFu, k2 != kNoKey)) count_key(k2, use_smem, hist, counts);
     }
-    count_key(k0, use_smem, hist, counts);
-    if (__any_sync(0xFFFFFFFFu, k1 != kNoKey)) count_key(k1, use_smem, hist, counts);
-    if (__any_sync(0xFFFFFFFFu, k2 != kNoKey)) count_key(k2, use_smem, hist, counts);
   }
   if (use_smem) {
     __syncthreads();
@@ -1352,21 +1471,22 @@ __global__ void __launch_bounds__(256) k_compact(const DevParams* __restrict__ P
       if (hist[k]) atomicAdd(&counts[k], (unsigned long long)hist[k]);
   }
   // the last block to finish commits the step: replica segments, ids, count, step, time
-  __shared__ bool s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&ctl->done_blocks, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const unsigned long long n_new = (tot >> 32) + (tot & 0xFFFFFFFFull);
-  if (!fail) {
-    for (int r = threadIdx.x; r < P.n_replicas; r += blockDim.x) {
-      const unsigned long long eb = scan[reps[r].beg], ee = scan[reps[r].end];
-      reps[r].next_id += (uint32_t)ee - (uint32_t)eb;
-      reps[r].beg = (uint32_t)(eb >> 32) + (uint32_t)eb;
-      reps[r].end = (uint32_t)(ee >> 32) + (uint32_t)ee;
+  for (int r = threadIdx.x; r < P.n_replicas; r += blockDim.x) {
+    if (!fail) {
+      const RepX rx = one ? rx1 : repx[r];
+      const uint32_t beg = rx.s_end - rx.surv + rx.p_beg;
+      reps[r].next_id += rx.prod;
+      reps[r].beg = beg;
+      reps[r].end = beg + rx.surv + rx.prod;
     }
+    rep_cons[r] = 0u;
+    rep_prod[r] = 0u;
   }
   // per-step totals over replicas of every species (ring buffer indexed by the new step)
   if (!fail && history_len > 0)
@@ -1378,7 +1498,7 @@ __global__ void __launch_bounds__(256) k_compact(const DevParams* __restrict__ P
       ctl->stats[RD_STAT_DECAYS] += ctl->n_decay;
       ctl->stats[RD_STAT_FIRED] += ctl->fired;
       if (ctl->fired > ctl->stats[RD_STAT_FIRED_HWM]) ctl->stats[RD_STAT_FIRED_HWM] = ctl->fired;
-      ctl->n = (uint32_t)n_new;
+      ctl->n = n_new;
       ctl->step += 1;
       ctl->t += P.dt;
     } else if (ctl->status == 0) {
@@ -1390,6 +1510,7 @@ __global__ void __launch_bounds__(256) k_compact(const DevParams* __restrict__ P
     ctl->n_accept = 0;
     ctl->n_decay = 0;
     ctl->done_blocks = 0;
+    ctl->done_res = 0;
   }
 }
 
@@ -1661,16 +1782,19 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_match_trivial");
   launch_coop(k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
               L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0, x1, L.id_cur, L.status,
-              prod, L.deg, (uint32_t)L.cap_pairs);
+              prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx);
   mark("k_match_resolve");
-  const int nbp = (int)((L.cap_particles + tile - 1) / tile);
-  launch_k(pdl, k_scan1<unsigned long long, LoadCompact>, nbp, 256, 0, s, LoadCompact{L.status}, (int64_t)0,
-           (const uint32_t*)&L.ctl->n, L.scan, (uint32_t*)nullptr, L.agg64, L.incl64, L.flags + L.flag_stride, L.ctl,
-           1);
-  mark("k_scan_compact");
+  const int nbp = (int)((L.cap_particles + kCompactTile - 1) / kCompactTile);
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
-  launch_k(pdl, k_compact<T>, Gp, B, hist_bytes, s, L.P, L.ctl, L.reps, x0, x1, L.id_cur, L.status, prod, L.scan,
-           xo, L.id_next, L.counts, L.n_counts, L.history, L.history_len);
+  // small systems: 1024 threads per tile (more independent placements per tile); large ones 256
+  if (L.cap_particles <= (int64_t)1 << 20)
+    launch_k(pdl, k_compact<T, 1024>, nbp, 1024, hist_bytes, s, L.P, L.ctl, L.reps, (const RepX*)L.repx, L.rep_cons,
+             L.rep_prod, x0, x1, L.id_cur, L.status, prod, L.agg64, L.incl64, L.flags + L.flag_stride, xo, L.id_next,
+             L.counts, L.n_counts, L.history, L.history_len);
+  else
+    launch_k(pdl, k_compact<T, 256>, nbp, 256, hist_bytes, s, L.P, L.ctl, L.reps, (const RepX*)L.repx, L.rep_cons,
+             L.rep_prod, x0, x1, L.id_cur, L.status, prod, L.agg64, L.incl64, L.flags + L.flag_stride, xo, L.id_next,
+             L.counts, L.n_counts, L.history, L.history_len);
   mark("k_compact");
 }
 

@@ -19,6 +19,9 @@ struct StepLaunch {
   int scan_items;
   bool pdl;                    // programmatic dependent launch between the step kernels
   int match_grid;              // blocks of the cooperative matching launch (all resident)
+  RepX* repx;                  // per-replica placement of the compaction
+  uint32_t* rep_cons;          // per-replica particles consumed this step
+  uint32_t* rep_prod;          // per-replica products formed this step
   int sweep_split;             // threads per binned particle in the sweep: 1 or the stencil rows
   int64_t cap_particles, cap_pairs, total_cells;
   int n_counts;
@@ -49,7 +52,6 @@ struct StepLaunch {
   uint32_t* flags;             // 2 x flag_stride tile flags
   int64_t flag_stride;
   uint32_t* accepted;          // accepted pair list
-  unsigned long long* scan;
   FiredPair* fired;
   uint32_t* fstate;
   uint32_t* conflict;
