@@ -194,6 +194,15 @@ int rd_num_particles(rd_handle* h, int64_t* n);
  * requested step is in the future or no longer kept. */
 int rd_count_history(rd_handle* h, int64_t first_step, int64_t n_steps, int64_t* out);
 
+/* Failure-detection check (no counterpart in the paper): runs the cell scan of a step once with
+ * its first tile withheld, so that the next tile's look-back waits on a flag that nothing sets.
+ * With the device waits bounded by spin_limit polls (> 0) the kernel latches RD_ETIMEOUT and
+ * returns instead of hanging.  Synchronises; *status_out (HOST int32[1]) receives the latched
+ * status (RD_ETIMEOUT when the bound works); then the control block is restored, so the handle
+ * keeps stepping from the same state.  Returns RD_OK, or the status already latched before the
+ * call, or RD_EINVAL. */
+int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out);
+
 /* Launch layout chosen at rd_init (no synchronisation): out[0] cell-edge choice (> 0: fixed factor
  * in units of the largest cut-off; < 0: per-replica density rule times -out[0]), out[1] total cells,
  * out[2] threads per block of the particle kernels, out[3] particle capacity, out[4] fired-pair

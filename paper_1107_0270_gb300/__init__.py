@@ -30,7 +30,7 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
            "rd_pair_probs", "rd_resample", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
            "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static",
-           "rd_info", "rd_count_history"]
+           "rd_info", "rd_count_history", "rd_check_bounded_wait"]
 
 
 class RDError(RuntimeError):
@@ -105,6 +105,7 @@ def _lib():
         L.rd_step_static.argtypes = [P(_Config), vp, i64, vp, vp, vp, u32, i64, i64, vp, vp, vp, vp, vp, vp]
         L.rd_info.argtypes = [vp, P(d), i32]
         L.rd_count_history.argtypes = [vp, i64, i64, P(i64)]
+        L.rd_check_bounded_wait.argtypes = [vp, C.c_uint32, P(i32)]
         L.rd_free.argtypes = [vp]
         L.rd_free.restype = None
         L.rd_strerror.argtypes = [C.c_int]
@@ -243,6 +244,13 @@ class Simulation:
         return {"counts": counts.reshape(self.n_replicas, self.n_species), "step": step.value,
                 "t": t.value, "stats": dict(zip(STAT_NAMES, stats.tolist()))}
 
+    def check_bounded_wait(self, spin_limit: int = 100_000) -> int:
+        """Run the cell scan once with a look-back wait that nothing satisfies, bounded by
+        spin_limit polls; returns the status the device latched (RD_ETIMEOUT = 4 expected)."""
+        st = C.c_int32()
+        _check(_lib().rd_check_bounded_wait(self._h, int(spin_limit), C.byref(st)), "rd_check_bounded_wait")
+        return st.value
+
     def count_history(self, first_step: int = 0, n_steps: Optional[int] = None):
         """Totals per species (summed over replicas) for steps first_step .. first_step+n_steps-1."""
         if n_steps is None:
@@ -265,7 +273,9 @@ class Simulation:
         _check(_lib().rd_num_particles(self._h, C.byref(n)), "rd_num_particles")
         return n.value
 
-    def get_state(self):
+    def get_state(self, allow_error: bool = False):
+        """Current state (host copies).  allow_error: return it even when a device error
+        (RD_ECAPACITY / RD_ETIMEOUT) is latched, with the code under "status"."""
         n = C.c_int64(self.num_particles())
         x = np.zeros((max(n.value, 1), 3))
         sp = np.zeros(max(n.value, 1), np.int32)
@@ -276,10 +286,11 @@ class Simulation:
         rc = _lib().rd_get_state(self._h, C.byref(n), _ptr(x, C.c_double), _ptr(sp, C.c_int32),
                                  _ptr(ids, C.c_uint32), _ptr(rep, C.c_int32), _ptr(nxt, C.c_uint32),
                                  C.byref(step))
-        _check(rc, "rd_get_state")
+        if not (allow_error and rc in (3, 4)):
+            _check(rc, "rd_get_state")
         m = n.value
         return {"x": x[:m], "species": sp[:m], "ids": ids[:m], "replica": rep[:m], "next_id": nxt,
-                "step": step.value}
+                "step": step.value, "status": rc}
 
     def set_state(self, x, species, ids, replica=None, next_id=None, step: int = 0):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)

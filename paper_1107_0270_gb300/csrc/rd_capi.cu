@@ -1042,6 +1042,31 @@ int rd_last_fired(rd_handle* h, int64_t cap, int64_t* n_out, uint32_t* id_a, uin
   return ctl.status;
 }
 
+int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out) {
+  if (!h || !status_out || spin_limit == 0) return RD_EINVAL;
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl saved, probe;
+  RD_CUDA(cudaMemcpy(&saved, h->L.ctl, sizeof saved, cudaMemcpyDeviceToHost));
+  if (saved.status != 0) return saved.status;
+  probe = saved;
+  probe.epoch += 1;          // a scan epoch whose flags nobody has published yet
+  probe.tile_ctr[0] = 1;     // tile 0 is never taken: tile 1 waits for a flag that nothing sets
+  probe.spin_limit = spin_limit;
+  RD_CUDA(cudaMemcpy(h->L.ctl, &probe, sizeof probe, cudaMemcpyHostToDevice));
+  // the cell counts are all zero between steps; the scan rewrites the cell starts, which the next
+  // step rebuilds
+  launch_cell_scan(launch_for(h, h->cur), h->stream);
+  RD_CUDA(cudaGetLastError());
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  DevCtl after;
+  RD_CUDA(cudaMemcpy(&after, h->L.ctl, sizeof after, cudaMemcpyDeviceToHost));
+  *status_out = after.status;
+  DevCtl back = saved;
+  back.epoch = after.epoch;  // flags written by the probe must not look current later
+  RD_CUDA(cudaMemcpy(h->L.ctl, &back, sizeof back, cudaMemcpyHostToDevice));
+  return RD_OK;
+}
+
 int rd_info(rd_handle* h, double* out, int32_t n) {
   if (!h || !out || n < 0) return RD_EINVAL;
   const double v[8] = {h->factor, (double)h->L.total_cells, (double)h->L.block,

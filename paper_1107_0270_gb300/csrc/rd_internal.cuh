@@ -117,7 +117,7 @@ struct DevCtl {
   uint32_t live[2];        // live conflict pairs after a matching round (by round parity)
   uint32_t done_res;       // blocks of the matching / resolution kernel that finished
   uint32_t n_new;          // particles after this step (set with the replica table)
-  uint32_t pad_ctl;
+  uint32_t spin_limit;     // bound of the device waits in polls (0: the built-in bounds)
   double t;
   unsigned long long stats[RD_NSTATS];
 };

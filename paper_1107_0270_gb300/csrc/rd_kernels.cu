@@ -270,12 +270,13 @@ __device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch,
     }
     int64_t top = (int64_t)tile - 1;
     uint32_t spins = 0;
+    const uint32_t limit = ctl->spin_limit ? ctl->spin_limit : kSpinLimit;
     for (;;) {
       const int64_t q = top - lane;
       const uint32_t f = q >= 0 ? *(volatile uint32_t*)&flag[q] : ((epoch << 2) | 2u);
       const bool ready = (f >> 2) == epoch && (f & 3u) != 0u;
       if (!__all_sync(0xFFFFFFFFu, ready)) {
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
           if (lane == 0) set_status(ctl, RD_ETIMEOUT);
           break;
         }
@@ -678,8 +679,9 @@ __device__ __forceinline__ bool grid_barrier(DevCtl* ctl) {
       atomicAdd(&ctl->bar_gen, 1u);
     } else {
       uint32_t spins = 0;
+      const uint32_t limit = ctl->spin_limit ? ctl->spin_limit : kBarrierSpin;
       while (*gen == g) {
-        if (++spins > kBarrierSpin) {
+        if (++spins > limit) {
           set_status(ctl, RD_ETIMEOUT);
           ok = 0;
           break;
@@ -1796,6 +1798,14 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
              L.rep_prod, x0, x1, L.id_cur, L.status, prod, L.agg64, L.incl64, L.flags + L.flag_stride, xo, L.id_next,
              L.counts, L.n_counts, L.history, L.history_len);
   mark("k_compact");
+}
+
+void launch_cell_scan(const StepLaunch& L, cudaStream_t s) {
+  const int64_t tile = 256 * (int64_t)kScanItems;
+  const int nbc = (int)((L.total_cells + tile - 1) / tile);
+  k_scan1<uint32_t, LoadCellCount><<<nbc, 256, 0, s>>>(LoadCellCount{L.cell_count}, L.total_cells, nullptr,
+                                                       L.cell_start, L.cell_count, L.agg32, L.incl32, L.flags,
+                                                       L.ctl, 0);
 }
 
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {

@@ -88,6 +88,8 @@ struct KernelTimer {
 // blocks of the cooperative matching launch that fit on the device at once (>= 1)
 int match_grid_size(int device_sms);
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer);
+// the cell scan of a step on its own (bounded-wait check)
+void launch_cell_scan(const StepLaunch& L, cudaStream_t s);
 void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int32_t* sp_of, const uint32_t* id_of,
                            uint32_t n, cudaStream_t s);
 void launch_count(const StepLaunch& L, cudaStream_t s);
