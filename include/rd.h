@@ -250,7 +250,7 @@ int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* ca
 #define RD_STATIC_MAX_PARTICLES 16384
 #define RD_STATIC_MAX_CELLS 65536
 #define RD_STATIC_MAX_PAIRS 65536
-#define RD_STATIC_SCRATCH_BYTES (16u << 20)
+#define RD_STATIC_SCRATCH_BYTES (32u << 20)
 int rd_step_static(const rd_config* cfg, void* stream, int64_t n, const double* x_in,
                    const int32_t* species_in, const uint32_t* id_in, uint32_t next_id, int64_t step,
                    int64_t out_cap, double* x_out, int32_t* species_out, uint32_t* id_out,

@@ -351,25 +351,32 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
     const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
     const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
     const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
-    const size_t bytes = (size_t)n0 * n1 * sizeof(float);
-    auto make = [&](int kind, Tab2& T) -> cudaError_t {
+    // the inverse table's second axis: t = sqrt(-ln U) up to 4.2 (U >= 2^-24 needs t <= 4.08)
+    const double hinv = 0.025;
+    const int ninv = (int)std::ceil(4.2 / hinv) + 4;
+    auto make = [&](int kind, Tab2& T, int m1, double h1, const Tab2* fwd) -> cudaError_t {
+      const size_t bytes = (size_t)n0 * m1 * sizeof(float);
       float* t = (float*)alloc(bytes);
       float4* q4 = (float4*)alloc(4 * bytes);
       double* tot = (double*)alloc((size_t)n0 * sizeof(double));
       if (!t || !q4 || !tot) return cudaErrorMemoryAllocation;
-      launch_build_table(h->L.P, k, kind, t, q4, n0, n1, hstep, tot, h->stream);
+      launch_build_table(h->L.P, k, kind, t, q4, n0, m1, hstep, h1, tot, fwd, h->stream);
       T.v = t;
       T.q = q4;
       T.n0 = n0;
-      T.n1 = n1;
+      T.n1 = m1;
       T.h = (float)hstep;
       T.inv_h = (float)(1.0 / hstep);
+      T.h1 = (float)h1;
+      T.inv_h1 = (float)(1.0 / h1);
       return cudaGetLastError();
     };
     cudaError_t e = cudaSuccess;
-    if (c.pairs[k].bc == RD_BC_RAD) e = make(0, q.tab_preac);
-    if (e == cudaSuccess && c.dim == 2) e = make(1, q.tab_penc);
-    if (e == cudaSuccess && c.dim == 2) e = make(2, q.tab_tail);
+    if (c.pairs[k].bc == RD_BC_RAD) e = make(0, q.tab_preac, n1, hstep, nullptr);
+    if (e == cudaSuccess && c.dim == 2) e = make(1, q.tab_penc, n1, hstep, nullptr);
+    if (e == cudaSuccess && c.dim == 2) e = make(2, q.tab_tail, n1, hstep, nullptr);
+    if (e == cudaSuccess && c.pairs[k].bc != RD_BC_ABS)
+      e = make(3, q.tab_inv, ninv, hinv, c.dim == 2 ? &q.tab_tail : nullptr);
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -1134,7 +1141,7 @@ void rd_free(rd_handle* h) {
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr size_t kStaticScratchBytes = (size_t)RD_STATIC_SCRATCH_BYTES;
 constexpr int kStaticMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -1353,26 +1360,38 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   RD_CUDA(cudaMemsetAsync(L.rep_prod, 0, 4, s));
   RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
   if (c.precision == RD_MIXED) {
-    // the mixed step reads p_reac from an FP32 table: build it into the scratch array as well
+    // the mixed step reads p_reac and the propagator sample from FP32 tables: build them into
+    // the scratch array as well
     bool any = false;
     for (int k = 0; k < c.n_pairs; ++k) {
-      if (c.pairs[k].bc != RD_BC_RAD) continue;
+      if (c.pairs[k].bc == RD_BC_NONE || c.pairs[k].bc == RD_BC_ABS) continue;
       PairDev& q = tmp.hp.pairs[k];
       const double hstep = 0.025 * std::min(q.s, 1.0);
       const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
       const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
       const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
-      float* t = (float*)b.take((size_t)n0 * n1 * sizeof(float));
-      float4* q4 = (float4*)b.take((size_t)n0 * n1 * sizeof(float4));
+      const double hinv = 0.025;
+      const int ninv = (int)std::ceil(4.2 / hinv) + 4;
+      // only the quad copies are read by the step; the scalar table and the totals are build
+      // scratch shared by the tables (stream order keeps the builds apart)
+      float* t = (float*)b.take((size_t)n0 * std::max(n1, ninv) * sizeof(float));
       double* tot = (double*)b.take((size_t)n0 * sizeof(double));
-      if (!b.ok) return RD_EINVAL;
-      launch_build_table(L.P, k, 0, t, q4, n0, n1, hstep, tot, s);
-      q.tab_preac.v = t;
-      q.tab_preac.q = q4;
-      q.tab_preac.n0 = n0;
-      q.tab_preac.n1 = n1;
-      q.tab_preac.h = (float)hstep;
-      q.tab_preac.inv_h = (float)(1.0 / hstep);
+      auto make = [&](int kind, Tab2& T, int m1, double h1) -> bool {
+        float4* q4 = (float4*)b.take((size_t)n0 * m1 * sizeof(float4));
+        if (!b.ok) return false;
+        launch_build_table(L.P, k, kind, t, q4, n0, m1, hstep, h1, tot, nullptr, s);
+        T.v = nullptr;
+        T.q = q4;
+        T.n0 = n0;
+        T.n1 = m1;
+        T.h = (float)hstep;
+        T.inv_h = (float)(1.0 / hstep);
+        T.h1 = (float)h1;
+        T.inv_h1 = (float)(1.0 / h1);
+        return true;
+      };
+      if (c.pairs[k].bc == RD_BC_RAD && !make(0, q.tab_preac, n1, hstep)) return RD_EINVAL;
+      if (!make(3, q.tab_inv, ninv, hinv)) return RD_EINVAL;
       any = true;
     }
     if (any) RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));

@@ -43,10 +43,11 @@ struct Series2D;
 // Uniform 2D table over (d0, d) with spacing h; row/column 0 is a ghost point at -h and two ghost
 // points follow the last grid point (n0 x n1 stored values).  Catmull-Rom bicubic lookup.
 struct Tab2 {
-  const float* v;             // n0 x n1 values on the grid (d0, d) = (h (i-1), h (j-1))
+  const float* v;             // n0 x n1 values on the grid (x0, x1) = (h (i-1), h1 (j-1))
   const float4* q;            // q[i n1 + j] = v[i n1 + j-1 .. j+2]: one aligned load per stencil row
   int32_t n0, n1;
-  float inv_h, h;
+  float inv_h, h;             // first axis
+  float inv_h1, h1;           // second axis
 };
 
 struct PairDev {
@@ -60,6 +61,7 @@ struct PairDev {
   const Series2D* ser;
   // mixed step: FP32 tables of p_reac (2D and 3D), F = p_enc e^{d d0/tau} and -ln(tail) (2D)
   Tab2 tab_preac, tab_penc, tab_tail;
+  Tab2 tab_inv;               // propagator sample V = R - 1 at (R0 - 1, sqrt(-ln U))
 };
 
 struct DecayDev {
@@ -454,9 +456,41 @@ __device__ __forceinline__ void cr_w(float t, float w[4]) {
   w[3] = 0.5f * (t3 - t2);
 }
 
+// derivative of the Catmull-Rom weights with respect to t
+__device__ __forceinline__ void cr_dw(float t, float w[4]) {
+  const float t2 = t * t;
+  w[0] = 0.5f * (-3.0f * t2 + 4.0f * t - 1.0f);
+  w[1] = 0.5f * (9.0f * t2 - 10.0f * t);
+  w[2] = 0.5f * (-9.0f * t2 + 8.0f * t + 1.0f);
+  w[3] = 0.5f * (3.0f * t2 - 2.0f * t);
+}
+
+// bicubic Catmull-Rom value and its derivative along the second axis at (d0, d) >= 0
+__device__ __forceinline__ float tab_eval_dd(const Tab2& T, float d0, float d, float& dval) {
+  float x = d0 * T.inv_h + 1.0f, y = d * T.inv_h1 + 1.0f;
+  x = fminf(fmaxf(x, 1.0f), (float)(T.n0 - 3) - 1e-3f);
+  y = fminf(fmaxf(y, 1.0f), (float)(T.n1 - 3) - 1e-3f);
+  const int i = (int)x, j = (int)y;
+  float wx[4], wy[4], dwy[4];
+  cr_w(x - i, wx);
+  cr_w(y - j, wy);
+  cr_dw(y - j, dwy);
+  float4 v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = __ldg(T.q + (size_t)(i - 1 + a) * T.n1 + j);
+  float acc = 0.0f, dacc = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    acc += wx[a] * (wy[0] * v[a].x + wy[1] * v[a].y + wy[2] * v[a].z + wy[3] * v[a].w);
+    dacc += wx[a] * (dwy[0] * v[a].x + dwy[1] * v[a].y + dwy[2] * v[a].z + dwy[3] * v[a].w);
+  }
+  dval = dacc * T.inv_h1;
+  return acc;
+}
+
 // bicubic Catmull-Rom value at (d0, d) >= 0 (clamped to the table)
 __device__ __forceinline__ float tab_eval(const Tab2& T, float d0, float d) {
-  float x = d0 * T.inv_h + 1.0f, y = d * T.inv_h + 1.0f;
+  float x = d0 * T.inv_h + 1.0f, y = d * T.inv_h1 + 1.0f;
   x = fminf(fmaxf(x, 1.0f), (float)(T.n0 - 3) - 1e-3f);
   y = fminf(fmaxf(y, 1.0f), (float)(T.n1 - 3) - 1e-3f);
   const int i = (int)x, j = (int)y;

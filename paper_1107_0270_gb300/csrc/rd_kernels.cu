@@ -922,19 +922,32 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
 // ------------------------------------------------------------------------------------------------
 // Mixed step: positions, displacements and the propagator sample in FP32; p_reac in FP64.
 // ------------------------------------------------------------------------------------------------
-// 2D propagator sample from the -ln(tail) table: bisection on the interpolant (increasing in v)
+// Mixed-step propagator samples from the inverse table V(R0 - 1, sqrt(-ln U)) and one Newton step
+// on ln T: in 3D on the FP32 closed form, in 2D on the forward -ln(tail) table.
+__device__ __forceinline__ float resample3_tab(const PairDev& pr, float U, float R0) {
+  if (R0 < 1.0f) R0 = 1.0f;
+  const float w = R0 - 1.0f, s = pr.s_f;
+  const float lnU = logf(U);
+  float V = fmaxf(tab_eval(pr.tab_inv, w, sqrtf(-lnU)), 0.0f);
+  const float inv_4tau = 1.0f / (4.0f * s * s);
+  const float ln_ex0 = logf(erfcxf(w / (2.0f * s)));
+  float f, df;
+  lnT3_f(V, w, s, inv_4tau, ln_ex0, f, df);
+  if (df < 0.0f) V = fmaxf(V - (f - lnU) / df, 0.0f);
+  return 1.0f + V;
+}
+
 __device__ __forceinline__ float resample2_tab(const PairDev& pr, float U, float R0) {
   const float d0 = fmaxf(R0 - 1.0f, 0.0f), target = -logf(U);
-  float lo = 0.0f, hi = (float)(pr.tab_tail.n1 - 4) * pr.tab_tail.h;
-#pragma unroll 1
-  for (int it = 0; it < 32; ++it) {
-    const float mid = 0.5f * (lo + hi);
-    if (tab_eval(pr.tab_tail, d0, mid) < target)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return 1.0f + 0.5f * (lo + hi);
+  float V = fmaxf(tab_eval(pr.tab_inv, d0, sqrtf(target)), 0.0f);
+  float dF;
+  const float F = tab_eval_dd(pr.tab_tail, d0, V, dF);
+  if (dF > 0.0f) V = fmaxf(V - (F - target) / dF, 0.0f);
+  return 1.0f + V;
+}
+
+__device__ __noinline__ float resample_tab_ni(const PairDev& pr, bool d3, float U, float R0) {
+  return d3 ? resample3_tab(pr, U, R0) : resample2_tab(pr, U, R0);
 }
 
 __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev* __restrict__ reps,
@@ -964,7 +977,7 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     const uint4 w = draw_ni(P, step, f.ida, f.idb, TAG_RES, r);
     float R0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z) * pr.inv_sigma_f;
     R0 = fmaxf(R0, 1.0f);
-    const float Rn = d3 ? resample3_f_ni(u23(w.x), R0, pr.s_f) : resample2_tab(pr, u23(w.x), R0);
+    const float Rn = resample_tab_ni(pr, d3, u23(w.x), R0);
     const float len = sqrtf(rx * rx + ry * ry + rz * rz);
     float dx, dy, dz;
     if (len > 0.0f) {
@@ -1055,7 +1068,7 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     if (rule >= 0) {
       const PairDev& pr = P.pairs[rule];
       w = draw_ni(P, step, pid, kOneParticle, TAG_RES, r);
-      const float Rn = d3 ? resample3_f_ni(u23(w.x), 1.0f, pr.s_f) : resample2_tab(pr, u23(w.x), 1.0f);
+      const float Rn = resample_tab_ni(pr, d3, u23(w.x), 1.0f);
       const float ln = Rn * pr.sigma_f;
       rx = ln * dx; ry = ln * dy; rz = ln * dz;
       if (pr.bc == RD_BC_ABS)
@@ -1088,6 +1101,123 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     }
   }
   status[i] = st | (np << ST_NPROD_SHIFT);
+}
+
+// Rounds of locally-dominant matching for a short conflict list (at most kMatchSmemPairs pairs),
+// by one block in shared memory: every particle of the list gets a local slot (open addressing on
+// its index, load factor <= 1/2), so the per-round minima are shared-memory atomics.  Same rule as
+// the global rounds: a pair is accepted when its (key, id_a, id_b) is the smallest at both of its
+// particles among the live pairs.  Returns false if the round bound ran out.
+constexpr int kMatchSmemPairs = 256, kMatchSmemSlots = 1024;
+
+__device__ __noinline__ bool match_rounds_smem(const DevParams& P, DevCtl* __restrict__ ctl,
+                                               const FiredPair* __restrict__ fired, uint32_t* __restrict__ fstate,
+                                               int32_t* __restrict__ matched, const uint32_t* __restrict__ conflict,
+                                               uint32_t* __restrict__ accepted, uint32_t nc) {
+  __shared__ uint32_t s_e[kMatchSmemPairs];
+  __shared__ unsigned long long s_key[kMatchSmemPairs], s_pid[kMatchSmemPairs];
+  __shared__ uint16_t s_sa[kMatchSmemPairs], s_sb[kMatchSmemPairs];
+  __shared__ uint8_t s_state[kMatchSmemPairs];     // 1 live, 2 accepted, 0 dead
+  __shared__ uint32_t s_h[kMatchSmemSlots];
+  __shared__ unsigned long long s_bk[kMatchSmemSlots], s_bp[kMatchSmemSlots];
+  __shared__ uint8_t s_m[kMatchSmemSlots];
+  __shared__ uint32_t s_live;
+  __shared__ unsigned long long s_acc;
+  __shared__ int s_err;
+  for (int k = threadIdx.x; k < kMatchSmemSlots; k += blockDim.x) {
+    s_h[k] = 0xFFFFFFFFu;
+    s_bk[k] = ~0ull;
+    s_bp[k] = ~0ull;
+    s_m[k] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_acc = 0ull;
+    s_err = 0;
+  }
+  __syncthreads();
+  auto slot_of = [&](uint32_t pidx) -> uint32_t {
+    uint32_t h = (pidx * 2654435761u) >> (32 - 10);
+    for (int probe = 0; probe < kMatchSmemSlots; ++probe) {
+      const uint32_t prev = atomicCAS(&s_h[h], 0xFFFFFFFFu, pidx);
+      if (prev == 0xFFFFFFFFu || prev == pidx) return h;
+      h = (h + 1u) & (kMatchSmemSlots - 1);
+    }
+    s_err = 1;   // cannot happen at load factor <= 1/2
+    return 0u;
+  };
+  for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+    const uint32_t e = conflict[q];
+    const FiredPair f = fired[e];
+    s_e[q] = e;
+    s_key[q] = (unsigned long long)__double_as_longlong(f.key);
+    s_pid[q] = ((unsigned long long)f.ida << 32) | f.idb;
+    s_sa[q] = (uint16_t)slot_of(f.ia);
+    s_sb[q] = (uint16_t)slot_of(f.ib);
+    s_state[q] = 1;
+  }
+  __syncthreads();
+  int rounds = 0;
+  bool ok = s_err == 0;
+  while (ok) {
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      if (s_state[q] != 1) continue;
+      atomicMin(&s_bk[s_sa[q]], s_key[q]);
+      atomicMin(&s_bk[s_sb[q]], s_key[q]);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      if (s_state[q] != 1) continue;
+      if (s_bk[s_sa[q]] == s_key[q]) atomicMin(&s_bp[s_sa[q]], s_pid[q]);
+      if (s_bk[s_sb[q]] == s_key[q]) atomicMin(&s_bp[s_sb[q]], s_pid[q]);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      if (s_state[q] != 1) continue;
+      const uint32_t a = s_sa[q], b = s_sb[q];
+      if (s_bk[a] == s_key[q] && s_bk[b] == s_key[q] && s_bp[a] == s_pid[q] && s_bp[b] == s_pid[q]) {
+        s_m[a] = 1;
+        s_m[b] = 1;
+        s_state[q] = 2;
+        const uint32_t e = s_e[q];
+        const FiredPair f = fired[e];
+        matched[f.ia] = (int32_t)f.ib;
+        matched[f.ib] = (int32_t)f.ia;
+        fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
+        accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
+        atomicAdd(&s_acc, 1ull);
+      }
+    }
+    if (threadIdx.x == 0) s_live = 0u;
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < nc; q += blockDim.x) {
+      if (s_state[q] != 1) continue;
+      const uint32_t a = s_sa[q], b = s_sb[q];
+      if (s_m[a] || s_m[b]) {
+        s_state[q] = 0;
+        fstate[s_e[q]] = (fstate[s_e[q]] & ~3u) | FS_DEAD;
+      } else {
+        s_bk[a] = ~0ull;
+        s_bk[b] = ~0ull;
+        s_bp[a] = ~0ull;
+        s_bp[b] = ~0ull;
+        atomicAdd(&s_live, 1u);
+      }
+    }
+    __syncthreads();
+    ++rounds;
+    if (s_live == 0u) break;
+    if (rounds >= P.match_max_rounds) {
+      ok = false;
+      break;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (!ok) set_status(ctl, RD_ETIMEOUT);
+    if (s_acc) atomicAdd(&ctl->stats[RD_STAT_MATCHED], s_acc);
+    atomicAdd(&ctl->stats[RD_STAT_MATCH_ROUNDS], (unsigned long long)rounds);
+  }
+  __syncthreads();
+  return ok;
 }
 
 // Compaction table over replicas, by one block: survivors = particles - consumed; exclusive
@@ -1204,7 +1334,15 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
       }
     }
   }
-  if (nc > 0 && (multi || blockIdx.x == 0)) {
+  if (nc > 0 && !multi && nc <= (uint32_t)kMatchSmemPairs && blockIdx.x == 0) {
+    // short list: block 0 matches in shared memory, then resolves the pairs it accepted
+    if (match_rounds_smem(P, ctl, fired, fstate, matched, conflict, accepted, nc)) {
+      const uint32_t n_acc = *(volatile uint32_t*)&ctl->n_accept;
+      for (uint32_t q = n_triv + threadIdx.x; q < n_acc; q += blockDim.x)
+        resolve_item<T>(P, reps, fired, fstate, true, accepted[q], step, x0, x1, id, status, prodpos, rep_cons,
+                        rep_prod, n_react, n_res, n_rec, n_near);
+    }
+  } else if (nc > 0 && (multi || blockIdx.x == 0)) {
     const uint32_t nthr = multi ? gridDim.x * blockDim.x : blockDim.x;
     const uint32_t tid = multi ? blockIdx.x * blockDim.x + threadIdx.x : threadIdx.x;
     auto sync = [&]() -> bool {
@@ -1610,15 +1748,16 @@ __global__ void k_resample(const DevParams* __restrict__ Pp, int rule, const dou
                            const double* __restrict__ u, int64_t n, double* __restrict__ out) {
   const PairDev& pr = Pp->pairs[rule];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = (Pp->precision == RD_MIXED && Pp->dim == 2 ? (double)resample2_tab(pr, (float)u[k], (float)(r0[k] / pr.sigma))
-                                                        : resample_dim(*Pp, pr, u[k], r0[k] / pr.sigma)) * pr.sigma;
+    out[k] = (Pp->precision == RD_MIXED ? (double)resample_tab_ni(pr, Pp->dim == 3, (float)u[k], (float)(r0[k] / pr.sigma))
+                                        : resample_dim(*Pp, pr, u[k], r0[k] / pr.sigma)) * pr.sigma;
 }
 
 
 // ================================================================================================
 // Per-run FP32 tables for the mixed step, built in FP64 from the same pair functions.  Entry
 // (i, j) sits at d0 = (i-1) h, d = (j-1) h; row/column 0 is a ghost filled by extrapolation.
-// kind 0: p_reac; kind 1: F = p_enc e^{d d0/tau} (2D); kind 2: -ln(tail) of the propagator (2D).
+// kind 0: p_reac; kind 1: F = p_enc e^{d d0/tau} (2D); kind 2: -ln(tail) of the propagator (2D);
+// kind 3: the propagator sample V = R - 1 at U = exp(-t^2) (3D; second axis t with its own step).
 // ================================================================================================
 __global__ void k_tail_totals(const DevParams* __restrict__ Pp, int rule, int n0, double h, double* __restrict__ tot) {
   const PairDev& pr = Pp->pairs[rule];
@@ -1629,7 +1768,7 @@ __global__ void k_tail_totals(const DevParams* __restrict__ Pp, int rule, int n0
 }
 
 __global__ void k_build_table(const DevParams* __restrict__ Pp, int rule, int kind, float* __restrict__ out, int n0,
-                              int n1, double h, const double* __restrict__ tot) {
+                              int n1, double h, double h1, const double* __restrict__ tot) {
   const DevParams& P = *Pp;
   const PairDev& pr = P.pairs[rule];
   const int64_t total = (int64_t)n0 * n1;
@@ -1644,9 +1783,13 @@ __global__ void k_build_table(const DevParams* __restrict__ Pp, int rule, int ki
       const double x = d * d0 / pr.tau;
       v = x > 60.0 ? 1.0 : p_enc_dim(P, pr, 1.0 + d, 1.0 + d0) * exp(x);
       if (d <= 0.0 || d0 <= 0.0) v = 1.0;
-    } else {
+    } else if (kind == 2) {
       const double t = 1.0 - cdf2(pair2d(pr), d, 1.0 + d0, P.gl16) / tot[i];
       v = t > 1e-30 ? -log(t) : 69.0;
+    } else {
+      // kind 3 (3D): V = R - 1 of the propagator sample at U = exp(-t^2), t on the second axis
+      const double t = (j - 1) * h1;
+      v = t > 0.0 ? resample3(exp(-t * t), 1.0 + d0, pr.s) - 1.0 : 0.0;
     }
     out[e] = (float)v;
   }
@@ -1677,12 +1820,36 @@ __global__ void k_table_quads(const float* __restrict__ T, int n0, int n1, float
   }
 }
 
+// 2D inverse table from a finished forward -ln(tail) table: at each node (d0, t) the V where the
+// forward interpolant reaches t^2 (bisection on the interpolant, increasing in V).
+__global__ void k_build_inverse2(Tab2 fwd, float* __restrict__ out, int n0, int n1, double h, double h1) {
+  const int64_t total = (int64_t)n0 * n1;
+  const float vmax = (float)(fwd.n1 - 4) * fwd.h1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n1), j = (int)(e % n1);
+    if (i == 0 || j == 0) continue;
+    const float d0 = (float)((i - 1) * h), t = (float)((j - 1) * h1), target = t * t;
+    float lo = 0.0f, hi = vmax;
+    for (int it = 0; it < 40; ++it) {
+      const float mid = 0.5f * (lo + hi);
+      if (tab_eval(fwd, d0, mid) < target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    out[e] = j == 1 ? 0.0f : 0.5f * (lo + hi);
+  }
+}
+
 void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
-                        double* tot, cudaStream_t s) {
+                        double h1, double* tot, const Tab2* fwd, cudaStream_t s) {
   if (kind == 2) k_tail_totals<<<(n0 + 63) / 64, 64, 0, s>>>(P, rule, n0, h, tot);
   const int64_t total = (int64_t)n0 * n1;
   const int G = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
-  k_build_table<<<G, 128, 0, s>>>(P, rule, kind, out, n0, n1, h, tot);
+  if (kind == 3 && fwd)
+    k_build_inverse2<<<G, 128, 0, s>>>(*fwd, out, n0, n1, h, h1);
+  else
+    k_build_table<<<G, 128, 0, s>>>(P, rule, kind, out, n0, n1, h, h1, tot);
   k_table_ghosts<<<(n0 + 255) / 256, 256, 0, s>>>(out, n0, n1);
   k_table_ghost_row<<<(n1 + 255) / 256, 256, 0, s>>>(out, n1);
   k_table_quads<<<G, 128, 0, s>>>(out, n0, n1, quad);

@@ -2,7 +2,8 @@
 the step's fired pairs in ascending (key, id_a, id_b) (Section 3: each particle takes part in at
 most one reaction, the pair with the smallest exponential race key wins).  The dense 2D membrane
 at tau = 0.8 puts thousands of pairs into the iterative rounds, which then run on the whole
-cooperative grid; the sparse 3D system keeps them on a single block."""
+cooperative grid; smaller membranes at the same density put hundreds there (one block, global
+memory); the sparse 3D system a few (one block, shared memory)."""
 import numpy as np
 import pytest
 
@@ -16,6 +17,7 @@ if not torch.cuda.is_available():
 
 import paper_1107_0270_gb300 as pkg  # noqa: E402
 
+SHARED_MEMORY_MAX = 256   # conflict pairs matched by one block in shared memory
 SINGLE_BLOCK_MAX = 2048   # conflict pairs handled by one block (above: the cooperative grid)
 
 
@@ -64,5 +66,23 @@ def test_sparse_3d_matching_is_greedy(precision):
         f = sim.last_fired()
         acc, a, b = greedy_accept(f)
         assert np.array_equal(acc, f["accepted"])
-        assert 0 < conflict_pairs(a, b) <= SINGLE_BLOCK_MAX
+        assert 0 < conflict_pairs(a, b) <= SHARED_MEMORY_MAX
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_mid_size_conflict_lists_are_greedy(precision):
+    # membranes at the full-size density with fewer particles: at least one lands its conflict
+    # list between the shared-memory and the cooperative regimes
+    seen = []
+    for n_each in (2000, 4000, 8000, 16000):
+        L = 10.0 * (n_each / 200_000) ** 0.5
+        sim = pkg.Simulation(W.membrane_2d(seed=5, n_each=n_each, L=L), precision=precision)
+        for _ in range(2):
+            sim.step()
+            f = sim.last_fired()
+            acc, a, b = greedy_accept(f)
+            assert np.array_equal(acc, f["accepted"]), n_each
+            seen.append(conflict_pairs(a, b))
+        sim.close()
+    assert any(SHARED_MEMORY_MAX < c <= SINGLE_BLOCK_MAX for c in seen), seen

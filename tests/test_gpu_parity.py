@@ -137,6 +137,26 @@ def test_resample_matches_oracle(tau):
     sim.close()
 
 
+@pytest.mark.parametrize("tau", [0.08, 0.8, 8.0])
+def test_mixed_resample_inverts_the_oracle_tail(tau):
+    # the mixed step samples the propagator from an FP32 inverse table and one Newton step: the
+    # oracle's tail at the sampled separation must give back the uniform (draws as in the step,
+    # U >= 2^-24)
+    sigma, D = 0.005, 2.0
+    dt = tau * sigma ** 2 / D
+    system = W.System(dim=3, L=1.0, dt=dt, seed=1, D=[1.0, 1.0, 0.5], n_init=[1, 1, 0],
+                      pairs=[W.PairRule(0, 1, sigma, "rad", 0.02, 2)])
+    rng = np.random.default_rng(6)
+    r0 = sigma * (1 + rng.uniform(0, 5 * math.sqrt(2 * tau), 2000))
+    r0[:200] = sigma
+    u = rng.uniform(2.0 ** -24, 1, 2000)
+    sim = pkg.Simulation(system, precision="mixed")
+    rn = sim.resample(torch.tensor(r0, device="cuda"), torch.tensor(u, device="cuda")).cpu().numpy()
+    back = np.array([O.tail3(b / sigma - 1.0, a / sigma, tau) for a, b in zip(r0, rn)])
+    assert np.max(np.abs(back - u)) <= 2e-5
+    sim.close()
+
+
 def test_stepwise_parity_irreversible():
     totals, obs = stepwise(W.irreversible_3d(), 30)
     assert totals["fired"] > 0
