@@ -415,29 +415,45 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     out["pair_prob_evals_per_s"] = res
     if not args.no_workloads:
         out["workloads"] = other_workloads(torch, pkg, flush)
-    # end to end through the C ABI with host buffers: per step, upload the state from pinned host
-    # memory (rd_set_state), one step, read back the state and the observables (rd_get_state,
-    # rd_observables)
+    # end to end through the C ABI with host buffers: per step, upload the state from page-locked
+    # host memory (rd_set_state), one step, read the state and the observables back into host
+    # memory (rd_get_state, rd_observables)
     sim = pkg.Simulation(workload(args, seed=3), precision=args.precision)
     sim.run(4)
-    st = sim.get_state()
-    n_e2e = 10
+    cap = 2 * sim.num_particles() + 1024
+
+    def pinned(shape, dtype):
+        return torch.empty(shape, dtype=dtype, pin_memory=True).numpy()
+
+    bufs = [{"x": pinned((cap, 3), torch.float64), "species": pinned(cap, torch.int32),
+             "ids": pinned(cap, torch.int32).view(np.uint32), "replica": pinned(cap, torch.int32),
+             "next_id": pinned(1, torch.int32).view(np.uint32)} for _ in range(2)]
+    st = sim.get_state(out=bufs[0])
+
+    def e2e_step(st, k):
+        sim.set_state(st["x"], st["species"], st["ids"], st["replica"], st["next_id"], st["step"])
+        sim.step()
+        nst = sim.get_state(out=bufs[(k + 1) % 2])
+        sim.observables()
+        return nst
+
+    for k in range(3):
+        st = e2e_step(st, k)
+    n_e2e = 50
     t0 = time.perf_counter()
     ps = 0
     h2d = d2h = 0
-    for _ in range(n_e2e):
+    for k in range(n_e2e):
         n = st["ids"].shape[0]
-        sim.set_state(st["x"], st["species"], st["ids"], st["replica"], st["next_id"], st["step"])
-        sim.step()
-        st = sim.get_state()
-        sim.observables()
+        st = e2e_step(st, k)
         ps += n
         h2d += n * (24 + 4 + 4 + 4)
         d2h += st["ids"].shape[0] * (24 + 4 + 4 + 4) + 8 * 3
     el = time.perf_counter() - t0
     out["e2e"] = {"value": ps / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // n_e2e,
                   "d2h_bytes_per_step": d2h // n_e2e,
-                  "path": "rd_set_state(host) + rd_step + rd_get_state(host) + rd_observables per step"}
+                  "path": "rd_set_state (page-locked host arrays) + rd_step + rd_get_state (page-locked "
+                          "host arrays) + rd_observables, per step"}
     sim.close()
     return out
 

@@ -273,15 +273,22 @@ class Simulation:
         _check(_lib().rd_num_particles(self._h, C.byref(n)), "rd_num_particles")
         return n.value
 
-    def get_state(self, allow_error: bool = False):
+    def get_state(self, allow_error: bool = False, out=None):
         """Current state (host copies).  allow_error: return it even when a device error
-        (RD_ECAPACITY / RD_ETIMEOUT) is latched, with the code under "status"."""
-        n = C.c_int64(self.num_particles())
-        x = np.zeros((max(n.value, 1), 3))
-        sp = np.zeros(max(n.value, 1), np.int32)
-        ids = np.zeros(max(n.value, 1), np.uint32)
-        rep = np.zeros(max(n.value, 1), np.int32)
-        nxt = np.zeros(self.n_replicas, np.uint32)
+        (RD_ECAPACITY / RD_ETIMEOUT) is latched, with the code under "status".  out: optional dict
+        of caller-owned arrays ("x" (m, 3) float64, "species" int32, "ids" uint32, "replica"
+        int32, "next_id" uint32) with room for the current particles (e.g. page-locked buffers);
+        the returned arrays are views of them."""
+        if out is None:
+            n = C.c_int64(self.num_particles())
+            x = np.zeros((max(n.value, 1), 3))
+            sp = np.zeros(max(n.value, 1), np.int32)
+            ids = np.zeros(max(n.value, 1), np.uint32)
+            rep = np.zeros(max(n.value, 1), np.int32)
+            nxt = np.zeros(self.n_replicas, np.uint32)
+        else:
+            x, sp, ids, rep, nxt = out["x"], out["species"], out["ids"], out["replica"], out["next_id"]
+            n = C.c_int64(ids.shape[0])
         step = C.c_int64()
         rc = _lib().rd_get_state(self._h, C.byref(n), _ptr(x, C.c_double), _ptr(sp, C.c_int32),
                                  _ptr(ids, C.c_uint32), _ptr(rep, C.c_int32), _ptr(nxt, C.c_uint32),

@@ -52,6 +52,15 @@ struct rd_handle {
   std::vector<double> factors;       // cell-edge factors (one, or the autotuner's candidates)
   double tuned_ms = 0.0;
   double factor = 1.0;               // cell-edge factor in use
+  // staging of rd_set_state / rd_get_state (allocated on first use, capacity-sized)
+  double* st_x = nullptr;
+  int32_t* st_sp = nullptr;
+  uint32_t* st_id = nullptr;
+  int32_t* st_rep = nullptr;
+  uint32_t* st_cnt = nullptr;        // per replica: particles, largest id + 1, next_id in
+  uint32_t* st_maxid = nullptr;
+  uint32_t* st_next = nullptr;
+  int32_t* st_err = nullptr;
 };
 
 static void* dev_alloc(rd_handle* h, size_t bytes) {
@@ -897,12 +906,27 @@ static inline uint32_t wbits_host(const void* rec, size_t vsize) {
   return b;
 }
 
+static bool ensure_staging(rd_handle* h) {
+  if (h->st_x) return true;
+  const int64_t cap = h->L.cap_particles;
+  const int R = h->cfg.n_replicas;
+  h->st_x = (double*)dev_alloc(h, (size_t)cap * 24);
+  h->st_sp = (int32_t*)dev_alloc(h, (size_t)cap * 4);
+  h->st_id = (uint32_t*)dev_alloc(h, (size_t)cap * 4);
+  h->st_rep = (int32_t*)dev_alloc(h, (size_t)cap * 4);
+  h->st_cnt = (uint32_t*)dev_alloc(h, (size_t)R * 4);
+  h->st_maxid = (uint32_t*)dev_alloc(h, (size_t)R * 4);
+  h->st_next = (uint32_t*)dev_alloc(h, (size_t)R * 4);
+  h->st_err = (int32_t*)dev_alloc(h, 16);
+  return h->st_x && h->st_sp && h->st_id && h->st_rep && h->st_cnt && h->st_maxid && h->st_next && h->st_err;
+}
+
 int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, uint32_t* id, int32_t* replica,
                  uint32_t* next_id, int64_t* step) {
   if (!h || !n_inout) return RD_EINVAL;
-  RD_CUDA(cudaStreamSynchronize(h->stream));
   DevCtl ctl;
-  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
+  RD_CUDA(cudaMemcpyAsync(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost, h->stream));
+  RD_CUDA(cudaStreamSynchronize(h->stream));
   const int64_t n = ctl.n;
   if (*n_inout < n) {
     *n_inout = n;
@@ -910,31 +934,23 @@ int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, ui
   }
   *n_inout = n;
   if (step) *step = ctl.step;
-  std::vector<char> raw((size_t)n * h->vsize);
-  if (n) RD_CUDA(cudaMemcpy(raw.data(), h->xbuf[h->cur], (size_t)n * h->vsize, cudaMemcpyDeviceToHost));
-  if (id && n) RD_CUDA(cudaMemcpy(id, h->idbuf[h->cur], (size_t)n * 4, cudaMemcpyDeviceToHost));
-  for (int64_t i = 0; i < n; ++i) {
-    const char* rec = raw.data() + (size_t)i * h->vsize;
-    const uint32_t wb = wbits_host(rec, h->vsize);
-    if (x) {
-      if (h->vsize == 32) {
-        double v[3];
-        std::memcpy(v, rec, 24);
-        x[3 * i] = v[0]; x[3 * i + 1] = v[1]; x[3 * i + 2] = v[2];
-      } else {
-        float v[3];
-        std::memcpy(v, rec, 12);
-        x[3 * i] = v[0]; x[3 * i + 1] = v[1]; x[3 * i + 2] = v[2];
-      }
-    }
-    if (species) species[i] = (int32_t)(wb & 0xFFu);
-    if (replica) replica[i] = (int32_t)(wb >> 8);
+  if (n > 0 && (x || species || replica)) {
+    if (!ensure_staging(h)) return RD_ENOMEM;
+    launch_get_state(h->L, h->xbuf[h->cur], n, x ? h->st_x : nullptr, species ? h->st_sp : nullptr,
+                     replica ? h->st_rep : nullptr, h->stream);
+    RD_CUDA(cudaGetLastError());
+    if (x) RD_CUDA(cudaMemcpyAsync(x, h->st_x, (size_t)n * 24, cudaMemcpyDeviceToHost, h->stream));
+    if (species) RD_CUDA(cudaMemcpyAsync(species, h->st_sp, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (replica) RD_CUDA(cudaMemcpyAsync(replica, h->st_rep, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
   }
+  if (id && n > 0) RD_CUDA(cudaMemcpyAsync(id, h->idbuf[h->cur], (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+  std::vector<RepDev> reps;
   if (next_id) {
-    std::vector<RepDev> reps(h->cfg.n_replicas);
-    RD_CUDA(cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost));
-    for (size_t r = 0; r < reps.size(); ++r) next_id[r] = reps[r].next_id;
+    reps.resize(h->cfg.n_replicas);
+    RD_CUDA(cudaMemcpyAsync(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost, h->stream));
   }
+  RD_CUDA(cudaStreamSynchronize(h->stream));
+  for (size_t r = 0; r < reps.size(); ++r) next_id[r] = reps[r].next_id;
   return ctl.status;
 }
 
@@ -944,63 +960,32 @@ int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* specie
   if (n > h->L.cap_particles) return RD_ECAPACITY;
   if (step < 0 || step > 0xFFFFFFFFll) return RD_EINVAL;
   const rd_config& c = h->cfg;
-  RD_CUDA(cudaStreamSynchronize(h->stream));
-  std::vector<RepDev> reps(c.n_replicas);
-  RD_CUDA(cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost));
-  std::vector<uint32_t> maxid(c.n_replicas, 0);
-  std::vector<int64_t> cnt(c.n_replicas, 0);
-  std::vector<char> raw((size_t)std::max<int64_t>(n, 1) * h->vsize);
-  int prev_r = -1;
-  int64_t prev_id = -1;
-  for (int64_t i = 0; i < n; ++i) {
-    const int r = replica ? replica[i] : 0;
-    if (r < 0 || r >= c.n_replicas || species[i] < 0 || species[i] >= c.n_species) return RD_EINVAL;
-    if (r < prev_r || (r == prev_r && (int64_t)id[i] <= prev_id)) return RD_EINVAL;
-    if (r != prev_r) prev_id = -1;
-    prev_r = r;
-    prev_id = id[i];
-    const double L = reps[r].L;
-    for (int d = 0; d < c.dim; ++d)
-      if (!(x[3 * i + d] >= 0.0 && x[3 * i + d] < L)) return RD_EINVAL;
-    cnt[r]++;
-    maxid[r] = std::max(maxid[r], id[i] + 1);
-    const uint32_t wb = pack_sp((uint32_t)species[i], (uint32_t)r);
-    char* rec = raw.data() + (size_t)i * h->vsize;
-    if (h->vsize == 32) {
-      double v[3] = {x[3 * i], x[3 * i + 1], c.dim == 3 ? x[3 * i + 2] : 0.0};
-      std::memcpy(rec, v, 24);
-      uint64_t b = wb;
-      std::memcpy(rec + 24, &b, 8);
-    } else {
-      float v[3] = {(float)x[3 * i], (float)x[3 * i + 1], c.dim == 3 ? (float)x[3 * i + 2] : 0.0f};
-      for (int d = 0; d < 3; ++d)
-        if (!(v[d] < reps[r].Lf)) v[d] = 0.0f;
-      std::memcpy(rec, v, 12);
-      std::memcpy(rec + 12, &wb, 4);
-    }
+  if (!ensure_staging(h)) return RD_ENOMEM;
+  cudaStream_t s = h->stream;
+  // raw inputs to the device; validation and packing there, into the spare state buffer, so that
+  // a rejected state leaves the current one untouched
+  if (n > 0) {
+    RD_CUDA(cudaMemcpyAsync(h->st_x, x, (size_t)n * 24, cudaMemcpyHostToDevice, s));
+    RD_CUDA(cudaMemcpyAsync(h->st_sp, species, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    RD_CUDA(cudaMemcpyAsync(h->st_id, id, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    if (replica) RD_CUDA(cudaMemcpyAsync(h->st_rep, replica, (size_t)n * 4, cudaMemcpyHostToDevice, s));
   }
-  int64_t off = 0;
-  for (int r = 0; r < c.n_replicas; ++r) {
-    reps[r].beg = (uint32_t)off;
-    off += cnt[r];
-    reps[r].end = (uint32_t)off;
-    reps[r].next_id = next_id ? std::max(next_id[r], maxid[r]) : maxid[r];
-  }
-  if (n) {
-    RD_CUDA(cudaMemcpy(h->xbuf[h->cur], raw.data(), (size_t)n * h->vsize, cudaMemcpyHostToDevice));
-    RD_CUDA(cudaMemcpy(h->idbuf[h->cur], id, (size_t)n * 4, cudaMemcpyHostToDevice));
-  }
-  RD_CUDA(cudaMemcpy(h->L.reps, reps.data(), reps.size() * sizeof(RepDev), cudaMemcpyHostToDevice));
-  DevCtl ctl;
-  RD_CUDA(cudaMemcpy(&ctl, h->L.ctl, sizeof ctl, cudaMemcpyDeviceToHost));
-  ctl.n = (uint32_t)n;
-  ctl.step = (uint32_t)step;
-  ctl.t = (double)step * c.dt;
-  ctl.status = 0;
-  RD_CUDA(cudaMemcpy(h->L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice));
-  launch_count(launch_for(h, h->cur), h->stream);
+  if (next_id) RD_CUDA(cudaMemcpyAsync(h->st_next, next_id, (size_t)c.n_replicas * 4, cudaMemcpyHostToDevice, s));
+  RD_CUDA(cudaMemsetAsync(h->st_cnt, 0, (size_t)c.n_replicas * 4, s));
+  RD_CUDA(cudaMemsetAsync(h->st_maxid, 0, (size_t)c.n_replicas * 4, s));
+  RD_CUDA(cudaMemsetAsync(h->st_err, 0, 4, s));
+  const int spare = 1 - h->cur;
+  launch_set_state(h->L, n, h->st_x, h->st_sp, h->st_id, replica ? h->st_rep : nullptr, h->xbuf[spare],
+                   h->idbuf[spare], h->st_cnt, h->st_maxid, next_id ? h->st_next : nullptr, h->st_err, step, s);
   RD_CUDA(cudaGetLastError());
-  RD_CUDA(cudaStreamSynchronize(h->stream));
+  int32_t err = 0;
+  RD_CUDA(cudaMemcpyAsync(&err, h->st_err, 4, cudaMemcpyDeviceToHost, s));
+  RD_CUDA(cudaStreamSynchronize(s));
+  if (err) return RD_EINVAL;
+  h->cur = spare;
+  launch_count(launch_for(h, h->cur), s);
+  RD_CUDA(cudaGetLastError());
+  RD_CUDA(cudaStreamSynchronize(s));
   return RD_OK;
 }
 

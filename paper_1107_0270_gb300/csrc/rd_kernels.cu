@@ -1967,6 +1967,124 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_compact");
 }
 
+// ================================================================================================
+// State transfer on the device: validation + packing of a caller's state, and unpacking.
+// ================================================================================================
+// Validates element i of a caller's state (replica and species in range, (replica, id) strictly
+// increasing, position inside the box) and packs it into out / ido; counts particles and the
+// largest id per replica.  Any failure sets *err.
+template <class V>
+__global__ void k_set_state(const DevParams* __restrict__ Pp, const RepDev* __restrict__ reps, int64_t n,
+                            const double* __restrict__ x, const int32_t* __restrict__ sp,
+                            const uint32_t* __restrict__ id, const int32_t* __restrict__ rep, V* __restrict__ out,
+                            uint32_t* __restrict__ ido, uint32_t* __restrict__ cnt, uint32_t* __restrict__ maxid,
+                            int32_t* __restrict__ err) {
+  const DevParams& P = *Pp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = rep ? rep[i] : 0;
+    const int s = sp[i];
+    bool ok = r >= 0 && r < P.n_replicas && s >= 0 && s < P.n_species;
+    if (ok && i > 0) {
+      const int rp = rep ? rep[i - 1] : 0;
+      ok = r > rp || (r == rp && id[i] > id[i - 1]);
+    }
+    if (!ok) {
+      atomicOr(err, 1);
+      continue;
+    }
+    const RepDev& rd = reps[r];
+    const double px = x[3 * i], py = x[3 * i + 1], pz = P.dim == 3 ? x[3 * i + 2] : 0.0;
+    if (!(px >= 0.0 && px < rd.L && py >= 0.0 && py < rd.L && (P.dim == 2 || (pz >= 0.0 && pz < rd.L)))) {
+      atomicOr(err, 1);
+      continue;
+    }
+    const uint32_t wb = ((uint32_t)r << 8) | (uint32_t)s;
+    V v;
+    if constexpr (sizeof(V) == 32) {
+      v.x = px; v.y = py; v.z = pz;
+      v.w = w_from_bits_d(wb);
+    } else {
+      float f[3] = {(float)px, (float)py, (float)pz};
+      for (int d = 0; d < 3; ++d)
+        if (!(f[d] < rd.Lf)) f[d] = 0.0f;
+      v = make_float4(f[0], f[1], f[2], w_from_bits_f(wb));
+    }
+    out[i] = v;
+    ido[i] = id[i];
+    atomicAdd(&cnt[r], 1u);
+    atomicMax(&maxid[r], id[i] + 1u);
+  }
+}
+
+// Replica segments and control words of an accepted state (one block; nothing if *err).
+__global__ void k_set_state_finish(const DevParams* __restrict__ Pp, RepDev* __restrict__ reps, DevCtl* __restrict__ ctl,
+                                   const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ maxid,
+                                   const uint32_t* __restrict__ next_id_in, const int32_t* __restrict__ err, int64_t n,
+                                   int64_t step) {
+  __shared__ unsigned long long sm[32];
+  if (*err) return;
+  const DevParams& P = *Pp;
+  unsigned long long carry = 0;
+  for (int base = 0; base < P.n_replicas; base += blockDim.x) {
+    const int r = base + (int)threadIdx.x;
+    const unsigned long long c = r < P.n_replicas ? cnt[r] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = carry + block_exclusive_scan<unsigned long long, int>(c, sm, tot);
+    if (r < P.n_replicas) {
+      reps[r].beg = (uint32_t)ex;
+      reps[r].end = (uint32_t)(ex + c);
+      reps[r].next_id = next_id_in ? max(next_id_in[r], maxid[r]) : maxid[r];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    ctl->n = (uint32_t)n;
+    ctl->step = (uint32_t)step;
+    ctl->t = (double)step * P.dt;
+    ctl->status = 0;
+  }
+}
+
+// Unpacks n records into positions (n x 3 doubles), species and replica (each optional).
+template <class V>
+__global__ void k_get_state(const V* __restrict__ in, int64_t n, double* __restrict__ x, int32_t* __restrict__ sp,
+                            int32_t* __restrict__ rep) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const V v = in[i];
+    const uint32_t wb = w_bits(v.w);
+    if (x) {
+      x[3 * i] = (double)v.x;
+      x[3 * i + 1] = (double)v.y;
+      x[3 * i + 2] = (double)v.z;
+    }
+    if (sp) sp[i] = (int32_t)(wb & 0xFFu);
+    if (rep) rep[i] = (int32_t)(wb >> 8);
+  }
+}
+
+void launch_set_state(const StepLaunch& L, int64_t n, const double* x, const int32_t* sp, const uint32_t* id,
+                      const int32_t* rep, void* out, uint32_t* ido, uint32_t* cnt, uint32_t* maxid,
+                      const uint32_t* next_id_in, int32_t* err, int64_t step, cudaStream_t s) {
+  const int G = grid_for(n, 256, L.max_grid);
+  if (n > 0) {
+    if (L.precision == RD_MIXED)
+      k_set_state<float4><<<G, 256, 0, s>>>(L.P, L.reps, n, x, sp, id, rep, (float4*)out, ido, cnt, maxid, err);
+    else
+      k_set_state<d4><<<G, 256, 0, s>>>(L.P, L.reps, n, x, sp, id, rep, (d4*)out, ido, cnt, maxid, err);
+  }
+  k_set_state_finish<<<1, 256, 0, s>>>(L.P, L.reps, L.ctl, cnt, maxid, next_id_in, err, n, step);
+}
+
+void launch_get_state(const StepLaunch& L, const void* in, int64_t n, double* x, int32_t* sp, int32_t* rep,
+                      cudaStream_t s) {
+  if (n <= 0) return;
+  const int G = grid_for(n, 256, L.max_grid);
+  if (L.precision == RD_MIXED)
+    k_get_state<float4><<<G, 256, 0, s>>>((const float4*)in, n, x, sp, rep);
+  else
+    k_get_state<d4><<<G, 256, 0, s>>>((const d4*)in, n, x, sp, rep);
+}
+
 void launch_cell_scan(const StepLaunch& L, cudaStream_t s) {
   const int64_t tile = 256 * (int64_t)kScanItems;
   const int nbc = (int)((L.total_cells + tile - 1) / tile);

@@ -88,6 +88,12 @@ struct KernelTimer {
 // blocks of the cooperative matching launch that fit on the device at once (>= 1)
 int match_grid_size(int device_sms);
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer);
+// device-side state transfer (validation + packing into out / ido; unpacking)
+void launch_set_state(const StepLaunch& L, int64_t n, const double* x, const int32_t* sp, const uint32_t* id,
+                      const int32_t* rep, void* out, uint32_t* ido, uint32_t* cnt, uint32_t* maxid,
+                      const uint32_t* next_id_in, int32_t* err, int64_t step, cudaStream_t s);
+void launch_get_state(const StepLaunch& L, const void* in, int64_t n, double* x, int32_t* sp, int32_t* rep,
+                      cudaStream_t s);
 // the cell scan of a step on its own (bounded-wait check)
 void launch_cell_scan(const StepLaunch& L, cudaStream_t s);
 void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int32_t* sp_of, const uint32_t* id_of,
