@@ -110,6 +110,11 @@ typedef struct {
                                          stencil row when the autotuner finds it faster), 1 one
                                          thread per particle, 2 one thread per (particle, row) */
   int32_t pad_cfg;
+  double drift[RD_MAX_SPECIES][3];    /* deterministic drift velocity per species (um/s); each step first
+                                         moves every particle by drift * dt (periodic wrap), then the
+                                         Brownian / reaction step runs from there with the pair
+                                         probabilities taken from the Brownian end points.  All zero: no
+                                         drift step */
   rd_allocator allocator;
 } rd_config;
 

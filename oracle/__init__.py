@@ -51,7 +51,8 @@ class _System(C.Structure):
                 ("c_cut", C.c_double), ("tau_s", C.c_double), ("seed", C.c_uint64),
                 ("replica", C.c_uint32), ("pad_", C.c_uint32),
                 ("D", C.c_double * MAX_SPECIES), ("pairs", _Pair * MAX_PAIRS),
-                ("decays", _Decay * MAX_DECAYS)]
+                ("decays", _Decay * MAX_DECAYS), ("drift_dx", (C.c_double * 3) * MAX_SPECIES),
+                ("has_drift", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -255,6 +256,12 @@ def _system_struct(system, replica: int = 0, L: float | None = None) -> _System:
     for i, dc in enumerate(system.decays):
         prods = list(dc.products) + [-1, -1]
         s.decays[i] = _Decay(dc.parent, len(dc.products), prods[0], prods[1], dc.kd, dc.sigma_place)
+    drift = getattr(system, "drift", None)
+    if drift is not None:
+        s.has_drift = 1
+        for i, v in enumerate(drift):
+            for d in range(3):
+                s.drift_dx[i][d] = float(v[d]) * float(system.dt)    # displacement per step, v dt
     return s
 
 

@@ -45,6 +45,10 @@ typedef struct {
   double D[OR_MAX_SPECIES];
   or_pair pairs[OR_MAX_PAIRS];
   or_decay decays[OR_MAX_DECAYS];
+  /* deterministic drift displacement per step and species (v dt), applied as a split step before
+   * the Brownian step; has_drift = 0 skips it */
+  double drift_dx[OR_MAX_SPECIES][3];
+  int32_t has_drift, pad2_;
 } or_system;
 
 typedef struct {

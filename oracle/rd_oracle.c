@@ -727,6 +727,23 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
   products_t* prod = (products_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(products_t));
   for (int64_t i = 0; i < n; ++i) partner[i] = -1;
 
+  /* Deterministic forces as a split step (Section 3 keeps them outside the Green's-function part):
+   * every particle first moves by its species' drift displacement v dt (periodic wrap).  The
+   * reaction-diffusion step below starts from these positions, so p_enc and p_reac see only the
+   * Brownian end points. */
+  double* xs = NULL;
+  const double* xstart = in->x;
+  if (sys->has_drift) {
+    xs = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+      for (int d = 0; d < 3; ++d) {
+        double v = in->x[3 * i + d];
+        if (d < dim) v = wrap(v + sys->drift_dx[in->sp[i]][d], L);
+        xs[3 * i + d] = v;
+      }
+    xstart = xs;
+  }
+
   /* Step 4 of Section 3, drawn first (start-of-step state): Poisson decay with probability
    * 1 - exp(-k_d dt), Eq. (rad_prob); with several channels the total rate decides and a second
    * uniform picks the channel in proportion to its rate. */
@@ -759,7 +776,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
     if (!decayed[i]) normals(sys, step, in->id[i], OR_TAG_DISP0, dim, nrm);
     double ell = sqrt(2.0 * sys->D[in->sp[i]] * dt);
     for (int d = 0; d < 3; ++d) {
-      double v = in->x[3 * i + d];
+      double v = xstart[3 * i + d];
       if (d < dim && !decayed[i]) v = wrap(v + ell * nrm[d], L);
       x1[3 * i + d] = v;
     }
@@ -779,7 +796,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
       int64_t b = a == i ? j : i;
       double r0v[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
       for (int d = 0; d < dim; ++d) {
-        r0v[d] = min_image(in->x[3 * b + d] - in->x[3 * a + d], L);
+        r0v[d] = min_image(xstart[3 * b + d] - xstart[3 * a + d], L);
         rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
       }
       double r02 = norm2(r0v, dim);
@@ -844,7 +861,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
     double rv[3] = {0, 0, 0}, r0v[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) {
       rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
-      r0v[d] = min_image(in->x[3 * b + d] - in->x[3 * a + d], L);
+      r0v[d] = min_image(xstart[3 * b + d] - xstart[3 * a + d], L);
     }
     /* centre of diffusion, Eq. (Rcoo): R = (D_B r_A + D_A r_B)/D_eff = r_A + (D_A/D_eff) r */
     double c[3] = {0, 0, 0};
@@ -901,7 +918,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
     const or_decay* dc = &sys->decays[decayed[i] - 1];
     consumed[i] = 1;
     st.decays++;
-    const double* x0 = &in->x[3 * i];
+    const double* x0 = &xstart[3 * i];
     if (dc->n_products == 1) {
       double nrm[4] = {0, 0, 0, 0};
       normals(sys, step, in->id[i], OR_TAG_DISS0, dim, nrm);
@@ -1012,6 +1029,6 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
   }
   st.products = nprod;
   if (stats) *stats = st;
-  free(x1); free(decayed); free(consumed); free(partner); free(prod); free(fired);
+  free(x1); free(decayed); free(consumed); free(partner); free(prod); free(fired); free(xs);
   return status;
 }

@@ -75,6 +75,7 @@ class _Config(C.Structure):
                 ("capacity_factor", C.c_double), ("pair_capacity", C.c_int64),
                 ("cell_factor_x100", C.c_int32), ("block_size", C.c_int32),
                 ("sweep_split", C.c_int32), ("pad_cfg", C.c_int32),
+                ("drift", (C.c_double * 3) * MAX_SPECIES),
                 ("allocator", _Allocator)]
 
 
@@ -181,6 +182,11 @@ def make_config(system, precision: Optional[str] = None, capacity_factor: float 
         cfg.cell_factor_x100 = int(round(float(cell_factor) * 100))
     cfg.block_size = int(block_size)
     cfg.sweep_split = int(sweep_split)
+    drift = getattr(system, "drift", None)
+    if drift is not None:
+        for i, v in enumerate(drift):
+            for d in range(3):
+                cfg.drift[i][d] = float(v[d])
     return cfg, rep_arr
 
 

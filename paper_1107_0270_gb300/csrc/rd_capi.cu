@@ -114,8 +114,14 @@ static int validate(const rd_config* c) {
   if (!(c->dt > 0.0) || !(c->c_cut >= 0.0)) return RD_EINVAL;
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32 != 0)) return RD_EINVAL;
   if (c->sweep_split < 0 || c->sweep_split > 2) return RD_EINVAL;
-  for (int s = 0; s < c->n_species; ++s)
+  double L_min = 1e300;
+  for (int r = 0; r < c->n_replicas; ++r) L_min = std::min(L_min, c->replicas[r].L);
+  for (int s = 0; s < c->n_species; ++s) {
     if (!(c->D[s] >= 0.0)) return RD_EINVAL;
+    // the drift step wraps once: its displacement per step stays below half a box
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(c->drift[s][d]) || !(std::fabs(c->drift[s][d] * c->dt) < 0.5 * L_min)) return RD_EINVAL;
+  }
   for (int k = 0; k < c->n_pairs; ++k) {
     const rd_pair_rule& p = c->pairs[k];
     if (p.s1 < 0 || p.s1 >= c->n_species || p.s2 < 0 || p.s2 >= c->n_species) return RD_EINVAL;
@@ -197,6 +203,12 @@ static void derive_params(rd_handle* h) {
     P.pair_of[p.s2][p.s1] = (int8_t)k;
     P.binned_mask |= (1u << p.s1) | (1u << p.s2);
   }
+  for (int sp = 0; sp < c.n_species; ++sp)
+    for (int d = 0; d < 3; ++d) {
+      P.drift_dx[sp][d] = d < c.dim ? c.drift[sp][d] * c.dt : 0.0;
+      P.drift_dx_f[sp][d] = (float)P.drift_dx[sp][d];
+      if (P.drift_dx[sp][d] != 0.0) P.has_drift = 1;
+    }
   for (int k = 0; k < c.n_decays; ++k) {
     const rd_decay& d = c.decays[k];
     DecayDev& q = P.decays[k];
@@ -707,6 +719,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.decay_list = (uint32_t*)A(cap * 4);
   L.best_key = (unsigned long long*)A(cap * 8);
   L.best_pid = (unsigned long long*)A(cap * 8);
+  L.x0d = h->hp.has_drift ? A(cap * vs) : nullptr;
   L.repx = (RepX*)A((size_t)c.n_replicas * sizeof(RepX));
   L.rep_cons = (uint32_t*)A((size_t)c.n_replicas * 4);
   L.rep_prod = (uint32_t*)A((size_t)c.n_replicas * 4);
@@ -1306,6 +1319,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.decay_list = (uint32_t*)b.take(cap * 4);
   L.best_key = (unsigned long long*)b.take(cap * 8);
   L.best_pid = (unsigned long long*)b.take(cap * 8);
+  L.x0d = tmp.hp.has_drift ? b.take(cap * vs) : nullptr;
   L.repx = (RepX*)b.take(sizeof(RepX));
   L.rep_cons = (uint32_t*)b.take(4);
   L.rep_prod = (uint32_t*)b.take(4);

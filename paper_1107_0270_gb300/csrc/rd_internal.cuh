@@ -90,6 +90,9 @@ struct DevParams {
   DecayDev decays[kMaxDecays];
   double rcut2_max;            // largest squared cut-off over the pair rules
   float rcut2_max_f, pad2;
+  int32_t has_drift, pad3;
+  double drift_dx[kMaxSpecies][3];   // drift displacement per step (v dt) of the split step
+  float drift_dx_f[kMaxSpecies][3];
 };
 
 struct RepDev {

@@ -93,7 +93,8 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
                           uint32_t* __restrict__ status, int32_t* __restrict__ matched,
                           uint32_t* __restrict__ deg, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
                           uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list,
-                          unsigned long long* __restrict__ counts, int n_counts) {
+                          unsigned long long* __restrict__ counts, int n_counts,
+                          typename V4<T>::type* __restrict__ x0d) {
   pdl_enter();
   const DevParams& P = *Pp;
   if (blockIdx.x == 0) {
@@ -110,11 +111,25 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
   const uint32_t n = ctl->n, step = ctl->step;
   const int dim = P.dim;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const auto p = x0[i];
+    auto p = x0[i];
     const uint32_t wb = w_bits(p.w);
     const uint32_t sp = wb & 0xFFu, r = wb >> 8;
     const uint32_t pid = id[i];
     const RepDev& rep = reps[r];
+    if (x0d) {
+      // deterministic forces as a split step: the drift displacement first; the rest of the step
+      // starts from the drifted position (kept in x0d for the later kernels)
+      if constexpr (sizeof(T) == 8) {
+        p.x = wrap(p.x + P.drift_dx[sp][0], rep.L);
+        p.y = wrap(p.y + P.drift_dx[sp][1], rep.L);
+        if (dim == 3) p.z = wrap(p.z + P.drift_dx[sp][2], rep.L);
+      } else {
+        p.x = wrap_f(p.x + P.drift_dx_f[sp][0], rep.Lf);
+        p.y = wrap_f(p.y + P.drift_dx_f[sp][1], rep.Lf);
+        if (dim == 3) p.z = wrap_f(p.z + P.drift_dx_f[sp][2], rep.Lf);
+      }
+      x0d[i] = p;
+    }
     uint32_t st = 0;
     if (P.ktot[sp] > 0.0) {
       const uint4 w = draw(P, step, pid, kOneParticle, TAG_UNI, r);
@@ -1926,15 +1941,17 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
 
   mark("begin");
   const bool pdl = L.pdl;
+  // start-of-step positions of the step proper: drifted copies when there is a drift step
+  V* x0s = L.x0d ? (V*)L.x0d : x0;
   launch_k(pdl, k_prepare<T>, Gp, B, 0, s, L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg,
-           L.cell_of, L.slot, L.cell_count, L.decay_list, L.counts, L.n_counts);
+           L.cell_of, L.slot, L.cell_count, L.decay_list, L.counts, L.n_counts, L.x0d ? x0s : (V*)nullptr);
   mark("k_prepare");
   const int nbc = (int)((L.total_cells + tile - 1) / tile);
   launch_k(pdl, k_scan1<uint32_t, LoadCellCount>, nbc, 256, 0, s, LoadCellCount{L.cell_count}, L.total_cells,
            (const uint32_t*)nullptr, L.cell_start, L.cell_count, L.agg32, L.incl32, L.flags, L.ctl, 0);
   mark("k_scan_cells");
-  launch_k(pdl, k_scatter_cells<T>, Gp, B, 0, s, L.ctl, x0, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0, sx1,
-           L.sidx);
+  launch_k(pdl, k_scatter_cells<T>, Gp, B, 0, s, L.ctl, x0s, x1, L.id_cur, L.cell_of, L.slot, L.cell_start, sx0,
+           sx1, L.sidx);
   mark("k_scatter_cells");
   const uint32_t split = L.sweep_split > 1 ? (uint32_t)L.sweep_split : 1u;
   const int Gs = grid_for(L.cap_particles * (int64_t)split, 256, L.max_grid);
@@ -1950,7 +1967,7 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
            L.best_key, L.best_pid, (uint32_t)L.cap_pairs);
   mark("k_match_trivial");
   launch_coop(k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
-              L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0, x1, L.id_cur, L.status,
+              L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0s, x1, L.id_cur, L.status,
               prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx);
   mark("k_match_resolve");
   const int nbp = (int)((L.cap_particles + kCompactTile - 1) / kCompactTile);

@@ -72,6 +72,8 @@ class System:
     tau_s: float = 0.01
     precision: str = "fp64"
     replicas: Optional[List[Replica]] = None
+    # deterministic drift velocity per species (um/s, a 3-vector each), applied as a split step
+    drift: Optional[Sequence[Sequence[float]]] = None
 
     @property
     def n_species(self) -> int:
