@@ -505,10 +505,14 @@ double or_p_enc2(double R, double R0, double tau, double tau_s) {
 /* Eq. (psurv_radII) in 2D; the free parts cancel (Section 4.2), and in the small-time regime so
  * does the common prefactor of Eqs. (smallTEabs)/(smallTEabsII): p_reac = (B_ref - B_rad)/(B_ref + B_abs)
  * with B the brackets (g_abs^bc carries the opposite sign). */
+/* The radiation bracket's series coefficients grow like powers of h: the series is used only while
+ * h sqrt(tau) <= OR_SERIES_H_SQRT_TAU (truncation error ~1e-8 there); beyond, the exact Weber
+ * integral (strongly reactive pairs). */
+#define OR_SERIES_H_SQRT_TAU 0.3
 double or_p_reac2(double R, double R0, double tau, double h, double tau_s) {
   if (R < 1.0) R = 1.0;
   if (R0 < 1.0) R0 = 1.0;
-  if (tau <= tau_s) {
+  if (tau <= tau_s && h * sqrt(tau) <= OR_SERIES_H_SQRT_TAU) {
     double bref = series_bracket(OR_BC_REF, R, R0, tau, h, 12);
     double brad = series_bracket(OR_BC_RAD, R, R0, tau, h, 12);
     double babs = series_bracket(OR_BC_ABS, R, R0, tau, h, 12);

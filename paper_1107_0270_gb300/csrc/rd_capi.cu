@@ -328,6 +328,8 @@ static Series2D series_coeffs(double h) {
 }
 
 // Builds the 2D data of every 2D pair type into device memory from `alloc`, patching hp.
+constexpr double kSeriesHSqrtTau = 0.3;   // series limit of the radiation bracket in 2D
+
 template <class Alloc>
 static bool build_2d(const rd_config& c, DevParams& hp, Alloc alloc) {
   double gx[16], gw[16];
@@ -340,12 +342,15 @@ static bool build_2d(const rd_config& c, DevParams& hp, Alloc alloc) {
   for (int k = 0; k < c.n_pairs; ++k) {
     PairDev& q = hp.pairs[k];
     if (c.pairs[k].bc == RD_BC_NONE) continue;
+    // small-time series for tau <= tau_s; for the radiation bracket only while h sqrt(tau) <= 0.3
+    // (its coefficients grow like powers of h), else the exact Weber quadrature
     q.series2d = q.tau <= c.tau_s ? 1 : 0;
+    q.series2d_rad = q.series2d && q.h * std::sqrt(q.tau) <= kSeriesHSqrtTau ? 1 : 0;
     Series2D S = series_coeffs(q.h);
     void* ds = alloc(sizeof(Series2D));
     if (!ds || cudaMemcpy(ds, &S, sizeof S, cudaMemcpyHostToDevice) != cudaSuccess) return false;
     q.ser = (const Series2D*)ds;
-    if (!q.series2d) {
+    if (!q.series2d || (c.pairs[k].bc == RD_BC_RAD && !q.series2d_rad)) {
       const double Rmax = std::sqrt(q.rcut2) / q.sigma + 13.0 * q.s + 3.0;
       std::vector<WeberNode> nodes = weber_nodes(q.tau, q.h, Rmax);
       void* dn = alloc(nodes.size() * sizeof(WeberNode));

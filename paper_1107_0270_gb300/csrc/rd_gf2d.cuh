@@ -136,6 +136,7 @@ __device__ __forceinline__ double gfree2_d(double R, double R0, double tau) {
 
 struct Pair2D {
   bool series;           // tau <= tau_s
+  bool series_rad;       // p_reac from the series too (tau <= tau_s and h sqrt(tau) small)
   double tau, s, h;
   const WeberNode* nodes;
   int n_nodes;
@@ -162,7 +163,7 @@ __device__ __forceinline__ double p_reac2(const Pair2D& q, double R, double R0) 
   if (R < 1.0) R = 1.0;
   if (R0 < 1.0) R0 = 1.0;
   double p;
-  if (q.series) {
+  if (q.series_rad) {
     double ie[kSeriesTerms];
     ierfc_scaled_all((R + R0 - 2.0) / (2.0 * q.s), kSeriesTerms, ie);
     const double ba = series_bracket2(*q.ser, 0, R, R0, q.s, ie);

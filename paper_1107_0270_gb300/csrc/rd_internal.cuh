@@ -57,6 +57,7 @@ struct PairDev {
   float s_f, alpha_f, pad_f[2];
   // 2D: small-time series (series2d != 0) or Weber quadrature nodes
   int32_t series2d, n_nodes;
+  int32_t series2d_rad, pad_s;   // p_reac from the series as well (else the Weber quadrature)
   const WeberNode* nodes;
   const Series2D* ser;
   // mixed step: FP32 tables of p_reac (2D and 3D), F = p_enc e^{d d0/tau} and -ln(tail) (2D)

@@ -59,6 +59,7 @@ __device__ __forceinline__ int cell_coord_f(float x, float inv_edge, int n) {
 __device__ __forceinline__ Pair2D pair2d(const PairDev& pr) {
   Pair2D q;
   q.series = pr.series2d != 0;
+  q.series_rad = pr.series2d_rad != 0;
   q.tau = pr.tau;
   q.s = pr.s;
   q.h = pr.h;

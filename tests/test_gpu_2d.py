@@ -22,9 +22,11 @@ def pair_system(tau, sigma=0.005, D=0.2, ka=0.01):
                     pairs=[W.PairRule(0, 1, sigma, "rad", ka, 2)])
 
 
-@pytest.mark.parametrize("tau", [0.005, 0.08, 0.8])
-def test_pair_probs_2d_fp64(tau):
-    system = pair_system(tau)
+# ka = 37.7 um^2/s gives h = 30 at D = 0.2: with tau = 0.005 (h sqrt(tau) = 2.1) p_enc still comes
+# from the small-time series and p_reac from the Weber quadrature
+@pytest.mark.parametrize("tau,ka", [(0.005, 0.01), (0.08, 0.01), (0.8, 0.01), (0.005, 37.7)])
+def test_pair_probs_2d_fp64(tau, ka):
+    system = pair_system(tau, ka=ka)
     pr = system.pairs[0]
     r0, r = W.pair_samples(400, pr.sigma, 0.2, system.dt, dim=2, seed=int(tau * 1e4))
     sim = pkg.Simulation(system, precision="fp64")
@@ -35,7 +37,10 @@ def test_pair_probs_2d_fp64(tau):
     # far from contact both differences sink below the rounding of g_free (by e^{-(R-1)(R0-1)/tau})
     m = pe_o >= 1e-4
     assert m.sum() > 100
-    assert np.max(np.abs(prc.cpu().numpy()[m] - pr_o[m])) <= 1e-10
+    # both sides integrate the g's to ~1e-13 of g_free; the ratio divides by (g_ref - g_abs) ~
+    # p_enc g_free, so the bound is 1e-13 / p_enc (1e-9 at the mask edge, 1e-13 at contact)
+    err = np.abs(prc.cpu().numpy()[m] - pr_o[m])
+    assert np.all(err <= 1e-13 / pe_o[m] + 1e-12), err.max()
     sim.close()
 
 
@@ -56,9 +61,9 @@ def test_resample_2d_fp64(tau):
     sim.close()
 
 
-@pytest.mark.parametrize("tau", [0.005, 0.08, 0.8])
-def test_pair_probs_2d_mixed_tables_within_2e6(tau):
-    system = pair_system(tau)
+@pytest.mark.parametrize("tau,ka", [(0.005, 0.01), (0.08, 0.01), (0.8, 0.01), (0.005, 37.7)])
+def test_pair_probs_2d_mixed_tables_within_2e6(tau, ka):
+    system = pair_system(tau, ka=ka)
     pr = system.pairs[0]
     r0, r = W.pair_samples(400, pr.sigma, 0.2, system.dt, dim=2, seed=int(tau * 1e4) + 7)
     sim = pkg.Simulation(system, precision="mixed")

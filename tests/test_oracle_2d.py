@@ -190,3 +190,14 @@ def test_2d_step_conserves_and_keeps_order():
         assert c[0] + c[2] == 40 and c[1] + c[2] == 40
         assert np.all(np.diff(st.ids.astype(np.int64)) > 0)
         assert np.all(st.x[:, 2] == 0.0)
+
+
+@pytest.mark.parametrize("h,tau,R,R0", [(30.0, 0.005, 1.02, 1.01), (100.0, 0.002, 1.1, 1.05)])
+def test_p_reac2_of_strongly_reactive_pairs_matches_laplace_inversion(h, tau, R, R0):
+    # h sqrt(tau) ~ 2-4.5: the small-time series of the radiation bracket no longer converges, so
+    # p_reac switches to the exact Weber integral; against the Laplace-domain solution
+    gr = gbc_laplace("ref", R, R0, tau, h)
+    gd = gbc_laplace("rad", R, R0, tau, h)
+    ga = gbc_laplace("abs", R, R0, tau, h)
+    ref = (gr - gd) / (gr - ga)
+    assert abs(O.p_reac2(R, R0, tau, h) - ref) < 1e-8, (O.p_reac2(R, R0, tau, h), ref)
