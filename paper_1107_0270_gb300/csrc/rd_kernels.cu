@@ -84,8 +84,9 @@ __device__ __forceinline__ double resample_dim(const DevParams& P, const PairDev
 }
 
 // ================================================================================================
-// K0: unimolecular decay draws (start-of-step state), free displacement of the other particles,
-// and the first half of the counting sort by cell (start-of-step positions).
+// K0: drift step (deterministic forces, when configured), unimolecular decay draws (start-of-step
+// state), free displacement of the other particles, and the first half of the counting sort by
+// cell (start-of-step positions).
 // ================================================================================================
 template <class T>
 __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
@@ -732,10 +733,11 @@ __device__ __noinline__ void normals64_ni(const DevParams& P, uint32_t c0, uint3
   normals64(P, c0, id, tag0, r, dim, n);
 }
 
-// K5: accepted pairs (Section 3, steps 2(a)-(c)).  Absorbing: react.  Reflective / radiation:
-// new separation length from the radial propagator G_ref - G_abs (direction of the free step kept,
-// centre of diffusion unchanged); radiation reacts with p_reac (Eq. psurv_radII).  A product sits
-// at the centre of diffusion (Eq. Rcoo).  All in FP64.
+// Resolution of an accepted pair (device functions of K5; Section 3, steps 2(a)-(c)).  Absorbing:
+// react.  Reflective / radiation: new separation length from the radial propagator G_ref - G_abs
+// (direction of the free step kept, centre of diffusion unchanged); radiation reacts with p_reac
+// (Eq. psurv_radII).  A product sits at the centre of diffusion (Eq. Rcoo).  FP64 step first, the
+// mixed step's forms further down.
 // ================================================================================================
 template <class T>
 __device__ __forceinline__ void load3(const typename V4<T>::type& v, double o[3]) {
@@ -833,7 +835,7 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
 }
 
 // ================================================================================================
-// K6: unimolecular products (Section 2.2.5).  One product: parent position plus a free step with
+// Unimolecular products (device functions of K5; Section 2.2.5).  One product: parent position plus a free step with
 // the product's D.  Two products: centre of diffusion = parent position + free step with D_R;
 // separation a n (n uniform) propagated by G_ref - G_abs from contact, geminate recombination by
 // p_reac(R', 1); non-interacting products start sigma_place apart and separate freely.
