@@ -739,6 +739,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.fired = (FiredPair*)A(pair_cap * sizeof(FiredPair));
   L.fstate = (uint32_t*)A(pair_cap * 4);
   L.conflict = (uint32_t*)A(pair_cap * 4);
+  L.crec = (ConflictRec*)A(pair_cap * sizeof(ConflictRec));
   L.counts = (unsigned long long*)A((size_t)L.n_counts * 8);
   L.history_len = kHistoryLen;
   L.history = (long long*)A((size_t)kHistoryLen * c.n_species * 8);
@@ -1340,6 +1341,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.fired = (FiredPair*)b.take(pair_cap * sizeof(FiredPair));
   L.fstate = (uint32_t*)b.take(pair_cap * 4);
   L.conflict = (uint32_t*)b.take(pair_cap * 4);
+  L.crec = (ConflictRec*)b.take(pair_cap * sizeof(ConflictRec));
   L.counts = (unsigned long long*)b.take((size_t)L.n_counts * 8);
   L.P = (const DevParams*)b.take(sizeof(DevParams));
   L.ctl = (DevCtl*)b.take(sizeof(DevCtl));

@@ -135,6 +135,13 @@ struct RepX {
   uint32_t p_beg, s_end, surv, prod;
 };
 
+// A conflict pair as the matching rounds read it (one coalesced 32-B load per pair and phase):
+// its fired-list index, particle indices, round state (FS_*), key bits and (id_a << 32 | id_b).
+struct ConflictRec {
+  uint32_t e, ia, ib, st;
+  unsigned long long key, pid;
+};
+
 struct FiredPair {          // 32 B
   uint32_t ia, ib;          // particle indices of this step, id[ia] < id[ib]
   uint32_t ida, idb;        // their ids

@@ -642,7 +642,8 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
                                 int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
                                 uint32_t* __restrict__ accepted,
                                 unsigned long long* __restrict__ best_key,
-                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs) {
+                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs,
+                                ConflictRec* __restrict__ crec) {
   pdl_enter();
   if (ctl->status) return;
   const uint32_t nf = min(ctl->fired, cap_pairs);
@@ -666,7 +667,16 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
         uint32_t base = 0;
         if (lane == leader) base = atomicAdd(&ctl->n_conflict, (uint32_t)__popc(m));
         base = __shfl_sync(m, base, leader);
-        conflict[base + __popc(m & ((1u << lane) - 1u))] = e;
+        const uint32_t q = base + __popc(m & ((1u << lane) - 1u));
+        conflict[q] = e;
+        ConflictRec c;
+        c.e = e;
+        c.ia = f.ia;
+        c.ib = f.ib;
+        c.st = FS_LIVE;
+        c.key = (unsigned long long)__double_as_longlong(f.key);
+        c.pid = ((unsigned long long)f.ida << 32) | f.idb;
+        crec[q] = c;
         best_key[f.ia] = ~0ull;
         best_key[f.ib] = ~0ull;
         best_pid[f.ia] = ~0ull;
@@ -1323,7 +1333,8 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
     const uint32_t* __restrict__ decay_list, const typename V4<T>::type* __restrict__ x0,
     typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
     typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs,
-    uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx) {
+    uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx,
+    ConflictRec* __restrict__ crec) {
   pdl_enter();
   __shared__ unsigned long long acc_s;
   __shared__ uint32_t live_s;
@@ -1373,54 +1384,68 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
       ctl->live[0] = 0u;
       ctl->live[1] = 0u;
     }
+    // FP32 keys (mixed step) fit one 64-bit word with the partner's id: at a shared particle the
+    // order (key, partner id) is the order (key, id_a, id_b) of its pairs, so the minimum takes
+    // one atomic per endpoint; FP64 keys take the key and then the (id_a, id_b) minimum
+    const bool packed = P.precision == RD_MIXED;
     int rounds = 0;
     bool ok = sync();
     while (ok) {
       for (uint32_t q = tid; q < nc; q += nthr) {
-        const uint32_t e = conflict[q];
-        if ((fstate[e] & 3u) != FS_LIVE) continue;
-        const unsigned long long kb = (unsigned long long)__double_as_longlong(fired[e].key);
-        atomicMin(&best_key[fired[e].ia], kb);
-        atomicMin(&best_key[fired[e].ib], kb);
+        const ConflictRec c = crec[q];
+        if (c.st != FS_LIVE) continue;
+        if (packed) {
+          const unsigned long long kb = (unsigned long long)__float_as_uint((float)__longlong_as_double((long long)c.key)) << 32;
+          atomicMin(&best_key[c.ia], kb | (uint32_t)c.pid);
+          atomicMin(&best_key[c.ib], kb | (uint32_t)(c.pid >> 32));
+        } else {
+          atomicMin(&best_key[c.ia], c.key);
+          atomicMin(&best_key[c.ib], c.key);
+        }
       }
       if (!(ok = sync())) break;
-      for (uint32_t q = tid; q < nc; q += nthr) {
-        const uint32_t e = conflict[q];
-        if ((fstate[e] & 3u) != FS_LIVE) continue;
-        const FiredPair f = fired[e];
-        const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
-        const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
-        if (best_key[f.ia] == kb) atomicMin(&best_pid[f.ia], pid);
-        if (best_key[f.ib] == kb) atomicMin(&best_pid[f.ib], pid);
+      if (!packed) {
+        for (uint32_t q = tid; q < nc; q += nthr) {
+          const ConflictRec c = crec[q];
+          if (c.st != FS_LIVE) continue;
+          if (best_key[c.ia] == c.key) atomicMin(&best_pid[c.ia], c.pid);
+          if (best_key[c.ib] == c.key) atomicMin(&best_pid[c.ib], c.pid);
+        }
+        if (!(ok = sync())) break;
       }
-      if (!(ok = sync())) break;
       for (uint32_t q = tid; q < nc; q += nthr) {
-        const uint32_t e = conflict[q];
-        if ((fstate[e] & 3u) != FS_LIVE) continue;
-        const FiredPair f = fired[e];
-        const unsigned long long kb = (unsigned long long)__double_as_longlong(f.key);
-        const unsigned long long pid = ((unsigned long long)f.ida << 32) | f.idb;
-        if (best_key[f.ia] == kb && best_key[f.ib] == kb && best_pid[f.ia] == pid && best_pid[f.ib] == pid) {
-          matched[f.ia] = (int32_t)f.ib;
-          matched[f.ib] = (int32_t)f.ia;
-          fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
-          accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
+        const ConflictRec c = crec[q];
+        if (c.st != FS_LIVE) continue;
+        bool win;
+        if (packed) {
+          const unsigned long long kb = (unsigned long long)__float_as_uint((float)__longlong_as_double((long long)c.key)) << 32;
+          win = best_key[c.ia] == (kb | (uint32_t)c.pid) && best_key[c.ib] == (kb | (uint32_t)(c.pid >> 32));
+        } else {
+          win = best_key[c.ia] == c.key && best_key[c.ib] == c.key && best_pid[c.ia] == c.pid &&
+                best_pid[c.ib] == c.pid;
+        }
+        if (win) {
+          matched[c.ia] = (int32_t)c.ib;
+          matched[c.ib] = (int32_t)c.ia;
+          fstate[c.e] = (fstate[c.e] & ~3u) | FS_ACCEPTED;
+          crec[q].st = FS_ACCEPTED;
+          accepted[atomicAdd(&ctl->n_accept, 1u)] = c.e;
           atomicAdd(&acc_s, 1ull);
         }
       }
       if (threadIdx.x == 0) live_s = 0u;
       if (!(ok = sync())) break;
       for (uint32_t q = tid; q < nc; q += nthr) {
-        const uint32_t e = conflict[q];
-        if ((fstate[e] & 3u) != FS_LIVE) continue;
-        const FiredPair f = fired[e];
-        if (matched[f.ia] >= 0 || matched[f.ib] >= 0) {
-          fstate[e] = (fstate[e] & ~3u) | FS_DEAD;
+        const ConflictRec c = crec[q];
+        if (c.st != FS_LIVE) continue;
+        if (matched[c.ia] >= 0 || matched[c.ib] >= 0) {
+          crec[q].st = FS_DEAD;
+          fstate[c.e] = (fstate[c.e] & ~3u) | FS_DEAD;
         } else {
-          best_key[f.ia] = ~0ull;
-          best_key[f.ib] = ~0ull;
-          best_pid[f.ia] = ~0ull;
-          best_pid[f.ib] = ~0ull;
+          best_key[c.ia] = ~0ull;
+          best_key[c.ib] = ~0ull;
+          best_pid[c.ia] = ~0ull;
+          best_pid[c.ib] = ~0ull;
           atomicAdd(&live_s, 1u);
         }
       }
@@ -1967,11 +1992,11 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
   launch_k(pdl, k_match_trivial, Gf, 256, 0, s, L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted,
-           L.best_key, L.best_pid, (uint32_t)L.cap_pairs);
+           L.best_key, L.best_pid, (uint32_t)L.cap_pairs, L.crec);
   mark("k_match_trivial");
   launch_coop(k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
               L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0s, x1, L.id_cur, L.status,
-              prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx);
+              prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx, L.crec);
   mark("k_match_resolve");
   const int nbp = (int)((L.cap_particles + kCompactTile - 1) / kCompactTile);
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;

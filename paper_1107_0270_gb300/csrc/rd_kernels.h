@@ -20,6 +20,7 @@ struct StepLaunch {
   bool pdl;                    // programmatic dependent launch between the step kernels
   int match_grid;              // blocks of the cooperative matching launch (all resident)
   void* x0d;                   // drifted start positions (drift step only; nullptr without drift)
+  ConflictRec* crec;           // conflict pairs of the matching rounds (fired-pair capacity)
   RepX* repx;                  // per-replica placement of the compaction
   uint32_t* rep_cons;          // per-replica particles consumed this step
   uint32_t* rep_prod;          // per-replica products formed this step
