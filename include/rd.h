@@ -109,7 +109,9 @@ typedef struct {
   int32_t sweep_split;                /* cell sweep: 0 automatic (one thread per particle, or one per
                                          stencil row when the autotuner finds it faster), 1 one
                                          thread per particle, 2 one thread per (particle, row) */
-  int32_t pad_cfg;
+  int32_t cell_reach;                 /* cell sweep stencil: 0 automatic (2 for dense 2D systems, else 1),
+                                         1 cells of at least one cut-off, 2 (2D only) cells of at least
+                                         half a cut-off with a stencil two cells wide */
   double drift[RD_MAX_SPECIES][3];    /* deterministic drift velocity per species (um/s); each step first
                                          moves every particle by drift * dt (periodic wrap), then the
                                          Brownian / reaction step runs from there with the pair
@@ -212,8 +214,9 @@ int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out
  * in units of the largest cut-off; < 0: per-replica density rule times -out[0]), out[1] total cells,
  * out[2] threads per block of the particle kernels, out[3] particle capacity, out[4] fired-pair
  * capacity, out[5] autotuned ms per step (0 if not tuned), out[6] largest cut-off radius, out[7]
- * threads per binned particle in the cell sweep (1, or one per stencil row).  Writes min(n, 8)
- * values to the caller-owned HOST array. */
+ * threads per binned particle in the cell sweep (1, or one per stencil row), out[8] stencil reach
+ * in cells (1, or 2 for 2D cells of half a cut-off).  Writes min(n, 9) values to the caller-owned
+ * HOST array. */
 int rd_info(rd_handle* h, double* out, int32_t n);
 
 /* Name of the kernel-level timing hook: rd_time_kernels enables CUDA-event timing of every kernel

@@ -74,7 +74,7 @@ class _Config(C.Structure):
                 ("decays", _Decay * MAX_DECAYS), ("replicas", C.POINTER(_Replica)),
                 ("capacity_factor", C.c_double), ("pair_capacity", C.c_int64),
                 ("cell_factor_x100", C.c_int32), ("block_size", C.c_int32),
-                ("sweep_split", C.c_int32), ("pad_cfg", C.c_int32),
+                ("sweep_split", C.c_int32), ("cell_reach", C.c_int32),
                 ("drift", (C.c_double * 3) * MAX_SPECIES),
                 ("allocator", _Allocator)]
 
@@ -141,11 +141,13 @@ def _ptr(a, ctype):
 
 
 def make_config(system, precision: Optional[str] = None, capacity_factor: float = 2.0,
-                pair_capacity: int = 0, cell_factor=None, block_size: int = 256, sweep_split: int = 0):
+                pair_capacity: int = 0, cell_factor=None, block_size: int = 256, sweep_split: int = 0,
+                cell_reach: int = 0):
     """Build the C configuration from a system description (see ``workloads.System``).
     cell_factor: cell edge in units of the largest cut-off; None = density-based per replica
     (about 0.25 interacting particles per cell), "tune" = timed autotuning at creation.
-    sweep_split: 0 automatic, 1 one sweep thread per particle, 2 one per (particle, stencil row)."""
+    sweep_split: 0 automatic, 1 one sweep thread per particle, 2 one per (particle, stencil row).
+    cell_reach: 0 automatic, 1 cells of a cut-off, 2 (2D) cells of half a cut-off, two-cell stencil."""
     cfg = _Config()
     cfg.dim = int(system.dim)
     cfg.precision = PRECISION[precision or system.precision]
@@ -182,6 +184,7 @@ def make_config(system, precision: Optional[str] = None, capacity_factor: float 
         cfg.cell_factor_x100 = int(round(float(cell_factor) * 100))
     cfg.block_size = int(block_size)
     cfg.sweep_split = int(sweep_split)
+    cfg.cell_reach = int(cell_reach)
     drift = getattr(system, "drift", None)
     if drift is not None:
         for i, v in enumerate(drift):
@@ -195,7 +198,7 @@ class Simulation:
 
     def __init__(self, system, precision: Optional[str] = None, device: int = 0, stream=None,
                  capacity_factor: float = 2.0, pair_capacity: int = 0, cell_factor=None,
-                 block_size: int = 256, sweep_split: int = 0):
+                 block_size: int = 256, sweep_split: int = 0, cell_reach: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -208,7 +211,7 @@ class Simulation:
         self.n_replicas = len(system.replica_list())
         self.precision = precision or system.precision
         cfg, self._rep_arr = make_config(system, self.precision, capacity_factor, pair_capacity,
-                                         cell_factor, block_size, sweep_split)
+                                         cell_factor, block_size, sweep_split, cell_reach)
         dev = self.device.index
 
         def _alloc(nbytes, stream_ptr, ctx):
@@ -267,12 +270,12 @@ class Simulation:
         return out[:n_steps]
 
     def info(self):
-        v = np.zeros(8)
-        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 8), "rd_info")
+        v = np.zeros(9)
+        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 9), "rd_info")
         return {"cell_factor": abs(v[0]), "cell_rule": "density" if v[0] < 0 else "fixed",
                 "cells": int(v[1]), "block": int(v[2]),
                 "capacity": int(v[3]), "pair_capacity": int(v[4]), "tuned_ms_per_step": v[5],
-                "r_cut_max": v[6], "sweep_split": int(v[7])}
+                "r_cut_max": v[6], "sweep_split": int(v[7]), "reach": int(v[8])}
 
     def num_particles(self) -> int:
         n = C.c_int64()

@@ -52,6 +52,7 @@ struct rd_handle {
   std::vector<double> factors;       // cell-edge factors (one, or the autotuner's candidates)
   double tuned_ms = 0.0;
   double factor = 1.0;               // cell-edge factor in use
+  int reach = 1;                     // stencil reach of the cell sweep (2: 2D cells of half a cut-off)
   // staging of rd_set_state / rd_get_state (allocated on first use, capacity-sized)
   double* st_x = nullptr;
   int32_t* st_sp = nullptr;
@@ -114,6 +115,7 @@ static int validate(const rd_config* c) {
   if (!(c->dt > 0.0) || !(c->c_cut >= 0.0)) return RD_EINVAL;
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32 != 0)) return RD_EINVAL;
   if (c->sweep_split < 0 || c->sweep_split > 2) return RD_EINVAL;
+  if (c->cell_reach < 0 || c->cell_reach > 2 || (c->cell_reach == 2 && c->dim != 2)) return RD_EINVAL;
   double L_min = 1e300;
   for (int r = 0; r < c->n_replicas; ++r) L_min = std::min(L_min, c->replicas[r].L);
   for (int s = 0; s < c->n_species; ++s) {
@@ -437,13 +439,13 @@ static double density_edge_factor(double nb, double volume, int dim, double rc) 
   return std::min(4.0, std::max(1.0, f));
 }
 
-// Cell grid of every replica.  factor > 0: cell edge = factor x the largest cut-off in every
+// Cell grid of every replica.  factor > 0: cell edge = factor x the largest cut-off / reach in every
 // replica; factor < 0: each replica's own density-based edge factor times -factor (never below one
 // cut-off), so that replicas of very different concentrations each get a suitable grid.  A grid is
 // coarsened until it has at most 4 cells per interacting particle (+64).  Fills the grid fields of
 // out[r].
 static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& reps, uint32_t binned_mask,
-                            double rc, double factor, std::vector<RepDev>& out) {
+                            double rc, double factor, int reach, std::vector<RepDev>& out) {
   int64_t total = 0;
   for (size_t r = 0; r < reps.size(); ++r) {
     const rd_replica& rp = reps[r];
@@ -460,8 +462,9 @@ static int64_t layout_cells(const rd_config& c, const std::vector<rd_replica>& r
       for (int a = 0; a < 3; ++a) {
         int n = 1;
         if (a < c.dim && rc > 0.0) {
-          const double m = std::floor(rp.L / (rc * f * (1.0 + 1e-6)));
-          n = m >= 3.0 ? (int)std::min(m, 4096.0) : 1;
+          // cell edge >= r_cut / reach; the stencil needs 2 reach + 1 distinct cells per axis
+          const double m = std::floor(rp.L * reach / (rc * f * (1.0 + 1e-6)));
+          n = m >= 2.0 * reach + 1.0 ? (int)std::min(m, 4096.0) : 1;
         }
         d.nc[a] = n;
         d.inv_edge[a] = n / rp.L;
@@ -483,7 +486,7 @@ static cudaError_t apply_factor(rd_handle* h, double factor) {
   std::vector<RepDev> reps(c.n_replicas);
   cudaError_t e = cudaMemcpy(reps.data(), h->L.reps, reps.size() * sizeof(RepDev), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return e;
-  h->L.total_cells = layout_cells(c, h->reps_host, h->hp.binned_mask, max_cutoff(c), factor, reps);
+  h->L.total_cells = layout_cells(c, h->reps_host, h->hp.binned_mask, max_cutoff(c), factor, h->reach, reps);
   return cudaMemcpy(h->L.reps, reps.data(), reps.size() * sizeof(RepDev), cudaMemcpyHostToDevice);
 }
 
@@ -571,7 +574,7 @@ static cudaError_t autotune(rd_handle* h) {
   }
   h->L.block = best_block;
   // one thread per (particle, stencil row) in the sweep, for small systems
-  const int rows = h->cfg.dim == 3 ? 5 : 2;
+  const int rows = h->cfg.dim == 3 ? 5 : (h->reach == 2 ? 3 : 2);
   if (h->cfg.sweep_split == 0 && (double)h->L.cap_particles * rows < 4.0e9) {
     h->L.sweep_split = rows;
     const float ms = std::min(trial(), trial());
@@ -635,6 +638,19 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   // factor is explicit (cell_factor_x100 > 0), density-based (0) or autotuned (< 0)
   const double rc = max_cutoff(c);
   const uint32_t bmask = h->hp.binned_mask;
+  // stencil reach: 2 (cells of half a cut-off) for dense 2D systems (>= 1.5 binned particles per
+  // cut-off square), where it examines about a third fewer neighbours; else 1
+  if (c.cell_reach > 0) {
+    h->reach = c.cell_reach;
+  } else if (c.dim == 2 && rc > 0.0) {
+    double nb = 0.0, area = 0.0;
+    for (const rd_replica& rp : h->reps_host) {
+      for (int sp = 0; sp < c.n_species; ++sp)
+        if ((bmask >> sp) & 1u) nb += (double)rp.n_init[sp];
+      area += rp.L * rp.L;
+    }
+    h->reach = nb / area * rc * rc >= 1.5 ? 2 : 1;
+  }
   // cell-edge choices: > 0 a fixed factor, < 0 the per-replica density rule times -value
   std::vector<double> factors;
   if (c.cell_factor_x100 > 0) {
@@ -664,9 +680,9 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   int64_t max_cells = 0;
   {
     std::vector<RepDev> tmp = h->reps_init;
-    for (double f : factors) max_cells = std::max(max_cells, layout_cells(c, h->reps_host, bmask, rc, f, tmp));
+    for (double f : factors) max_cells = std::max(max_cells, layout_cells(c, h->reps_host, bmask, rc, f, h->reach, tmp));
   }
-  total_cells = layout_cells(c, h->reps_host, bmask, rc, factors[0], h->reps_init);
+  total_cells = layout_cells(c, h->reps_host, bmask, rc, factors[0], h->reach, h->reps_init);
   h->factors = factors;
   h->factor = factors[0];
   if (max_cells >= (int64_t)0xFFFFFFF0) {
@@ -686,7 +702,9 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   StepLaunch& L = h->L;
   std::memset(&L, 0, sizeof L);
   L.pdl = true;
-  L.sweep_split = c.sweep_split == 2 && (double)cap * (c.dim == 3 ? 5 : 2) < 4.0e9 ? (c.dim == 3 ? 5 : 2) : 1;
+  L.reach = h->reach;
+  const int rows = c.dim == 3 ? 5 : (h->reach == 2 ? 3 : 2);
+  L.sweep_split = c.sweep_split == 2 && (double)cap * rows < 4.0e9 ? rows : 1;
   L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
@@ -1002,9 +1020,9 @@ int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* specie
   RD_CUDA(cudaStreamSynchronize(s));
   if (err) return RD_EINVAL;
   h->cur = spare;
+  // the counts of the new state follow in stream order (the next call that reads them synchronises)
   launch_count(launch_for(h, h->cur), s);
   RD_CUDA(cudaGetLastError());
-  RD_CUDA(cudaStreamSynchronize(s));
   return RD_OK;
 }
 
@@ -1080,10 +1098,10 @@ int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out
 
 int rd_info(rd_handle* h, double* out, int32_t n) {
   if (!h || !out || n < 0) return RD_EINVAL;
-  const double v[8] = {h->factor, (double)h->L.total_cells, (double)h->L.block,
+  const double v[9] = {h->factor, (double)h->L.total_cells, (double)h->L.block,
                        (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
-                       max_cutoff(h->cfg), (double)h->L.sweep_split};
-  for (int k = 0; k < n && k < 8; ++k) out[k] = v[k];
+                       max_cutoff(h->cfg), (double)h->L.sweep_split, (double)h->reach};
+  for (int k = 0; k < n && k < 9; ++k) out[k] = v[k];
   return RD_OK;
 }
 

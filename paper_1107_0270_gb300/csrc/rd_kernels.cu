@@ -427,7 +427,7 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
 // ================================================================================================
 constexpr int kSweepRanges = 10;
 
-template <class T, bool kSplit>
+template <class T, bool kSplit, int kReach>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
                                                   const RepDev* __restrict__ reps,
                                                   const typename V4<T>::type* __restrict__ sx0,
@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
     if (t < work) {
       const uint32_t k = kSplit ? t / split : t;
       const int row_lo = kSplit ? (int)(t - k * split) : 0;
-      const int row_hi = kSplit ? row_lo + 1 : kSweepRanges / 2;
+      // rows of the half stencil: reach 1 (cell edge >= r_cut): 5 in 3D, 2 in 2D; reach 2 (2D only,
+      // cell edge >= r_cut / 2): rows y, y+1, y+2, each x-2 .. x+2 (own row x .. x+2)
+      constexpr int kRows = kReach == 2 ? 3 : kSweepRanges / 2;
+      const int row_hi = kSplit ? row_lo + 1 : kRows;
       const auto a0 = sx0[k];
       const auto a1 = sx1[k];
       const uint32_t wa = w_bits(a0.w);
@@ -474,28 +477,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
         if (dim == 3) cz = cell_coord_f(a0.z, rep.inv_edge_f[2], rep.nc[2]);
       }
       const int nc0 = rep.nc[0];
-      // the grid has 1 or >= 3 cells along each axis; with 1 only the own cell counts
-      const bool ox = nc0 >= 3, oy = rep.nc[1] >= 3, oz = dim == 3 && rep.nc[2] >= 3;
+      // the grid has 1 or >= 2 kReach + 1 cells along each axis; with 1 only the own cell counts
+      constexpr int kMinCells = 2 * kReach + 1;
+      const bool ox = nc0 >= kMinCells, oy = rep.nc[1] >= kMinCells, oz = dim == 3 && rep.nc[2] >= kMinCells;
       // all row ranges first (independent loads in flight together), the non-empty ones kept in
       // order, then one flattened walk over them
       int nr = 0;
 #pragma unroll
-      for (int row = 0; row < kSweepRanges / 2; ++row) {
-        const int dy = row == 0 ? 0 : (row == 1 ? 1 : row - 3);
-        const int dz = row < 2 ? 0 : 1;
+      for (int row = 0; row < kRows; ++row) {
+        const int dy = kReach == 2 ? row : (row == 0 ? 0 : (row == 1 ? 1 : row - 3));
+        const int dz = (kReach == 2 || row < 2) ? 0 : 1;
         if (row >= row_lo && row < row_hi && (dy == 0 || oy) && (dz == 0 || oz)) {
           int yy = cy + dy, zz = cz + dz;
           yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
           zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
           const int64_t rowc = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * nc0;
-          const int xl = (row == 0 || !ox) ? cx : max(cx - 1, 0);
-          const int xh = ox ? min(cx + 1, nc0 - 1) : cx;
+          const int xl = (row == 0 || !ox) ? cx : max(cx - kReach, 0);
+          const int xh = ox ? min(cx + kReach, nc0 - 1) : cx;
           const uint2 main_rg = make_uint2(row == 0 ? k + 1 : cell_start[rowc + xl], cell_start[rowc + xh + 1]);
           uint2 wrap_rg = make_uint2(0u, 0u);
-          if (ox && row != 0 && cx == 0)
-            wrap_rg = make_uint2(cell_start[rowc + nc0 - 1], cell_start[rowc + nc0]);
-          else if (ox && cx == nc0 - 1)
-            wrap_rg = make_uint2(cell_start[rowc], cell_start[rowc + 1]);
+          if (ox && row != 0 && cx - kReach < 0)          // cells nc0 + cx - kReach .. nc0 - 1
+            wrap_rg = make_uint2(cell_start[rowc + nc0 + cx - kReach], cell_start[rowc + nc0]);
+          else if (ox && cx + kReach >= nc0)               // cells 0 .. cx + kReach - nc0
+            wrap_rg = make_uint2(cell_start[rowc], cell_start[rowc + cx + kReach - nc0 + 1]);
           if (main_rg.y > main_rg.x) ranges[nr++][threadIdx.x] = main_rg;
           if (wrap_rg.y > wrap_rg.x) ranges[nr++][threadIdx.x] = wrap_rg;
         }
@@ -1983,12 +1987,14 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_scatter_cells");
   const uint32_t split = L.sweep_split > 1 ? (uint32_t)L.sweep_split : 1u;
   const int Gs = grid_for(L.cap_particles * (int64_t)split, 256, L.max_grid);
-  if (split > 1)
-    launch_k(pdl, k_sweep<T, true>, Gs, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start,
-             L.total_cells, L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs, split);
+  auto sweep = [&](auto kernel) {
+    launch_k(pdl, kernel, Gs, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired,
+             L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs, split);
+  };
+  if (L.reach == 2)
+    split > 1 ? sweep(k_sweep<T, true, 2>) : sweep(k_sweep<T, false, 2>);
   else
-    launch_k(pdl, k_sweep<T, false>, Gs, 256, 0, s, L.P, L.ctl, L.reps, sx0, sx1, L.sidx, L.cell_start,
-             L.total_cells, L.fired, L.fstate, L.deg, L.matched, (uint32_t)L.cap_pairs, split);
+    split > 1 ? sweep(k_sweep<T, true, 1>) : sweep(k_sweep<T, false, 1>);
   mark("k_sweep");
   const int Gf = grid_for(L.cap_pairs, 256, L.max_grid);
   launch_k(pdl, k_match_trivial, Gf, 256, 0, s, L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted,

@@ -25,6 +25,7 @@ struct StepLaunch {
   uint32_t* rep_cons;          // per-replica particles consumed this step
   uint32_t* rep_prod;          // per-replica products formed this step
   int sweep_split;             // threads per binned particle in the sweep: 1 or the stencil rows
+  int reach;                   // stencil reach in cells: 1 (cell edge >= r_cut) or 2 (2D, >= r_cut / 2)
   int64_t cap_particles, cap_pairs, total_cells;
   int n_counts;
   const DevParams* P;

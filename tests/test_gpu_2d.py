@@ -86,10 +86,11 @@ def membrane(dt, n_each=60, L=0.3):
     return W.membrane_2d(n_each=n_each, L=L, dt=dt)
 
 
-@pytest.mark.parametrize("dt,split", [(1e-4, 1), (1e-6, 1), (1e-4, 2)])
-def test_stepwise_parity_2d(dt, split):
+@pytest.mark.parametrize("dt,split,reach", [(1e-4, 1, 1), (1e-6, 1, 1), (1e-4, 2, 1), (1e-4, 1, 2), (1e-4, 2, 2)])
+def test_stepwise_parity_2d(dt, split, reach):
     system = membrane(dt)
-    sim = pkg.Simulation(system, precision="fp64", sweep_split=split)
+    sim = pkg.Simulation(system, precision="fp64", sweep_split=split, cell_reach=reach)
+    assert sim.info()["reach"] == reach
     totals = {"fired": 0, "resampled": 0}
     for k in range(4):
         g0 = sim.get_state()
