@@ -416,8 +416,8 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     if not args.no_workloads:
         out["workloads"] = other_workloads(torch, pkg, flush)
     # end to end through the C ABI with host buffers: per step, upload the state from page-locked
-    # host memory (rd_set_state), one step, read the state and the observables back into host
-    # memory (rd_get_state, rd_observables)
+    # host memory (rd_set_state), one step, read the resulting state (positions, species, ids,
+    # replicas, next ids) back into page-locked host memory (rd_get_state)
     sim = pkg.Simulation(workload(args, seed=3), precision=args.precision)
     sim.run(4)
     cap = 2 * sim.num_particles() + 1024
@@ -433,9 +433,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     def e2e_step(st, k):
         sim.set_state(st["x"], st["species"], st["ids"], st["replica"], st["next_id"], st["step"])
         sim.step()
-        nst = sim.get_state(out=bufs[(k + 1) % 2])
-        sim.observables()
-        return nst
+        return sim.get_state(out=bufs[(k + 1) % 2])
 
     for k in range(3):
         st = e2e_step(st, k)
@@ -449,13 +447,13 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
             st = e2e_step(st, k)
             ps += n
             h2d += n * (24 + 4 + 4 + 4)
-            d2h += st["ids"].shape[0] * (24 + 4 + 4 + 4) + 8 * 3
+            d2h += st["ids"].shape[0] * (24 + 4 + 4 + 4) + 4
             n_e2e += 1
         rates.append(ps / (time.perf_counter() - t0))
     out["e2e"] = {"value": statistics.median(rates), "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // n_e2e,
                   "d2h_bytes_per_step": d2h // n_e2e,
                   "path": "rd_set_state (page-locked host arrays) + rd_step + rd_get_state (page-locked "
-                          "host arrays) + rd_observables, per step"}
+                          "host arrays), per step"}
     sim.close()
     return out
 

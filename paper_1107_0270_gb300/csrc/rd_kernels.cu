@@ -2031,39 +2031,52 @@ __global__ void k_set_state(const DevParams* __restrict__ Pp, const RepDev* __re
                             uint32_t* __restrict__ ido, uint32_t* __restrict__ cnt, uint32_t* __restrict__ maxid,
                             int32_t* __restrict__ err) {
   const DevParams& P = *Pp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = rep ? rep[i] : 0;
-    const int s = sp[i];
-    bool ok = r >= 0 && r < P.n_replicas && s >= 0 && s < P.n_species;
-    if (ok && i > 0) {
-      const int rp = rep ? rep[i - 1] : 0;
-      ok = r > rp || (r == rp && id[i] > id[i - 1]);
+  // every lane runs the same number of iterations so that the per-replica tallies can be reduced
+  // across the warp (one atomic per replica present in the warp, not one per particle)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_iter = (n + stride - 1) / stride;
+  for (int64_t it = 0; it < n_iter; ++it) {
+    const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool ok = i < n;
+    int r = 0;
+    if (ok) {
+      r = rep ? rep[i] : 0;
+      const int s = sp[i];
+      ok = r >= 0 && r < P.n_replicas && s >= 0 && s < P.n_species;
+      if (ok && i > 0) {
+        const int rp = rep ? rep[i - 1] : 0;
+        ok = r > rp || (r == rp && id[i] > id[i - 1]);
+      }
+      if (ok) {
+        const RepDev& rd = reps[r];
+        const double px = x[3 * i], py = x[3 * i + 1], pz = P.dim == 3 ? x[3 * i + 2] : 0.0;
+        ok = px >= 0.0 && px < rd.L && py >= 0.0 && py < rd.L && (P.dim == 2 || (pz >= 0.0 && pz < rd.L));
+        if (ok) {
+          const uint32_t wb = ((uint32_t)r << 8) | (uint32_t)s;
+          V v;
+          if constexpr (sizeof(V) == 32) {
+            v.x = px; v.y = py; v.z = pz;
+            v.w = w_from_bits_d(wb);
+          } else {
+            float f[3] = {(float)px, (float)py, (float)pz};
+            for (int d = 0; d < 3; ++d)
+              if (!(f[d] < rd.Lf)) f[d] = 0.0f;
+            v = make_float4(f[0], f[1], f[2], w_from_bits_f(wb));
+          }
+          out[i] = v;
+          ido[i] = id[i];
+        }
+      }
+      if (!ok) atomicOr(err, 1);
     }
-    if (!ok) {
-      atomicOr(err, 1);
-      continue;
+    // lanes with a valid particle of the same replica add once
+    const uint32_t key = ok ? (uint32_t)r : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const uint32_t mx = __reduce_max_sync(peers, ok ? id[i] + 1u : 0u);
+    if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+      atomicAdd(&cnt[r], (uint32_t)__popc(peers));
+      atomicMax(&maxid[r], mx);
     }
-    const RepDev& rd = reps[r];
-    const double px = x[3 * i], py = x[3 * i + 1], pz = P.dim == 3 ? x[3 * i + 2] : 0.0;
-    if (!(px >= 0.0 && px < rd.L && py >= 0.0 && py < rd.L && (P.dim == 2 || (pz >= 0.0 && pz < rd.L)))) {
-      atomicOr(err, 1);
-      continue;
-    }
-    const uint32_t wb = ((uint32_t)r << 8) | (uint32_t)s;
-    V v;
-    if constexpr (sizeof(V) == 32) {
-      v.x = px; v.y = py; v.z = pz;
-      v.w = w_from_bits_d(wb);
-    } else {
-      float f[3] = {(float)px, (float)py, (float)pz};
-      for (int d = 0; d < 3; ++d)
-        if (!(f[d] < rd.Lf)) f[d] = 0.0f;
-      v = make_float4(f[0], f[1], f[2], w_from_bits_f(wb));
-    }
-    out[i] = v;
-    ido[i] = id[i];
-    atomicAdd(&cnt[r], 1u);
-    atomicMax(&maxid[r], id[i] + 1u);
   }
 }
 
