@@ -1930,19 +1930,22 @@ static void launch_k(bool pdl, void (*kernel)(KArgs...), int grid, int block, si
 }
 
 // Cooperative launch (all blocks resident at once, as the grid barrier requires; a grid larger
-// than the device can hold is refused by the runtime).
+// than the device can hold is refused by the runtime), optionally with programmatic dependent
+// launch: the kernel's blocks wait for the previous kernel before their first grid barrier.
 template <typename... KArgs, typename... Args>
-static void launch_coop(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
+static void launch_coop(bool pdl, void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)block);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -2000,7 +2003,7 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   launch_k(pdl, k_match_trivial, Gf, 256, 0, s, L.ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted,
            L.best_key, L.best_pid, (uint32_t)L.cap_pairs, L.crec);
   mark("k_match_trivial");
-  launch_coop(k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
+  launch_coop(pdl, k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
               L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0s, x1, L.id_cur, L.status,
               prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx, L.crec);
   mark("k_match_resolve");
