@@ -71,6 +71,23 @@ def test_invalid_configurations_are_rejected(lib, mutate):
     assert rc == 1 and not h.value          # RD_EINVAL, no handle
 
 
+@pytest.mark.parametrize("kw,mutate", [
+    ({"block_size": 300}, None),                                                 # above 256
+    ({"block_size": 100}, None),                                                 # not a multiple of 32
+    ({"sweep_split": 3}, None),
+    ({"cell_reach": 2}, None),                                                   # reach 2 is 2D only
+    ({"cell_reach": 3}, None),
+    ({}, lambda s: setattr(s, "drift", [(1e6, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0)])),  # > L/2 per step
+    ({}, lambda s: setattr(s, "drift", [(float("nan"), 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0)])),
+])
+def test_invalid_launch_options_are_rejected(lib, kw, mutate):
+    s = W.irreversible_3d()
+    if mutate:
+        mutate(s)
+    rc, h = _init_rc(lib, s, **kw)
+    assert rc == 1 and not h.value
+
+
 def test_strerror(lib):
     lib.rd_strerror.restype = C.c_char_p
     assert lib.rd_strerror(0) == b"ok"
