@@ -412,7 +412,38 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
         t = statistics.median(times)
         res[prec] = {"evals_per_s": r0.numel() / t, "gbs": r0.numel() * 24 / t / 1e9, "pairs": r0.numel()}
         sim.close()
+    # error of the mixed probabilities at scale: the 2^20 distinct pairs of the batch, mixed against
+    # the FP64 GPU values (which match the oracle to 1e-12)
+    ru0, ru = torch.tensor(r0n, device="cuda"), torch.tensor(rn, device="cuda")
+    vals = {}
+    for prec in ("mixed", "fp64"):
+        sim = pkg.Simulation(workload(args, seed=2), precision=prec)
+        pe, pre = sim.pair_probs(ru0, ru)
+        sim.sync()
+        vals[prec] = (pe.cpu().numpy(), pre.cpu().numpy())
+        sim.close()
+    d_enc = np.abs(vals["mixed"][0] - vals["fp64"][0])
+    d_reac = np.abs(vals["mixed"][1] - vals["fp64"][1])
+    res["mixed_max_abs_error"] = {"p_enc": float(d_enc.max()), "p_reac": float(d_reac.max()),
+                                  "pairs": int(d_enc.size), "target": 2e-6}
     out["pair_prob_evals_per_s"] = res
+    # the other time steps of the same configuration, mixed and FP64 (device-timed graph launches)
+    sweep = {}
+    for dt in (1e-6, 1e-4):
+        for prec in ("mixed", "fp64"):
+            system = W.reversible_3d(dt=dt, seed=1, n_each=args.n_each, L=box_edge(args), equilibrium_start=True)
+            sim = pkg.Simulation(system, precision=prec)
+            sim.run(4)
+            sim.sync()
+            o0 = sim.observables()
+            el, nst = timed_graph_run(sim, torch, flush, 200)
+            o1 = sim.observables()
+            sweep[f"dt={dt:g}:{prec}"] = {
+                "value": (o1["stats"]["particle_steps"] - o0["stats"]["particle_steps"]) / el,
+                "unit": "particle-steps/s", "ms_per_step": 1e3 * el / nst,
+                "candidates_per_step": (o1["stats"]["candidates"] - o0["stats"]["candidates"]) / nst}
+            sim.close()
+    out["dt_sweep"] = sweep
     if not args.no_workloads:
         out["workloads"] = other_workloads(torch, pkg, flush)
     # end to end through the C ABI with host buffers: per step, upload the state from page-locked
