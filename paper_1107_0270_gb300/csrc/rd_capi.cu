@@ -932,17 +932,6 @@ int rd_num_particles(rd_handle* h, int64_t* n) {
   return RD_OK;
 }
 
-static inline uint32_t wbits_host(const void* rec, size_t vsize) {
-  if (vsize == 32) {
-    uint64_t b;
-    std::memcpy(&b, (const char*)rec + 24, 8);
-    return (uint32_t)b;
-  }
-  uint32_t b;
-  std::memcpy(&b, (const char*)rec + 12, 4);
-  return b;
-}
-
 static bool ensure_staging(rd_handle* h) {
   if (h->st_x) return true;
   const int64_t cap = h->L.cap_particles;

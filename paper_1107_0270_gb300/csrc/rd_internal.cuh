@@ -364,7 +364,7 @@ __device__ __forceinline__ void lnT3(double V, double w, double s, double inv_4t
   df = -(1.0 + V) * (q_ierfc(y, ey) + kSqrtPi * z * ey) / (s * kSqrtPi * body);
 }
 
-// FP32 evaluation of ln T and its derivative (seed of the FP64 solve).
+// FP32 evaluation of ln T and its derivative (the FP64 solve's seed; the mixed step's Newton step).
 __device__ __forceinline__ void lnT3_f(float V, float w, float s, float inv_4tau, float ln_ex0, float& f, float& df) {
   const float z = (V + w) / (2.0f * s);
   const float ez = erfcxf(z), y = s + z, ey = erfcxf(y);
@@ -427,36 +427,6 @@ __device__ __forceinline__ double resample3(double U, double R0, double s) {
     if (hi >= 0.0 && hi - lo <= 4e-16 * fmax(hi, s)) break;
   }
   return 1.0 + V;
-}
-
-// FP32 propagator sample for the mixed step: the Newton iteration of resample3 in float until the
-// step is below 2e-6 of the length scale.
-__device__ __forceinline__ float resample3_f(float U, float R0, float s) {
-  if (R0 < 1.0f) R0 = 1.0f;
-  const float w = R0 - 1.0f;
-  const float inv_4tau = 1.0f / (4.0f * s * s);
-  const float lnU = logf(U);
-  const float ln_ex0 = logf(erfcxf(w / (2.0f * s)));
-  float lo = 0.0f, hi = -1.0f, V = 0.0f;
-  for (int it = 0; it < 40; ++it) {
-    float f, df;
-    lnT3_f(V, w, s, inv_4tau, ln_ex0, f, df);
-    const float g = f - lnU;
-    if (g == 0.0f) break;
-    if (g > 0.0f)
-      lo = V;
-    else
-      hi = V;
-    float Vn = V - g / df;
-    const bool inside = Vn >= lo && (hi < 0.0f || Vn <= hi);
-    if (!inside) Vn = hi < 0.0f ? lo + fmaxf(lo, s) : 0.5f * (lo + hi);
-    const float step = fabsf(Vn - V);
-    V = Vn;
-    if (inside && step <= 2e-6f * fmaxf(V, s)) break;
-    if (hi >= 0.0f && hi - lo <= 2e-7f * fmaxf(hi, s)) break;
-  }
-  if (!(V >= 0.0f) || !isfinite(V)) V = 0.0f;
-  return 1.0f + V;
 }
 
 __device__ __forceinline__ void cr_w(float t, float w[4]) {

@@ -737,7 +737,6 @@ __device__ __noinline__ uint4 draw_ni(const DevParams& P, uint32_t c0, uint32_t 
                                       uint32_t replica) {
   return draw(P, c0, ida, idb, tag, replica);
 }
-__device__ __noinline__ float resample3_f_ni(float U, float R0, float s) { return resample3_f(U, R0, s); }
 __device__ __noinline__ double resample_dim_ni(const DevParams& P, const PairDev& pr, double U, double R0) {
   return resample_dim(P, pr, U, R0);
 }
