@@ -104,6 +104,13 @@ def lib():
         L.or_philox4x32_10.restype = None
         L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                        C.POINTER(C.c_uint32)]
+        L.or_fpt_refine.restype = C.c_int
+        L.or_fpt_refine.argtypes = [C.c_int, d, d, d, d, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32,
+                                    C.POINTER(C.c_uint32), C.POINTER(d), C.POINTER(d),
+                                    C.POINTER(C.c_uint32), C.POINTER(d)]
+        L.or_fpt_direction.restype = C.c_int
+        L.or_fpt_direction.argtypes = [C.c_int, d, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(d),
+                                       C.POINTER(d)]
         L.or_init_positions.restype = C.c_int
         L.or_init_positions.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64), C.POINTER(_State)]
         L.or_step.restype = C.c_int
@@ -195,6 +202,37 @@ def S_abs2(R0, tau):
 
 def resample2(U, R0, tau, tau_s=0.01):
     return lib().or_resample2(U, R0, tau, tau_s)
+
+
+def fpt_refine(dim, R0, R, tau, levels, seed, stream, tau_s=0.01, max_attempts=1 << 20):
+    """First-passage refinement of one encountered pair (Appendix; scaled units): returns
+    (bin, R_lo, R_hi, attempts, margin, ok); the first contact lies in [bin, bin + 1) tau / 2^levels."""
+    b, a = C.c_uint32(), C.c_uint32()
+    lo, hi, mg = C.c_double(), C.c_double(), C.c_double()
+    st = lib().or_fpt_refine(int(dim), float(R0), float(R), float(tau), float(tau_s), int(levels),
+                             int(seed) & (2**64 - 1), int(stream) & (2**64 - 1), int(max_attempts),
+                             C.byref(b), C.byref(lo), C.byref(hi), C.byref(a), C.byref(mg))
+    return b.value, lo.value, hi.value, a.value, mg.value, st == 0
+
+
+def fpt_direction(dim, kappa, seed, stream, attempt):
+    """The refinement's end-point direction draw: (1 - cos(theta), sin(theta)), or None."""
+    omc, sn = C.c_double(), C.c_double()
+    ok = lib().or_fpt_direction(int(dim), float(kappa), int(seed), int(stream), int(attempt),
+                                C.byref(omc), C.byref(sn))
+    return (omc.value, sn.value) if ok else None
+
+
+def fpt_refine_batch(dim, R0, R, tau, levels, seed, streams, tau_s=0.01, max_attempts=1 << 20):
+    """fpt_refine over arrays R0, R, streams (same tau): arrays bin, R_lo, R_hi, attempts, margin."""
+    n = len(R0)
+    out = {"bin": np.zeros(n, np.uint32), "R_lo": np.zeros(n), "R_hi": np.zeros(n),
+           "attempts": np.zeros(n, np.uint32), "margin": np.zeros(n)}
+    for k in range(n):
+        b, lo, hi, a, mg, _ = fpt_refine(dim, R0[k], R[k], tau, levels, seed, int(streams[k]), tau_s,
+                                         max_attempts)
+        out["bin"][k], out["R_lo"][k], out["R_hi"][k], out["attempts"][k], out["margin"][k] = b, lo, hi, a, mg
+    return out
 
 
 def pair_probs(system, r0, r, rule: int = 0):

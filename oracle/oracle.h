@@ -100,6 +100,18 @@ double or_tail2(double V, double R0, double tau, double tau_s);
 double or_resample2(double U, double R0, double tau, double tau_s);
 double or_S_abs2(double R0, double tau);
 
+/* First-passage refinement of an encountered pair (Appendix): bisects a step of length tau
+ * (scaled units) `levels` times; *bin = index of the interval of length tau / 2^levels that holds
+ * the first contact, *R_lo, *R_hi = separations at that interval's ends, *attempts = midpoint
+ * draws used, *margin = min |U - p_enc| over the encounter decisions taken.  Returns 1 (bin =
+ * 0xFFFFFFFF, R_lo = R_hi = NaN) when max_attempts draws did not suffice, else 0. */
+int or_fpt_refine(int dim, double R0, double R, double tau, double tau_s, int levels, uint64_t seed,
+                  uint64_t strm, uint32_t max_attempts, uint32_t* bin, double* R_lo, double* R_hi,
+                  uint32_t* attempts, double* margin);
+
+int or_fpt_direction(int dim, double kappa, uint64_t seed, uint64_t strm, uint32_t a, double* omc,
+                     double* sn);
+
 /* Whole step and initial condition. */
 int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st);
 int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* stats, or_trace* trace);

@@ -1036,3 +1036,162 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
   free(x1); free(decayed); free(consumed); free(partner); free(prod); free(fired); free(xs);
   return status;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* First-passage refinement (Appendix, "Relation to first-passage time simulation algorithms"): */
+/* a pair that went from separation R0 to R in a step of length tau (scaled units) and          */
+/* encountered the contact surface on the way.  The step is halved `levels` times; at every      */
+/* level the separation at the midpoint of the current interval is drawn from the bridge of the  */
+/* radial process between the interval's end separations, and the half that holds the first     */
+/* contact is chosen with p_enc of the two halves.  The encounter is known for the whole         */
+/* interval, so the midpoint and the two halves' encounter decisions are redrawn until at least  */
+/* one half has an encounter; the first contact then lies in the first half if that one has an  */
+/* encounter, else in the second.                                                                */
+/*                                                                                                */
+/* Radial bridge midpoint (the paper states the 1D Gaussian law, Eq. midPGauss, mean half the    */
+/* displacement, variance half of that of one half-interval step, and leaves the higher-         */
+/* dimensional form to the reader): the end point's direction relative to the start is drawn    */
+/* from the free Gaussian restricted to the sphere |r| = R_f, a von Mises-Fisher law with         */
+/* concentration kappa = R_i R_f / (2 t) (3D: cos(theta) by inversion of its CDF; 2D: the von     */
+/* Mises law by the rejection method of Best and Fisher, Appl. Stat. 28 (1979) 152); the         */
+/* midpoint vector is then (r_i + r_f)/2 plus a Gaussian of variance t/2 per component, and its  */
+/* length is the bridge midpoint of the radial process.  The azimuth of r_f about r_i and the    */
+/* sign of the 2D angle do not change the law of |m| (the Gaussian is isotropic) and are fixed.  */
+/*                                                                                                */
+/* Random numbers: Philox4x32-10 with key (seed lo, seed hi) and counter (stream lo, stream hi,  */
+/* a, OR_TAG_FPT | w << 8), a = the pair's attempt number counted over all levels, w = word:     */
+/*   w = 0: U_dir (3D direction), U_e1 (encounter in the first half)                             */
+/*   w = 1: two normals (Box-Muller);  w = 2: a third normal (3D)                                */
+/*   w = 3: U_e2 (encounter in the second half)                                                  */
+/*   w = 4 + j: the j-th von Mises trial (2D), j < 64                                            */
+/* ------------------------------------------------------------------------------------------ */
+#define OR_TAG_FPT 13
+#define OR_VM_TRIALS 64
+
+static void fpt_draw(uint64_t seed, uint64_t strm, uint32_t a, uint32_t w, double* u0, double* u1) {
+  uint32_t ctr[4] = {(uint32_t)(strm & 0xFFFFFFFFu), (uint32_t)(strm >> 32), a, OR_TAG_FPT | (w << 8)};
+  uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  or_philox4x32_10(ctr, key, o);
+  *u0 = or_u52(o[0], o[1]);
+  *u1 = or_u52(o[2], o[3]);
+}
+
+/* 3D: 1 - cos(theta) for a von Mises-Fisher direction with concentration kappa, from the CDF   */
+/* F(w) = (e^{kappa w} - e^{-kappa}) / (e^{kappa} - e^{-kappa}) inverted at 1 - u:               */
+/* 1 - w = -log(1 + (1 - u) (e^{-2 kappa} - 1)) / kappa.                                          */
+static double vmf3_one_minus_cos(double kappa, double u) {
+  return -log1p((1.0 - u) * expm1(-2.0 * kappa)) / kappa;
+}
+
+/* 2D: von Mises angle with concentration kappa (Best & Fisher 1979), returned as (1 - cos, sin).*/
+/* rho = 2 kappa / (t + sqrt(2 t)) with t = 1 + sqrt(1 + 4 kappa^2) and r = (1 + rho^2)/(2 rho); */
+/* a trial takes z = cos(pi u1), f = (1 + r z)/(r + z), c = kappa (r - f) and accepts when        */
+/* c (2 - c) > u2 or log(c / u2) + 1 - c >= 0; cos(theta) = f.  The differences r - f and 1 - f   */
+/* are formed without cancellation: r - f = (r^2 - 1)/(r + z), 1 - f = (r - 1)(1 - z)/(r + z).  */
+/* Returns 0 when all trials were rejected.                                                      */
+static int vm2_draw(double kappa, uint64_t seed, uint64_t strm, uint32_t a, double* omc, double* sn) {
+  const double s4 = sqrt(1.0 + 4.0 * kappa * kappa), t = 1.0 + s4;
+  const double rho = 2.0 * kappa / (t + sqrt(2.0 * t));
+  const double one_m_rho = (1.0 + 1.0 / (s4 + 2.0 * kappa) + sqrt(2.0 * t)) / (t + sqrt(2.0 * t));
+  const double r = (1.0 + rho * rho) / (2.0 * rho);
+  const double r_m1 = one_m_rho * one_m_rho / (2.0 * rho);
+  const double r2_m1 = (one_m_rho * (1.0 + rho)) * (one_m_rho * (1.0 + rho)) / (4.0 * rho * rho);
+  for (uint32_t j = 0; j < OR_VM_TRIALS; ++j) {
+    double u1, u2;
+    fpt_draw(seed, strm, a, 4 + j, &u1, &u2);
+    const double sh = sin(0.5 * PI * u1), ch = cos(0.5 * PI * u1);
+    const double one_m_z = 2.0 * sh * sh, one_p_z = 2.0 * ch * ch;
+    const double r_p_z = r_m1 + one_p_z;            /* r + z */
+    const double c = kappa * r2_m1 / r_p_z;         /* kappa (r - f) */
+    if (c * (2.0 - c) > u2 || log(c / u2) + 1.0 - c >= 0.0) {
+      const double omf = r_m1 * one_m_z / r_p_z;   /* 1 - f */
+      const double opf = (r + 1.0) * one_p_z / r_p_z;
+      *omc = omf;
+      *sn = sqrt(omf * opf);
+      return 1;
+    }
+  }
+  return 0;
+}
+
+/* The direction draw alone (for the tests of the two samplers): 1 - cos(theta) and sin(theta)
+ * of the end point relative to the start for concentration kappa, attempt a. */
+int or_fpt_direction(int dim, double kappa, uint64_t seed, uint64_t strm, uint32_t a, double* omc,
+                     double* sn) {
+  if (dim == 3) {
+    double u_dir, u_e1;
+    fpt_draw(seed, strm, a, 0, &u_dir, &u_e1);
+    *omc = vmf3_one_minus_cos(kappa, u_dir);
+    *sn = sqrt(*omc * (2.0 - *omc));
+    return 1;
+  }
+  return vm2_draw(kappa, seed, strm, a, omc, sn);
+}
+
+static double fpt_p_enc(int dim, double R, double R0, double tau, double tau_s) {
+  return dim == 3 ? or_p_enc3(R, R0, tau) : or_p_enc2(R, R0, tau, tau_s);
+}
+
+int or_fpt_refine(int dim, double R0, double R, double tau, double tau_s, int levels, uint64_t seed,
+                  uint64_t strm, uint32_t max_attempts, uint32_t* bin, double* R_lo, double* R_hi,
+                  uint32_t* attempts, double* margin) {
+  double Ri = R0, Rf = R, t = tau, mg = INFINITY;
+  uint32_t b = 0, a = 0;
+  int status = 0;
+  for (int k = 0; k < levels && status == 0; ++k) {
+    for (;;) {
+      if (a >= max_attempts) { status = 1; break; }
+      double u_dir, u_e1, u_e2, unused, xi[4];
+      fpt_draw(seed, strm, a, 0, &u_dir, &u_e1);
+      {
+        double v0, v1;
+        fpt_draw(seed, strm, a, 1, &v0, &v1);
+        box_muller(v0, v1, &xi[0], &xi[1]);
+        xi[2] = 0.0;
+        if (dim == 3) {
+          fpt_draw(seed, strm, a, 2, &v0, &v1);
+          box_muller(v0, v1, &xi[2], &xi[3]);
+        }
+      }
+      fpt_draw(seed, strm, a, 3, &u_e2, &unused);
+      /* end point in the frame of the start point r_i = (R_i, 0, 0) */
+      const double kappa = Ri * Rf / (2.0 * t);
+      double omc, sn;
+      if (dim == 3) {
+        omc = vmf3_one_minus_cos(kappa, u_dir);
+        sn = sqrt(omc * (2.0 - omc));
+      } else if (!vm2_draw(kappa, seed, strm, a, &omc, &sn)) {
+        status = 1;
+        break;
+      }
+      const double sd = sqrt(0.5 * t);
+      const double m0 = 0.5 * (Ri + Rf * (1.0 - omc)) + sd * xi[0];
+      const double m1 = 0.5 * Rf * sn + sd * xi[1];
+      const double m2 = dim == 3 ? sd * xi[2] : 0.0;
+      const double Rm = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+      a++;
+      const double p1 = fpt_p_enc(dim, Rm, Ri, 0.5 * t, tau_s);
+      if (fabs(u_e1 - p1) < mg) mg = fabs(u_e1 - p1);
+      if (u_e1 < p1) {            /* first contact in the first half */
+        Rf = Rm;
+        b = 2 * b;
+        break;
+      }
+      const double p2 = fpt_p_enc(dim, Rf, Rm, 0.5 * t, tau_s);
+      if (fabs(u_e2 - p2) < mg) mg = fabs(u_e2 - p2);
+      if (u_e2 < p2) {            /* no contact in the first half, so it is in the second */
+        Ri = Rm;
+        b = 2 * b + 1;
+        break;
+      }
+    }
+    t *= 0.5;
+  }
+  if (bin) *bin = status ? 0xFFFFFFFFu : b;
+  if (R_lo) *R_lo = status ? NAN : Ri;
+  if (R_hi) *R_hi = status ? NAN : Rf;
+  if (attempts) *attempts = a;
+  if (margin) *margin = mg;
+  return status;
+}
