@@ -427,6 +427,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     res["mixed_max_abs_error"] = {"p_enc": float(d_enc.max()), "p_reac": float(d_reac.max()),
                                   "pairs": int(d_enc.size), "target": 2e-6}
     out["pair_prob_evals_per_s"] = res
+    out["first_passage"] = fpt_measurement(args, torch, pkg, flush, r0n, rn)
     # the other time steps of the same configuration, mixed and FP64 (device-timed graph launches)
     sweep = {}
     for dt in (1e-6, 1e-4):
@@ -487,6 +488,60 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
                           "host arrays), per step"}
     sim.close()
     return out
+
+
+def fpt_measurement(args, torch, pkg, flush, r0n, rn, levels=10):
+    """First-passage refinement (rd_first_passage) of 2^20 encountered pairs of the headline rule:
+    candidate-shaped pairs kept with probability p_enc (the library's own FP64 p_enc, outside the
+    timed region), bisected `levels` times; device-timed, with the oracle on a sample beside it."""
+    system = workload(args, seed=2)
+    pr = system.pairs[0]
+    sim = pkg.Simulation(system, precision="fp64")
+    r0c, rc = torch.tensor(r0n, device="cuda"), torch.tensor(rn, device="cuda")
+    pe, _ = sim.pair_probs(r0c, rc)
+    sim.sync()
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    keep = torch.rand(pe.shape, device="cuda", dtype=torch.float64, generator=gen) < pe
+    r0e, re = r0c[keep], rc[keep]
+    reps = -(-(1 << 20) // max(1, r0e.numel()))
+    r0e, re = r0e.repeat(reps)[: 1 << 20].contiguous(), re.repeat(reps)[: 1 << 20].contiguous()
+    n = r0e.numel()
+    streams = torch.arange(n, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        g = sim.first_passage(r0e, re, streams, levels)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(5):
+        flush.add_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(sim.stream):
+            sim.stream.wait_stream(torch.cuda.current_stream())
+            a.record(sim.stream)
+        g = sim.first_passage(r0e, re, streams, levels)
+        with torch.cuda.stream(sim.stream):
+            b.record(sim.stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) * 1e-3)
+    t = statistics.median(times)
+    att = g["attempts"].double()
+    failed = int((g["bin"] < 0).sum().item())
+    res = {"pairs": n, "distinct_pairs": int(keep.sum().item()), "levels": levels,
+           "ms": 1e3 * t, "pairs_per_s": n / t, "mean_attempts": float(att.mean().item()),
+           "max_attempts": int(att.max().item()), "over_attempt_bound": failed}
+    sim.close()
+    # CPU baseline: the oracle on a bounded sample of the same pairs, one host thread
+    import oracle as O
+
+    m = 2000
+    Drel = system.D[pr.s1] + system.D[pr.s2]
+    tau = Drel * system.dt / pr.sigma ** 2
+    a0, a1 = r0e[:m].cpu().numpy() / pr.sigma, re[:m].cpu().numpy() / pr.sigma
+    t0 = time.perf_counter()
+    O.fpt_refine_batch(system.dim, a0, a1, tau, levels, system.seed, np.arange(m, dtype=np.uint64))
+    res["cpu_baseline"] = {"value": m / (time.perf_counter() - t0), "unit": "pairs/s", "cores": 1,
+                           "kind": "oracle", "sample": f"the first {m} of the same pairs"}
+    return res
 
 
 def other_workloads(torch, pkg, flush):

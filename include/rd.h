@@ -183,6 +183,27 @@ int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r,
 int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n,
                 double* r_new);
 
+/* First-passage refinement of encountered pairs (Appendix, "Relation to first-passage time
+ * simulation algorithms"): for k < n, a pair of rule `rule` whose separation went from r0[k] to
+ * r[k] in one step dt and that met the contact surface during it.  The step is halved `levels`
+ * times (0..24); at each level the separation at the midpoint is drawn from the radial Brownian
+ * bridge and the half holding the first contact is chosen with p_enc of the two halves, redrawn
+ * until one half has an encounter (the encounter is known for the whole interval).
+ * Outputs: bin[k] = j such that the first contact lies in [j, j + 1) dt / 2^levels; r_lo[k],
+ * r_hi[k] = separations at that interval's ends; attempts[k] = midpoint draws used.  A pair whose
+ * draws exceed max_attempts (0: RD_FPT_MAX_ATTEMPTS; the expected count is about 1/p_enc of the
+ * whole step plus a few per level) gets bin = 0xFFFFFFFF and NaN separations.
+ * Random numbers: Philox4x32-10 with the handle's seed, counter (stream[k] low word, high word,
+ * attempt, 13 | word << 8).  Pointers are DEVICE pointers: r0, r (double, physical lengths),
+ * stream (uint64), bin (uint32) required; r_lo, r_hi (double), attempts (uint32) may be NULL.
+ * In 2D the half intervals longer than tau_s use Weber quadrature nodes built on the first call
+ * for each (rule, levels) (allocation and a synchronisation then); accuracy holds for
+ * separations up to the rule's cut-off plus 13 sqrt(D dt).  Asynchronous on the handle's stream. */
+#define RD_FPT_MAX_ATTEMPTS (1u << 20)
+int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double* r,
+                     const uint64_t* stream, int64_t n, int32_t levels, uint32_t max_attempts,
+                     uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts);
+
 /* Diagnostics of the last step (synchronises): the fired (encounter) pairs as ids, their p_enc,
  * their selection key -ln(U_sel)/p_enc and whether the conflict resolution accepted them (the
  * accepted set is the greedy matching in ascending (key, id_a, id_b)).  cap: capacity of the

@@ -28,7 +28,7 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
           5: "RD_ECUDA", 6: "RD_ENOTREADY"}
 # exported symbols declared in include/rd.h
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
-           "rd_pair_probs", "rd_resample", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
+           "rd_pair_probs", "rd_resample", "rd_first_passage", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
            "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static",
            "rd_info", "rd_count_history", "rd_check_bounded_wait"]
 
@@ -99,6 +99,7 @@ def _lib():
         L.rd_set_state.argtypes = [vp, i64, P(d), P(i32), P(u32), P(i32), P(u32), i64]
         L.rd_pair_probs.argtypes = [vp, i32, vp, vp, i64, vp, vp]
         L.rd_resample.argtypes = [vp, i32, vp, vp, i64, vp]
+        L.rd_first_passage.argtypes = [vp, i32, vp, vp, vp, i64, i32, C.c_uint32, vp, vp, vp, vp]
         L.rd_last_fired.argtypes = [vp, i64, P(i64), P(u32), P(u32), P(d), P(i32), P(i32), P(d)]
         L.rd_num_particles.argtypes = [vp, P(i64)]
         L.rd_time_kernels.argtypes = [vp, i32]
@@ -365,6 +366,27 @@ class Simulation:
         _check(_lib().rd_resample(self._h, rule, r0.data_ptr(), u.data_ptr(), r0.numel(), out.data_ptr()),
                "rd_resample")
         torch.cuda.current_stream(r0.device).wait_stream(self.stream)
+        return out
+
+    def first_passage(self, r0, r, stream, levels: int, rule: int = 0, max_attempts: int = 0):
+        """First-passage refinement of encountered pairs (device tensors r0, r float64 and stream
+        int64): dict of bin (int32 view of uint32), r_lo, r_hi, attempts."""
+        import torch
+
+        assert r0.is_cuda and r.is_cuda and stream.is_cuda and stream.dtype == torch.int64
+        r0, r, stream = r0.contiguous(), r.contiguous(), stream.contiguous()
+        n = r0.numel()
+        dev = r0.device
+        out = {"bin": torch.empty(n, dtype=torch.int32, device=dev),
+               "r_lo": torch.empty(n, dtype=torch.float64, device=dev),
+               "r_hi": torch.empty(n, dtype=torch.float64, device=dev),
+               "attempts": torch.empty(n, dtype=torch.int32, device=dev)}
+        self.stream.wait_stream(torch.cuda.current_stream(dev))
+        _check(_lib().rd_first_passage(self._h, rule, r0.data_ptr(), r.data_ptr(), stream.data_ptr(), n, levels,
+                                       max_attempts, out["bin"].data_ptr(), out["r_lo"].data_ptr(),
+                                       out["r_hi"].data_ptr(), out["attempts"].data_ptr()),
+               "rd_first_passage")
+        torch.cuda.current_stream(dev).wait_stream(self.stream)
         return out
 
     # -- per-kernel timing of one step -----------------------------------------------------------

@@ -62,6 +62,8 @@ struct rd_handle {
   uint32_t* st_maxid = nullptr;
   uint32_t* st_next = nullptr;
   int32_t* st_err = nullptr;
+  // Weber nodes of the first-passage refinement's half intervals (2D), per rule and level
+  std::vector<std::pair<const void*, int>> fpt_nodes[RD_MAX_PAIRS];
 };
 
 static void* dev_alloc(rd_handle* h, size_t bytes) {
@@ -1030,6 +1032,49 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
   if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
   if (n == 0) return RD_OK;
   launch_resample(h->L.P, rule, r0, u, n, r_new, h->L.max_grid, h->stream);
+  RD_CUDA(cudaGetLastError());
+  return RD_OK;
+}
+
+int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double* r, const uint64_t* stream,
+                     int64_t n, int32_t levels, uint32_t max_attempts, uint32_t* bin, double* r_lo, double* r_hi,
+                     uint32_t* attempts) {
+  if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || levels < 0 || levels > kFptMaxLevels) return RD_EINVAL;
+  if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
+  if (n > 0 && (!r0 || !r || !stream || !bin)) return RD_EINVAL;
+  if (n == 0) return RD_OK;
+  const PairDev& q = h->hp.pairs[rule];
+  FptArgs A{};
+  A.dim = h->cfg.dim;
+  A.levels = levels;
+  A.max_attempts = max_attempts ? max_attempts : RD_FPT_MAX_ATTEMPTS;
+  A.seed_lo = h->hp.seed_lo;
+  A.seed_hi = h->hp.seed_hi;
+  A.tau = q.tau;
+  A.sigma = q.sigma;
+  A.ser = q.ser;
+  if (A.dim == 2) {
+    auto& sets = h->fpt_nodes[rule];
+    const double Rmax = std::sqrt(q.rcut2) / q.sigma + 13.0 * q.s + 3.0;
+    for (int l = (int)sets.size(); l < levels; ++l) {
+      const double tl = std::ldexp(q.tau, -(l + 1));
+      if (tl <= h->cfg.tau_s) {
+        sets.emplace_back(nullptr, 0);
+        continue;
+      }
+      std::vector<WeberNode> nodes = weber_nodes(tl, q.h, Rmax);
+      void* dn = dev_alloc(h, nodes.size() * sizeof(WeberNode));
+      if (!dn) return RD_ENOMEM;
+      RD_CUDA(cudaMemcpyAsync(dn, nodes.data(), nodes.size() * sizeof(WeberNode), cudaMemcpyHostToDevice, h->stream));
+      RD_CUDA(cudaStreamSynchronize(h->stream));
+      sets.emplace_back(dn, (int)nodes.size());
+    }
+    for (int l = 0; l < levels; ++l) {
+      A.lv[l].nodes = sets[l].first;
+      A.lv[l].n_nodes = sets[l].second;
+    }
+  }
+  launch_first_passage(A, r0, r, stream, n, bin, r_lo, r_hi, attempts, h->L.max_grid, h->stream);
   RD_CUDA(cudaGetLastError());
   return RD_OK;
 }

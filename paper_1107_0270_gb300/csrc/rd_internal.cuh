@@ -19,7 +19,8 @@ constexpr int kSmemCounts = 6144;                // per-block histogram of (repl
 // Random-stream tags (counter word 3, low byte; replica index in the upper 24 bits).
 enum Tag : uint32_t {
   TAG_INIT0 = 1, TAG_INIT1 = 2, TAG_UNI = 3, TAG_DISP0 = 4, TAG_DISP1 = 5, TAG_ENC = 6,
-  TAG_RES = 7, TAG_DIR = 8, TAG_DISS0 = 9, TAG_DISS1 = 10, TAG_DISS2 = 11, TAG_DISS3 = 12
+  TAG_RES = 7, TAG_DIR = 8, TAG_DISS0 = 9, TAG_DISS1 = 10, TAG_DISS2 = 11, TAG_DISS3 = 12,
+  TAG_FPT = 13
 };
 
 // Per-particle status word written every step.

@@ -110,4 +110,23 @@ void launch_build_table(const DevParams* P, int rule, int kind, float* out, floa
 void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
                      int max_grid, cudaStream_t s);
 
+// First-passage refinement of encountered pairs (one pair rule, one step length).
+constexpr int kFptMaxLevels = 24;
+struct FptLevel {              // p_enc data of the half intervals of level l (2D)
+  const void* nodes;           // Weber nodes for tau / 2^(l+1) (nullptr: small-time series)
+  int n_nodes;
+};
+struct FptArgs {
+  int dim, levels;
+  uint32_t max_attempts;
+  uint32_t seed_lo, seed_hi;
+  double tau;                  // D dt / sigma^2 of the rule
+  double sigma;
+  const void* ser;             // 2D small-time series coefficients of the rule
+  FptLevel lv[kFptMaxLevels];
+};
+void launch_first_passage(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
+                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, int max_grid,
+                          cudaStream_t s);
+
 }  // namespace rd

@@ -1,0 +1,133 @@
+"""First-passage refinement on the GPU (rd_first_passage) against the oracle: bins, interval-end
+separations and draw counts pair by pair in 2D and 3D, the degenerate cases, and at 2^20 pairs the
+bin law against the closed-form 3D first-contact density."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1107_0270_gb300 as pkg  # noqa: E402
+
+MARGIN = 1e-9      # decisions closer than this to their threshold may flip with the last bits of p_enc
+
+
+def _rule_scale(system, rule=0):
+    pr = system.pairs[rule]
+    D = system.D[pr.s1] + system.D[pr.s2]
+    return pr.sigma, D * system.dt / pr.sigma ** 2
+
+
+def _inputs(n, sigma, tau, seed):
+    rng = np.random.default_rng(seed)
+    s = math.sqrt(tau)
+    R0 = 1.0 + np.abs(rng.normal(0.0, 0.7 * s, n))
+    R = 1.0 + rng.normal(0.3 * s, 0.8 * s, n)          # some end inside the contact sphere
+    R0[: max(1, n // 50)] = 1.0                         # a few start in contact
+    streams = (np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) ^ np.uint64(0xABCDEF0123456789)
+    return R0 * sigma, R * sigma, streams
+
+
+def _compare(system, levels, n, seed, rule=0):
+    sigma, tau = _rule_scale(system, rule)
+    r0, r, streams = _inputs(n, sigma, tau, seed)
+    sim = pkg.Simulation(system, precision="fp64")
+    dev = torch.device("cuda")
+    g = sim.first_passage(torch.tensor(r0, device=dev), torch.tensor(r, device=dev),
+                          torch.tensor(streams.view(np.int64), device=dev), levels, rule=rule)
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    sim.close()
+    o = O.fpt_refine_batch(system.dim, r0 / sigma, r / sigma, tau, levels, system.seed, streams,
+                           tau_s=system.tau_s)
+    sure = o["margin"] > MARGIN
+    assert sure.mean() > 0.98
+    assert np.array_equal(g["bin"].view(np.uint32)[sure], o["bin"][sure])
+    assert np.array_equal(g["attempts"][sure].astype(np.uint32), o["attempts"][sure])
+    for k, ko in (("r_lo", "R_lo"), ("r_hi", "R_hi")):
+        np.testing.assert_allclose(g[k][sure], o[ko][sure] * sigma, rtol=1e-11, atol=0)
+    return g, o
+
+
+@pytest.mark.parametrize("levels", [1, 6, 16])
+def test_refinement_matches_oracle_3d(levels):
+    _compare(W.reversible_3d(), levels, 4000, seed=levels)
+
+
+def test_refinement_matches_oracle_3d_absorbing_rule():
+    system = W.network_3d(dt=2e-5, scale=2e-4)
+    _compare(system, 8, 2000, seed=3, rule=1)
+
+
+def test_refinement_matches_oracle_2d():
+    # tau = 0.8: the half intervals of levels 0-5 use Weber quadrature, the later ones the series
+    _compare(W.membrane_2d(), 8, 300, seed=4)
+
+
+def test_degenerate_inputs():
+    system = W.reversible_3d()
+    sigma, tau = _rule_scale(system)
+    sim = pkg.Simulation(system, precision="fp64")
+    dev = torch.device("cuda")
+    r0 = torch.tensor([1.3 * sigma, 1.0 * sigma, 8.0 * sigma], dtype=torch.float64, device=dev)
+    r = torch.tensor([1.4 * sigma, 1.5 * sigma, 8.0 * sigma], dtype=torch.float64, device=dev)
+    st = torch.tensor([5, 6, 7], dtype=torch.int64, device=dev)
+    g = sim.first_passage(r0, r, st, 0)
+    assert g["bin"].tolist() == [0, 0, 0] and g["attempts"].tolist() == [0, 0, 0]
+    assert torch.equal(g["r_lo"], r0) and torch.equal(g["r_hi"], r)
+    g = sim.first_passage(r0[:2], r[:2], st[:2], 10)
+    assert g["bin"][1].item() == 0 and g["attempts"][1].item() == 10     # in contact at the start
+    g = sim.first_passage(r0[2:], r[2:], st[2:], 4, max_attempts=16)       # p_enc ~ 1e-30: bound hit
+    assert g["bin"].item() == -1 and g["attempts"].item() == 16 and math.isnan(g["r_lo"].item())
+    e = torch.empty(0, dtype=torch.float64, device=dev)
+    g = sim.first_passage(e, e, torch.empty(0, dtype=torch.int64, device=dev), 5)
+    assert g["bin"].numel() == 0
+    with pytest.raises(pkg.RDError):
+        sim.first_passage(r0, r, st, 25)
+    sim.close()
+
+
+def _bin_probs3(R0, R, tau, K):
+    def f(s):
+        if s <= 0.0 or s >= tau:
+            return 0.0
+        rho = (R0 - 1.0) / (R0 * math.sqrt(4.0 * math.pi * s ** 3)) * math.exp(-(R0 - 1.0) ** 2 / (4.0 * s))
+        u = tau - s
+        g = (R / 1.0) / math.sqrt(4.0 * math.pi * u) * (math.exp(-(R - 1.0) ** 2 / (4.0 * u))
+                                                       - math.exp(-(R + 1.0) ** 2 / (4.0 * u)))
+        return rho * g
+    edges = np.linspace(0.0, tau, 2 ** K + 1)
+    return np.array([integrate.quad(f, a, b, epsabs=0, epsrel=1e-11, limit=200)[0]
+                     for a, b in zip(edges[:-1], edges[1:])])
+
+
+def test_bin_law_at_scale_3d():
+    system = W.reversible_3d()
+    sigma, tau = _rule_scale(system)
+    n, K, R0, R = 1 << 20, 5, 1.2, 1.35
+    dev = torch.device("cuda")
+    sim = pkg.Simulation(system, precision="fp64")
+    g = sim.first_passage(torch.full((n,), R0 * sigma, dtype=torch.float64, device=dev),
+                          torch.full((n,), R * sigma, dtype=torch.float64, device=dev),
+                          torch.arange(n, dtype=torch.int64, device=dev), K)
+    bins = g["bin"].cpu().numpy()
+    sim.close()
+    assert bins.min() >= 0 and bins.max() < 2 ** K
+    counts = np.bincount(bins, minlength=2 ** K)
+    p = _bin_probs3(R0, R, tau, K)
+    p = p / p.sum()
+    exp = n * p
+    keep = exp >= 5
+    obs = np.append(counts[keep], counts[~keep].sum())
+    ex = np.append(exp[keep], exp[~keep].sum())
+    if ex[-1] == 0:
+        obs, ex = obs[:-1], ex[:-1]
+    assert stats.chisquare(obs, ex * obs.sum() / ex.sum()).pvalue > 1e-4
