@@ -427,7 +427,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     res["mixed_max_abs_error"] = {"p_enc": float(d_enc.max()), "p_reac": float(d_reac.max()),
                                   "pairs": int(d_enc.size), "target": 2e-6}
     out["pair_prob_evals_per_s"] = res
-    out["first_passage"] = fpt_measurement(args, torch, pkg, flush, r0n, rn)
+    out["first_passage"] = fpt_measurement(args, torch, pkg, flush)
     # the other time steps of the same configuration, mixed and FP64 (device-timed graph launches)
     sweep = {}
     for dt in (1e-6, 1e-4):
@@ -490,49 +490,19 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     return out
 
 
-def fpt_measurement(args, torch, pkg, flush, r0n, rn, levels=10):
-    """First-passage refinement (rd_first_passage) of 2^20 encountered pairs of the headline rule:
-    candidate-shaped pairs kept with probability p_enc (the library's own FP64 p_enc, outside the
-    timed region), bisected `levels` times; device-timed, with the oracle on a sample beside it."""
+def fpt_measurement(args, torch, pkg, flush, levels=10):
+    """First-passage refinement (rd_first_passage) of 2^20 encountered pairs of the headline rule,
+    device-timed, with the oracle on a sample of the same pairs beside it."""
+    from paper_1107_0270_gb300 import fpt_bench
+
     system = workload(args, seed=2)
-    pr = system.pairs[0]
-    sim = pkg.Simulation(system, precision="fp64")
-    r0c, rc = torch.tensor(r0n, device="cuda"), torch.tensor(rn, device="cuda")
-    pe, _ = sim.pair_probs(r0c, rc)
-    sim.sync()
-    gen = torch.Generator(device="cuda").manual_seed(5)
-    keep = torch.rand(pe.shape, device="cuda", dtype=torch.float64, generator=gen) < pe
-    r0e, re = r0c[keep], rc[keep]
-    reps = -(-(1 << 20) // max(1, r0e.numel()))
-    r0e, re = r0e.repeat(reps)[: 1 << 20].contiguous(), re.repeat(reps)[: 1 << 20].contiguous()
-    n = r0e.numel()
-    streams = torch.arange(n, dtype=torch.int64, device="cuda")
-    for _ in range(3):
-        g = sim.first_passage(r0e, re, streams, levels)
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(5):
-        flush.add_(1)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(sim.stream):
-            sim.stream.wait_stream(torch.cuda.current_stream())
-            a.record(sim.stream)
-        g = sim.first_passage(r0e, re, streams, levels)
-        with torch.cuda.stream(sim.stream):
-            b.record(sim.stream)
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b) * 1e-3)
-    t = statistics.median(times)
-    att = g["attempts"].double()
-    failed = int((g["bin"] < 0).sum().item())
-    res = {"pairs": n, "distinct_pairs": int(keep.sum().item()), "levels": levels,
-           "ms": 1e3 * t, "pairs_per_s": n / t, "mean_attempts": float(att.mean().item()),
-           "max_attempts": int(att.max().item()), "over_attempt_bound": failed}
-    sim.close()
+    r0e, re, distinct = fpt_bench.encountered_pairs(pkg, torch, system, 1 << 20)
+    res = fpt_bench.time_refinement(pkg, torch, system, r0e, re, levels, flush=flush)
+    res["distinct_pairs"] = distinct
     # CPU baseline: the oracle on a bounded sample of the same pairs, one host thread
     import oracle as O
 
+    pr = system.pairs[0]
     m = 2000
     Drel = system.D[pr.s1] + system.D[pr.s2]
     tau = Drel * system.dt / pr.sigma ** 2

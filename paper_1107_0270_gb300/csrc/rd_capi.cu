@@ -64,6 +64,10 @@ struct rd_handle {
   int32_t* st_err = nullptr;
   // Weber nodes of the first-passage refinement's half intervals (2D), per rule and level
   std::vector<std::pair<const void*, int>> fpt_nodes[RD_MAX_PAIRS];
+  // work queues of the refinement's later phases (capacity in pairs each), search records, counters
+  FptItem* fpt_queue = nullptr;
+  int64_t fpt_qcap = 0;
+  uint32_t* fpt_qctl = nullptr;
 };
 
 static void* dev_alloc(rd_handle* h, size_t bytes) {
@@ -1042,6 +1046,7 @@ int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double*
   if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || levels < 0 || levels > kFptMaxLevels) return RD_EINVAL;
   if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
   if (n > 0 && (!r0 || !r || !stream || !bin)) return RD_EINVAL;
+  if (n > (int64_t)0xFFFFFFFFll) return RD_EINVAL;
   if (n == 0) return RD_OK;
   const PairDev& q = h->hp.pairs[rule];
   FptArgs A{};
@@ -1074,7 +1079,22 @@ int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double*
       A.lv[l].n_nodes = sets[l].second;
     }
   }
-  launch_first_passage(A, r0, r, stream, n, bin, r_lo, r_hi, attempts, h->L.max_grid, h->stream);
+  if (n > h->fpt_qcap) {
+    // each queue holds a pair at most once per round, so n entries per queue suffice
+    void* q = dev_alloc(h, 4 * (size_t)n * sizeof(FptItem) + (size_t)n * sizeof(FptSearch));
+    if (!q) return RD_ENOMEM;
+    if (!h->fpt_qctl) {
+      h->fpt_qctl = (uint32_t*)dev_alloc(h, kFptCtlWords * sizeof(uint32_t));
+      if (!h->fpt_qctl) return RD_ENOMEM;
+    }
+    h->fpt_queue = (FptItem*)q;
+    h->fpt_qcap = n;
+  }
+  FptItem* qb = h->fpt_queue;
+  const int64_t qc = h->fpt_qcap;
+  FptItem* warp_q[2] = {qb, qb + qc};
+  launch_first_passage(A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q, qb + 2 * qc, qb + 3 * qc,
+                       (FptSearch*)(qb + 4 * qc), h->fpt_qctl, h->L.max_grid / 16, h->stream);
   RD_CUDA(cudaGetLastError());
   return RD_OK;
 }

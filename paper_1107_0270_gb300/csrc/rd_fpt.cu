@@ -74,80 +74,420 @@ __device__ __noinline__ double fpt_p_enc2(const void* nodes, int n_nodes, const 
   return p_enc2(q, R, R0);
 }
 
-__device__ __forceinline__ double fpt_p_enc(const FptArgs& A, int level, double R, double R0, double tau) {
-  return A.dim == 3 ? p_enc3(R, R0, 1.0 / tau) : fpt_p_enc2(A.lv[level].nodes, A.lv[level].n_nodes, A.ser, R, R0, tau);
+// 3D p_enc of a half interval.  Once (R + R0 - 1)/tau > 40 (so R R0 / tau > 40 too), both expm1
+// terms of the closed form are -1 to within 5e-18 and p_enc = exp(-(R-1)(R0-1)/tau) to that
+// accuracy; the deeper levels of the bisection are almost all in that range.
+__device__ __forceinline__ double fpt_p_enc3(double R, double R0, double tau) {
+  if (R <= 1.0) return 1.0;
+  if (R0 < 1.0) R0 = 1.0;
+  const double inv_tau = 1.0 / tau;
+  if ((R + R0 - 1.0) * inv_tau > 40.0) return exp(-(R - 1.0) * (R0 - 1.0) * inv_tau);
+  return p_enc3(R, R0, inv_tau);
 }
 
+__device__ __forceinline__ double fpt_p_enc(const FptArgs& A, int level, double R, double R0, double tau) {
+  return A.dim == 3 ? fpt_p_enc3(R, R0, tau) : fpt_p_enc2(A.lv[level].nodes, A.lv[level].n_nodes, A.ser, R, R0, tau);
+}
+
+// One midpoint draw of attempt a on the interval (Ri, Rf, t) of level l: 0 = rejected (no
+// encounter in either half), 1 = first contact in the first half, 2 = in the second half (no
+// contact in the first), -1 = the von Mises trials ran out; *Rm = the midpoint separation.
+__device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t strm, uint32_t a, double Ri, double Rf,
+                                           double t, double& Rm) {
+  double u_dir, u_e1, u_e2, unused, v0, v1, x0, x1, x2 = 0.0, x3;
+  fpt_draw(A, strm, a, 0, u_dir, u_e1);
+  fpt_draw(A, strm, a, 1, v0, v1);
+  box_muller(v0, v1, x0, x1);
+  if (A.dim == 3) {
+    fpt_draw(A, strm, a, 2, v0, v1);
+    box_muller(v0, v1, x2, x3);
+  }
+  fpt_draw(A, strm, a, 3, u_e2, unused);
+  const double kappa = Ri * Rf / (2.0 * t);
+  double omc, sn;
+  if (A.dim == 3) {
+    omc = -log1p((1.0 - u_dir) * expm1(-2.0 * kappa)) / kappa;
+    sn = sqrt(omc * (2.0 - omc));
+  } else if (!vm2_draw(A, kappa, strm, a, omc, sn)) {
+    return -1;
+  }
+  const double sd = sqrt(0.5 * t);
+  const double m0 = 0.5 * (Ri + Rf * (1.0 - omc)) + sd * x0;
+  const double m1 = 0.5 * Rf * sn + sd * x1;
+  const double m2 = sd * x2;
+  Rm = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+  if (u_e1 < fpt_p_enc(A, l, Rm, Ri, 0.5 * t)) return 1;
+  if (u_e2 < fpt_p_enc(A, l, Rf, Rm, 0.5 * t)) return 2;
+  return 0;
+}
+
+__device__ __forceinline__ void fpt_write(const FptArgs& A, int64_t k, bool ok, uint32_t b, uint32_t a, double Ri,
+                                          double Rf, uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts) {
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  bin[k] = ok ? b : 0xFFFFFFFFu;
+  if (r_lo) r_lo[k] = ok ? Ri * A.sigma : nan;
+  if (r_hi) r_hi[k] = ok ? Rf * A.sigma : nan;
+  if (attempts) attempts[k] = a;
+}
+
+__device__ __forceinline__ FptItem fpt_item(double Ri, double Rf, double t, uint32_t k, uint32_t b, uint32_t a,
+                                            int l) {
+  FptItem it;
+  it.Ri = Ri;
+  it.Rf = Rf;
+  it.t = t;
+  it.k = k;
+  it.b = b;
+  it.a = a;
+  it.l = (uint32_t)l;
+  return it;
+}
+
+// Phase 1: persistent threads, one pair per lane, one draw per lane and iteration; a lane whose
+// pair is done takes the next pair from a work counter (warp-aggregated), so the lanes of a warp
+// stay busy whatever the draw counts of their pairs.  A pair that needs more than `budget` draws
+// is queued with its state for phase 2.  The draws are indexed by the attempt number, so where an
+// attempt runs does not change the result.
 __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const double* __restrict__ r0,
                                                        const double* __restrict__ r,
                                                        const uint64_t* __restrict__ stream, int64_t n,
                                                        uint32_t* __restrict__ bin, double* __restrict__ r_lo,
-                                                       double* __restrict__ r_hi, uint32_t* __restrict__ attempts) {
+                                                       double* __restrict__ r_hi, uint32_t* __restrict__ attempts,
+                                                       FptItem* __restrict__ queue, uint32_t* __restrict__ qctl,
+                                                       uint32_t budget) {
+  const uint32_t lane = threadIdx.x & 31u;
   const double inv_sigma = 1.0 / A.sigma;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t strm = stream[k];
-    double Ri = r0[k] * inv_sigma, Rf = r[k] * inv_sigma, t = A.tau;
-    uint32_t b = 0, a = 0;
-    bool ok = true;
+  int64_t k = 0;
+  uint64_t strm = 0;
+  double Ri = 0.0, Rf = 0.0, t = 0.0;
+  uint32_t b = 0, a = 0;
+  int l = 0;
+  bool need = true, done = false;
 #pragma unroll 1
-    for (int l = 0; l < A.levels && ok; ++l) {
+  for (;;) {
+    const unsigned nm = __ballot_sync(0xFFFFFFFFu, need);
+    if (nm) {
+      const int leader = __ffs(nm) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd((unsigned long long*)&qctl[kFptPairCtr], (unsigned long long)__popc(nm));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (need) {
+        const unsigned long long kk = base + __popc(nm & ((1u << lane) - 1u));
+        need = false;
+        if ((int64_t)kk < n) {
+          k = (int64_t)kk;
+          strm = stream[k];
+          Ri = r0[k] * inv_sigma;
+          Rf = r[k] * inv_sigma;
+          t = A.tau;
+          b = a = 0;
+          l = 0;
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(0xFFFFFFFFu, done)) break;
+    if (done) continue;
+    if (l >= A.levels) {
+      fpt_write(A, k, true, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      need = true;
+      continue;
+    }
+    if (a >= A.max_attempts) {
+      fpt_write(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      need = true;
+      continue;
+    }
+    if (a >= budget) {
+      queue[atomicAdd(&qctl[kFptRound0 + kFptWarpIn], 1u)] = fpt_item(Ri, Rf, t, (uint32_t)k, b, a, l);
+      need = true;
+      continue;
+    }
+    double Rm;
+    const int d = fpt_attempt(A, l, strm, a, Ri, Rf, t, Rm);
+    if (d < 0) {                // the attempt that ran out of von Mises trials is not counted
+      fpt_write(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      need = true;
+      continue;
+    }
+    ++a;
+    if (d != 0) {
+      if (d == 1) {
+        Rf = Rm;
+        b = 2 * b;
+      } else {
+        Ri = Rm;
+        b = 2 * b + 1;
+      }
+      ++l;
+      t *= 0.5;
+    }
+  }
+}
+
+// Phase 2: one warp per queued pair; each round the 32 lanes try the next 32 attempts and the
+// lowest-numbered decisive one wins (the attempt the serial loop would stop at).  A pair that has
+// drawn `budget` more times since it was queued moves on to queue_out (phase 3).
+__global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, const uint64_t* __restrict__ stream,
+                                                            uint32_t* __restrict__ bin, double* __restrict__ r_lo,
+                                                            double* __restrict__ r_hi,
+                                                            uint32_t* __restrict__ attempts,
+                                                            const FptItem* __restrict__ queue, int count_word,
+                                                            int next_word, FptItem* __restrict__ queue_out,
+                                                            int out_word, uint32_t* __restrict__ qctl,
+                                                            uint32_t budget) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll 1
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(&qctl[next_word], 1u);
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    if (item >= *(volatile uint32_t*)&qctl[count_word]) break;
+    const FptItem it = queue[item];
+    const uint64_t strm = stream[it.k];
+    double Ri = it.Ri, Rf = it.Rf, t = it.t;
+    uint32_t b = it.b, a = it.a;
+    bool ok = true, moved = false;
+#pragma unroll 1
+    for (int l = (int)it.l; l < A.levels && ok && !moved; ++l) {
 #pragma unroll 1
       for (;;) {
         if (a >= A.max_attempts) {
           ok = false;
           break;
         }
-        double u_dir, u_e1, u_e2, unused, v0, v1, x0, x1, x2 = 0.0, x3;
-        fpt_draw(A, strm, a, 0, u_dir, u_e1);
-        fpt_draw(A, strm, a, 1, v0, v1);
-        box_muller(v0, v1, x0, x1);
-        if (A.dim == 3) {
-          fpt_draw(A, strm, a, 2, v0, v1);
-          box_muller(v0, v1, x2, x3);
+        if (a - it.a >= budget) {
+          if (lane == 0) queue_out[atomicAdd(&qctl[out_word], 1u)] = fpt_item(Ri, Rf, t, it.k, b, a, l);
+          moved = true;
+          break;
         }
-        fpt_draw(A, strm, a, 3, u_e2, unused);
-        const double kappa = Ri * Rf / (2.0 * t);
-        double omc, sn;
-        if (A.dim == 3) {
-          omc = -log1p((1.0 - u_dir) * expm1(-2.0 * kappa)) / kappa;
-          sn = sqrt(omc * (2.0 - omc));
-        } else if (!vm2_draw(A, kappa, strm, a, omc, sn)) {
+        const uint32_t mine = a + lane;
+        double Rm = 0.0;
+        int d = 0;
+        if (mine < A.max_attempts) d = fpt_attempt(A, l, strm, mine, Ri, Rf, t, Rm);
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, d != 0);
+        if (m == 0) {
+          const uint32_t room = A.max_attempts - a;
+          a += room < 32u ? room : 32u;
+          continue;
+        }
+        const int w = __ffs(m) - 1;
+        const double rw = __shfl_sync(0xFFFFFFFFu, Rm, w);
+        const int dw = __shfl_sync(0xFFFFFFFFu, d, w);
+        a += dw < 0 ? (uint32_t)w : (uint32_t)w + 1u;
+        if (dw < 0) {
           ok = false;
-          break;
-        }
-        const double sd = sqrt(0.5 * t);
-        const double m0 = 0.5 * (Ri + Rf * (1.0 - omc)) + sd * x0;
-        const double m1 = 0.5 * Rf * sn + sd * x1;
-        const double m2 = sd * x2;
-        const double Rm = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
-        ++a;
-        if (u_e1 < fpt_p_enc(A, l, Rm, Ri, 0.5 * t)) {
-          Rf = Rm;
+        } else if (dw == 1) {
+          Rf = rw;
           b = 2 * b;
-          break;
-        }
-        if (u_e2 < fpt_p_enc(A, l, Rf, Rm, 0.5 * t)) {
-          Ri = Rm;
+        } else {
+          Ri = rw;
           b = 2 * b + 1;
-          break;
         }
+        break;
       }
       t *= 0.5;
     }
-    bin[k] = ok ? b : 0xFFFFFFFFu;
-    if (r_lo) r_lo[k] = ok ? Ri * A.sigma : __longlong_as_double(0x7FF8000000000000ll);
-    if (r_hi) r_hi[k] = ok ? Rf * A.sigma : __longlong_as_double(0x7FF8000000000000ll);
-    if (attempts) attempts[k] = a;
+    if (!moved && lane == 0) fpt_write(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+  }
+}
+
+// The levels from `l` on of one pair, by one block: the rounds of a level widen from 32 to
+// blockDim.x attempts (a level that resolves quickly costs one warp's round) and the lowest-numbered
+// decisive attempt of a round wins.  Stops after `budget` draws.  Shared scratch: s_win, s_rm, s_dec.
+// Returns 0 (all levels done), 1 (failed: attempt bound or von Mises trials) or 2 (budget reached;
+// the state is that of level l).
+__device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri, double& Rf, double& t, uint32_t& b,
+                            uint32_t& a, uint32_t budget, uint32_t* s_win, double* s_rm, int* s_dec) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, a0 = a;
+#pragma unroll 1
+  for (; l < A.levels; ++l) {
+    uint32_t width = 32;
+#pragma unroll 1
+    for (;;) {
+      if (a >= A.max_attempts) return 1;
+      if (a - a0 >= budget) return 2;
+      if (tid == 0) *s_win = 0xFFFFFFFFu;
+      __syncthreads();
+      const uint32_t mine = a + tid;
+      double Rm = 0.0;
+      int d = 0;
+      if (tid < width && mine < A.max_attempts) {
+        d = fpt_attempt(A, l, strm, mine, Ri, Rf, t, Rm);
+        if (d != 0) atomicMin(s_win, tid);
+      }
+      __syncthreads();
+      const uint32_t w = *s_win;
+      if (w != 0xFFFFFFFFu && tid == w) {
+        *s_rm = Rm;
+        *s_dec = d;
+      }
+      __syncthreads();
+      if (w == 0xFFFFFFFFu) {
+        const uint32_t room = A.max_attempts - a;
+        a += room < width ? room : width;
+        width = width * 2 < nt ? width * 2 : nt;
+        continue;
+      }
+      const int dw = *s_dec;
+      a += dw < 0 ? w : w + 1;
+      if (dw < 0) return 1;
+      if (dw == 1) {
+        Rf = *s_rm;
+        b = 2 * b;
+      } else {
+        Ri = *s_rm;
+        b = 2 * b + 1;
+      }
+      break;
+    }
+    t *= 0.5;
+  }
+  return 0;
+}
+
+// Phase 3: one block per pair that needs thousands of draws (work counter over the queue); a pair
+// that has drawn `budget` more times since it was queued moves on to the grid phase with a fresh
+// search record.
+__global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
+    const FptArgs A, const uint64_t* __restrict__ stream, uint32_t* __restrict__ bin, double* __restrict__ r_lo,
+    double* __restrict__ r_hi, uint32_t* __restrict__ attempts, const FptItem* __restrict__ queue,
+    FptItem* __restrict__ queue4, FptSearch* __restrict__ search, uint32_t* __restrict__ qctl, int words,
+    uint32_t budget) {
+  __shared__ uint32_t s_item, s_win;
+  __shared__ double s_rm;
+  __shared__ int s_dec;
+  const uint32_t tid = threadIdx.x;
+#pragma unroll 1
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&qctl[words + kFptBlockNext], 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= *(volatile uint32_t*)&qctl[words + kFptBlockIn]) break;
+    const FptItem it = queue[item];
+    const uint64_t strm = stream[it.k];
+    double Ri = it.Ri, Rf = it.Rf, t = it.t;
+    uint32_t b = it.b, a = it.a;
+    int l = (int)it.l;
+    const int st = block_levels(A, strm, l, Ri, Rf, t, b, a, budget, &s_win, &s_rm, &s_dec);
+    if (tid == 0) {
+      if (st == 2) {
+        const uint32_t j = atomicAdd(&qctl[words + kFptGridIn], 1u);
+        queue4[j] = fpt_item(Ri, Rf, t, it.k, b, a, l);
+        FptSearch z;
+        z.next_chunk = 0;
+        z.winner = 0xFFFFFFFFu;
+        z.exited = 0;
+        z.pad = 0;
+        search[j] = z;
+      } else {
+        fpt_write(A, it.k, st == 0, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 4: the very few pairs that need tens of thousands of draws at one level, each searched by
+// a group of blocks (the grid split into kFptGridGroups groups).  Every block of a group visits the
+// group's pairs in order; for a pair it takes chunks of blockDim.x
+// consecutive attempts of the pair's current level from the pair's chunk counter and lowers the
+// pair's winner (the lowest decisive attempt found) with atomicMin; it leaves the pair once a chunk
+// starts at or past the winner.  Chunks are handed out in order, so when the last block leaves,
+// every attempt below the winner has been tried and the winner is the attempt the serial loop
+// would stop at; that block replays it and queues the pair's next level for the next round of
+// phases 2-4.  No block waits for another.
+__global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
+    const FptArgs A, const uint64_t* __restrict__ stream, uint32_t* __restrict__ bin, double* __restrict__ r_lo,
+    double* __restrict__ r_hi, uint32_t* __restrict__ attempts, const FptItem* __restrict__ queue,
+    FptSearch* __restrict__ search, FptItem* __restrict__ queue_next, uint32_t* __restrict__ qctl, int words) {
+  __shared__ uint32_t s_chunk, s_stop, s_last;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t count = qctl[words + kFptGridIn];
+  // the grid works in groups of blocks (block index mod groups); group g takes items g, g + groups, ...
+  const uint32_t groups = gridDim.x >= 8 * kFptGridGroups ? kFptGridGroups : 1u;
+  const uint32_t g = blockIdx.x % groups;
+  const uint32_t gsize = gridDim.x / groups + (g < gridDim.x % groups ? 1u : 0u);
+#pragma unroll 1
+  for (uint32_t item = g; item < count; item += groups) {
+    const FptItem it = queue[item];
+    FptSearch* sr = &search[item];
+    const uint64_t strm = stream[it.k];
+#pragma unroll 1
+    for (;;) {
+      if (tid == 0) {
+        const uint32_t c = atomicAdd(&sr->next_chunk, 1u);
+        const unsigned long long st = (unsigned long long)it.a + (unsigned long long)c * nt;
+        const uint32_t w = atomicAdd(&sr->winner, 0u);
+        s_chunk = c;
+        s_stop = (st >= w || st >= A.max_attempts) ? 1u : 0u;
+      }
+      __syncthreads();
+      if (s_stop) break;
+      const unsigned long long mine = (unsigned long long)it.a + (unsigned long long)s_chunk * nt + tid;
+      if (mine < A.max_attempts) {
+        double Rm;
+        const int d = fpt_attempt(A, (int)it.l, strm, (uint32_t)mine, it.Ri, it.Rf, it.t, Rm);
+        if (d != 0) atomicMin(&sr->winner, (uint32_t)mine);
+      }
+      __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&sr->exited, 1u) == gsize - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) continue;
+    __threadfence();
+    if (tid == 0) {
+      const uint32_t win = *(volatile uint32_t*)&sr->winner;
+      double Ri = it.Ri, Rf = it.Rf;
+      uint32_t b = it.b, a = A.max_attempts;
+      bool ok = false;
+      if (win != 0xFFFFFFFFu) {           // replay the winning attempt
+        double Rm;
+        const int dw = fpt_attempt(A, (int)it.l, strm, win, Ri, Rf, it.t, Rm);
+        a = dw < 0 ? win : win + 1;
+        ok = dw >= 0;
+        if (dw == 1) {
+          Rf = Rm;
+          b = 2 * b;
+        } else if (dw == 2) {
+          Ri = Rm;
+          b = 2 * b + 1;
+        }
+      }
+      if (ok && (int)it.l + 1 < A.levels)
+        queue_next[atomicAdd(&qctl[words + kFptRoundWords + kFptWarpIn], 1u)] =
+            fpt_item(Ri, Rf, 0.5 * it.t, it.k, b, a, (int)it.l + 1);
+      else
+        fpt_write(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+    }
+    __syncthreads();
   }
 }
 
 void launch_first_passage(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
-                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, int max_grid,
+                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, FptItem* warp_q[2],
+                          FptItem* block_q, FptItem* grid_q, FptSearch* search, uint32_t* qctl, int device_sms,
                           cudaStream_t s) {
-  int64_t g = (n + 127) / 128;
-  if (g > max_grid) g = max_grid;
-  if (g < 1) g = 1;
-  k_first_passage<<<(unsigned)g, 128, 0, s>>>(A, r0, r, stream, n, bin, r_lo, r_hi, attempts);
+  auto clamp = [](int64_t g, int64_t gmax) { return (unsigned)(g > gmax ? gmax : (g < 1 ? 1 : g)); };
+  const unsigned gw = clamp((n + 1023) / 1024, (int64_t)device_sms * 4);
+  const unsigned gb = clamp((n + 4095) / 4096, (int64_t)device_sms * 2);
+  cudaMemsetAsync(qctl, 0, kFptCtlWords * sizeof(uint32_t), s);
+  k_first_passage<<<clamp((n + 127) / 128, (int64_t)device_sms * 4), 128, 0, s>>>(
+      A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q[0], qctl, kFptBudget);
+  // one round of phases 2-4 per level: a pair whose current level is hard goes through them once
+  // more at a later level; a round with nothing queued ends at once
+  for (int round = 0; round < A.levels; ++round) {
+    const int w = kFptRound0 + round * kFptRoundWords;
+    k_first_passage_warp<<<gw, 128, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, warp_q[round & 1], w + kFptWarpIn,
+                                            w + kFptWarpNext, block_q, w + kFptBlockIn, qctl, kFptWarpBudget);
+    k_first_passage_block<<<gb, kFptBlockThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, block_q, grid_q,
+                                                          search, qctl, w, kFptBlockBudget);
+    k_first_passage_grid<<<gb, kFptGridThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, grid_q, search,
+                                                        warp_q[(round + 1) & 1], qctl, w);
+  }
 }
 
 }  // namespace rd

@@ -125,8 +125,29 @@ struct FptArgs {
   const void* ser;             // 2D small-time series coefficients of the rule
   FptLevel lv[kFptMaxLevels];
 };
+constexpr uint32_t kFptBudget = 256;        // draws per pair in the lane-per-pair phase
+constexpr uint32_t kFptWarpBudget = 4352;   // draws per pair before the block-per-pair phase
+constexpr uint32_t kFptBlockBudget = 32768; // draws per pair before the grid phase
+constexpr int kFptBlockThreads = 512;       // threads per pair in the block-per-pair phase
+constexpr int kFptGridThreads = 256;        // threads per block (and attempts per chunk) of the grid phase
+constexpr uint32_t kFptGridGroups = 4;      // block groups of the grid phase, each searching its own pairs
+// control words of one refinement launch: a 64-bit pair counter, then per round of phases 2-4 the
+// queue lengths and work counters of the warp, block and grid phases
+enum : int {
+  kFptPairCtr = 0, kFptRound0 = 8, kFptRoundWords = 8,
+  kFptWarpIn = 0, kFptWarpNext = 1, kFptBlockIn = 2, kFptBlockNext = 3, kFptGridIn = 4,
+  kFptCtlWords = kFptRound0 + kFptRoundWords * (kFptMaxLevels + 1)
+};
+struct FptItem {                            // a pair's state when it moves to a later phase
+  double Ri, Rf, t;
+  uint32_t k, b, a, l;
+};
+struct FptSearch {                          // the grid phase's search state of one pair
+  uint32_t next_chunk, winner, exited, pad;
+};
 void launch_first_passage(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
-                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, int max_grid,
+                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, FptItem* warp_q[2],
+                          FptItem* block_q, FptItem* grid_q, FptSearch* search, uint32_t* qctl, int device_sms,
                           cudaStream_t s);
 
 }  // namespace rd

@@ -59,7 +59,31 @@ def _compare(system, levels, n, seed, rule=0):
 
 @pytest.mark.parametrize("levels", [1, 6, 16])
 def test_refinement_matches_oracle_3d(levels):
-    _compare(W.reversible_3d(), levels, 4000, seed=levels)
+    g, _ = _compare(W.reversible_3d(), levels, 4000, seed=levels)
+    if levels == 16:                         # pairs finished in each of the three phases
+        assert (g["attempts"] <= 256).any() and ((g["attempts"] > 256) & (g["attempts"] <= 4352)).any()
+        assert (g["attempts"] > 4352).any()
+
+
+def test_heavy_pairs_match_oracle():
+    # p_enc ~ 1.3e-5: tens to hundreds of thousands of draws, through the warp, block and grid phases
+    system = W.reversible_3d()
+    sigma, tau = _rule_scale(system)
+    n, R = 8, 4.0
+    dev = torch.device("cuda")
+    sim = pkg.Simulation(system, precision="fp64")
+    g = sim.first_passage(torch.full((n,), R * sigma, dtype=torch.float64, device=dev),
+                          torch.full((n,), R * sigma, dtype=torch.float64, device=dev),
+                          torch.arange(n, dtype=torch.int64, device=dev), 6)
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    sim.close()
+    o = O.fpt_refine_batch(3, np.full(n, R), np.full(n, R), tau, 6, system.seed, np.arange(n, dtype=np.uint64))
+    assert np.all(o["margin"] > MARGIN)
+    assert np.array_equal(g["bin"].view(np.uint32), o["bin"])
+    assert np.array_equal(g["attempts"].astype(np.uint32), o["attempts"])
+    np.testing.assert_allclose(g["r_lo"], o["R_lo"] * sigma, rtol=1e-11, atol=0)
+    np.testing.assert_allclose(g["r_hi"], o["R_hi"] * sigma, rtol=1e-11, atol=0)
+    assert (o["attempts"] > 32768).sum() >= 2 and ((o["attempts"] > 4352) & (o["attempts"] <= 32768)).any()
 
 
 def test_refinement_matches_oracle_3d_absorbing_rule():
@@ -87,6 +111,9 @@ def test_degenerate_inputs():
     assert g["bin"][1].item() == 0 and g["attempts"][1].item() == 10     # in contact at the start
     g = sim.first_passage(r0[2:], r[2:], st[2:], 4, max_attempts=16)       # p_enc ~ 1e-30: bound hit
     assert g["bin"].item() == -1 and g["attempts"].item() == 16 and math.isnan(g["r_lo"].item())
+    for bound in (1000, 6000, 40000):   # bound hit in the warp, block and grid phases
+        g = sim.first_passage(r0[2:], r[2:], st[2:], 4, max_attempts=bound)
+        assert g["bin"].item() == -1 and g["attempts"].item() == bound and math.isnan(g["r_hi"].item())
     e = torch.empty(0, dtype=torch.float64, device=dev)
     g = sim.first_passage(e, e, torch.empty(0, dtype=torch.int64, device=dev), 5)
     assert g["bin"].numel() == 0
