@@ -1079,8 +1079,10 @@ static void fpt_draw(uint64_t seed, uint64_t strm, uint32_t a, uint32_t w, doubl
 
 /* 3D: 1 - cos(theta) for a von Mises-Fisher direction with concentration kappa, from the CDF   */
 /* F(w) = (e^{kappa w} - e^{-kappa}) / (e^{kappa} - e^{-kappa}) inverted at 1 - u:               */
-/* 1 - w = -log(1 + (1 - u) (e^{-2 kappa} - 1)) / kappa.                                          */
+/* 1 - w = -log(u + (1 - u) e^{-2 kappa}) / kappa, evaluated as written for u <= 1/2 and as       */
+/* -log1p((1 - u) expm1(-2 kappa)) / kappa above (no cancellation in either range).               */
 static double vmf3_one_minus_cos(double kappa, double u) {
+  if (u <= 0.5) return -log(u + (1.0 - u) * exp(-2.0 * kappa)) / kappa;
   return -log1p((1.0 - u) * expm1(-2.0 * kappa)) / kappa;
 }
 
