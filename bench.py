@@ -492,13 +492,14 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
 
 def fpt_measurement(args, torch, pkg, flush, levels=10):
     """First-passage refinement (rd_first_passage) of 2^20 encountered pairs of the headline rule,
-    device-timed, with the oracle on a sample of the same pairs beside it."""
+    FP64 and FP32 (mixed handle), device-timed, with the oracle on a sample of the same pairs beside it."""
     from paper_1107_0270_gb300 import fpt_bench
 
     system = workload(args, seed=2)
     r0e, re, distinct = fpt_bench.encountered_pairs(pkg, torch, system, 1 << 20)
-    res = fpt_bench.time_refinement(pkg, torch, system, r0e, re, levels, flush=flush)
-    res["distinct_pairs"] = distinct
+    res = {"distinct_pairs": distinct}
+    for prec in ("fp64", "mixed"):
+        res[prec] = fpt_bench.time_refinement(pkg, torch, system, r0e, re, levels, flush=flush, precision=prec)
     # CPU baseline: the oracle on a bounded sample of the same pairs, one host thread
     import oracle as O
 

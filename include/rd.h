@@ -196,6 +196,10 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
  * Random numbers: Philox4x32-10 with the handle's seed, counter (stream[k] low word, high word,
  * attempt, 13 | word << 8).  Pointers are DEVICE pointers: r0, r (double, physical lengths),
  * stream (uint64), bin (uint32) required; r_lo, r_hi (double), attempts (uint32) may be NULL.
+ * Precision: FP64, except on a mixed-precision handle in 3D, where every draw is evaluated in FP32
+ * on contact distances R - 1 (the same Philox words; decisions agree with FP64 ones except within
+ * about 1e-6 of their thresholds, separations to about 1e-6 relative).  Negative separations are
+ * read as 0.
  * In 2D the half intervals longer than tau_s use Weber quadrature nodes built on the first call
  * for each (rule, levels) (allocation and a synchronisation then); accuracy holds for
  * separations up to the rule's cut-off plus 13 sqrt(D dt).  n < 2^32.  Asynchronous on the handle's

@@ -1052,6 +1052,7 @@ int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double*
   FptArgs A{};
   A.dim = h->cfg.dim;
   A.levels = levels;
+  A.f32 = h->cfg.precision == RD_MIXED && h->cfg.dim == 3;
   A.max_attempts = max_attempts ? max_attempts : RD_FPT_MAX_ATTEMPTS;
   A.seed_lo = h->hp.seed_lo;
   A.seed_hi = h->hp.seed_hi;

@@ -30,6 +30,14 @@ __device__ __forceinline__ void fpt_draw(const FptArgs& A, uint64_t strm, uint32
   u1 = u52(o.z, o.w);
 }
 
+// 3D von Mises-Fisher direction: 1 - cos(theta) = -log(u + (1 - u) e^{-2 kappa}) / kappa (the CDF
+// inverted at 1 - u), as written for u <= 1/2 and through log1p/expm1 above, so that neither range
+// cancels.
+__device__ __forceinline__ double vmf3_omc(double kappa, double u) {
+  if (u <= 0.5) return -log(u + (1.0 - u) * exp(-2.0 * kappa)) / kappa;
+  return -log1p((1.0 - u) * expm1(-2.0 * kappa)) / kappa;
+}
+
 // von Mises angle (Best & Fisher 1979) as (1 - cos, sin), with the differences r - f and 1 - f
 // formed from 1 - rho so that large kappa keeps its digits; false when all trials were rejected.
 __device__ bool vm2_draw(const FptArgs& A, double kappa, uint64_t strm, uint32_t a, double& omc, double& sn) {
@@ -106,7 +114,7 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
   const double kappa = Ri * Rf / (2.0 * t);
   double omc, sn;
   if (A.dim == 3) {
-    omc = -log1p((1.0 - u_dir) * expm1(-2.0 * kappa)) / kappa;
+    omc = vmf3_omc(kappa, u_dir);
     sn = sqrt(omc * (2.0 - omc));
   } else if (!vm2_draw(A, kappa, strm, a, omc, sn)) {
     return -1;
@@ -121,9 +129,80 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
   return 0;
 }
 
-__device__ __forceinline__ void fpt_write(const FptArgs& A, int64_t k, bool ok, uint32_t b, uint32_t a, double Ri,
-                                          double Rf, uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts) {
+// FP32 form of one attempt (3D, mixed-precision handles).  It reads the same Philox words as the
+// FP64 form (each uniform is the FP64 one rounded to FP32) and carries contact
+// distances d = R - 1, so that separations near contact keep their digits: with the midpoint
+// m = (1 + e0, m1, m2) in the frame of r_i, |m|^2 - 1 = e0 (2 + e0) + m1^2 + m2^2 and
+// d_m = (|m|^2 - 1) / (|m| + 1).
+// the FP64 uniform ((x >> 12) + 1/2) 2^-52 of x = hi:lo, rounded once to FP32 (integer conversion,
+// no FP64 arithmetic)
+__device__ __forceinline__ float fpt_uf(uint32_t hi, uint32_t lo) {
+  const unsigned long long m = ((((unsigned long long)hi << 32) | lo) >> 12) * 2ull + 1ull;
+  return __ull2float_rn(m) * 0x1p-53f;
+}
+
+__device__ __forceinline__ void fpt_draw_f(const FptArgs& A, uint64_t strm, uint32_t a, uint32_t w, float& u0,
+                                           float& u1) {
+  const uint4 o = philox(make_uint4((uint32_t)strm, (uint32_t)(strm >> 32), a, TAG_FPT | (w << 8)), A.seed_lo,
+                         A.seed_hi);
+  u0 = fpt_uf(o.x, o.y);
+  u1 = fpt_uf(o.z, o.w);
+}
+
+// p_enc in 3D from contact distances (FP32); the expm1 ratio is 1 to within 2e-9 once
+// (d + d0 + 1) / tau > 20.
+__device__ __forceinline__ float fpt_p_enc3_f(float d, float d0, float inv_tau) {
+  if (d <= 0.0f) return 1.0f;
+  if (d0 < 0.0f) d0 = 0.0f;
+  if ((d + d0 + 1.0f) * inv_tau > 20.0f) return expf(-d * d0 * inv_tau);
+  return p_enc3_f(d, d0, inv_tau);
+}
+
+__device__ __forceinline__ int fpt_attempt_f(const FptArgs& A, uint64_t strm, uint32_t a, float di, float df, float t,
+                                             float& dm) {
+  float u_dir, u_e1, u_e2, unused, v0, v1, x0, x1, x2, x3;
+  fpt_draw_f(A, strm, a, 0, u_dir, u_e1);
+  fpt_draw_f(A, strm, a, 1, v0, v1);
+  box_muller_f(v0, v1, x0, x1);
+  fpt_draw_f(A, strm, a, 2, v0, v1);
+  box_muller_f(v0, v1, x2, x3);
+  fpt_draw_f(A, strm, a, 3, u_e2, unused);
+  const float Rf = 1.0f + df;
+  const float kappa = (1.0f + di) * Rf / (2.0f * t);
+  const float omc = u_dir <= 0.5f ? -logf(u_dir + (1.0f - u_dir) * expf(-2.0f * kappa)) / kappa
+                                  : -log1pf((1.0f - u_dir) * expm1f(-2.0f * kappa)) / kappa;
+  const float sn = sqrtf(omc * (2.0f - omc));
+  const float sd = sqrtf(0.5f * t);
+  const float e0 = 0.5f * (di + df) - 0.5f * Rf * omc + sd * x0;
+  const float m1 = 0.5f * Rf * sn + sd * x1;
+  const float m2 = sd * x2;
+  const float q = e0 * (2.0f + e0) + m1 * m1 + m2 * m2;
+  dm = q / (sqrtf(1.0f + q) + 1.0f);
+  const float inv_h = 2.0f / t;
+  if (u_e1 < fpt_p_enc3_f(dm, di, inv_h)) return 1;
+  if (u_e2 < fpt_p_enc3_f(df, dm, inv_h)) return 2;
+  return 0;
+}
+
+// The precision dispatch: the FP64 form works on separations R, the FP32 form on d = R - 1.
+template <bool F32>
+__device__ __forceinline__ int fpt_attempt_p(const FptArgs& A, int l, uint64_t strm, uint32_t a, double Xi, double Xf,
+                                             double t, double& Xm) {
+  if constexpr (F32) {
+    float dm;
+    const int r = fpt_attempt_f(A, strm, a, (float)Xi, (float)Xf, (float)t, dm);
+    Xm = (double)dm;
+    return r;
+  } else {
+    return fpt_attempt(A, l, strm, a, Xi, Xf, t, Xm);
+  }
+}
+
+template <bool F32>
+__device__ __forceinline__ void fpt_write(const FptArgs& A, int64_t k, bool ok, uint32_t b, uint32_t a, double Xi,
+                                          double Xf, uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts) {
   const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  const double Ri = F32 ? 1.0 + Xi : Xi, Rf = F32 ? 1.0 + Xf : Xf;
   bin[k] = ok ? b : 0xFFFFFFFFu;
   if (r_lo) r_lo[k] = ok ? Ri * A.sigma : nan;
   if (r_hi) r_hi[k] = ok ? Rf * A.sigma : nan;
@@ -148,6 +227,7 @@ __device__ __forceinline__ FptItem fpt_item(double Ri, double Rf, double t, uint
 // stay busy whatever the draw counts of their pairs.  A pair that needs more than `budget` draws
 // is queued with its state for phase 2.  The draws are indexed by the attempt number, so where an
 // attempt runs does not change the result.
+template <bool F32>
 __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const double* __restrict__ r0,
                                                        const double* __restrict__ r,
                                                        const uint64_t* __restrict__ stream, int64_t n,
@@ -177,8 +257,8 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
         if ((int64_t)kk < n) {
           k = (int64_t)kk;
           strm = stream[k];
-          Ri = r0[k] * inv_sigma;
-          Rf = r[k] * inv_sigma;
+          Ri = fmax(r0[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0);     // a separation is not negative
+          Rf = fmax(r[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0);
           t = A.tau;
           b = a = 0;
           l = 0;
@@ -190,12 +270,12 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
     if (__all_sync(0xFFFFFFFFu, done)) break;
     if (done) continue;
     if (l >= A.levels) {
-      fpt_write(A, k, true, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      fpt_write<F32>(A, k, true, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
       need = true;
       continue;
     }
     if (a >= A.max_attempts) {
-      fpt_write(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      fpt_write<F32>(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
       need = true;
       continue;
     }
@@ -205,9 +285,9 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
       continue;
     }
     double Rm;
-    const int d = fpt_attempt(A, l, strm, a, Ri, Rf, t, Rm);
+    const int d = fpt_attempt_p<F32>(A, l, strm, a, Ri, Rf, t, Rm);
     if (d < 0) {                // the attempt that ran out of von Mises trials is not counted
-      fpt_write(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+      fpt_write<F32>(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
       need = true;
       continue;
     }
@@ -229,6 +309,7 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
 // Phase 2: one warp per queued pair; each round the 32 lanes try the next 32 attempts and the
 // lowest-numbered decisive one wins (the attempt the serial loop would stop at).  A pair that has
 // drawn `budget` more times since it was queued moves on to queue_out (phase 3).
+template <bool F32>
 __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, const uint64_t* __restrict__ stream,
                                                             uint32_t* __restrict__ bin, double* __restrict__ r_lo,
                                                             double* __restrict__ r_hi,
@@ -265,7 +346,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
         const uint32_t mine = a + lane;
         double Rm = 0.0;
         int d = 0;
-        if (mine < A.max_attempts) d = fpt_attempt(A, l, strm, mine, Ri, Rf, t, Rm);
+        if (mine < A.max_attempts) d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
         const unsigned m = __ballot_sync(0xFFFFFFFFu, d != 0);
         if (m == 0) {
           const uint32_t room = A.max_attempts - a;
@@ -289,7 +370,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
       }
       t *= 0.5;
     }
-    if (!moved && lane == 0) fpt_write(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+    if (!moved && lane == 0) fpt_write<F32>(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
   }
 }
 
@@ -298,6 +379,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
 // decisive attempt of a round wins.  Stops after `budget` draws.  Shared scratch: s_win, s_rm, s_dec.
 // Returns 0 (all levels done), 1 (failed: attempt bound or von Mises trials) or 2 (budget reached;
 // the state is that of level l).
+template <bool F32>
 __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri, double& Rf, double& t, uint32_t& b,
                             uint32_t& a, uint32_t budget, uint32_t* s_win, double* s_rm, int* s_dec) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x, a0 = a;
@@ -314,7 +396,7 @@ __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri,
       double Rm = 0.0;
       int d = 0;
       if (tid < width && mine < A.max_attempts) {
-        d = fpt_attempt(A, l, strm, mine, Ri, Rf, t, Rm);
+        d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
         if (d != 0) atomicMin(s_win, tid);
       }
       __syncthreads();
@@ -350,6 +432,7 @@ __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri,
 // Phase 3: one block per pair that needs thousands of draws (work counter over the queue); a pair
 // that has drawn `budget` more times since it was queued moves on to the grid phase with a fresh
 // search record.
+template <bool F32>
 __global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
     const FptArgs A, const uint64_t* __restrict__ stream, uint32_t* __restrict__ bin, double* __restrict__ r_lo,
     double* __restrict__ r_hi, uint32_t* __restrict__ attempts, const FptItem* __restrict__ queue,
@@ -370,7 +453,7 @@ __global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
     double Ri = it.Ri, Rf = it.Rf, t = it.t;
     uint32_t b = it.b, a = it.a;
     int l = (int)it.l;
-    const int st = block_levels(A, strm, l, Ri, Rf, t, b, a, budget, &s_win, &s_rm, &s_dec);
+    const int st = block_levels<F32>(A, strm, l, Ri, Rf, t, b, a, budget, &s_win, &s_rm, &s_dec);
     if (tid == 0) {
       if (st == 2) {
         const uint32_t j = atomicAdd(&qctl[words + kFptGridIn], 1u);
@@ -382,7 +465,7 @@ __global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
         z.pad = 0;
         search[j] = z;
       } else {
-        fpt_write(A, it.k, st == 0, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+        fpt_write<F32>(A, it.k, st == 0, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
       }
     }
     __syncthreads();
@@ -398,6 +481,7 @@ __global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
 // every attempt below the winner has been tried and the winner is the attempt the serial loop
 // would stop at; that block replays it and queues the pair's next level for the next round of
 // phases 2-4.  No block waits for another.
+template <bool F32>
 __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
     const FptArgs A, const uint64_t* __restrict__ stream, uint32_t* __restrict__ bin, double* __restrict__ r_lo,
     double* __restrict__ r_hi, uint32_t* __restrict__ attempts, const FptItem* __restrict__ queue,
@@ -428,7 +512,7 @@ __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
       const unsigned long long mine = (unsigned long long)it.a + (unsigned long long)s_chunk * nt + tid;
       if (mine < A.max_attempts) {
         double Rm;
-        const int d = fpt_attempt(A, (int)it.l, strm, (uint32_t)mine, it.Ri, it.Rf, it.t, Rm);
+        const int d = fpt_attempt_p<F32>(A, (int)it.l, strm, (uint32_t)mine, it.Ri, it.Rf, it.t, Rm);
         if (d != 0) atomicMin(&sr->winner, (uint32_t)mine);
       }
       __syncthreads();
@@ -446,7 +530,7 @@ __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
       bool ok = false;
       if (win != 0xFFFFFFFFu) {           // replay the winning attempt
         double Rm;
-        const int dw = fpt_attempt(A, (int)it.l, strm, win, Ri, Rf, it.t, Rm);
+        const int dw = fpt_attempt_p<F32>(A, (int)it.l, strm, win, Ri, Rf, it.t, Rm);
         a = dw < 0 ? win : win + 1;
         ok = dw >= 0;
         if (dw == 1) {
@@ -461,13 +545,14 @@ __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
         queue_next[atomicAdd(&qctl[words + kFptRoundWords + kFptWarpIn], 1u)] =
             fpt_item(Ri, Rf, 0.5 * it.t, it.k, b, a, (int)it.l + 1);
       else
-        fpt_write(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+        fpt_write<F32>(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
     }
     __syncthreads();
   }
 }
 
-void launch_first_passage(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
+template <bool F32>
+static void launch_fpt(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
                           uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, FptItem* warp_q[2],
                           FptItem* block_q, FptItem* grid_q, FptSearch* search, uint32_t* qctl, int device_sms,
                           cudaStream_t s) {
@@ -475,19 +560,30 @@ void launch_first_passage(const FptArgs& A, const double* r0, const double* r, c
   const unsigned gw = clamp((n + 1023) / 1024, (int64_t)device_sms * 4);
   const unsigned gb = clamp((n + 4095) / 4096, (int64_t)device_sms * 2);
   cudaMemsetAsync(qctl, 0, kFptCtlWords * sizeof(uint32_t), s);
-  k_first_passage<<<clamp((n + 127) / 128, (int64_t)device_sms * 4), 128, 0, s>>>(
+  k_first_passage<F32><<<clamp((n + 127) / 128, (int64_t)device_sms * 4), 128, 0, s>>>(
       A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q[0], qctl, kFptBudget);
   // one round of phases 2-4 per level: a pair whose current level is hard goes through them once
   // more at a later level; a round with nothing queued ends at once
   for (int round = 0; round < A.levels; ++round) {
     const int w = kFptRound0 + round * kFptRoundWords;
-    k_first_passage_warp<<<gw, 128, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, warp_q[round & 1], w + kFptWarpIn,
+    k_first_passage_warp<F32><<<gw, 128, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, warp_q[round & 1], w + kFptWarpIn,
                                             w + kFptWarpNext, block_q, w + kFptBlockIn, qctl, kFptWarpBudget);
-    k_first_passage_block<<<gb, kFptBlockThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, block_q, grid_q,
+    k_first_passage_block<F32><<<gb, kFptBlockThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, block_q, grid_q,
                                                           search, qctl, w, kFptBlockBudget);
-    k_first_passage_grid<<<gb, kFptGridThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, grid_q, search,
+    k_first_passage_grid<F32><<<gb, kFptGridThreads, 0, s>>>(A, stream, bin, r_lo, r_hi, attempts, grid_q, search,
                                                         warp_q[(round + 1) & 1], qctl, w);
   }
+}
+
+void launch_first_passage(const FptArgs& A, const double* r0, const double* r, const uint64_t* stream, int64_t n,
+                          uint32_t* bin, double* r_lo, double* r_hi, uint32_t* attempts, FptItem* warp_q[2],
+                          FptItem* block_q, FptItem* grid_q, FptSearch* search, uint32_t* qctl, int device_sms,
+                          cudaStream_t s) {
+  if (A.f32)
+    launch_fpt<true>(A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q, block_q, grid_q, search, qctl, device_sms, s);
+  else
+    launch_fpt<false>(A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q, block_q, grid_q, search, qctl, device_sms,
+                      s);
 }
 
 }  // namespace rd

@@ -118,6 +118,7 @@ struct FptLevel {              // p_enc data of the half intervals of level l (2
 };
 struct FptArgs {
   int dim, levels;
+  int f32;                     // 3D in FP32 on contact distances (mixed-precision handles)
   uint32_t max_attempts;
   uint32_t seed_lo, seed_hi;
   double tau;                  // D dt / sigma^2 of the rule

@@ -34,10 +34,11 @@ def encountered_pairs(pkg, torch, system, n, seed=11):
     return r0e.repeat(reps)[:n].contiguous(), re.repeat(reps)[:n].contiguous(), distinct
 
 
-def time_refinement(pkg, torch, system, r0e, re, levels, reps=5, warmup=3, flush=None):
+def time_refinement(pkg, torch, system, r0e, re, levels, reps=5, warmup=3, flush=None, precision="fp64"):
     """Median device time of rd_first_passage over `reps` launches (CUDA events on the handle's
-    stream; the L2 is overwritten between launches when `flush` is given)."""
-    sim = pkg.Simulation(system, precision="fp64")
+    stream; the L2 is overwritten between launches when `flush` is given).  precision "mixed"
+    selects the FP32 evaluation (3D)."""
+    sim = pkg.Simulation(system, precision=precision)
     n = r0e.numel()
     streams = torch.arange(n, dtype=torch.int64, device="cuda")
     for _ in range(warmup):
@@ -79,11 +80,13 @@ def main(argv=None):
     ap.add_argument("--pairs", type=int, default=1 << 20)
     ap.add_argument("--levels", type=int, default=10)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     a = ap.parse_args(argv)
     system = W.reversible_3d(seed=2)
     flush = torch.empty(512 << 18, dtype=torch.float32, device="cuda")
     r0e, re, distinct = encountered_pairs(pkg, torch, system, a.pairs)
-    res = time_refinement(pkg, torch, system, r0e, re, a.levels, reps=a.reps, flush=flush)
+    res = time_refinement(pkg, torch, system, r0e, re, a.levels, reps=a.reps, flush=flush, precision=a.precision)
+    res["precision"] = a.precision
     res["distinct_pairs"] = distinct
     print(json.dumps(res))
 

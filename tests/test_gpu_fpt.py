@@ -19,6 +19,9 @@ if not torch.cuda.is_available():
 import paper_1107_0270_gb300 as pkg  # noqa: E402
 
 MARGIN = 1e-9      # decisions closer than this to their threshold may flip with the last bits of p_enc
+# FP32 refinement (mixed handles, 3D): p_enc in FP32 is within 2e-6 of the FP64 value and the
+# uniforms within 2^-24 relative, so decisions are compared where they are 2e-5 from the threshold
+MARGIN_F32 = 2e-5
 
 
 def _rule_scale(system, rule=0):
@@ -31,16 +34,16 @@ def _inputs(n, sigma, tau, seed):
     rng = np.random.default_rng(seed)
     s = math.sqrt(tau)
     R0 = 1.0 + np.abs(rng.normal(0.0, 0.7 * s, n))
-    R = 1.0 + rng.normal(0.3 * s, 0.8 * s, n)          # some end inside the contact sphere
+    R = np.abs(1.0 + rng.normal(0.3 * s, 0.8 * s, n))  # some end inside the contact sphere
     R0[: max(1, n // 50)] = 1.0                         # a few start in contact
     streams = (np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)) ^ np.uint64(0xABCDEF0123456789)
     return R0 * sigma, R * sigma, streams
 
 
-def _compare(system, levels, n, seed, rule=0):
+def _compare(system, levels, n, seed, rule=0, precision="fp64"):
     sigma, tau = _rule_scale(system, rule)
     r0, r, streams = _inputs(n, sigma, tau, seed)
-    sim = pkg.Simulation(system, precision="fp64")
+    sim = pkg.Simulation(system, precision=precision)
     dev = torch.device("cuda")
     g = sim.first_passage(torch.tensor(r0, device=dev), torch.tensor(r, device=dev),
                           torch.tensor(streams.view(np.int64), device=dev), levels, rule=rule)
@@ -48,12 +51,13 @@ def _compare(system, levels, n, seed, rule=0):
     sim.close()
     o = O.fpt_refine_batch(system.dim, r0 / sigma, r / sigma, tau, levels, system.seed, streams,
                            tau_s=system.tau_s)
-    sure = o["margin"] > MARGIN
-    assert sure.mean() > 0.98
+    f32 = precision == "mixed" and system.dim == 3
+    sure = o["margin"] > (MARGIN_F32 if f32 else MARGIN)
+    assert sure.mean() > 0.97
     assert np.array_equal(g["bin"].view(np.uint32)[sure], o["bin"][sure])
     assert np.array_equal(g["attempts"][sure].astype(np.uint32), o["attempts"][sure])
     for k, ko in (("r_lo", "R_lo"), ("r_hi", "R_hi")):
-        np.testing.assert_allclose(g[k][sure], o[ko][sure] * sigma, rtol=1e-11, atol=0)
+        np.testing.assert_allclose(g[k][sure], o[ko][sure] * sigma, rtol=2e-5 if f32 else 1e-11, atol=0)
     return g, o
 
 
@@ -84,6 +88,13 @@ def test_heavy_pairs_match_oracle():
     np.testing.assert_allclose(g["r_lo"], o["R_lo"] * sigma, rtol=1e-11, atol=0)
     np.testing.assert_allclose(g["r_hi"], o["R_hi"] * sigma, rtol=1e-11, atol=0)
     assert (o["attempts"] > 32768).sum() >= 2 and ((o["attempts"] > 4352) & (o["attempts"] <= 32768)).any()
+
+
+@pytest.mark.parametrize("levels", [6, 16])
+def test_refinement_fp32_matches_oracle_3d(levels):
+    g, _ = _compare(W.reversible_3d(), levels, 4000, seed=10 + levels, precision="mixed")
+    if levels == 16:
+        assert (g["attempts"] > 4352).any()
 
 
 def test_refinement_matches_oracle_3d_absorbing_rule():
@@ -136,12 +147,13 @@ def _bin_probs3(R0, R, tau, K):
                      for a, b in zip(edges[:-1], edges[1:])])
 
 
-def test_bin_law_at_scale_3d():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bin_law_at_scale_3d(precision):
     system = W.reversible_3d()
     sigma, tau = _rule_scale(system)
     n, K, R0, R = 1 << 20, 5, 1.2, 1.35
     dev = torch.device("cuda")
-    sim = pkg.Simulation(system, precision="fp64")
+    sim = pkg.Simulation(system, precision=precision)
     g = sim.first_passage(torch.full((n,), R0 * sigma, dtype=torch.float64, device=dev),
                           torch.full((n,), R * sigma, dtype=torch.float64, device=dev),
                           torch.arange(n, dtype=torch.int64, device=dev), K)
