@@ -15,6 +15,8 @@
 // Random numbers: Philox4x32-10, key = seed, counter (stream lo, stream hi, a, TAG_FPT | w << 8)
 // with a the pair's attempt number over all levels and w: 0 = (U_dir, U_e1), 1 = two normals,
 // 2 = a third normal (3D), 3 = U_e2, 4 + j = the j-th von Mises trial (2D, j < 64).
+#include <type_traits>
+
 #include "rd_gf2d.cuh"
 #include "rd_kernels.h"
 
@@ -110,7 +112,6 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
     fpt_draw(A, strm, a, 2, v0, v1);
     box_muller(v0, v1, x2, x3);
   }
-  fpt_draw(A, strm, a, 3, u_e2, unused);
   const double kappa = Ri * Rf / (2.0 * t);
   double omc, sn;
   if (A.dim == 3) {
@@ -125,6 +126,7 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
   const double m2 = sd * x2;
   Rm = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
   if (u_e1 < fpt_p_enc(A, l, Rm, Ri, 0.5 * t)) return 1;
+  fpt_draw(A, strm, a, 3, u_e2, unused);       // the second half's draw, needed only now
   if (u_e2 < fpt_p_enc(A, l, Rf, Rm, 0.5 * t)) return 2;
   return 0;
 }
@@ -134,11 +136,10 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
 // distances d = R - 1, so that separations near contact keep their digits: with the midpoint
 // m = (1 + e0, m1, m2) in the frame of r_i, |m|^2 - 1 = e0 (2 + e0) + m1^2 + m2^2 and
 // d_m = (|m|^2 - 1) / (|m| + 1).
-// the FP64 uniform ((x >> 12) + 1/2) 2^-52 of x = hi:lo, rounded once to FP32 (integer conversion,
-// no FP64 arithmetic)
+// the FP64 uniform ((x >> 12) + 1/2) 2^-52 of x = hi:lo as hi 2^-32 + ((lo >> 12) + 1/2) 2^-52 in
+// FP32 (32-bit conversions only; within one FP32 rounding of the FP64 value)
 __device__ __forceinline__ float fpt_uf(uint32_t hi, uint32_t lo) {
-  const unsigned long long m = ((((unsigned long long)hi << 32) | lo) >> 12) * 2ull + 1ull;
-  return __ull2float_rn(m) * 0x1p-53f;
+  return fmaf(__uint2float_rn(hi), 0x1p-32f, (__uint2float_rn(lo >> 12) + 0.5f) * 0x1p-52f);
 }
 
 __device__ __forceinline__ void fpt_draw_f(const FptArgs& A, uint64_t strm, uint32_t a, uint32_t w, float& u0,
@@ -166,7 +167,6 @@ __device__ __forceinline__ int fpt_attempt_f(const FptArgs& A, uint64_t strm, ui
   box_muller_f(v0, v1, x0, x1);
   fpt_draw_f(A, strm, a, 2, v0, v1);
   box_muller_f(v0, v1, x2, x3);
-  fpt_draw_f(A, strm, a, 3, u_e2, unused);
   const float Rf = 1.0f + df;
   const float kappa = (1.0f + di) * Rf / (2.0f * t);
   const float omc = u_dir <= 0.5f ? -logf(u_dir + (1.0f - u_dir) * expf(-2.0f * kappa)) / kappa
@@ -180,22 +180,23 @@ __device__ __forceinline__ int fpt_attempt_f(const FptArgs& A, uint64_t strm, ui
   dm = q / (sqrtf(1.0f + q) + 1.0f);
   const float inv_h = 2.0f / t;
   if (u_e1 < fpt_p_enc3_f(dm, di, inv_h)) return 1;
+  fpt_draw_f(A, strm, a, 3, u_e2, unused);     // the second half's draw, needed only now
   if (u_e2 < fpt_p_enc3_f(df, dm, inv_h)) return 2;
   return 0;
 }
 
-// The precision dispatch: the FP64 form works on separations R, the FP32 form on d = R - 1.
+// The precision dispatch: the FP64 form works on separations R, the FP32 form on d = R - 1; the
+// interval state (Xi, Xf, t) is kept in the form's own type.
 template <bool F32>
-__device__ __forceinline__ int fpt_attempt_p(const FptArgs& A, int l, uint64_t strm, uint32_t a, double Xi, double Xf,
-                                             double t, double& Xm) {
-  if constexpr (F32) {
-    float dm;
-    const int r = fpt_attempt_f(A, strm, a, (float)Xi, (float)Xf, (float)t, dm);
-    Xm = (double)dm;
-    return r;
-  } else {
+using fpt_real = typename std::conditional<F32, float, double>::type;
+
+template <bool F32>
+__device__ __forceinline__ int fpt_attempt_p(const FptArgs& A, int l, uint64_t strm, uint32_t a, fpt_real<F32> Xi,
+                                             fpt_real<F32> Xf, fpt_real<F32> t, fpt_real<F32>& Xm) {
+  if constexpr (F32)
+    return fpt_attempt_f(A, strm, a, Xi, Xf, t, Xm);
+  else
     return fpt_attempt(A, l, strm, a, Xi, Xf, t, Xm);
-  }
 }
 
 template <bool F32>
@@ -237,9 +238,10 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
                                                        uint32_t budget) {
   const uint32_t lane = threadIdx.x & 31u;
   const double inv_sigma = 1.0 / A.sigma;
+  using real = fpt_real<F32>;
   int64_t k = 0;
   uint64_t strm = 0;
-  double Ri = 0.0, Rf = 0.0, t = 0.0;
+  real Ri = 0, Rf = 0, t = 0;
   uint32_t b = 0, a = 0;
   int l = 0;
   bool need = true, done = false;
@@ -257,9 +259,9 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
         if ((int64_t)kk < n) {
           k = (int64_t)kk;
           strm = stream[k];
-          Ri = fmax(r0[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0);     // a separation is not negative
-          Rf = fmax(r[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0);
-          t = A.tau;
+          Ri = (real)(fmax(r0[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0));     // a separation is not negative
+          Rf = (real)(fmax(r[k], 0.0) * inv_sigma - (F32 ? 1.0 : 0.0));
+          t = (real)A.tau;
           b = a = 0;
           l = 0;
         } else {
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
       need = true;
       continue;
     }
-    double Rm;
+    real Rm;
     const int d = fpt_attempt_p<F32>(A, l, strm, a, Ri, Rf, t, Rm);
     if (d < 0) {                // the attempt that ran out of von Mises trials is not counted
       fpt_write<F32>(A, k, false, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
         b = 2 * b + 1;
       }
       ++l;
-      t *= 0.5;
+      t *= (real)0.5;
     }
   }
 }
@@ -325,9 +327,10 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
     if (lane == 0) item = atomicAdd(&qctl[next_word], 1u);
     item = __shfl_sync(0xFFFFFFFFu, item, 0);
     if (item >= *(volatile uint32_t*)&qctl[count_word]) break;
+    using real = fpt_real<F32>;
     const FptItem it = queue[item];
     const uint64_t strm = stream[it.k];
-    double Ri = it.Ri, Rf = it.Rf, t = it.t;
+    real Ri = (real)it.Ri, Rf = (real)it.Rf, t = (real)it.t;
     uint32_t b = it.b, a = it.a;
     bool ok = true, moved = false;
 #pragma unroll 1
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
           break;
         }
         const uint32_t mine = a + lane;
-        double Rm = 0.0;
+        real Rm = 0;
         int d = 0;
         if (mine < A.max_attempts) d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
         const unsigned m = __ballot_sync(0xFFFFFFFFu, d != 0);
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
           continue;
         }
         const int w = __ffs(m) - 1;
-        const double rw = __shfl_sync(0xFFFFFFFFu, Rm, w);
+        const real rw = __shfl_sync(0xFFFFFFFFu, Rm, w);
         const int dw = __shfl_sync(0xFFFFFFFFu, d, w);
         a += dw < 0 ? (uint32_t)w : (uint32_t)w + 1u;
         if (dw < 0) {
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
         }
         break;
       }
-      t *= 0.5;
+      t *= (real)0.5;
     }
     if (!moved && lane == 0) fpt_write<F32>(A, it.k, ok, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
   }
@@ -380,8 +383,10 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
 // Returns 0 (all levels done), 1 (failed: attempt bound or von Mises trials) or 2 (budget reached;
 // the state is that of level l).
 template <bool F32>
-__device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri, double& Rf, double& t, uint32_t& b,
-                            uint32_t& a, uint32_t budget, uint32_t* s_win, double* s_rm, int* s_dec) {
+__device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, fpt_real<F32>& Ri, fpt_real<F32>& Rf,
+                            fpt_real<F32>& t, uint32_t& b, uint32_t& a, uint32_t budget, uint32_t* s_win, double* s_rm,
+                            int* s_dec) {
+  using real = fpt_real<F32>;
   const uint32_t tid = threadIdx.x, nt = blockDim.x, a0 = a;
 #pragma unroll 1
   for (; l < A.levels; ++l) {
@@ -393,7 +398,7 @@ __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri,
       if (tid == 0) *s_win = 0xFFFFFFFFu;
       __syncthreads();
       const uint32_t mine = a + tid;
-      double Rm = 0.0;
+      real Rm = 0;
       int d = 0;
       if (tid < width && mine < A.max_attempts) {
         d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
@@ -416,15 +421,15 @@ __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, double& Ri,
       a += dw < 0 ? w : w + 1;
       if (dw < 0) return 1;
       if (dw == 1) {
-        Rf = *s_rm;
+        Rf = (real)*s_rm;
         b = 2 * b;
       } else {
-        Ri = *s_rm;
+        Ri = (real)*s_rm;
         b = 2 * b + 1;
       }
       break;
     }
-    t *= 0.5;
+    t *= (real)0.5;
   }
   return 0;
 }
@@ -448,9 +453,10 @@ __global__ void __launch_bounds__(kFptBlockThreads) k_first_passage_block(
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= *(volatile uint32_t*)&qctl[words + kFptBlockIn]) break;
+    using real = fpt_real<F32>;
     const FptItem it = queue[item];
     const uint64_t strm = stream[it.k];
-    double Ri = it.Ri, Rf = it.Rf, t = it.t;
+    real Ri = (real)it.Ri, Rf = (real)it.Rf, t = (real)it.t;
     uint32_t b = it.b, a = it.a;
     int l = (int)it.l;
     const int st = block_levels<F32>(A, strm, l, Ri, Rf, t, b, a, budget, &s_win, &s_rm, &s_dec);
@@ -511,8 +517,9 @@ __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
       if (s_stop) break;
       const unsigned long long mine = (unsigned long long)it.a + (unsigned long long)s_chunk * nt + tid;
       if (mine < A.max_attempts) {
-        double Rm;
-        const int d = fpt_attempt_p<F32>(A, (int)it.l, strm, (uint32_t)mine, it.Ri, it.Rf, it.t, Rm);
+        fpt_real<F32> Rm;
+        const int d = fpt_attempt_p<F32>(A, (int)it.l, strm, (uint32_t)mine, (fpt_real<F32>)it.Ri,
+                                         (fpt_real<F32>)it.Rf, (fpt_real<F32>)it.t, Rm);
         if (d != 0) atomicMin(&sr->winner, (uint32_t)mine);
       }
       __syncthreads();
@@ -529,8 +536,9 @@ __global__ void __launch_bounds__(kFptGridThreads) k_first_passage_grid(
       uint32_t b = it.b, a = A.max_attempts;
       bool ok = false;
       if (win != 0xFFFFFFFFu) {           // replay the winning attempt
-        double Rm;
-        const int dw = fpt_attempt_p<F32>(A, (int)it.l, strm, win, Ri, Rf, it.t, Rm);
+        fpt_real<F32> Rm;
+        const int dw = fpt_attempt_p<F32>(A, (int)it.l, strm, win, (fpt_real<F32>)Ri, (fpt_real<F32>)Rf,
+                                          (fpt_real<F32>)it.t, Rm);
         a = dw < 0 ? win : win + 1;
         ok = dw >= 0;
         if (dw == 1) {
@@ -560,7 +568,8 @@ static void launch_fpt(const FptArgs& A, const double* r0, const double* r, cons
   const unsigned gw = clamp((n + 1023) / 1024, (int64_t)device_sms * 4);
   const unsigned gb = clamp((n + 4095) / 4096, (int64_t)device_sms * 2);
   cudaMemsetAsync(qctl, 0, kFptCtlWords * sizeof(uint32_t), s);
-  k_first_passage<F32><<<clamp((n + 127) / 128, (int64_t)device_sms * 4), 128, 0, s>>>(
+  // the FP32 lane phase needs 45 registers a thread, so it keeps twice the blocks resident
+  k_first_passage<F32><<<clamp((n + 127) / 128, (int64_t)device_sms * (F32 ? 8 : 4)), 128, 0, s>>>(
       A, r0, r, stream, n, bin, r_lo, r_hi, attempts, warp_q[0], qctl, kFptBudget);
   // one round of phases 2-4 per level: a pair whose current level is hard goes through them once
   // more at a later level; a round with nothing queued ends at once
