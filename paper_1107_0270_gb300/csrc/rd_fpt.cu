@@ -112,6 +112,7 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
     fpt_draw(A, strm, a, 2, v0, v1);
     box_muller(v0, v1, x2, x3);
   }
+  fpt_draw(A, strm, a, 3, u_e2, unused);
   const double kappa = Ri * Rf / (2.0 * t);
   double omc, sn;
   if (A.dim == 3) {
@@ -126,7 +127,6 @@ __device__ __forceinline__ int fpt_attempt(const FptArgs& A, int l, uint64_t str
   const double m2 = sd * x2;
   Rm = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
   if (u_e1 < fpt_p_enc(A, l, Rm, Ri, 0.5 * t)) return 1;
-  fpt_draw(A, strm, a, 3, u_e2, unused);       // the second half's draw, needed only now
   if (u_e2 < fpt_p_enc(A, l, Rf, Rm, 0.5 * t)) return 2;
   return 0;
 }
@@ -304,6 +304,10 @@ __global__ void __launch_bounds__(128) k_first_passage(const FptArgs A, const do
       }
       ++l;
       t *= (real)0.5;
+      if (l >= A.levels) {      // done: the lane takes its next pair in the next iteration
+        fpt_write<F32>(A, k, true, b, a, Ri, Rf, bin, r_lo, r_hi, attempts);
+        need = true;
+      }
     }
   }
 }
