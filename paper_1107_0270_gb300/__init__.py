@@ -288,7 +288,8 @@ class Simulation:
         (RD_ECAPACITY / RD_ETIMEOUT) is latched, with the code under "status".  out: optional dict
         of caller-owned arrays ("x" (m, 3) float64, "species" int32, "ids" uint32, "replica"
         int32, "next_id" uint32) with room for the current particles (e.g. page-locked buffers);
-        the returned arrays are views of them."""
+        the returned arrays are views of them.  Without a "replica" array in `out` the replica
+        indices are not copied and "replica" is None (a single system needs none)."""
         if out is None:
             n = C.c_int64(self.num_particles())
             x = np.zeros((max(n.value, 1), 3))
@@ -297,7 +298,7 @@ class Simulation:
             rep = np.zeros(max(n.value, 1), np.int32)
             nxt = np.zeros(self.n_replicas, np.uint32)
         else:
-            x, sp, ids, rep, nxt = out["x"], out["species"], out["ids"], out["replica"], out["next_id"]
+            x, sp, ids, rep, nxt = out["x"], out["species"], out["ids"], out.get("replica"), out["next_id"]
             n = C.c_int64(ids.shape[0])
         step = C.c_int64()
         rc = _lib().rd_get_state(self._h, C.byref(n), _ptr(x, C.c_double), _ptr(sp, C.c_int32),
@@ -306,8 +307,8 @@ class Simulation:
         if not (allow_error and rc in (3, 4)):
             _check(rc, "rd_get_state")
         m = n.value
-        return {"x": x[:m], "species": sp[:m], "ids": ids[:m], "replica": rep[:m], "next_id": nxt,
-                "step": step.value, "status": rc}
+        return {"x": x[:m], "species": sp[:m], "ids": ids[:m], "replica": None if rep is None else rep[:m],
+                "next_id": nxt, "step": step.value, "status": rc}
 
     def set_state(self, x, species, ids, replica=None, next_id=None, step: int = 0):
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)

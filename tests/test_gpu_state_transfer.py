@@ -67,3 +67,27 @@ def test_rejected_pinned_state_leaves_the_handle_untouched():
     for k in ("x", "species", "ids", "replica", "next_id"):
         assert np.array_equal(after[k], before[k]), k
     sim.close()
+
+
+def test_single_system_transfer_without_replica_array():
+    # a single system needs no per-particle replica indices: omitted on both sides of the ABI,
+    # the state round trip is the same as with them
+    s = W.reversible_3d(dt=2e-5, seed=4, n_each=400, L=0.6)
+    a = pkg.Simulation(s, precision="mixed")
+    b = pkg.Simulation(s, precision="mixed")
+    a.run(3)
+    full = a.get_state()
+    buf = pinned_buffers(2 * len(full["ids"]) + 64, 1)
+    del buf["replica"]
+    st = a.get_state(out=buf)
+    assert st["replica"] is None
+    for k in ("x", "species", "ids", "next_id"):
+        assert np.array_equal(st[k], full[k]), k
+    b.set_state(st["x"], st["species"], st["ids"], None, st["next_id"], st["step"])
+    a.run(4)
+    b.run(4)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("x", "species", "ids", "replica", "next_id"):
+        assert np.array_equal(sa[k], sb[k]), k
+    a.close()
+    b.close()
