@@ -1,5 +1,5 @@
 // First-passage refinement of encountered pairs (Appendix of the paper, "Relation to first-passage
-// time simulation algorithms"): one thread per pair bisects the step `levels` times.
+// time simulation algorithms"): each pair's step is bisected `levels` times.
 //
 // At each level the separation at the midpoint of the current interval [t0, t0 + t] is drawn from
 // the bridge of the radial process between the interval's end separations R_i, R_f, and the half
@@ -15,6 +15,12 @@
 // Random numbers: Philox4x32-10, key = seed, counter (stream lo, stream hi, a, TAG_FPT | w << 8)
 // with a the pair's attempt number over all levels and w: 0 = (U_dir, U_e1), 1 = two normals,
 // 2 = a third normal (3D), 3 = U_e2, 4 + j = the j-th von Mises trial (2D, j < 64).
+//
+// The number of draws a pair needs is heavy-tailed (about 1/p_enc at the first level), so the
+// attempts of a pair run in four tiers by count: a lane (phase 1), a warp (2), a block (3) and a
+// group of blocks (4); since draws are indexed by the attempt number and the lowest-numbered
+// decisive attempt always wins, every tier reproduces the serial loop.  On mixed-precision handles
+// in 3D an attempt is evaluated in FP32 on contact distances (fpt_attempt_f), otherwise in FP64.
 #include <type_traits>
 
 #include "rd_gf2d.cuh"
