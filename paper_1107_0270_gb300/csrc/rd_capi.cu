@@ -83,6 +83,20 @@ static void* dev_alloc(rd_handle* h, size_t bytes) {
   return p;
 }
 
+// Returns one allocation of dev_alloc (stream-ordered: work already queued on the stream that uses
+// it runs first).
+static void dev_release(rd_handle* h, void* p) {
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    if (h->allocs[i].first != p) continue;
+    if (h->cfg.allocator.release)
+      h->cfg.allocator.release(p, h->allocs[i].second, (void*)h->stream, h->cfg.allocator.ctx);
+    else if (!h->cfg.allocator.alloc)
+      cudaFreeAsync(p, h->stream);
+    h->allocs.erase(h->allocs.begin() + i);
+    return;
+  }
+}
+
 static void free_all(rd_handle* h) {
   for (auto& a : h->allocs) {
     if (h->cfg.allocator.release)
@@ -1084,6 +1098,7 @@ int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double*
     // each queue holds a pair at most once per round, so n entries per queue suffice
     void* q = dev_alloc(h, 4 * (size_t)n * sizeof(FptItem) + (size_t)n * sizeof(FptSearch));
     if (!q) return RD_ENOMEM;
+    if (h->fpt_queue) dev_release(h, h->fpt_queue);
     if (!h->fpt_qctl) {
       h->fpt_qctl = (uint32_t*)dev_alloc(h, kFptCtlWords * sizeof(uint32_t));
       if (!h->fpt_qctl) return RD_ENOMEM;

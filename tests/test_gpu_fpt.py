@@ -107,6 +107,24 @@ def test_refinement_matches_oracle_2d():
     _compare(W.membrane_2d(), 8, 300, seed=4)
 
 
+def test_growing_batches_on_one_handle():
+    # a larger batch than before replaces the work queues; results equal a fresh handle's
+    system = W.reversible_3d()
+    sigma, tau = _rule_scale(system)
+    dev = torch.device("cuda")
+    r0, r, streams = _inputs(5000, sigma, tau, seed=21)
+    args = [torch.tensor(v, device=dev) for v in (r0, r, streams.view(np.int64))]
+    sim = pkg.Simulation(system, precision="fp64")
+    for n in (100, 5000):
+        g = sim.first_passage(*(a[:n] for a in args), 8)
+    fresh = pkg.Simulation(system, precision="fp64")
+    h = fresh.first_passage(*args, 8)
+    for k in ("bin", "r_lo", "r_hi", "attempts"):
+        assert torch.equal(g[k], h[k]), k
+    sim.close()
+    fresh.close()
+
+
 def test_degenerate_inputs():
     system = W.reversible_3d()
     sigma, tau = _rule_scale(system)
