@@ -202,8 +202,9 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
  * read as 0.
  * In 2D the half intervals longer than tau_s use Weber quadrature nodes built on the first call
  * for each (rule, levels) (allocation and a synchronisation then); accuracy holds for
- * separations up to the rule's cut-off plus 13 sqrt(D dt).  n < 2^32.  Asynchronous on the handle's
- * stream. */
+ * separations up to the rule's cut-off plus 13 sqrt(D dt).  n < 2^32.  A call with more pairs than
+ * any before on the handle allocates its work queues (136 bytes per pair, through the handle's
+ * allocator) and releases the previous ones.  Asynchronous on the handle's stream. */
 #define RD_FPT_MAX_ATTEMPTS (1u << 20)
 int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double* r,
                      const uint64_t* stream, int64_t n, int32_t levels, uint32_t max_attempts,
