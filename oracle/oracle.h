@@ -3,8 +3,9 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's CPU-baseline
  * leg may load or call this library.  It shares no code, header, table or helper with the CUDA
- * library; it is written from the paper (Sections 2-4) and from the published definitions of the
- * algorithms it uses (Philox4x32-10, Box-Muller, the erfc continued fraction).
+ * library; it is written from the paper (Sections 2-4 and the Appendix) and from the published
+ * definitions of the algorithms it uses (Philox4x32-10, Box-Muller, the erfc continued fraction,
+ * Best and Fisher's von Mises sampler).
  *
  * Units: lengths in the caller's unit (um), times in s.  Inside the Green's-function routines all
  * lengths are scaled by the contact radius a (R = r/a) and time by a^2/D (tau = D t / a^2), as in
