@@ -356,10 +356,10 @@ __global__ void __launch_bounds__(128) k_first_passage_warp(const FptArgs A, con
           moved = true;
           break;
         }
-        const uint32_t mine = a + lane;
+        const unsigned long long mine = (unsigned long long)a + lane;
         real Rm = 0;
         int d = 0;
-        if (mine < A.max_attempts) d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
+        if (mine < A.max_attempts) d = fpt_attempt_p<F32>(A, l, strm, (uint32_t)mine, Ri, Rf, t, Rm);
         const unsigned m = __ballot_sync(0xFFFFFFFFu, d != 0);
         if (m == 0) {
           const uint32_t room = A.max_attempts - a;
@@ -407,11 +407,11 @@ __device__ int block_levels(const FptArgs& A, uint64_t strm, int& l, fpt_real<F3
       if (a - a0 >= budget) return 2;
       if (tid == 0) *s_win = 0xFFFFFFFFu;
       __syncthreads();
-      const uint32_t mine = a + tid;
+      const unsigned long long mine = (unsigned long long)a + tid;
       real Rm = 0;
       int d = 0;
       if (tid < width && mine < A.max_attempts) {
-        d = fpt_attempt_p<F32>(A, l, strm, mine, Ri, Rf, t, Rm);
+        d = fpt_attempt_p<F32>(A, l, strm, (uint32_t)mine, Ri, Rf, t, Rm);
         if (d != 0) atomicMin(s_win, tid);
       }
       __syncthreads();
