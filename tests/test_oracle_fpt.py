@@ -152,14 +152,25 @@ def _brute_force_first_contact(dim, R0, tau, n_paths, n_sub, seed):
     return 1.0 + d_prev, first
 
 
-@pytest.mark.parametrize("dim,R0,tau,n_paths", [(3, 1.3, 0.5, 40000), (2, 1.2, 0.2, 8000)])
-def test_refined_bin_matches_brute_force(dim, R0, tau, n_paths):
+def _brute_force_vs_oracle(dim, R0, tau, n_paths, tau_oracle):
     K, n_sub = 3, 256
     R, first = _brute_force_first_contact(dim, R0, tau, n_paths, n_sub, seed=[dim, 17])
     m = first >= 0
     R, first = R[m], first[m]
     bf = np.bincount(first * 2 ** K // n_sub, minlength=2 ** K)
-    out = O.fpt_refine_batch(dim, np.full(R.size, R0), R, tau, K, 23, np.arange(R.size, dtype=np.uint64))
+    out = O.fpt_refine_batch(dim, np.full(R.size, R0), R, tau_oracle, K, 23, np.arange(R.size, dtype=np.uint64))
     orc = np.bincount(out["bin"].astype(np.int64), minlength=2 ** K)
     table = np.vstack([bf, orc])
-    assert stats.chi2_contingency(table).pvalue > 1e-3, table
+    return stats.chi2_contingency(table).pvalue, table
+
+
+@pytest.mark.parametrize("dim,R0,tau,n_paths", [(3, 1.3, 0.5, 40000), (2, 1.2, 0.2, 8000)])
+def test_refined_bin_matches_brute_force(dim, R0, tau, n_paths):
+    p, table = _brute_force_vs_oracle(dim, R0, tau, n_paths, tau)
+    assert p > 1e-3, table
+
+
+def test_brute_force_detects_a_wrong_refinement_2d():
+    # the 2D comparison rejects the refinement run on twice the step's time scale
+    p, table = _brute_force_vs_oracle(2, 1.2, 0.2, 8000, 0.4)
+    assert p < 1e-6, table
