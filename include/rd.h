@@ -204,7 +204,11 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
  * for each (rule, levels) (allocation and a synchronisation then); accuracy holds for
  * separations up to the rule's cut-off plus 13 sqrt(D dt).  n < 2^32.  A call with more pairs than
  * any before on the handle allocates its work queues (136 bytes per pair, through the handle's
- * allocator) and releases the previous ones.  Asynchronous on the handle's stream. */
+ * allocator) and releases the previous ones.  Asynchronous on the handle's stream.
+ * Errors: RD_EINVAL (no handle, rule out of range or without a boundary condition, n < 0 or
+ * n >= 2^32, levels outside 0..24, a required pointer NULL with n > 0), RD_ENOMEM (work queues or
+ * Weber nodes), RD_ECUDA (launch).  A pair that hits the attempt bound is not an error (see
+ * above). */
 #define RD_FPT_MAX_ATTEMPTS (1u << 20)
 int rd_first_passage(rd_handle* h, int32_t rule, const double* r0, const double* r,
                      const uint64_t* stream, int64_t n, int32_t levels, uint32_t max_attempts,
