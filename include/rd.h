@@ -44,8 +44,11 @@ typedef enum {
 typedef enum { RD_BC_NONE = 0, RD_BC_ABS = 1, RD_BC_REF = 2, RD_BC_RAD = 3 } rd_bc;
 
 /* Arithmetic of the step.  RD_FP64: every stage in double precision.  RD_MIXED: positions stored
- * as float4, displacements, binning and the per-candidate p_enc in FP32; conflict resolution,
- * resampling, p_reac, time and observable sums in FP64. */
+ * as float4; displacements, binning, the per-candidate p_enc (3D closed form; 2D per-run table),
+ * the encounter and selection draws and the conflict keys in FP32; p_reac and the propagator
+ * sample of an encountered pair from per-run FP32 tables (bicubic) built on the device in FP64 at
+ * rd_init, the propagator sample refined by one FP32 Newton step; time and observable sums in
+ * FP64 / int64.  Per-pair probability error against FP64: below 2e-6 absolute. */
 typedef enum { RD_FP64 = 0, RD_MIXED = 1 } rd_precision;
 
 /* Interaction of species s1 and s2 (unordered).  sigma: contact radius a_eff (length unit of the
@@ -173,7 +176,8 @@ int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* specie
  * (Eq. bayes1D with radial Green's functions), p_reac[k] = reaction probability for a pair that
  * met the boundary and ended at r[k] (Eq. psurv_radII).  r0, r, p_enc, p_reac are DEVICE pointers
  * (double, n entries each; p_enc or p_reac may be NULL), evaluated in the handle's precision
- * (RD_MIXED: p_enc in FP32, p_reac in FP64).  Asynchronous on the handle's stream. */
+ * (RD_MIXED: p_enc in FP32 as the step evaluates it, p_reac from the same FP32 table as the step;
+ * RD_FP64: both in FP64).  Asynchronous on the handle's stream. */
 int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r, int64_t n,
                   double* p_enc, double* p_reac);
 
@@ -263,17 +267,23 @@ int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* ca
  * refused (inside a larger application's memory budget, under an allocator that forbids
  * allocation after start-up, or in a real-time loop that must not synchronise on an allocation).
  * rd_step_static advances a small single-replica system (cfg->n_replicas == 1, box edge
- * cfg->replicas[0].L; n_init is ignored; 3D only, RD_ENOTREADY otherwise) by one dt, exactly as
- * rd_step does, without calling
+ * cfg->replicas[0].L; n_init is ignored; 3D only: dim 2 returns RD_ENOTREADY) by one dt, exactly
+ * as rd_step does, without calling
  * cudaMalloc, cudaFree or any allocating routine: every scratch buffer of the step lives in one
  * fixed device array of RD_STATIC_SCRATCH_BYTES that the library reserves on every GPU that loads
  * it, until the process exits.
  *
  * Limits: n <= RD_STATIC_MAX_PARTICLES, at most RD_STATIC_MAX_PAIRS encounter pairs per step (more
- * latch RD_ECAPACITY in *status_out and leave the state unchanged), the cell grid is coarsened to
- * RD_STATIC_MAX_CELLS cells.  Larger inputs are rejected with RD_EINVAL before any work.
+ * latch RD_ECAPACITY in *status_out and the outputs then hold the unchanged input state), the cell
+ * grid is coarsened to RD_STATIC_MAX_CELLS cells.  With RD_MIXED the per-run FP32 tables of p_reac
+ * and of the propagator sample are built inside the same array on every call (a fraction of a
+ * millisecond); their size grows like (r_cut/sigma) (r_cut/sigma + 13 sqrt(tau)) / tau with
+ * tau = (D_A + D_B) dt / sigma^2, so large steps do not fit: the 10 uM reversible system
+ * (sigma = 0.005, D_A + D_B = 2) fits at dt = 1e-5 but not at dt = 1e-4 in RD_MIXED (RD_FP64 needs
+ * no tables).  Inputs beyond any limit are rejected with RD_EINVAL before anything is enqueued, and
+ * the outputs are left untouched.
  *
- * Inputs (DEVICE pointers, caller-owned): x_in double[n*3] (z ignored in 2D, positions in [0,L)),
+ * Inputs (DEVICE pointers, caller-owned): x_in double[n*3] (positions in [0,L)),
  * species_in int32[n], id_in uint32[n] sorted ascending; next_id = first id for new products;
  * step = step index that keys the random streams.  Outputs (DEVICE pointers, caller-owned):
  * x_out double[out_cap*3], species_out int32[out_cap], id_out uint32[out_cap] with
@@ -284,7 +294,8 @@ int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* ca
  * entry point clears what must start at zero).  Calls whose work overlaps on the GPU (different
  * streams, or several host threads) race on that array and give wrong results: serialise them.
  * Set-up: the first call on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.
+ * current; make that first call before any stream capture begins.  (This note is about that
+ * set-up only.)
  * ------------------------------------------------------------------------------------------- */
 #define RD_STATIC_MAX_PARTICLES 16384
 #define RD_STATIC_MAX_CELLS 65536

@@ -113,6 +113,8 @@ def lib():
                                        C.POINTER(d)]
         L.or_init_positions.restype = C.c_int
         L.or_init_positions.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64), C.POINTER(_State)]
+        L.or_set_fault.restype = None
+        L.or_set_fault.argtypes = [C.c_int]
         L.or_step.restype = C.c_int
         L.or_step.argtypes = [C.POINTER(_System), C.POINTER(_State), C.POINTER(_State),
                               C.POINTER(_Stats), C.POINTER(_Trace)]
@@ -252,6 +254,23 @@ def pair_probs(system, r0, r, rule: int = 0):
         prc = np.array([p_reac2(b / pr.sigma, a / pr.sigma, tau, h, system.tau_s)
                         for a, b in zip(r0, r)])
     return pe, prc
+
+
+class planted_fault:
+    """Context manager of the negative controls: plants one deliberate mistake in the oracle's
+    conflict resolution (1: key -ln(U_sel) * p_enc; 2: descending greedy order; 3: U_enc reused as
+    U_sel) and removes it on exit."""
+
+    def __init__(self, fault: int):
+        self.fault = int(fault)
+
+    def __enter__(self):
+        lib().or_set_fault(self.fault)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_fault(0)
+        return False
 
 
 # ------------------------------------------------------------------------------------------------

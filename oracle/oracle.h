@@ -113,6 +113,10 @@ int or_fpt_refine(int dim, double R0, double R, double tau, double tau_s, int le
 int or_fpt_direction(int dim, double kappa, uint64_t seed, uint64_t strm, uint32_t a, double* omc,
                      double* sn);
 
+/* Test hook of the negative controls (0: none; 1: key -ln(U) p; 2: descending greedy order;
+ * 3: U_enc reused as U_sel).  Never set outside a test. */
+void or_set_fault(int fault);
+
 /* Whole step and initial condition. */
 int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st);
 int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* stats, or_trace* trace);

@@ -519,13 +519,15 @@ double or_p_reac2(double R, double R0, double tau, double h, double tau_s) {
     double p = (bref - brad) / (bref + babs);
     return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
   }
-  double g[4];
-  for (int bc = OR_BC_ABS; bc <= OR_BC_RAD; ++bc) {
-    weber_ctx c = {R, R0, tau, h, {0, 0, 0, 0}, 0};
-    c.coef[bc] = 1.0;
-    g[bc] = weber(&c);
-  }
-  double p = (g[OR_BC_REF] - g[OR_BC_RAD]) / (g[OR_BC_REF] - g[OR_BC_ABS]);
+  /* numerator and denominator of Eq. (psurv_radII) each integrated as one difference (the free
+   * parts cancel inside the integrand, Section 4.2), so that the adaptive rule's tolerance is
+   * relative to the difference itself, not to the much larger single Green's functions */
+  weber_ctx num = {R, R0, tau, h, {0, 0, 0, 0}, 0}, den = {R, R0, tau, h, {0, 0, 0, 0}, 0};
+  num.coef[OR_BC_REF] = 1.0;
+  num.coef[OR_BC_RAD] = -1.0;
+  den.coef[OR_BC_REF] = 1.0;
+  den.coef[OR_BC_ABS] = -1.0;
+  double p = weber(&num) / weber(&den);
   return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
 }
 
@@ -706,6 +708,18 @@ static int cmp_fired(const void* x, const void* y) {
   return 0;
 }
 
+/* Test hook for negative controls: plants one deliberate mistake in the conflict resolution so
+ * that a test can show its statistic rejects it.  0 (default): the method as specified.
+ *   1: key = -ln(U_sel) * p_enc instead of -ln(U_sel) / p_enc
+ *   2: fired pairs accepted greedily in DESCENDING key order
+ *   3: the encounter draw U_enc reused as the selection draw */
+static int g_fault = 0;
+void or_set_fault(int fault) { g_fault = fault; }
+
+static int cmp_fired_faulty(const void* x, const void* y) {
+  return g_fault == 2 ? -cmp_fired(x, y) : cmp_fired(x, y);
+}
+
 typedef struct {
   int n;             /* number of products (0..2) */
   int species[2];
@@ -837,7 +851,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
       fired[fn].idb = in->id[b];
       fired[fn].tidx = tidx;
       fired[fn].p = p;
-      fired[fn].key = -log(u_sel) / p;
+      fired[fn].key = g_fault == 1 ? -log(u_sel) * p : (g_fault == 3 ? -log(u_enc) / p : -log(u_sel) / p);
       fired[fn].rule = q->rule;
       fn++;
     }
@@ -845,7 +859,7 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
   st.fired = fn;
 
   /* Conflict resolution (Section 3, "Details"): greedy in ascending (key, id_a, id_b). */
-  if (fn > 1) qsort(fired, (size_t)fn, sizeof(fired_pair), cmp_fired);
+  if (fn > 1) qsort(fired, (size_t)fn, sizeof(fired_pair), cmp_fired_faulty);
   for (int64_t e = 0; e < fn; ++e) {
     if (partner[fired[e].a] >= 0 || partner[fired[e].b] >= 0) continue;
     partner[fired[e].a] = fired[e].b;

@@ -426,9 +426,22 @@ def step_static(system, x, species, ids, next_id: int, step: int, precision: Opt
     import torch
 
     lib = _lib()
-    cfg, rep_arr = make_config(system, precision)
     n = int(ids.numel())
     dev = x.device
+    # the entry point takes raw device pointers: check shapes, types and device here
+    if not (x.is_cuda and species.is_cuda and ids.is_cuda):
+        raise ValueError("x, species and ids must be CUDA tensors")
+    if not (x.device == species.device == ids.device):
+        raise ValueError("x, species and ids must be on one device")
+    if dev.index != torch.cuda.current_device():
+        raise ValueError("the tensors' device must be the current CUDA device")
+    if x.dtype != torch.float64 or tuple(x.shape) != (n, 3):
+        raise ValueError("x must be float64 of shape (n, 3)")
+    if species.dtype != torch.int32 or species.numel() != n:
+        raise ValueError("species must be int32 with n entries")
+    if ids.dtype != torch.int32:
+        raise ValueError("ids must be int32 (holding uint32 ids) with n entries")
+    cfg, rep_arr = make_config(system, precision)
     cap = max(2 * n, 1)
     x_out = torch.empty((cap, 3), dtype=torch.float64, device=dev)
     sp_out = torch.empty(cap, dtype=torch.int32, device=dev)

@@ -107,6 +107,21 @@ static void free_all(rd_handle* h) {
   h->allocs.clear();
 }
 
+// Streaming multiprocessors of the current device, cached per device (grid caps of the launches).
+static int device_sms() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  cache[dev] = sms;
+  return sms;
+}
+
 static StepLaunch launch_for(rd_handle* h, int cur) {
   StepLaunch L = h->L;
   L.x_cur = h->xbuf[cur];
@@ -408,7 +423,7 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
       float4* q4 = (float4*)alloc(4 * bytes);
       double* tot = (double*)alloc((size_t)n0 * sizeof(double));
       if (!t || !q4 || !tot) return cudaErrorMemoryAllocation;
-      launch_build_table(h->L.P, k, kind, t, q4, n0, m1, hstep, h1, tot, fwd, h->stream);
+      launch_build_table(h->L.P, k, kind, t, q4, n0, m1, hstep, h1, tot, fwd, device_sms(), h->stream);
       T.v = t;
       T.q = q4;
       T.n0 = n0;
@@ -441,9 +456,7 @@ static int match_grid_for_current_device() {
   std::lock_guard<std::mutex> lock(mu);
   auto it = cache.find(dev);
   if (it != cache.end()) return it->second;
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-  const int g = match_grid_size(sms);
+  const int g = match_grid_size(device_sms());
   cache[dev] = g;
   return g;
 }
@@ -728,7 +741,7 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
-  L.max_grid = 152 * 16;
+  L.max_grid = device_sms() * 16;
   L.scan_items = 8;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;
@@ -1387,7 +1400,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.match_grid = match_grid_for_current_device();
   L.precision = c.precision;
   L.block = 256;
-  L.max_grid = 152 * 16;
+  L.max_grid = device_sms() * 16;
   L.scan_items = 8;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;
@@ -1440,6 +1453,50 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.id_cur = id0;
   L.id_next = id1;
 
+  // mixed precision: the step reads p_reac and the propagator sample from FP32 tables, built into
+  // the scratch array on every call.  Their space is laid out here, before anything is enqueued,
+  // so that a table that does not fit is rejected with the outputs untouched.
+  struct TableJob {
+    int rule, kind, m1;
+    double hstep, h1;
+    float* t;
+    double* tot;
+    float4* q4;
+    int n0;
+  };
+  std::vector<TableJob> jobs;
+  if (c.precision == RD_MIXED) {
+    for (int k = 0; k < c.n_pairs; ++k) {
+      if (c.pairs[k].bc == RD_BC_NONE || c.pairs[k].bc == RD_BC_ABS) continue;
+      PairDev& q = tmp.hp.pairs[k];
+      const double hstep = 0.025 * std::min(q.s, 1.0);
+      const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
+      const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
+      const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
+      const double hinv = 0.025;
+      const int ninv = (int)std::ceil(4.2 / hinv) + 4;
+      // only the quad copies are read by the step; the scalar table and the totals are build
+      // scratch shared by the tables of one rule (stream order keeps the builds apart)
+      float* t = (float*)b.take((size_t)n0 * std::max(n1, ninv) * sizeof(float));
+      double* tot = (double*)b.take((size_t)n0 * sizeof(double));
+      auto plan = [&](int kind, Tab2& T, int m1, double h1) {
+        float4* q4 = (float4*)b.take((size_t)n0 * m1 * sizeof(float4));
+        jobs.push_back({k, kind, m1, hstep, h1, t, tot, q4, n0});
+        T.v = nullptr;
+        T.q = q4;
+        T.n0 = n0;
+        T.n1 = m1;
+        T.h = (float)hstep;
+        T.inv_h = (float)(1.0 / hstep);
+        T.h1 = (float)h1;
+        T.inv_h1 = (float)(1.0 / h1);
+      };
+      if (c.pairs[k].bc == RD_BC_RAD) plan(0, q.tab_preac, n1, hstep);
+      plan(3, q.tab_inv, ninv, hinv);
+    }
+  }
+  if (!b.ok) return RD_EINVAL;
+
   DevCtl ctl;
   std::memset(&ctl, 0, sizeof ctl);
   ctl.n = (uint32_t)n;
@@ -1452,47 +1509,20 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   RD_CUDA(cudaMemsetAsync(L.counts, 0, (size_t)L.n_counts * 8, s));
   RD_CUDA(cudaMemsetAsync(L.rep_cons, 0, 4, s));
   RD_CUDA(cudaMemsetAsync(L.rep_prod, 0, 4, s));
-  RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
-  if (c.precision == RD_MIXED) {
-    // the mixed step reads p_reac and the propagator sample from FP32 tables: build them into
-    // the scratch array as well
-    bool any = false;
-    for (int k = 0; k < c.n_pairs; ++k) {
-      if (c.pairs[k].bc == RD_BC_NONE || c.pairs[k].bc == RD_BC_ABS) continue;
-      PairDev& q = tmp.hp.pairs[k];
-      const double hstep = 0.025 * std::min(q.s, 1.0);
-      const double d0max = std::sqrt(q.rcut2) / q.sigma - 1.0 + hstep;
-      const double dmax = d0max + 13.0 * q.s + 2.0 * hstep;
-      const int n0 = (int)std::ceil(d0max / hstep) + 4, n1 = (int)std::ceil(dmax / hstep) + 4;
-      const double hinv = 0.025;
-      const int ninv = (int)std::ceil(4.2 / hinv) + 4;
-      // only the quad copies are read by the step; the scalar table and the totals are build
-      // scratch shared by the tables (stream order keeps the builds apart)
-      float* t = (float*)b.take((size_t)n0 * std::max(n1, ninv) * sizeof(float));
-      double* tot = (double*)b.take((size_t)n0 * sizeof(double));
-      auto make = [&](int kind, Tab2& T, int m1, double h1) -> bool {
-        float4* q4 = (float4*)b.take((size_t)n0 * m1 * sizeof(float4));
-        if (!b.ok) return false;
-        launch_build_table(L.P, k, kind, t, q4, n0, m1, hstep, h1, tot, nullptr, s);
-        T.v = nullptr;
-        T.q = q4;
-        T.n0 = n0;
-        T.n1 = m1;
-        T.h = (float)hstep;
-        T.inv_h = (float)(1.0 / hstep);
-        T.h1 = (float)h1;
-        T.inv_h1 = (float)(1.0 / h1);
-        return true;
-      };
-      if (c.pairs[k].bc == RD_BC_RAD && !make(0, q.tab_preac, n1, hstep)) return RD_EINVAL;
-      if (!make(3, q.tab_inv, ninv, hinv)) return RD_EINVAL;
-      any = true;
-    }
-    if (any) RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+  // the tables are built from the parameter block: first without the table pointers, then the
+  // complete block once they are built
+  DevParams hp0 = tmp.hp;
+  for (int k = 0; k < c.n_pairs; ++k) {
+    hp0.pairs[k].tab_preac = Tab2{};
+    hp0.pairs[k].tab_inv = Tab2{};
   }
+  RD_CUDA(cudaMemcpyAsync((void*)L.P, &hp0, sizeof(DevParams), cudaMemcpyHostToDevice, s));
+  for (const TableJob& j : jobs)
+    launch_build_table(L.P, j.rule, j.kind, j.t, j.q4, j.n0, j.m1, j.hstep, j.h1, j.tot, nullptr, device_sms(), s);
+  if (!jobs.empty()) RD_CUDA(cudaMemcpyAsync((void*)L.P, &tmp.hp, sizeof(DevParams), cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemcpyAsync(L.reps, &rep, sizeof rep, cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemcpyAsync(L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, s));
-  const int G = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8);
+  const int G = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), (int64_t)device_sms() * 8);
   if (n > 0) {
     if (vs == 32)
       k_static_pack<d4><<<G, 256, 0, s>>>(n, c.dim, rp.L, x_in, species_in, id_in, (d4*)xb0, id0);
@@ -1500,7 +1530,7 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
       k_static_pack<float4><<<G, 256, 0, s>>>(n, c.dim, rp.L, x_in, species_in, id_in, (float4*)xb0, id0);
   }
   launch_step(L, s, nullptr);
-  const int Go = (int)std::min<int64_t>(std::max<int64_t>((2 * n + 255) / 256, 1), 152 * 8);
+  const int Go = (int)std::min<int64_t>(std::max<int64_t>((2 * n + 255) / 256, 1), (int64_t)device_sms() * 8);
   if (vs == 32)
     k_static_unpack<d4><<<Go, 256, 0, s>>>(L.ctl, L.reps, (const d4*)xb1, id1, x_out, species_out, id_out, n_out,
                                            next_id_out, status_out);

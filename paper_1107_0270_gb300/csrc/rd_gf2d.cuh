@@ -129,6 +129,27 @@ __device__ __forceinline__ void weber_g(const WeberNode* __restrict__ nodes, int
   out[2] = s2;
 }
 
+// Eq. (psurv_radII) numerator and denominator as single Weber sums of differences (the free parts
+// cancel node by node, Section 4.2): num = sum_i w_i [C_ref C_ref - C_rad C_rad](R, R0; x_i),
+// den = sum_i w_i [C_ref C_ref - C_abs C_abs](R, R0; x_i).
+__device__ __forceinline__ void weber_reac_diffs(const WeberNode* __restrict__ nodes, int n, double R, double R0,
+                                                 double& num, double& den) {
+  double sn = 0.0, sd = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const WeberNode& nd = nodes[i];
+    const double jr = j0(R * nd.x), yr = y0(R * nd.x);
+    const double jr0 = j0(R0 * nd.x), yr0 = y0(R0 * nd.x);
+    const double ca = (yr * nd.a[0] - jr * nd.b[0]) * (yr0 * nd.a[0] - jr0 * nd.b[0]);
+    const double cf = (yr * nd.a[1] - jr * nd.b[1]) * (yr0 * nd.a[1] - jr0 * nd.b[1]);
+    const double cd = (yr * nd.a[2] - jr * nd.b[2]) * (yr0 * nd.a[2] - jr0 * nd.b[2]);
+    sn += nd.w * (cf - cd);
+    sd += nd.w * (cf - ca);
+  }
+  num = sn;
+  den = sd;
+}
+
 // radial free function e^{-(R-R0)^2/4tau} I0e(R R0/2tau) / (4 pi tau)
 __device__ __forceinline__ double gfree2_d(double R, double R0, double tau) {
   return exp(-(R - R0) * (R - R0) / (4.0 * tau)) * i0e_d(R * R0 / (2.0 * tau)) / (4.0 * kPi * tau);
@@ -171,9 +192,9 @@ __device__ __forceinline__ double p_reac2(const Pair2D& q, double R, double R0) 
     const double bd = series_bracket2(*q.ser, 2, R, R0, q.s, ie);
     p = (bf - bd) / (bf + ba);
   } else {
-    double g[3];
-    weber_g(q.nodes, q.n_nodes, R, R0, 7u, g);
-    p = (g[1] - g[2]) / (g[1] - g[0]);
+    double num, den;
+    weber_reac_diffs(q.nodes, q.n_nodes, R, R0, num, den);
+    p = num / den;
   }
   return p < 0.0 ? 0.0 : (p > 1.0 ? 1.0 : p);
 }

@@ -1888,10 +1888,10 @@ __global__ void k_build_inverse2(Tab2 fwd, float* __restrict__ out, int n0, int 
 }
 
 void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
-                        double h1, double* tot, const Tab2* fwd, cudaStream_t s) {
+                        double h1, double* tot, const Tab2* fwd, int device_sms, cudaStream_t s) {
   if (kind == 2) k_tail_totals<<<(n0 + 63) / 64, 64, 0, s>>>(P, rule, n0, h, tot);
   const int64_t total = (int64_t)n0 * n1;
-  const int G = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
+  const int G = (int)std::min<int64_t>((total + 127) / 128, (int64_t)device_sms * 32);
   if (kind == 3 && fwd)
     k_build_inverse2<<<G, 128, 0, s>>>(*fwd, out, n0, n1, h, h1);
   else

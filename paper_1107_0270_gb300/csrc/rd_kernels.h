@@ -106,7 +106,7 @@ void launch_pair_probs(const DevParams* P, int rule, const double* r0, const dou
                        double* pr, int max_grid, cudaStream_t s);
 // kind 3 with fwd != nullptr: the 2D inverse table from the forward -ln(tail) table fwd
 void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
-                        double h1, double* tot, const Tab2* fwd, cudaStream_t s);
+                        double h1, double* tot, const Tab2* fwd, int device_sms, cudaStream_t s);
 void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
                      int max_grid, cudaStream_t s);
 

@@ -33,14 +33,18 @@ def test_pair_probs_2d_fp64(tau, ka):
     pe, prc = sim.pair_probs(torch.tensor(r0, device="cuda"), torch.tensor(r, device="cuda"))
     pe_o, pr_o = O.pair_probs(system, r0, r)
     assert np.max(np.abs(pe.cpu().numpy() - pe_o)) <= 1e-11
-    # p_reac = (g_ref - g_rad)/(g_ref - g_abs) is only conditioned where the pair can encounter:
-    # far from contact both differences sink below the rounding of g_free (by e^{-(R-1)(R0-1)/tau})
-    m = pe_o >= 1e-4
+    # p_reac = (g_ref - g_rad)/(g_ref - g_abs) is a ratio of two differences that both vanish far
+    # from contact.  Both sides integrate each difference as one integrand (the oracle adaptively,
+    # the GPU on its fixed Weber nodes), so the error of a difference is a fraction of the Weber
+    # integrand's scale, ~g_free, not of the difference itself (~p_enc g_free).  The oracle's error,
+    # pinned against 30-digit Laplace inversions, is <= 1e-14 p_reac / p_enc; the bound allows ten
+    # times that for each side plus rounding: 1e-12 + 1e-13 / p_enc, where p_enc >= 1e-7 (a pair
+    # further out fires once in 1e7 steps; below that both differences approach the integrand's
+    # rounding level)
+    m = pe_o >= 1e-7
     assert m.sum() > 100
-    # both sides integrate the g's to ~1e-13 of g_free; the ratio divides by (g_ref - g_abs) ~
-    # p_enc g_free, so the bound is 1e-13 / p_enc (1e-9 at the mask edge, 1e-13 at contact)
     err = np.abs(prc.cpu().numpy()[m] - pr_o[m])
-    assert np.all(err <= 1e-13 / pe_o[m] + 1e-12), err.max()
+    assert np.all(err <= 1e-13 / pe_o[m] + 1e-12), (err.max(), (err / (1e-13 / pe_o[m] + 1e-12)).max())
     sim.close()
 
 
@@ -70,7 +74,7 @@ def test_pair_probs_2d_mixed_tables_within_2e6(tau, ka):
     pe, prc = sim.pair_probs(torch.tensor(r0, device="cuda"), torch.tensor(r, device="cuda"))
     pe_o, pr_o = O.pair_probs(system, r0, r)
     assert np.max(np.abs(pe.cpu().numpy() - pe_o)) <= 2e-6
-    m = pe_o >= 1e-4
+    m = pe_o >= 1e-7
     assert np.max(np.abs(prc.cpu().numpy()[m] - pr_o[m])) <= 2e-6
     # propagator samples from the tail table: the sampled separations invert the oracle tail
     rng = np.random.default_rng(11)

@@ -201,3 +201,28 @@ def test_p_reac2_of_strongly_reactive_pairs_matches_laplace_inversion(h, tau, R,
     ga = gbc_laplace("abs", R, R0, tau, h)
     ref = (gr - gd) / (gr - ga)
     assert abs(O.p_reac2(R, R0, tau, h) - ref) < 1e-8, (O.p_reac2(R, R0, tau, h), ref)
+
+
+
+def _golden_p_reac2():
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "p_reac2_laplace.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(tuple(float(v) for v in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("R,R0,tau,h,ref", _golden_p_reac2())
+def test_p_reac2_relative_accuracy_far_from_contact(R, R0, tau, h, ref):
+    # Eq. (psurv_radII) is a ratio of two differences of Green's functions that both vanish far from
+    # contact (their ratio stays O(1)); each difference is integrated as one integrand (the free
+    # parts cancel, Section 4.2), so p_reac keeps its relative accuracy where p_enc is small.
+    # Reference: Talbot inversions (30 digits) of the Laplace-domain differences
+    # (tests/golden/make_p_reac2_laplace.py).  Measured: |dp|/p <= 1e-14 / p_enc (p_enc 0.95 .. 3e-8).
+    pe = O.p_enc2(R, R0, tau)
+    p = O.p_reac2(R, R0, tau, h)
+    assert abs(p - ref) <= ref * (1e-13 + 1e-14 / pe), (p, ref, pe)
