@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")   # the all-core CPU-baseline build
 _SOURCES = [os.path.join(_HERE, "rd_oracle.c")]
 
 MAX_SPECIES, MAX_PAIRS, MAX_DECAYS = 16, 32, 16
@@ -23,15 +24,22 @@ BC = {"none": 0, "abs": 1, "ref": 2, "rad": 3}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (gcc, -O2, no floating-point contraction) and return the .so path."""
+    """Compile the oracle (gcc, -O2, no floating-point contraction) and return the .so path; also
+    the OpenMP build of the same source (the all-core CPU baseline: the pair loop on all threads,
+    same results) when the compiler supports it."""
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(p) for p in _SOURCES + [os.path.join(_HERE, "oracle.h")])
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp] + _SOURCES + ["-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+            tmp = path + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared"] + extra + \
+                  ["-o", tmp] + _SOURCES + ["-lm"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                if extra:          # no OpenMP here: the baseline reports the single-thread build only
+                    continue
+                raise RuntimeError(f"oracle build failed:\n{r.stderr}")
+            os.replace(tmp, path)
     return _LIB_PATH
 
 
@@ -52,7 +60,7 @@ class _System(C.Structure):
                 ("replica", C.c_uint32), ("pad_", C.c_uint32),
                 ("D", C.c_double * MAX_SPECIES), ("pairs", _Pair * MAX_PAIRS),
                 ("decays", _Decay * MAX_DECAYS), ("drift_dx", (C.c_double * 3) * MAX_SPECIES),
-                ("has_drift", C.c_int32), ("pad2_", C.c_int32)]
+                ("has_drift", C.c_int32), ("angle_mode", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -75,13 +83,26 @@ class _Trace(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
+    """The oracle library; openmp=True: the OpenMP build (None if it could not be built)."""
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            build()
+            if not os.path.exists(_LIB_OMP_PATH):
+                return None
+            _lib_omp = _bind(C.CDLL(_LIB_OMP_PATH))
+        return _lib_omp
     if _lib is None:
-        path = build()
-        L = C.CDLL(path)
+        _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def _bind(L):
+    if True:
         d = C.c_double
         for name, args in [("or_p_enc3", [d, d, d]), ("or_p_reac3", [d, d, d, d]),
                            ("or_tail3", [d, d, d]), ("or_resample3", [d, d, d]),
@@ -113,13 +134,30 @@ def lib():
                                        C.POINTER(d)]
         L.or_init_positions.restype = C.c_int
         L.or_init_positions.argtypes = [C.POINTER(_System), C.POINTER(C.c_int64), C.POINTER(_State)]
+        L.or_ang_coeffs.restype = C.c_int
+        L.or_ang_coeffs.argtypes = [C.c_int, C.c_int, d, d, d, C.POINTER(d), C.c_int]
+        L.or_ang_sample.restype = d
+        L.or_ang_sample.argtypes = [C.c_int, d, d, d, d]
+        L.or_ang_density.restype = d
+        L.or_ang_density.argtypes = [C.c_int, d, d, d, d]
+        L.or_gf_partial.restype = d
+        L.or_gf_partial.argtypes = [C.c_int, C.c_int, d, d, d, d]
+        L.or_propagate.restype = None
+        L.or_propagate.argtypes = [C.c_int, C.POINTER(d), d, d, d, d, d, C.POINTER(d)]
         L.or_set_fault.restype = None
         L.or_set_fault.argtypes = [C.c_int]
         L.or_step.restype = C.c_int
         L.or_step.argtypes = [C.POINTER(_System), C.POINTER(_State), C.POINTER(_State),
                               C.POINTER(_Stats), C.POINTER(_Trace)]
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int
+        L.or_threads.argtypes = []
+    return L
+
+
+def threads(openmp: bool = True) -> int:
+    """Threads the (OpenMP) oracle build uses for a step; 1 for the serial build."""
+    L = lib(openmp)
+    return 1 if L is None else int(L.or_threads())
 
 
 # ------------------------------------------------------------------------------------------------
@@ -237,6 +275,39 @@ def fpt_refine_batch(dim, R0, R, tau, levels, seed, streams, tau_s=0.01, max_att
     return out
 
 
+ANG_WHICH = {"encountered": 0, "abs": 1, "ref": 2, "free": 3}
+
+
+def ang_coeffs(dim, R, R0, tau, which="encountered", cap=1201):
+    """Partial-wave integrals D_n (n = 0..N) of the exact propagation law (scaled units)."""
+    D = np.zeros(cap)
+    N = lib().or_ang_coeffs(int(dim), ANG_WHICH[which], float(R), float(R0), float(tau),
+                            D.ctypes.data_as(C.POINTER(C.c_double)), cap)
+    return D[:N + 1].copy()
+
+
+def ang_sample(dim, U, R, R0, tau):
+    """Angle of the new separation to the start separation at CDF value U (3D: its cosine)."""
+    return lib().or_ang_sample(int(dim), float(U), float(R), float(R0), float(tau))
+
+
+def ang_density(dim, v, R, R0, tau):
+    return lib().or_ang_density(int(dim), float(v), float(R), float(R0), float(tau))
+
+
+def propagate(dim, r0, tau, u_res, u_ang, u_azi, tau_s=0.01):
+    """New separation vector (scaled units) of an encountered pair from start vector r0."""
+    a = (C.c_double * 3)(*[float(v) for v in list(r0) + [0.0] * (3 - len(r0))])
+    o = (C.c_double * 3)()
+    lib().or_propagate(int(dim), a, float(tau), float(tau_s), float(u_res), float(u_ang), float(u_azi), o)
+    return np.array([o[0], o[1], o[2]])
+
+
+def gf_partial(dim, which, v, R, R0, tau):
+    """Full Green's function at separation R and angle v (3D: v = cos) from its partial waves."""
+    return lib().or_gf_partial(int(dim), ANG_WHICH[which], float(v), float(R), float(R0), float(tau))
+
+
 def pair_probs(system, r0, r, rule: int = 0):
     """p_enc and p_reac (reaction probability at end separation r from start r0) for arrays of
     physical separations, for pair rule ``rule`` of ``system`` (dimension-aware)."""
@@ -257,9 +328,9 @@ def pair_probs(system, r0, r, rule: int = 0):
 
 
 class planted_fault:
-    """Context manager of the negative controls: plants one deliberate mistake in the oracle's
-    conflict resolution (1: key -ln(U_sel) * p_enc; 2: descending greedy order; 3: U_enc reused as
-    U_sel) and removes it on exit."""
+    """Context manager of the negative controls: plants one deliberate mistake in the oracle
+    (1: conflict key -ln(U_sel) * p_enc; 2: descending greedy order; 3: U_enc reused as U_sel; 4: the
+    cylindrical Bessel derivative in the 3D boundary coefficients) and removes it on exit."""
 
     def __init__(self, fault: int):
         self.fault = int(fault)
@@ -313,6 +384,7 @@ def _system_struct(system, replica: int = 0, L: float | None = None) -> _System:
     for i, dc in enumerate(system.decays):
         prods = list(dc.products) + [-1, -1]
         s.decays[i] = _Decay(dc.parent, len(dc.products), prods[0], prods[1], dc.kd, dc.sigma_place)
+    s.angle_mode = 1 if getattr(system, "angle", "exact") == "free_step" else 0
     drift = getattr(system, "drift", None)
     if drift is not None:
         s.has_drift = 1
@@ -350,8 +422,10 @@ def init_state(system, replica: int = 0) -> State:
     return State(x[:n].copy(), sp[:n].copy(), ids[:n].copy(), 0, int(st.next_id), 0.0)
 
 
-def step(system, state: State, replica: int = 0, L: float | None = None, trace: bool = False):
-    """Advance ``state`` by one step.  Returns (new_state, stats dict[, trace dict])."""
+def step(system, state: State, replica: int = 0, L: float | None = None, trace: bool = False,
+         openmp: bool = False):
+    """Advance ``state`` by one step.  Returns (new_state, stats dict[, trace dict]).  openmp: run
+    the pair loop on all threads (the OpenMP build; same result, no trace)."""
     n = state.n
     cap = 2 * n + 16
     xin = np.ascontiguousarray(state.x, dtype=np.float64).reshape(-1, 3)
@@ -385,8 +459,9 @@ def step(system, state: State, replica: int = 0, L: float | None = None, trace: 
         tr.matched = arrays["matched"].ctypes.data_as(C.POINTER(C.c_int32))
     Lrep = system.replica_list()[replica].L if L is None else L
     sysc = _system_struct(system, replica, Lrep)
-    rc = lib().or_step(C.byref(sysc), C.byref(stin), C.byref(stout), C.byref(stats),
-                       C.byref(tr) if tr is not None else None)
+    Lb = lib(True) if (openmp and not trace) else None
+    rc = (Lb or lib()).or_step(C.byref(sysc), C.byref(stin), C.byref(stout), C.byref(stats),
+                              C.byref(tr) if tr is not None else None)
     if rc != 0:
         raise RuntimeError(f"or_step failed: {rc}")
     m = int(stout.n)

@@ -25,7 +25,7 @@ enum { OR_BC_NONE = 0, OR_BC_ABS = 1, OR_BC_REF = 2, OR_BC_RAD = 3 };
 enum {
   OR_TAG_INIT0 = 1, OR_TAG_INIT1 = 2, OR_TAG_UNI = 3, OR_TAG_DISP0 = 4, OR_TAG_DISP1 = 5,
   OR_TAG_ENC = 6, OR_TAG_RES = 7, OR_TAG_DIR = 8, OR_TAG_DISS0 = 9, OR_TAG_DISS1 = 10,
-  OR_TAG_DISS2 = 11, OR_TAG_DISS3 = 12
+  OR_TAG_DISS2 = 11, OR_TAG_DISS3 = 12, OR_TAG_ANG = 14
 };
 
 typedef struct {
@@ -49,7 +49,11 @@ typedef struct {
   /* deterministic drift displacement per step and species (v dt), applied as a split step before
    * the Brownian step; has_drift = 0 skips it */
   double drift_dx[OR_MAX_SPECIES][3];
-  int32_t has_drift, pad2_;
+  int32_t has_drift;
+  /* direction of an encountered pair's new separation: 0 = drawn from the full propagator
+   * G_ref - G_abs (Eq. passage_prob with Eqs. genericGF3D / genericGF); 1 = the free step's
+   * direction kept (only the length resampled) */
+  int32_t angle_mode;
 } or_system;
 
 typedef struct {
@@ -113,9 +117,26 @@ int or_fpt_refine(int dim, double R0, double R, double tau, double tau_s, int le
 int or_fpt_direction(int dim, double kappa, uint64_t seed, uint64_t strm, uint32_t a, double* omc,
                      double* sn);
 
+/* Exact angular propagation (partial waves of Eqs. genericGF3D / genericGF).  or_ang_coeffs: the
+ * integrals D_n, n = 0..N, of the reflective minus absorbing products (which = 0), or of the
+ * absorbing (1), reflective (2) or free (3) product alone; returns N (D holds N + 1 values, at most
+ * cap).  or_ang_sample: the angle of r' to r0 at CDF value U (3D: cos(angle); 2D: the angle in
+ * [0, pi]).  or_ang_density: its density. */
+int or_ang_coeffs(int dim, int which, double R, double R0, double tau, double* D, int cap);
+double or_ang_sample(int dim, double U, double R, double R0, double tau);
+double or_ang_density(int dim, double v, double R, double R0, double tau);
+double or_gf_partial(int dim, int which, double v, double R, double R0, double tau);
+/* One encountered pair's new separation vector (scaled units) from the start vector r0. */
+void or_propagate(int dim, const double* r0, double tau, double tau_s, double u_res, double u_ang, double u_azi,
+                  double* out);
+
 /* Test hook of the negative controls (0: none; 1: key -ln(U) p; 2: descending greedy order;
- * 3: U_enc reused as U_sel).  Never set outside a test. */
+ * 3: U_enc reused as U_sel; 4: the cylindrical Bessel derivative in the 3D boundary coefficients).
+ * Never set outside a test. */
 void or_set_fault(int fault);
+
+/* Threads of a step's pair loop: omp_get_max_threads() in the OpenMP build, else 1. */
+int or_threads(void);
 
 /* Whole step and initial condition. */
 int or_init_positions(const or_system* sys, const int64_t* n_init, or_state* st);

@@ -20,8 +20,10 @@
  *    paper's selection probability p_enc,j / sum p_enc among its own fired candidates.
  *  - unimolecular decays are drawn first from the start-of-step state; decaying particles neither
  *    move freely nor pair this step.  Products take no part in bimolecular reactions this step.
- *  - an encountered pair keeps the direction of its free-step separation; only its length is
- *    resampled from the radial propagator (Section 3, "Details", first item).
+ *  - an encountered pair's new separation is drawn from the full propagator G_ref - G_abs
+ *    (Eq. passage_prob): its length from the radial law, its angle to the start separation from
+ *    the partial-wave series of Eqs. genericGF3D / genericGF (angle_mode 0); angle_mode 1 keeps
+ *    the free step's direction instead.
  *  - products: a bimolecular product sits at the centre of diffusion (Eq. Rcoo) of the pair; ids
  *    are next_id + rank of the event ordered by its lower parent id; survivors keep their order
  *    and products are appended, so the particle array stays sorted by id.
@@ -29,11 +31,23 @@
 #define _DEFAULT_SOURCE
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define PI 3.14159265358979323846
+
+/* Test hook for negative controls: plants one deliberate mistake so that a test can show its
+ * statistic rejects it.  0 (default): the method as specified.
+ *   1: conflict key = -ln(U_sel) * p_enc instead of -ln(U_sel) / p_enc
+ *   2: fired pairs accepted greedily in DESCENDING key order
+ *   3: the encounter draw U_enc reused as the selection draw
+ *   4: the 3D boundary coefficients with the cylindrical derivative j_n' = j_{n-1} - n/z j_n */
+static int g_fault = 0;
+void or_set_fault(int fault) { g_fault = fault; }
 #define SQRT_PI 1.77245385090551602730
 #define NEAR_THRESHOLD 1e-9
 
@@ -588,6 +602,341 @@ double or_resample2(double U, double R0, double tau, double tau_s) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Exact propagation of an encountered pair (Eq. passage_prob with the full Green's functions of   */
+/* Eqs. genericGF3D / genericGF): the new separation vector r' is drawn from G_ref - G_abs.  Its   */
+/* length R' follows the radial law above (the n = 0 term); its angle to the start separation r0  */
+/* follows, given R', the partial-wave series                                                      */
+/*   3D: f(mu) = sum_n (2n+1) P_n(mu) D_n / (2 D_0),      mu = cos(angle),                         */
+/*   2D: f(theta) = [D_0 + 2 sum_{n>=1} D_n cos(n theta)] / (2 pi D_0),                           */
+/* with D_n the n-th Weber-type integral of the reflective minus the absorbing product,            */
+/*   3D: D_n = int_0^inf e^{-tau x^2} x^2 [C^ref_n(R',x) C^ref_n(R0,x) - C^abs_n(R',x) C^abs_n(R0,x)] dx, */
+/*   2D: the same with x instead of x^2 and the integer-order functions of Eq. fRad.               */
+/* 3D: J_{n+1/2}(z) = sqrt(2z/pi) j_n(z) (spherical Bessel), so the paper's F_{n+1/2}(R, x) equals  */
+/* sqrt(2Rx/pi) C_n(R, x) with C_n = [j_n(Rx) b_n(x) - y_n(Rx) a_n(x)] / sqrt(a_n^2 + b_n^2),        */
+/* a_n = h j_n(x) - x j_n'(x), b_n = h y_n(x) - x y_n'(x) (h = 0 reflective; h -> infinity         */
+/* absorbing: a_n = j_n, b_n = y_n), the sqrt(R R0) cancelling the prefactor of Eq. genericGF3D.    */
+/* The Bessel functions come from the three-term recurrences (Eq. 3termBessel): the second kind   */
+/* upward, the first kind downward from far above (Miller) normalised by its sum rule; Legendre    */
+/* polynomials by their recurrence.                                                                */
+/* ------------------------------------------------------------------------------------------ */
+#define ANG_NMAX 1200
+#define ANG_MMAX 8000     /* start order of the downward recurrences at most (z up to ~7000) */
+#define ANG_Y_BIG 1e280
+
+/* j_n(z), y_n(z), n = 0..N (3D; spherical Bessel functions of the first and second kind).  y_n
+ * upward: y_{n+1} = ((2n+1)/z) y_n - y_{n-1}, y_0 = -cos z / z, y_1 = -cos z / z^2 - sin z / z; once
+ * |y_n| passes ANG_Y_BIG the rest is set to -ANG_Y_BIG (such orders contribute nothing at that z).
+ * j_n downward from M = N + 40 + z: j_{n-1} = ((2n+1)/z) j_n - j_{n+1}, scaled by the sum rule
+ * sum_n (2n+1) j_n^2 = 1 with the sign of j_0 = sin z / z (or of j_1 near its zeros). */
+static void sph_bessel(int N, double z, double* j, double* y) {
+  double s = sin(z), c = cos(z);
+  y[0] = -c / z;
+  if (N >= 1) y[1] = -c / (z * z) - s / z;
+  for (int n = 1; n < N; ++n) {
+    if (fabs(y[n]) > ANG_Y_BIG) {
+      for (int m = n + 1; m <= N; ++m) y[m] = -ANG_Y_BIG;
+      break;
+    }
+    y[n + 1] = (2.0 * n + 1.0) / z * y[n] - y[n - 1];
+  }
+  int M = N + 40 + (int)z;
+  if (M > ANG_MMAX) M = ANG_MMAX;
+  double jp1 = 0.0, jn = 1e-30, sum = 0.0;
+  double tmp[ANG_MMAX + 2];
+  for (int n = M; n >= 0; --n) {
+    tmp[n] = jn;
+    sum += (2.0 * n + 1.0) * jn * jn;
+    double jm1 = n > 0 ? (2.0 * n + 1.0) / z * jn - jp1 : 0.0;
+    jp1 = jn;
+    jn = jm1;
+    if (fabs(jn) > 1e100) {           /* rescale the running values (and the sum) to stay finite */
+      for (int m = n; m <= M; ++m) tmp[m] *= 1e-100;
+      jn *= 1e-100;
+      jp1 *= 1e-100;
+      sum *= 1e-200;
+    }
+  }
+  double scale = 1.0 / sqrt(sum);
+  double j0 = s / z, j1 = s / (z * z) - c / z;
+  if (fabs(j0) >= fabs(j1)) {
+    if ((j0 < 0.0) != (tmp[0] < 0.0)) scale = -scale;
+  } else {
+    if ((j1 < 0.0) != (tmp[1] < 0.0)) scale = -scale;
+  }
+  for (int n = 0; n <= N; ++n) j[n] = tmp[n] * scale;
+}
+
+/* J_n(z), Y_n(z), n = 0..N (2D; integer order).  Y_n upward from libm's y0, y1:
+ * Y_{n+1} = (2n/z) Y_n - Y_{n-1}; J_n downward from M = N + 40 + z (Miller) normalised by
+ * J_0 + 2 sum_{k>=1} J_{2k} = 1. */
+static void cyl_bessel(int N, double z, double* J, double* Y) {
+  Y[0] = y0(z);
+  if (N >= 1) Y[1] = y1(z);
+  for (int n = 1; n < N; ++n) {
+    if (fabs(Y[n]) > ANG_Y_BIG) {
+      for (int m = n + 1; m <= N; ++m) Y[m] = -ANG_Y_BIG;
+      break;
+    }
+    Y[n + 1] = 2.0 * n / z * Y[n] - Y[n - 1];
+  }
+  int M = N + 40 + (int)z;
+  if (M > ANG_MMAX) M = ANG_MMAX;
+  if (M & 1) M--;
+  double jp1 = 0.0, jn = 1e-30, norm = 0.0;
+  double tmp[ANG_MMAX + 2];
+  for (int n = M; n >= 0; --n) {
+    tmp[n] = jn;
+    norm += (n == 0 ? 1.0 : (n % 2 == 0 ? 2.0 : 0.0)) * jn;
+    double jm1 = n > 0 ? 2.0 * n / z * jn - jp1 : 0.0;
+    jp1 = jn;
+    jn = jm1;
+    if (fabs(jn) > 1e150) {
+      for (int m = n; m <= M; ++m) tmp[m] *= 1e-150;
+      jn *= 1e-150;
+      jp1 *= 1e-150;
+      norm *= 1e-150;
+    }
+  }
+  for (int n = 0; n <= N; ++n) J[n] = tmp[n] / norm;
+}
+
+/* Boundary coefficients of order n at the abscissa x for the reflective (h = 0) and absorbing
+ * conditions, normalised: C_n(R, x) = Z1(Rx) cb - Z2(Rx) ca, with (ca, cb) = (a, b) / sqrt(a^2 + b^2).
+ * 3D: a = -x j_n'(x), b = -x y_n'(x) (ref); a = j_n(x), b = y_n(x) (abs).
+ * 2D (Eq. fRad): a = x J_n'(x), b = x Y_n'(x) (ref); a = J_n(x), b = Y_n(x) (abs).
+ * Derivatives: j_n' = j_{n-1} - (n+1)/z j_n (j_0' = -j_1); J_n' = J_{n-1} - n/z J_n (J_0' = -J_1). */
+static void bc_coeffs(int dim, int n, double x, const double* jx, const double* yx, double* ca_ref,
+                      double* cb_ref, double* ca_abs, double* cb_abs) {
+  double jd, yd;
+  if (dim == 3 && g_fault != 4) {
+    jd = n == 0 ? -jx[1] : jx[n - 1] - (n + 1.0) / x * jx[n];
+    yd = n == 0 ? -yx[1] : yx[n - 1] - (n + 1.0) / x * yx[n];
+  } else {
+    jd = n == 0 ? -jx[1] : jx[n - 1] - (double)n / x * jx[n];
+    yd = n == 0 ? -yx[1] : yx[n - 1] - (double)n / x * yx[n];
+  }
+  double a = -x * jd, b = -x * yd;
+  double nr = hypot(a, b);
+  *ca_ref = a / nr;
+  *cb_ref = b / nr;
+  nr = hypot(jx[n], yx[n]);
+  *ca_abs = jx[n] / nr;
+  *cb_abs = yx[n] / nr;
+}
+
+/* D_n, n = 0..N, for end separation R and start separation R0 (both > 0, scaled units), on a
+ * composite 16-point Gauss-Legendre rule over x in [0, X], X = sqrt(46/tau) (e^{-46} ~ 1e-20), with
+ * `panels` equal panels.  which = 0: G_ref - G_abs (the encountered propagator); which = 1: the
+ * absorbing, 2: the reflective, 3: the free function alone (C_n = j_n(Rx) / J_n(Rx)) -- the last
+ * three for the pins. */
+static void ang_D_grid(int dim, int which, int N, double R, double R0, double tau, int panels, double* D) {
+  gl_init();
+  for (int n = 0; n <= N; ++n) D[n] = 0.0;
+  /* 3D: panels in x on [0, X]; 2D: in t with x = t^2 on [0, sqrt(X)] (dx = 2t dt), which smooths
+   * the logarithmic behaviour of the integer-order boundary coefficients at x -> 0 */
+  double X = sqrt(46.0 / tau), hp = (dim == 3 ? X : sqrt(X)) / panels;
+  double *jx = (double*)malloc(sizeof(double) * (N + 2)), *yx = (double*)malloc(sizeof(double) * (N + 2));
+  double *jr = (double*)malloc(sizeof(double) * (N + 2)), *yr = (double*)malloc(sizeof(double) * (N + 2));
+  double *j0_ = (double*)malloc(sizeof(double) * (N + 2)), *y0_ = (double*)malloc(sizeof(double) * (N + 2));
+  for (int p = 0; p < panels; ++p) {
+    double m = (p + 0.5) * hp;
+    for (int i = 0; i < GL_N; ++i) {
+      double t = m + 0.5 * hp * gl_x[i];
+      double x = dim == 3 ? t : t * t;
+      double w = 0.5 * hp * gl_w[i] * exp(-tau * x * x) * (dim == 3 ? x * x : x * 2.0 * t);
+      int Nb = N + 1;
+      if (dim == 3) {
+        sph_bessel(Nb, x, jx, yx);
+        sph_bessel(N, R * x, jr, yr);
+        sph_bessel(N, R0 * x, j0_, y0_);
+      } else {
+        cyl_bessel(Nb, x, jx, yx);
+        cyl_bessel(N, R * x, jr, yr);
+        cyl_bessel(N, R0 * x, j0_, y0_);
+      }
+      for (int n = 0; n <= N; ++n) {
+        if (which == 3) {
+          D[n] += w * jr[n] * j0_[n];
+          continue;
+        }
+        if (yr[n] == -ANG_Y_BIG || y0_[n] == -ANG_Y_BIG || yx[n + 1] == -ANG_Y_BIG) continue;
+        double car, cbr, caa, cba;
+        bc_coeffs(dim, n, x, jx, yx, &car, &cbr, &caa, &cba);
+        double ref = (jr[n] * cbr - yr[n] * car) * (j0_[n] * cbr - y0_[n] * car);
+        double abs_ = (jr[n] * cba - yr[n] * caa) * (j0_[n] * cba - y0_[n] * caa);
+        D[n] += w * (which == 0 ? ref - abs_ : (which == 1 ? abs_ : ref));
+      }
+    }
+  }
+  free(jx); free(yx); free(jr); free(yr); free(j0_); free(y0_);
+}
+
+/* Number of partial waves kept: the free part's coefficients decay like I_{n+d/2-1}(kappa) with
+ * kappa = R R0 / (2 tau), negligible for n well beyond kappa. */
+static int ang_terms(double R, double R0, double tau) {
+  double kappa = R * R0 / (2.0 * tau);
+  int N = (int)ceil(kappa + 8.0 * sqrt(kappa + 1.0) + 14.0);
+  return N > ANG_NMAX ? ANG_NMAX : N;
+}
+
+/* D_n with the panel count doubled until the coefficients D_n / D_0 change by less than 1e-12
+ * (at most 4096 panels); returns the number of terms N (D has N + 1 entries). */
+int or_ang_coeffs(int dim, int which, double R, double R0, double tau, double* D, int cap) {
+  int N = ang_terms(R, R0, tau);
+  if (N + 1 > cap) N = cap - 1;
+  double X = sqrt(46.0 / tau);
+  int panels = 8 + (int)ceil(X * (R + R0) / 1.5);
+  double* prev = (double*)malloc(sizeof(double) * (N + 1));
+  ang_D_grid(dim, which, N, R, R0, tau, panels, D);
+  for (int it = 0; it < 8 && panels < 4096; ++it) {
+    memcpy(prev, D, sizeof(double) * (N + 1));
+    panels *= 2;
+    ang_D_grid(dim, which, N, R, R0, tau, panels, D);
+    double scale = fabs(D[0]) > 0.0 ? fabs(D[0]) : 1.0, diff = 0.0;
+    for (int n = 0; n <= N; ++n) diff = fmax(diff, fabs(D[n] - prev[n]));
+    if (diff <= 1e-12 * scale) break;
+  }
+  free(prev);
+  return N;
+}
+
+/* CDF of the conditional angle.  3D: F(mu) = (1 + mu)/2 + sum_{n>=1} (D_n/D_0) [P_{n+1}(mu) -
+ * P_{n-1}(mu)] / 2 (from the integral of P_n: [P_{n+1} - P_{n-1}] / (2n+1)); 2D, for theta in
+ * [0, pi]: F(theta) = [theta + 2 sum_{n>=1} (D_n/D_0) sin(n theta)/n] / pi. */
+static double ang_cdf(int dim, const double* D, int N, double v) {
+  if (dim == 3) {
+    double pm1 = 1.0, p = v, sum = 0.5 * (1.0 + v);       /* P_0, P_1 */
+    for (int n = 1; n <= N; ++n) {
+      double pp1 = ((2.0 * n + 1.0) * v * p - n * pm1) / (n + 1.0);
+      sum += 0.5 * D[n] / D[0] * (pp1 - pm1);
+      pm1 = p;
+      p = pp1;
+    }
+    return sum;
+  }
+  double sum = v;
+  for (int n = 1; n <= N; ++n) sum += 2.0 * D[n] / D[0] * sin(n * v) / n;
+  return sum / PI;
+}
+
+/* The angle of r' to r0 at CDF value U (bisection to the last bit): 3D cos(angle) in [-1, 1],
+ * 2D the angle in [0, pi]. */
+double or_ang_sample(int dim, double U, double R, double R0, double tau) {
+  double D[ANG_NMAX + 1];
+  int N = or_ang_coeffs(dim, 0, R, R0, tau, D, ANG_NMAX + 1);
+  double lo = dim == 3 ? -1.0 : 0.0, hi = dim == 3 ? 1.0 : PI;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (ang_cdf(dim, D, N, mid) < U)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* The full Green's function at (R, v) from its partial waves (for the pins; which as in
+ * or_ang_coeffs): 3D (1/4pi)(2/pi) sum_n (2n+1) P_n(mu) D_n with mu = v, 2D (1/2pi)
+ * [D_0 + 2 sum_{n>=1} D_n cos(n v)] (a = 1). */
+double or_gf_partial(int dim, int which, double v, double R, double R0, double tau) {
+  double D[ANG_NMAX + 1];
+  int N = or_ang_coeffs(dim, which, R, R0, tau, D, ANG_NMAX + 1);
+  if (dim == 3) {
+    double pm1 = 1.0, p = v, sum = D[0];
+    for (int n = 1; n <= N; ++n) {
+      sum += (2.0 * n + 1.0) * D[n] * p;
+      double pp1 = ((2.0 * n + 1.0) * v * p - n * pm1) / (n + 1.0);
+      pm1 = p;
+      p = pp1;
+    }
+    return sum / (4.0 * PI) * (2.0 / PI);
+  }
+  double sum = D[0];
+  for (int n = 1; n <= N; ++n) sum += 2.0 * D[n] * cos(n * v);
+  return sum / (2.0 * PI);
+}
+
+/* The conditional density of the angle (for the pins): 3D f(mu), 2D f(theta) on [0, pi] (twice
+ * the density on (-pi, pi]). */
+double or_ang_density(int dim, double v, double R, double R0, double tau) {
+  double D[ANG_NMAX + 1];
+  int N = or_ang_coeffs(dim, 0, R, R0, tau, D, ANG_NMAX + 1);
+  if (dim == 3) {
+    double pm1 = 1.0, p = v, sum = 0.5;
+    for (int n = 1; n <= N; ++n) {
+      sum += 0.5 * (2.0 * n + 1.0) * D[n] / D[0] * p;
+      double pp1 = ((2.0 * n + 1.0) * v * p - n * pm1) / (n + 1.0);
+      pm1 = p;
+      p = pp1;
+    }
+    return sum;
+  }
+  double sum = 1.0;
+  for (int n = 1; n <= N; ++n) sum += 2.0 * D[n] / D[0] * cos(n * v);
+  return sum / PI;
+}
+
+/* A unit vector e1 perpendicular to the unit vector u (3D): the coordinate axis along u's
+ * smallest component (the first such axis on ties), made perpendicular and normalised; e2 = u x e1. */
+static void perp_frame(const double* u, double* e1, double* e2) {
+  int k = 0;
+  if (fabs(u[1]) < fabs(u[k])) k = 1;
+  if (fabs(u[2]) < fabs(u[k])) k = 2;
+  double a[3] = {0, 0, 0};
+  a[k] = 1.0;
+  double d = u[k];
+  double v[3] = {a[0] - d * u[0], a[1] - d * u[1], a[2] - d * u[2]};
+  double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int i = 0; i < 3; ++i) e1[i] = v[i] / nv;
+  e2[0] = u[1] * e1[2] - u[2] * e1[1];
+  e2[1] = u[2] * e1[0] - u[0] * e1[2];
+  e2[2] = u[0] * e1[1] - u[1] * e1[0];
+}
+
+/* Unit direction of the new separation: angle from or_ang_sample at U_ang about the axis u (the
+ * start separation's direction), azimuth (3D) 2 pi U_azi, sign of the angle (2D) U_azi < 1/2.
+ * The step evaluates the series only while at most ANG_NSTEP partial waves are needed (kappa =
+ * R' R0 / 2 tau up to ~40); otherwise it returns 0 and the caller keeps the free step's direction. */
+#define ANG_NSTEP 127
+static int ang_direction(int dim, const double* u, double U_ang, double U_azi, double Rn, double R0, double tau,
+                         double* dir) {
+  if (ang_terms(Rn, R0, tau) > ANG_NSTEP) return 0;
+  if (dim == 3) {
+    double mu = or_ang_sample(3, U_ang, Rn, R0, tau);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu)), ph = 2.0 * PI * U_azi;
+    double e1[3], e2[3];
+    perp_frame(u, e1, e2);
+    double c = cos(ph), s = sin(ph);
+    for (int i = 0; i < 3; ++i) dir[i] = mu * u[i] + st * (c * e1[i] + s * e2[i]);
+  } else {
+    double th = or_ang_sample(2, U_ang, Rn, R0, tau);
+    if (U_azi < 0.5) th = -th;
+    double c = cos(th), s = sin(th);
+    dir[0] = c * u[0] - s * u[1];
+    dir[1] = s * u[0] + c * u[1];
+    dir[2] = 0.0;
+  }
+  return 1;
+}
+
+/* The whole propagation of one encountered pair (for the tests): start separation vector r0
+ * (scaled by a), new length from the radial law at tail fraction u_res, direction from
+ * ang_direction at (u_ang, u_azi); out = the new separation vector (scaled). */
+void or_propagate(int dim, const double* r0, double tau, double tau_s, double u_res, double u_ang, double u_azi,
+                  double* out) {
+  double l0 = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + (dim == 3 ? r0[2] * r0[2] : 0.0));
+  double R0 = l0 < 1.0 ? 1.0 : l0;
+  double Rn = dim == 3 ? or_resample3(u_res, R0, tau) : or_resample2(u_res, R0, tau, tau_s);
+  double u[3] = {1.0, 0.0, 0.0}, dir[3];
+  if (l0 > 0.0)
+    for (int d = 0; d < dim; ++d) u[d] = r0[d] / l0;
+  if (!ang_direction(dim, u, u_ang, u_azi, Rn, R0, tau, dir))
+    for (int d = 0; d < 3; ++d) dir[d] = u[d];
+  for (int d = 0; d < 3; ++d) out[d] = d < dim ? Rn * dir[d] : 0.0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Geometry in the periodic box.                                                                  */
 /* ------------------------------------------------------------------------------------------ */
 static double min_image(double d, double L) {
@@ -708,13 +1057,6 @@ static int cmp_fired(const void* x, const void* y) {
   return 0;
 }
 
-/* Test hook for negative controls: plants one deliberate mistake in the conflict resolution so
- * that a test can show its statistic rejects it.  0 (default): the method as specified.
- *   1: key = -ln(U_sel) * p_enc instead of -ln(U_sel) / p_enc
- *   2: fired pairs accepted greedily in DESCENDING key order
- *   3: the encounter draw U_enc reused as the selection draw */
-static int g_fault = 0;
-void or_set_fault(int fault) { g_fault = fault; }
 
 static int cmp_fired_faulty(const void* x, const void* y) {
   return g_fault == 2 ? -cmp_fired(x, y) : cmp_fired(x, y);
@@ -725,6 +1067,67 @@ typedef struct {
   int species[2];
   double x[2][3];
 } products_t;
+
+/* Steps 2-3 for the pair (i, j): returns -1 if it is not a candidate (decayed, non-interacting or
+ * beyond the cut-off), 0 if it is a candidate that did not fire, 1 if it fired (*f filled).
+ * Counts candidates, overlaps and near-threshold draws; appends the candidate to the trace. */
+static int test_pair(const or_system* sys, const or_state* in, const pair_param pp[OR_MAX_SPECIES][OR_MAX_SPECIES],
+                     const double* xstart, const double* x1, const int* decayed, uint32_t step, int64_t i,
+                     int64_t j, fired_pair* f, int64_t* cand, int64_t* ovl, int64_t* near, or_trace* trace) {
+  const int dim = sys->dim;
+  const double L = sys->L;
+  if (decayed[j]) return -1;
+  const pair_param* q = &pp[in->sp[i]][in->sp[j]];
+  if (q->rule < 0) return -1;
+  int64_t a = in->id[i] < in->id[j] ? i : j;
+  int64_t b = a == i ? j : i;
+  double r0v[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) {
+    r0v[d] = min_image(xstart[3 * b + d] - xstart[3 * a + d], L);
+    rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
+  }
+  double r02 = norm2(r0v, dim);
+  if (!(r02 < q->rcut2)) return -1;
+  double R0 = sqrt(r02) / q->sigma;
+  double R = sqrt(norm2(rv, dim)) / q->sigma;
+  double p = p_enc_dim(sys, R, R0, q->tau);
+  uint32_t w[4];
+  stream(sys, step, in->id[a], in->id[b], OR_TAG_ENC, w);
+  double u_enc = or_u52(w[0], w[1]), u_sel = or_u52(w[2], w[3]);
+  int fires = u_enc < p;
+  (*cand)++;
+  if (R <= 1.0) (*ovl)++;
+  if (fabs(u_enc - p) <= NEAR_THRESHOLD) (*near)++;
+  int64_t tidx = -1;
+  if (trace && trace->n < trace->cap) {
+    tidx = trace->n;
+    trace->ida[trace->n] = in->id[a];
+    trace->idb[trace->n] = in->id[b];
+    trace->p_enc[trace->n] = p;
+    trace->u_enc[trace->n] = u_enc;
+    trace->fired[trace->n] = fires;
+    trace->matched[trace->n] = 0;
+    trace->n++;
+  }
+  if (!fires) return 0;
+  f->a = a;
+  f->b = b;
+  f->ida = in->id[a];
+  f->idb = in->id[b];
+  f->tidx = tidx;
+  f->p = p;
+  f->key = g_fault == 1 ? -log(u_sel) * p : (g_fault == 3 ? -log(u_enc) / p : -log(u_sel) / p);
+  f->rule = q->rule;
+  return 1;
+}
+
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* stats,
             or_trace* trace) {
@@ -804,56 +1207,58 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
    * is tested with p_enc (overlap forces p_enc = 1) and a uniform draw. */
   int64_t fcap = 1024, fn = 0;
   fired_pair* fired = (fired_pair*)malloc(sizeof(fired_pair) * (size_t)fcap);
-  for (int64_t i = 0; i < n; ++i) {
-    if (decayed[i]) continue;
-    for (int64_t j = i + 1; j < n; ++j) {
-      if (decayed[j]) continue;
-      const pair_param* q = &pp[in->sp[i]][in->sp[j]];
-      if (q->rule < 0) continue;
-      int64_t a = in->id[i] < in->id[j] ? i : j;
-      int64_t b = a == i ? j : i;
-      double r0v[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
-      for (int d = 0; d < dim; ++d) {
-        r0v[d] = min_image(xstart[3 * b + d] - xstart[3 * a + d], L);
-        rv[d] = min_image(x1[3 * b + d] - x1[3 * a + d], L);
+#ifdef _OPENMP
+  /* The all-core CPU baseline build: rows of the pair loop on all threads, each with its own list;
+   * the greedy matching sorts the fired pairs by (key, id_a, id_b), so the lists' order does not
+   * matter and the result equals the serial loop's.  The per-candidate trace stays serial. */
+  if (!trace) {
+    int64_t cand = 0, ovl = 0, near = 0;
+#pragma omp parallel reduction(+ : cand, ovl, near)
+    {
+      int64_t lcap = 256, ln = 0;
+      fired_pair* loc = (fired_pair*)malloc(sizeof(fired_pair) * (size_t)lcap);
+#pragma omp for schedule(dynamic, 16)
+      for (int64_t i = 0; i < n; ++i) {
+        if (decayed[i]) continue;
+        for (int64_t j = i + 1; j < n; ++j) {
+          fired_pair f;
+          int rc = test_pair(sys, in, pp, xstart, x1, decayed, step, i, j, &f, &cand, &ovl, &near, NULL);
+          if (rc <= 0) continue;
+          if (ln == lcap) {
+            lcap *= 2;
+            loc = (fired_pair*)realloc(loc, sizeof(fired_pair) * (size_t)lcap);
+          }
+          loc[ln++] = f;
+        }
       }
-      double r02 = norm2(r0v, dim);
-      if (!(r02 < q->rcut2)) continue;
-      double R0 = sqrt(r02) / q->sigma;
-      double R = sqrt(norm2(rv, dim)) / q->sigma;
-      double p = p_enc_dim(sys, R, R0, q->tau);
-      uint32_t w[4];
-      stream(sys, step, in->id[a], in->id[b], OR_TAG_ENC, w);
-      double u_enc = or_u52(w[0], w[1]), u_sel = or_u52(w[2], w[3]);
-      int fires = u_enc < p;
-      st.candidates++;
-      if (R <= 1.0) st.overlaps++;
-      if (fabs(u_enc - p) <= NEAR_THRESHOLD) st.near_threshold++;
-      int64_t tidx = -1;
-      if (trace && trace->n < trace->cap) {
-        tidx = trace->n;
-        trace->ida[trace->n] = in->id[a];
-        trace->idb[trace->n] = in->id[b];
-        trace->p_enc[trace->n] = p;
-        trace->u_enc[trace->n] = u_enc;
-        trace->fired[trace->n] = fires;
-        trace->matched[trace->n] = 0;
-        trace->n++;
-      }
-      if (!fires) continue;
-      if (fn == fcap) {
-        fcap *= 2;
+#pragma omp critical
+      {
+        while (fn + ln > fcap) fcap *= 2;
         fired = (fired_pair*)realloc(fired, sizeof(fired_pair) * (size_t)fcap);
+        memcpy(fired + fn, loc, sizeof(fired_pair) * (size_t)ln);
+        fn += ln;
       }
-      fired[fn].a = a;
-      fired[fn].b = b;
-      fired[fn].ida = in->id[a];
-      fired[fn].idb = in->id[b];
-      fired[fn].tidx = tidx;
-      fired[fn].p = p;
-      fired[fn].key = g_fault == 1 ? -log(u_sel) * p : (g_fault == 3 ? -log(u_enc) / p : -log(u_sel) / p);
-      fired[fn].rule = q->rule;
-      fn++;
+      free(loc);
+    }
+    st.candidates += cand;
+    st.overlaps += ovl;
+    st.near_threshold += near;
+  } else
+#endif
+  {
+    for (int64_t i = 0; i < n; ++i) {
+      if (decayed[i]) continue;
+      for (int64_t j = i + 1; j < n; ++j) {
+        fired_pair f;
+        int rc = test_pair(sys, in, pp, xstart, x1, decayed, step, i, j, &f, &st.candidates, &st.overlaps,
+                           &st.near_threshold, trace);
+        if (rc <= 0) continue;
+        if (fn == fcap) {
+          fcap *= 2;
+          fired = (fired_pair*)realloc(fired, sizeof(fired_pair) * (size_t)fcap);
+        }
+        fired[fn++] = f;
+      }
     }
   }
   st.fired = fn;
@@ -896,16 +1301,29 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
       double R0 = sqrt(norm2(r0v, dim)) / q->sigma;
       if (R0 < 1.0) R0 = 1.0;
       double Rn = resample_dim(sys, u_res, R0, q->tau);
-      double len = sqrt(norm2(rv, dim));
       double dir[3] = {0, 0, 0};
-      if (len > 0.0) {
-        for (int d = 0; d < dim; ++d) dir[d] = rv[d] / len;
-      } else {
-        double l0 = sqrt(norm2(r0v, dim));
+      int exact = 0;
+      if (sys->angle_mode == 0) {
+        /* the direction from the full propagator: its angle to r0 from the partial-wave law
+         * given R', uniform azimuth (start separation zero: the x axis) */
+        double l0 = sqrt(norm2(r0v, dim)), u[3] = {1.0, 0.0, 0.0};
         if (l0 > 0.0)
-          for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
-        else
-          dir[0] = 1.0;
+          for (int d = 0; d < dim; ++d) u[d] = r0v[d] / l0;
+        uint32_t wa[4];
+        stream(sys, step, in->id[a], in->id[b], OR_TAG_ANG, wa);
+        exact = ang_direction(dim, u, or_u52(wa[0], wa[1]), or_u52(wa[2], wa[3]), Rn, R0, q->tau, dir);
+      }
+      if (!exact) {
+        double len = sqrt(norm2(rv, dim));
+        if (len > 0.0) {
+          for (int d = 0; d < dim; ++d) dir[d] = rv[d] / len;
+        } else {
+          double l0 = sqrt(norm2(r0v, dim));
+          if (l0 > 0.0)
+            for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
+          else
+            dir[0] = 1.0;
+        }
       }
       for (int d = 0; d < dim; ++d) {
         double nr = Rn * q->sigma * dir[d];
@@ -977,6 +1395,14 @@ int or_step(const or_system* sys, const or_state* in, or_state* out, or_stats* s
         stream(sys, step, in->id[i], 0xFFFFFFFFu, OR_TAG_RES, w);
         double u_res = or_u52(w[0], w[1]), u_reac = or_u52(w[2], w[3]);
         double Rn = resample_dim(sys, u_res, 1.0, q->tau);
+        if (sys->angle_mode == 0) {
+          /* from contact along dir: the new direction from the full propagator about dir */
+          double u[3] = {dir[0], dir[1], dir[2]}, nd[3];
+          uint32_t wa[4];
+          stream(sys, step, in->id[i], 0xFFFFFFFFu, OR_TAG_ANG, wa);
+          if (ang_direction(dim, u, or_u52(wa[0], wa[1]), or_u52(wa[2], wa[3]), Rn, 1.0, q->tau, nd))
+            for (int d = 0; d < 3; ++d) dir[d] = nd[d];
+        }
         for (int d = 0; d < dim; ++d) rv[d] = Rn * q->sigma * dir[d];
         if (rule->bc == OR_BC_ABS) {
           recombine = 1;

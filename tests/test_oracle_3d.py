@@ -224,6 +224,10 @@ def _isolated_pair_reaction_fraction(n_pairs, R0, steps, tau_target=0.2, h=0.199
     for seed in seeds:
         sys_, pos, sp = W.isolated_pairs_3d(n_pairs, R0, sigma=sigma, D=D, ka=ka, dt=dt, seed=seed,
                                             spacing=0.2)
+        # the reacted fraction of isolated pairs depends only on the radial process (the direction
+        # of a resampled separation changes no later radial law), so the cheaper free-step
+        # direction serves here
+        sys_.angle = "free_step"
         st = O.State(pos.copy(), sp.copy(), np.arange(2 * n_pairs, dtype=np.uint32), 0, 2 * n_pairs, 0.0)
         st = _run(sys_, st, steps)
         reacted += int(np.sum(st.species == 2))

@@ -39,6 +39,9 @@ def test_oracle_equilibrium_bound_count():
     n0 = 150
     L = (n0 / (W.PER_UM3_PER_UM * 10.0)) ** (1.0 / 3.0)
     system = W.reversible_3d(dt=1e-4, n_each=n0, L=L, equilibrium_start=True, seed=11)
+    # 30 000 oracle steps: the free-step direction keeps this within the CPU suite's budget; the
+    # full-size GPU equilibrium runs (test_gpu_equilibrium) use the exact propagator direction
+    system.angle = "free_step"
     st = O.init_state(system)
     xs = []
     for _ in range(30_000):

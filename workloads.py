@@ -74,6 +74,9 @@ class System:
     replicas: Optional[List[Replica]] = None
     # deterministic drift velocity per species (um/s, a 3-vector each), applied as a split step
     drift: Optional[Sequence[Sequence[float]]] = None
+    # direction of an encountered pair's new separation: "exact" (from the full propagator) or
+    # "free_step" (the free step's direction kept, only the length resampled)
+    angle: str = "exact"
 
     @property
     def n_species(self) -> int:
