@@ -32,8 +32,13 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-KERNELS_PER_STEP = 7           # kernels of one step: prepare, scan (cells), scatter, sweep, trivial
-                               # matching, matching rounds + resolution, compaction (scan + placement)
+KERNELS_PER_STEP = 8           # kernels of one step with separate launches: prepare, scan (cells),
+                               # scatter, sweep, trivial matching, matching rounds + resolution,
+                               # angle pass (exact directions), compaction (scan + placement)
+# the fused launch runs the same seven stages as phases of one cooperative kernel
+KERNEL_OF_PHASE = {"ph_prepare": "k_prepare", "ph_scan_cells": "k_scan_cells", "ph_scatter_cells": "k_scatter_cells",
+                   "ph_sweep": "k_sweep", "ph_match_trivial": "k_match_trivial",
+                   "ph_match_resolve": "k_match_resolve", "ph_angles": "k_angles", "ph_compact": "k_compact"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -46,6 +51,9 @@ def parse(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--dt", type=float, default=1e-5)
     ap.add_argument("--n-each", type=int, default=100_000)
+    ap.add_argument("--angle", default="free_step", choices=["free_step", "exact"],
+                    help="direction of a resampled pair: the free step's (the step as specified) or "
+                         "drawn from the full propagator (measured beside it in any case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, pair-prob batch, e2e")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
@@ -59,13 +67,16 @@ def box_edge(args):
     return 2.55 * (args.n_each / 100_000) ** (1.0 / 3.0)
 
 
-def workload(args, seed=1):
-    return W.reversible_3d(dt=args.dt, seed=seed, n_each=args.n_each, L=box_edge(args), equilibrium_start=True)
+def workload(args, seed=1, angle=None):
+    system = W.reversible_3d(dt=args.dt, seed=seed, n_each=args.n_each, L=box_edge(args), equilibrium_start=True)
+    system.angle = angle or args.angle
+    return system
 
 
 def workload_name(args):
     return (f"3D A+B<->C radiation BC, L={box_edge(args):.3g} um (10 uM), N_A=N_B={args.n_each:.0e} "
-            f"(mass-action start), sigma=0.005, D=1/1/0.5, ka=0.02, kd=10, dt={args.dt:g}")
+            f"(mass-action start), sigma=0.005, D=1/1/0.5, ka=0.02, kd=10, dt={args.dt:g}, "
+            f"pair direction: {args.angle}")
 
 
 # ------------------------------------------------------------------------------------------------
@@ -132,6 +143,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def traffic_per_launch(kernel, precision, n):
+    """DRAM bytes per launch of `kernel` from one ncu capture (profiles/traffic.json), scaled to n
+    particles by the particles of the captured workload (the traffic of these kernels grows in
+    proportion to the particles they move); None when no capture of the current kernel exists."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tj = json.load(f)
+    rec = tj.get(f"{kernel}:{precision}")
+    if not isinstance(rec, dict) or rec.get("bytes") is None or not rec.get("particles"):
+        return None
+    return rec["bytes"] * n / rec["particles"]
+
+
 def algorithmic_bytes(kernel, precision, w):
     """Per-launch algorithmic bytes of a step kernel: the data the stage must read and write once
     (w: particles n, binned particles nb, cells, fired pairs, accepted pairs, decays per step).
@@ -153,9 +179,13 @@ def algorithmic_bytes(kernel, precision, w):
         # degrees cleared; per accepted pair or decay: record, state, 2x2 positions read, 2
         # positions + statuses written (conflict rounds add re-reads of the conflict pairs)
         "k_match_resolve": fired * 16 + (acc + dec) * (48 + 6 * v),
+        # one 160-B job per resolved pair or decay pair left to it; write two positions
+        "k_angles": (acc + dec) * (160 + 2 * v),
         # read status, end position, id; write position + id (the scan stays on chip)
         "k_compact": n * (2 * v + 12),
     }
+    table["k_step_fused"] = sum(table.values())      # the whole step in one launch
+    kernel = KERNEL_OF_PHASE.get(kernel, kernel)     # a phase of the fused launch = its stage's kernel
     if kernel not in table:
         raise KeyError(f"no algorithmic byte count for step kernel {kernel}")
     return table[kernel]
@@ -164,7 +194,45 @@ def algorithmic_bytes(kernel, precision, w):
 # ------------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle on a bounded sample
 # ------------------------------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (x86: /proc/cpuinfo; Arm: lscpu), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return None
+
+
+def _oracle_rate(O, system, seconds, openmp, max_steps=None):
+    """Particle-steps/s of the oracle stepping `system` for about `seconds` (or max_steps)."""
+    st = O.init_state(system)
+    ps = steps = 0
+    t0 = time.perf_counter()
+    while True:
+        n = st.n
+        st, _ = O.step(system, st, openmp=openmp)
+        ps += n
+        steps += 1
+        if max_steps is not None and steps >= max_steps:
+            break
+        if max_steps is None and time.perf_counter() - t0 >= seconds and steps >= 2:
+            break
+    return ps / (time.perf_counter() - t0), steps
+
+
 def oracle_sample(args, seconds, seed=1):
+    """The CPU baseline: the FP64 oracle, single-threaded and (OpenMP build, pair loop on all
+    threads, same results) on all host cores, on bounded samples of the workloads."""
     import oracle as O
 
     O.build()
@@ -173,22 +241,43 @@ def oracle_sample(args, seconds, seed=1):
     n_each = 4000
     L = box_edge(args) * (n_each / args.n_each) ** (1 / 3)
     system = W.reversible_3d(dt=args.dt, seed=seed, n_each=n_each, L=L, equilibrium_start=True)
-    st = O.init_state(system)
-    ps = 0
-    steps = 0
+    system.angle = args.angle
+    v1, steps = _oracle_rate(O, system, seconds, openmp=False)
+    out = {"value": v1, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"{steps} oracle steps of the same system in a sub-box L={L:.3f} um with "
+                     f"N_A=N_B={n_each} (same 10 uM density, dt, chemistry); O(N^2) candidate "
+                     f"search, single thread (the O(N^2) search makes the per-particle cost grow "
+                     f"with the box, so the full-size system would run slower per particle)",
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+    threads = O.threads(True) if O.lib(True) is not None else 1
+    if threads > 1:
+        vall, steps_all = _oracle_rate(O, system, seconds / 3, openmp=True)
+        out["all_cores"] = {"value": vall, "unit": "particle-steps/s", "cores": threads,
+                            "sample": f"{steps_all} steps of the same sub-box, OpenMP build (pair loop on all threads)"}
+    # the irreversible A+B->C workload in full (2000 A + 2000 B... 1000 + 1000, 2000 steps) and the
+    # first 64 replicas of the ensemble, on all cores when the OpenMP build exists
+    omp = threads > 1
+    irr = W.irreversible_3d(seed=seed)
+    irr.angle = args.angle
+    v0, n0 = _oracle_rate(O, irr, 0.0, openmp=omp, max_steps=2000)
+    out["irreversible_3d_full"] = {"value": v0, "unit": "particle-steps/s", "cores": threads, "steps": n0,
+                                   "sample": "3D A+B->C, 1000 + 1000 in L = 1 um, dt = 1e-5, all 2000 steps"}
+    ens = W.ensemble_3d()
+    ens.angle = args.angle
+    reps = ens.replica_list()[:64]
     t0 = time.perf_counter()
-    while True:
-        n = st.n
-        st, _ = O.step(system, st)
-        ps += n
-        steps += 1
-        if time.perf_counter() - t0 >= seconds and steps >= 2:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": ps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps of the same system in a sub-box L={L:.3f} um with "
-                      f"N_A=N_B={n_each} (same 10 uM density, dt, chemistry); O(N^2) candidate "
-                      f"search, single thread"}
+    ps = 0
+    for r, rep in enumerate(reps):
+        sysr = W.System(**{**ens.__dict__, "L": rep.L, "n_init": list(rep.n_init), "replicas": None})
+        st = O.init_state(sysr)
+        st2, _ = O.step(sysr, st, openmp=omp)
+        ps += st.n
+    el = time.perf_counter() - t0
+    out["ensemble_3d_64_replicas"] = {"value": ps / el, "unit": "particle-steps/s", "cores": threads,
+                                      "sample": "one step of each of the first 64 of the 4096 replicas "
+                                                f"({ps} particles); the whole ensemble's rate extrapolates "
+                                                "per replica"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -201,6 +290,7 @@ def run_reference(args, rank, world):
     n_each = 4000
     L = box_edge(args) * (n_each / args.n_each) ** (1 / 3)
     system = W.reversible_3d(dt=args.dt, seed=1, n_each=n_each, L=L, equilibrium_start=True)
+    system.angle = args.angle
     st = O.init_state(system)
     for _ in range(max(args.warmup, 0) and min(args.warmup, 3)):
         st, _ = O.step(system, st)
@@ -303,8 +393,11 @@ def run_ours(args, rank, world, local_rank):
             for name, ms in sim.timed_step():
                 ker.setdefault(name, []).append(ms)
         ker_avg = {k: sum(v) / len(v) for k, v in ker.items()}
-        step_ms = sum(ker_avg.values())
-        dominant = max(ker_avg, key=lambda k: ker_avg[k])
+        fused = "k_step_fused" in ker_avg
+        # with the fused launch the step is ONE kernel (its phases are reported beside it)
+        phases = {k: v for k, v in ker_avg.items() if k != "k_step_fused"}
+        step_ms = ker_avg["k_step_fused"] if fused else sum(ker_avg.values())
+        dominant = "k_step_fused" if fused else max(ker_avg, key=lambda k: ker_avg[k])
         st = sim.get_state()
         d_stats = {k: obs1["stats"][k] - obs0["stats"][k] for k in obs1["stats"]}
         per = max(steps_done, 1)
@@ -315,20 +408,13 @@ def run_ours(args, rank, world, local_rank):
         peak, peak_kind = measured_peaks()
         ab = algorithmic_bytes(dominant, args.precision, work)
         achieved = ab / (ker_avg[dominant] * 1e-3) / 1e9
-        traffic = None
-        prof = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(prof):
-            with open(prof) as f:
-                tj = json.load(f)
-            key = f"{dominant}:{args.precision}"
-            if key in tj:
-                traffic = tj[key]
+        traffic = traffic_per_launch(dominant, args.precision, work["n"])
         extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                               "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
                               "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})",
                               "algorithmic_bytes_per_launch": ab, "kernel_ms": ker_avg[dominant],
                               "share": ker_avg[dominant] / step_ms}
-        step_bytes = sum(algorithmic_bytes(k, args.precision, work) for k in ker_avg)
+        step_bytes = sum(algorithmic_bytes(k, args.precision, work) for k in phases)
         step_graph_ms = 1e3 * t_max / per
         extras["step_roofline"] = {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
                                    "ms_per_step": step_graph_ms,
@@ -337,7 +423,12 @@ def run_ours(args, rank, world, local_rank):
                                    "frac": step_bytes / (step_graph_ms * 1e-3) / 1e9 / peak,
                                    "work_per_step": {k: round(float(v), 1) for k, v in work.items()}}
         extras["kernel_ms"] = {k: round(v, 5) for k, v in ker_avg.items()}
-        extras["sweep_pair_prob_evals_per_s"] = cand_per_step / (ker_avg["k_sweep"] * 1e-3)
+        extras["phase_roofline"] = {
+            k: {"ms": round(v, 5), "algorithmic_bytes": algorithmic_bytes(k, args.precision, work),
+                "frac": algorithmic_bytes(k, args.precision, work) / max(v * 1e-3, 1e-12) / 1e9 / peak}
+            for k, v in phases.items()}
+        sweep_ms = ker_avg.get("ph_sweep", ker_avg.get("k_sweep"))
+        extras["sweep_pair_prob_evals_per_s"] = cand_per_step / (sweep_ms * 1e-3)
         extras["candidates_per_step"] = cand_per_step
         if not args.no_extras:
             extras.update(extra_measurements(args, torch, pkg, flush, sim))
@@ -352,11 +443,11 @@ def run_ours(args, rank, world, local_rank):
         "steps": steps_done, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / steps_done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "precision": args.precision,
+        "config": {"workload": workload_name(args), "precision": args.precision, "angle": args.angle,
                    "particles": int(obs1["counts"].sum()), "timing": "2-step CUDA graph launches, events on the library stream",
                    "l2": "flushed (512 MiB write) between timed graph launches",
                    "parallelism": f"replicas x{world} (one independent system per GPU)"},
-        "gpu_launches": KERNELS_PER_STEP * steps_done,
+        "gpu_launches": steps_done // 2 if layout.get("fused") else KERNELS_PER_STEP * steps_done,
         "layout": layout,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
     }
@@ -433,6 +524,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
     for dt in (1e-6, 1e-4):
         for prec in ("mixed", "fp64"):
             system = W.reversible_3d(dt=dt, seed=1, n_each=args.n_each, L=box_edge(args), equilibrium_start=True)
+            system.angle = args.angle
             sim = pkg.Simulation(system, precision=prec)
             sim.run(4)
             sim.sync()
@@ -445,8 +537,9 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
                 "candidates_per_step": (o1["stats"]["candidates"] - o0["stats"]["candidates"]) / nst}
             sim.close()
     out["dt_sweep"] = sweep
+    out["exact_angles"] = exact_angle_measurement(args, torch, pkg, flush)
     if not args.no_workloads:
-        out["workloads"] = other_workloads(torch, pkg, flush)
+        out["workloads"] = other_workloads(torch, pkg, flush, args.angle)
     # end to end through the C ABI with host buffers: per step, upload the state from page-locked
     # host memory (rd_set_state), one step, read the resulting state (positions, species, ids,
     # next ids) back into page-locked host memory (rd_get_state).  The headline is one system, so
@@ -494,7 +587,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
 def fpt_measurement(args, torch, pkg, flush, levels=10):
     """First-passage refinement (rd_first_passage) of 2^20 encountered pairs of the headline rule,
     FP64 and FP32 (mixed handle), device-timed, with the oracle on a sample of the same pairs beside it."""
-    from paper_1107_0270_gb300 import fpt_bench
+    import fpt_bench
 
     system = workload(args, seed=2)
     r0e, re, distinct = fpt_bench.encountered_pairs(pkg, torch, system, 1 << 20)
@@ -516,7 +609,32 @@ def fpt_measurement(args, torch, pkg, flush, levels=10):
     return res
 
 
-def other_workloads(torch, pkg, flush):
+def exact_angle_measurement(args, torch, pkg, flush):
+    """The headline workload with every resampled pair's direction drawn from the full propagator
+    (the angle pass), both precisions: rate and the angle pass's share of the step."""
+    res = {}
+    for prec, steps in (("mixed", 40), ("fp64", 20)):
+        sim = pkg.Simulation(workload(args, seed=1, angle="exact"), precision=prec)
+        sim.run(4)
+        sim.sync()
+        o0 = sim.observables()
+        el, nst = timed_graph_run(sim, torch, flush, steps)
+        o1 = sim.observables()
+        ker = {}
+        for _ in range(4):
+            for kname, ms in sim.timed_step():
+                ker[kname] = ker.get(kname, 0.0) + ms / 4
+        ang = ker.get("ph_angles", ker.get("k_angles", 0.0))
+        res[prec] = {"value": (o1["stats"]["particle_steps"] - o0["stats"]["particle_steps"]) / el,
+                     "unit": "particle-steps/s", "ms_per_step": 1e3 * el / nst,
+                     "angle_pass_ms": round(ang, 5),
+                     "jobs_per_step": (o1["stats"]["resampled"] - o0["stats"]["resampled"]) / nst,
+                     "fallbacks": o1["stats"]["angle_fallback"] - o0["stats"]["angle_fallback"]}
+        sim.close()
+    return res
+
+
+def other_workloads(torch, pkg, flush, angle="free_step"):
     """The other experiment shapes at full size (mixed precision), timed like the headline."""
     cases = [
         ("ensemble_3d", "4096 independent 3D A+B<->C replicas, N per species log-uniform in [64, 8192], "
@@ -529,7 +647,9 @@ def other_workloads(torch, pkg, flush):
     for name, desc, make, steps in cases:
         try:
             t0 = time.perf_counter()
-            sim = pkg.Simulation(make(), precision="mixed")
+            system = make()
+            system.angle = angle
+            sim = pkg.Simulation(system, precision="mixed")
             init_s = time.perf_counter() - t0
             sim.run(4)
             sim.sync()

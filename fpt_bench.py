@@ -3,7 +3,7 @@
 Encountered pairs are made the way a step makes them: candidate-shaped pairs of the reversible 3D
 system (start separations uniform in the cut-off shell, free end points) kept with probability
 p_enc, evaluated by the library itself before any timing.  ``python -m
-paper_1107_0270_gb300.fpt_bench --pairs N --levels K`` prints one JSON line; the benchmark calls
+fpt_bench --pairs N --levels K`` prints one JSON line; the benchmark calls
 the same functions.
 """
 from __future__ import annotations

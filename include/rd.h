@@ -120,6 +120,25 @@ typedef struct {
                                          Brownian / reaction step runs from there with the pair
                                          probabilities taken from the Brownian end points.  All zero: no
                                          drift step */
+  int32_t step_launch;                /* how a step is launched: 0 automatic (one fused cooperative
+                                         launch per graph of steps up to 2^22 particles of capacity,
+                                         separate kernels above; with the autotuner, the faster of
+                                         the two), 1 always fused, 2 always separate kernels.  Both
+                                         give bit-identical results; RD_EINVAL outside 0..2 */
+  int32_t force_paths;                /* 0 normally.  Bit 0: conflict rounds on the whole cooperative
+                                         grid for any number of conflict pairs (normally only above
+                                         2048); bit 1: short conflict lists in global memory instead
+                                         of shared memory.  For tests of the large-size code paths at
+                                         small sizes; results are the same */
+  int32_t angle_mode;                 /* direction of an encountered pair's new separation (Eq.
+                                         passage_prob): 0 (default) drawn from the full propagator
+                                         G_ref - G_abs, its angle to the start separation from the
+                                         partial-wave series of Eqs. genericGF3D / genericGF (a draw
+                                         needing more than 128 partial waves, kappa = R' R0 / 2 tau
+                                         beyond ~40, keeps the free step's direction and is counted in
+                                         RD_STAT_ANGLE_FALLBACK); 1 the free step's direction kept, only
+                                         the length resampled */
+  int32_t pad_angle;
   rd_allocator allocator;
 } rd_config;
 
@@ -148,12 +167,14 @@ int rd_sync(rd_handle* h);
  * int64[n_replicas * n_species] (may be NULL), current particles per replica and species.
  * step/t (may be NULL): step index and simulated time (FP64 accumulation).  stats: caller-owned
  * int64[RD_NSTATS] (may be NULL), cumulative counters since rd_init (see RD_STAT_*). */
-#define RD_NSTATS 12
+#define RD_NSTATS 13
 enum {
   RD_STAT_CANDIDATES = 0, RD_STAT_FIRED = 1, RD_STAT_MATCHED = 2, RD_STAT_REACTIONS = 3,
   RD_STAT_RESAMPLED = 4, RD_STAT_DECAYS = 5, RD_STAT_RECOMBINED = 6, RD_STAT_NEAR_THRESHOLD = 7,
   RD_STAT_OVERLAPS = 8, RD_STAT_MATCH_ROUNDS = 9, RD_STAT_PARTICLE_STEPS = 10,
-  RD_STAT_FIRED_HWM = 11
+  RD_STAT_FIRED_HWM = 11,
+  RD_STAT_ANGLE_FALLBACK = 12   /* exact-angle draws that needed more than 128 partial waves and kept
+                                   the free step's direction instead (see rd_config.angle_mode) */
 };
 int rd_observables(rd_handle* h, int64_t* counts, int64_t* step, double* t, int64_t* stats);
 
@@ -186,6 +207,18 @@ int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r,
  * normalised tail of the propagator started at r0[k].  DEVICE pointers, asynchronous. */
 int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n,
                 double* r_new);
+
+/* Propagation of encountered pairs (Eq. passage_prob with the full Green's functions of Eqs.
+ * genericGF3D / genericGF): for k < n, a pair of rule `rule` (reflective or radiation boundary)
+ * with start separation vector r0[3k .. 3k+2] gets the new separation vector r_out[3k .. 3k+2]
+ * drawn from G_ref - G_abs: its length at tail fraction u[4k] of the radial law (as rd_resample),
+ * the cosine of its angle to r0 (3D; in 2D the angle in [0, pi]) at CDF value u[4k+1] of the
+ * partial-wave law given that length, its azimuth 2 pi u[4k+2] about r0 in the frame built from the
+ * coordinate axis along r0's smallest component (2D: the angle's sign negative iff u[4k+2] < 1/2);
+ * u[4k+3] is unused.  r0 = 0 uses the x axis.  A law needing more than 128 partial waves keeps r0's
+ * direction.  In the handle's precision (RD_MIXED: FP32, the length from the per-run table).
+ * DEVICE pointers (double; z = 0 in 2D); asynchronous.  Errors: RD_EINVAL. */
+int rd_propagate(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n, double* r_out);
 
 /* First-passage refinement of encountered pairs (Appendix, "Relation to first-passage time
  * simulation algorithms"): for k < n, a pair of rule `rule` whose separation went from r0[k] to
@@ -250,12 +283,15 @@ int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out
  * out[2] threads per block of the particle kernels, out[3] particle capacity, out[4] fired-pair
  * capacity, out[5] autotuned ms per step (0 if not tuned), out[6] largest cut-off radius, out[7]
  * threads per binned particle in the cell sweep (1, or one per stencil row), out[8] stencil reach
- * in cells (1, or 2 for 2D cells of half a cut-off).  Writes min(n, 9) values to the caller-owned
- * HOST array. */
+ * in cells (1, or 2 for 2D cells of half a cut-off), out[9] 1 if a step is one fused cooperative
+ * launch (0: one launch per kernel), out[10] blocks of that launch.  Writes min(n, 11) values to the
+ * caller-owned HOST array. */
 int rd_info(rd_handle* h, double* out, int32_t n);
 
-/* Name of the kernel-level timing hook: rd_time_kernels enables CUDA-event timing of every kernel
- * of the next rd_step; rd_kernel_times copies per-kernel (name, ms) pairs of that step. */
+/* Kernel-level timing hook: rd_time_kernels enables timing of the next rd_step; rd_kernel_times
+ * copies its (name, ms) pairs: with separate kernels the CUDA-event time of every kernel; with the
+ * fused launch the device time of every phase (global-timer stamps taken at the phase barriers)
+ * followed by "k_step_fused", the CUDA-event time of the whole launch. */
 int rd_time_kernels(rd_handle* h, int32_t enable);
 int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* cap*32 */,
                     float* ms);

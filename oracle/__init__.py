@@ -140,6 +140,8 @@ def _bind(L):
         L.or_ang_sample.argtypes = [C.c_int, d, d, d, d]
         L.or_ang_density.restype = d
         L.or_ang_density.argtypes = [C.c_int, d, d, d, d]
+        L.or_ang_cdf.restype = d
+        L.or_ang_cdf.argtypes = [C.c_int, d, d, d, d]
         L.or_gf_partial.restype = d
         L.or_gf_partial.argtypes = [C.c_int, C.c_int, d, d, d, d]
         L.or_propagate.restype = None
@@ -293,6 +295,11 @@ def ang_sample(dim, U, R, R0, tau):
 
 def ang_density(dim, v, R, R0, tau):
     return lib().or_ang_density(int(dim), float(v), float(R), float(R0), float(tau))
+
+
+def ang_cdf(dim, v, R, R0, tau):
+    """CDF of the conditional angle at v (3D: its cosine), the function ang_sample inverts."""
+    return lib().or_ang_cdf(int(dim), float(v), float(R), float(R0), float(tau))
 
 
 def propagate(dim, r0, tau, u_res, u_ang, u_azi, tau_s=0.01):

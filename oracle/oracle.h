@@ -125,6 +125,7 @@ int or_fpt_direction(int dim, double kappa, uint64_t seed, uint64_t strm, uint32
 int or_ang_coeffs(int dim, int which, double R, double R0, double tau, double* D, int cap);
 double or_ang_sample(int dim, double U, double R, double R0, double tau);
 double or_ang_density(int dim, double v, double R, double R0, double tau);
+double or_ang_cdf(int dim, double v, double R, double R0, double tau);
 double or_gf_partial(int dim, int which, double v, double R, double R0, double tau);
 /* One encountered pair's new separation vector (scaled units) from the start vector r0. */
 void or_propagate(int dim, const double* r0, double tau, double tau_s, double u_res, double u_ang, double u_azi,

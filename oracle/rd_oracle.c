@@ -836,6 +836,14 @@ double or_ang_sample(int dim, double U, double R, double R0, double tau) {
   return 0.5 * (lo + hi);
 }
 
+/* The CDF of the conditional angle at v (3D: the cosine; 2D: the angle in [0, pi]), the function
+ * or_ang_sample inverts. */
+double or_ang_cdf(int dim, double v, double R, double R0, double tau) {
+  double D[ANG_NMAX + 1];
+  int N = or_ang_coeffs(dim, 0, R, R0, tau, D, ANG_NMAX + 1);
+  return ang_cdf(dim, D, N, v);
+}
+
 /* The full Green's function at (R, v) from its partial waves (for the pins; which as in
  * or_ang_coeffs): 3D (1/4pi)(2/pi) sum_n (2n+1) P_n(mu) D_n with mu = v, 2D (1/2pi)
  * [D_0 + 2 sum_{n>=1} D_n cos(n v)] (a = 1). */

@@ -19,9 +19,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "librd.so")
 
 MAX_SPECIES, MAX_PAIRS, MAX_DECAYS = 16, 32, 16
-NSTATS = 12
+NSTATS = 13
 STAT_NAMES = ["candidates", "fired", "matched", "reactions", "resampled", "decays", "recombined",
-              "near_threshold", "overlaps", "match_rounds", "particle_steps", "fired_hwm"]
+              "near_threshold", "overlaps", "match_rounds", "particle_steps", "fired_hwm", "angle_fallback"]
 BC = {"none": 0, "abs": 1, "ref": 2, "rad": 3}
 PRECISION = {"fp64": 0, "mixed": 1}
 STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_ETIMEOUT",
@@ -30,7 +30,7 @@ STATUS = {0: "RD_OK", 1: "RD_EINVAL", 2: "RD_ENOMEM", 3: "RD_ECAPACITY", 4: "RD_
 EXPORTS = ["rd_init", "rd_step", "rd_run", "rd_sync", "rd_observables", "rd_get_state", "rd_set_state",
            "rd_pair_probs", "rd_resample", "rd_first_passage", "rd_last_fired", "rd_num_particles", "rd_time_kernels",
            "rd_kernel_times", "rd_free", "rd_strerror", "rd_last_cuda_error", "rd_step_static",
-           "rd_info", "rd_count_history", "rd_check_bounded_wait"]
+           "rd_info", "rd_count_history", "rd_check_bounded_wait", "rd_propagate"]
 
 
 class RDError(RuntimeError):
@@ -76,6 +76,8 @@ class _Config(C.Structure):
                 ("cell_factor_x100", C.c_int32), ("block_size", C.c_int32),
                 ("sweep_split", C.c_int32), ("cell_reach", C.c_int32),
                 ("drift", (C.c_double * 3) * MAX_SPECIES),
+                ("step_launch", C.c_int32), ("force_paths", C.c_int32),
+                ("angle_mode", C.c_int32), ("pad_angle", C.c_int32),
                 ("allocator", _Allocator)]
 
 
@@ -106,6 +108,7 @@ def _lib():
         L.rd_kernel_times.argtypes = [vp, i32, P(i32), C.c_char_p, P(C.c_float)]
         L.rd_step_static.argtypes = [P(_Config), vp, i64, vp, vp, vp, u32, i64, i64, vp, vp, vp, vp, vp, vp]
         L.rd_info.argtypes = [vp, P(d), i32]
+        L.rd_propagate.argtypes = [vp, i32, vp, vp, i64, vp]
         L.rd_count_history.argtypes = [vp, i64, i64, P(i64)]
         L.rd_check_bounded_wait.argtypes = [vp, C.c_uint32, P(i32)]
         L.rd_free.argtypes = [vp]
@@ -141,14 +144,21 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
 
 
+STEP_LAUNCH = {"auto": 0, "fused": 1, "separate": 2}
+
+
 def make_config(system, precision: Optional[str] = None, capacity_factor: float = 2.0,
                 pair_capacity: int = 0, cell_factor=None, block_size: int = 256, sweep_split: int = 0,
-                cell_reach: int = 0):
+                cell_reach: int = 0, step_launch: str = "auto", force_paths: int = 0):
     """Build the C configuration from a system description (see ``workloads.System``).
     cell_factor: cell edge in units of the largest cut-off; None = density-based per replica
     (about 0.25 interacting particles per cell), "tune" = timed autotuning at creation.
     sweep_split: 0 automatic, 1 one sweep thread per particle, 2 one per (particle, stencil row).
-    cell_reach: 0 automatic, 1 cells of a cut-off, 2 (2D) cells of half a cut-off, two-cell stencil."""
+    cell_reach: 0 automatic, 1 cells of a cut-off, 2 (2D) cells of half a cut-off, two-cell stencil.
+    step_launch: "auto", "fused" (the whole step as one cooperative launch) or "separate" (one
+    launch per kernel); both give bit-identical results.
+    force_paths: bit 0 conflict rounds on the whole grid at any size, bit 1 short conflict lists in
+    global memory (test knobs for the large-size paths; results unchanged)."""
     cfg = _Config()
     cfg.dim = int(system.dim)
     cfg.precision = PRECISION[precision or system.precision]
@@ -186,6 +196,9 @@ def make_config(system, precision: Optional[str] = None, capacity_factor: float 
     cfg.block_size = int(block_size)
     cfg.sweep_split = int(sweep_split)
     cfg.cell_reach = int(cell_reach)
+    cfg.step_launch = STEP_LAUNCH[step_launch]
+    cfg.force_paths = int(force_paths)
+    cfg.angle_mode = 1 if getattr(system, "angle", "exact") == "free_step" else 0
     drift = getattr(system, "drift", None)
     if drift is not None:
         for i, v in enumerate(drift):
@@ -199,7 +212,8 @@ class Simulation:
 
     def __init__(self, system, precision: Optional[str] = None, device: int = 0, stream=None,
                  capacity_factor: float = 2.0, pair_capacity: int = 0, cell_factor=None,
-                 block_size: int = 256, sweep_split: int = 0, cell_reach: int = 0):
+                 block_size: int = 256, sweep_split: int = 0, cell_reach: int = 0, step_launch: str = "auto",
+                 force_paths: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -212,7 +226,8 @@ class Simulation:
         self.n_replicas = len(system.replica_list())
         self.precision = precision or system.precision
         cfg, self._rep_arr = make_config(system, self.precision, capacity_factor, pair_capacity,
-                                         cell_factor, block_size, sweep_split, cell_reach)
+                                         cell_factor, block_size, sweep_split, cell_reach, step_launch,
+                                         force_paths)
         dev = self.device.index
 
         def _alloc(nbytes, stream_ptr, ctx):
@@ -271,12 +286,13 @@ class Simulation:
         return out[:n_steps]
 
     def info(self):
-        v = np.zeros(9)
-        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 9), "rd_info")
+        v = np.zeros(11)
+        _check(_lib().rd_info(self._h, _ptr(v, C.c_double), 11), "rd_info")
         return {"cell_factor": abs(v[0]), "cell_rule": "density" if v[0] < 0 else "fixed",
                 "cells": int(v[1]), "block": int(v[2]),
                 "capacity": int(v[3]), "pair_capacity": int(v[4]), "tuned_ms_per_step": v[5],
-                "r_cut_max": v[6], "sweep_split": int(v[7]), "reach": int(v[8])}
+                "r_cut_max": v[6], "sweep_split": int(v[7]), "reach": int(v[8]),
+                "fused": bool(v[9]), "fused_grid": int(v[10])}
 
     def num_particles(self) -> int:
         n = C.c_int64()
@@ -366,6 +382,21 @@ class Simulation:
         self.stream.wait_stream(torch.cuda.current_stream(r0.device))
         _check(_lib().rd_resample(self._h, rule, r0.data_ptr(), u.data_ptr(), r0.numel(), out.data_ptr()),
                "rd_resample")
+        torch.cuda.current_stream(r0.device).wait_stream(self.stream)
+        return out
+
+    def propagate(self, r0, u, rule: int = 0):
+        """New separation vectors of encountered pairs (device tensors: r0 float64 (n, 3), u float64
+        (n, 4)) drawn from the full propagator G_ref - G_abs (rd_propagate)."""
+        import torch
+
+        r0 = r0.contiguous()
+        u = u.contiguous()
+        assert r0.dtype == torch.float64 and u.dtype == torch.float64 and r0.shape[0] == u.shape[0]
+        out = torch.empty_like(r0)
+        self.stream.wait_stream(torch.cuda.current_stream(r0.device))
+        _check(_lib().rd_propagate(self._h, rule, r0.data_ptr(), u.data_ptr(), r0.shape[0], out.data_ptr()),
+               "rd_propagate")
         torch.cuda.current_stream(r0.device).wait_stream(self.stream)
         return out
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "librd.so")
 SOURCES = ["rd_kernels.cu", "rd_capi.cu", "rd_fpt.cu"]
-HEADERS = ["rd_internal.cuh", "rd_kernels.h", "rd_gf2d.cuh"]
+HEADERS = ["rd_internal.cuh", "rd_kernels.h", "rd_gf2d.cuh", "rd_angle.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

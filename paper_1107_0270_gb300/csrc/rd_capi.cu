@@ -31,6 +31,9 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 constexpr int kHistoryLen = 1 << 16;   // steps kept by the per-step count history
+// automatic step launch: fused up to this particle capacity (at 2 resident blocks per SM the
+// fused launch has fewer warps per SM than the separate sweep, which matters only far above it)
+constexpr int64_t kFusedMaxCapacity = (int64_t)1 << 22;
 
 struct rd_handle {
   rd_config cfg;
@@ -151,6 +154,8 @@ static int validate(const rd_config* c) {
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32 != 0)) return RD_EINVAL;
   if (c->sweep_split < 0 || c->sweep_split > 2) return RD_EINVAL;
   if (c->cell_reach < 0 || c->cell_reach > 2 || (c->cell_reach == 2 && c->dim != 2)) return RD_EINVAL;
+  if (c->step_launch < 0 || c->step_launch > 2 || (c->force_paths & ~3) != 0) return RD_EINVAL;
+  if (c->angle_mode < 0 || c->angle_mode > 1) return RD_EINVAL;
   double L_min = 1e300;
   for (int r = 0; r < c->n_replicas; ++r) L_min = std::min(L_min, c->replicas[r].L);
   for (int s = 0; s < c->n_species; ++s) {
@@ -189,10 +194,19 @@ static int validate(const rd_config* c) {
   return RD_OK;
 }
 
+static void gauss_legendre16(double* x, double* w);
+
 static void derive_params(rd_handle* h) {
   const rd_config& c = h->cfg;
   DevParams& P = h->hp;
   std::memset(&P, 0, sizeof P);
+  // 16-point Gauss-Legendre rule (2D quadratures and the exact angle law)
+  double gx[16], gw[16];
+  gauss_legendre16(gx, gw);
+  for (int i = 0; i < 16; ++i) {
+    P.gl16[i] = gx[i];
+    P.gl16[16 + i] = gw[i];
+  }
   P.dim = c.dim;
   P.n_species = c.n_species;
   P.precision = c.precision;
@@ -200,6 +214,9 @@ static void derive_params(rd_handle* h) {
   P.n_pairs = c.n_pairs;
   P.n_decays = c.n_decays;
   P.match_max_rounds = 4096;
+  P.match_single_max = (c.force_paths & 1) ? 0u : 2048u;
+  P.match_smem_max = (c.force_paths & 2) ? 0u : 256u;
+  P.angle_mode = c.angle_mode;
   P.dt = c.dt;
   P.seed_lo = (uint32_t)(c.seed & 0xFFFFFFFFu);
   P.seed_hi = (uint32_t)(c.seed >> 32);
@@ -369,12 +386,6 @@ constexpr double kSeriesHSqrtTau = 0.3;   // series limit of the radiation brack
 
 template <class Alloc>
 static bool build_2d(const rd_config& c, DevParams& hp, Alloc alloc) {
-  double gx[16], gw[16];
-  gauss_legendre16(gx, gw);
-  for (int i = 0; i < 16; ++i) {
-    hp.gl16[i] = gx[i];
-    hp.gl16[16 + i] = gw[i];
-  }
   if (c.dim != 2) return true;
   for (int k = 0; k < c.n_pairs; ++k) {
     PairDev& q = hp.pairs[k];
@@ -440,6 +451,26 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
     if (e == cudaSuccess && c.dim == 2) e = make(2, q.tab_tail, n1, hstep, nullptr);
     if (e == cudaSuccess && c.pairs[k].bc != RD_BC_ABS)
       e = make(3, q.tab_inv, ninv, hinv, c.dim == 2 ? &q.tab_tail : nullptr);
+    if (e == cudaSuccess && c.angle_mode == 0 && c.pairs[k].bc != RD_BC_ABS) {
+      // conditional angle law of the exact propagation: spacing s / 10 in R0 and R'; R0 up to the
+      // cut-off, R' up to 10 s beyond it (the radial law's tail at U = 2^-24 reaches about 8.2 s)
+      const double ha = 0.1 * q.s;
+      const double a0max = std::sqrt(q.rcut2) / q.sigma - 1.0, a1max = a0max + 10.0 * q.s;
+      const int m0 = (int)std::ceil(a0max / ha) + 3, m1 = (int)std::ceil(a1max / ha) + 3;
+      float* t = (float*)alloc((size_t)m0 * m1 * kAngTabStride * sizeof(float));
+      if (!t) return cudaErrorMemoryAllocation;
+      launch_build_ang_table(h->L.P, c.dim, q.tau, ha, m0, m1, t, device_sms(), h->stream);
+      AngTab& A = q.tab_ang;
+      A.v = t;
+      A.n0 = m0;
+      A.n1 = m1;
+      A.h = (float)ha;
+      A.inv_h = (float)(1.0 / ha);
+      A.d0max = (float)((m0 - 3) * ha);
+      A.d1max = (float)((m1 - 3) * ha);
+      A.inv_2tau = (float)(0.5 / q.tau);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -610,11 +641,27 @@ static cudaError_t autotune(rd_handle* h) {
   const int rows = h->cfg.dim == 3 ? 5 : (h->reach == 2 ? 3 : 2);
   if (h->cfg.sweep_split == 0 && (double)h->L.cap_particles * rows < 4.0e9) {
     h->L.sweep_split = rows;
+    const int g_split = fused_grid_size(h->L, device_sms());
+    const int fused0 = h->L.fused;
+    h->L.fused_grid = g_split;
+    if (g_split < 1) h->L.fused = 0;
+    const float ms = std::min(trial(), trial());
+    if (ms < best) {
+      best = ms;
+    } else {
+      h->L.sweep_split = 1;
+      h->L.fused = fused0;
+      h->L.fused_grid = fused_grid_size(h->L, device_sms());
+    }
+  }
+  // one fused launch per step or one launch per kernel (bit-identical results either way)
+  if (h->cfg.step_launch == 0 && h->L.fused_grid >= 1 && !(h->cfg.angle_mode == 0 && h->cfg.precision == RD_FP64)) {
+    h->L.fused = !h->L.fused;
     const float ms = std::min(trial(), trial());
     if (ms < best)
       best = ms;
     else
-      h->L.sweep_split = 1;
+      h->L.fused = !h->L.fused;
   }
   h->tuned_ms = best / 6.0;
   restore();
@@ -742,11 +789,18 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
   L.max_grid = device_sms() * 16;
+  // the FP64 step's exact angle pass can take far longer than a grid barrier waits (about a
+  // millisecond of FP64 work per pair), so automatically it runs as separate kernels
+  const bool long_phase = c.angle_mode == 0 && c.precision == RD_FP64;
+  L.fused = c.step_launch == 1 || (c.step_launch == 0 && cap <= kFusedMaxCapacity && !long_phase);
   L.scan_items = 8;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;
   L.total_cells = total_cells;
   L.n_counts = c.n_replicas * c.n_species;
+  L.fused_grid = fused_grid_size(L, device_sms());
+  if (L.fused_grid < 1) L.fused = 0;
+  cudaGetLastError();   // a refused attribute or occupancy query leaves no error behind
   const int64_t chunk = 256 * (int64_t)L.scan_items;
   const int64_t nbc = (max_cells + chunk - 1) / chunk, nbp = (cap + chunk - 1) / chunk;
   L.flag_stride = std::max(nbc, nbp) + 1;
@@ -791,6 +845,11 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.fstate = (uint32_t*)A(pair_cap * 4);
   L.conflict = (uint32_t*)A(pair_cap * 4);
   L.crec = (ConflictRec*)A(pair_cap * sizeof(ConflictRec));
+  // angle jobs: one per accepted pair (two particles each) and one per decay with a product pair
+  // (a decaying particle takes part in no pair), so never more than the particle capacity
+  L.angles = c.angle_mode == 0;
+  L.ang_cap = L.angles ? (uint32_t)cap : 1u;
+  L.ang_jobs = (AngJob*)A((size_t)L.ang_cap * sizeof(AngJob));
   L.counts = (unsigned long long*)A((size_t)L.n_counts * 8);
   L.history_len = kHistoryLen;
   L.history = (long long*)A((size_t)kHistoryLen * c.n_species * 8);
@@ -883,6 +942,28 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
 int rd_step(rd_handle* h) {
   if (!h) return RD_EINVAL;
   StepLaunch L = launch_for(h, h->cur);
+  if (h->time_next && L.fused) {
+    // per-phase device times from the phase clock of the fused launch, and the launch's event time
+    DevCtl before, after;
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    RD_CUDA(cudaMemcpy(&before, h->L.ctl, sizeof before, cudaMemcpyDeviceToHost));
+    h->timer.reset();
+    h->timer.mark("begin", h->stream);
+    launch_fused_steps(L, 1, h->stream);
+    h->timer.mark("k_step_fused", h->stream);
+    RD_CUDA(cudaGetLastError());
+    RD_CUDA(cudaStreamSynchronize(h->stream));
+    RD_CUDA(cudaMemcpy(&after, h->L.ctl, sizeof after, cudaMemcpyDeviceToHost));
+    h->last_times.clear();
+    for (int k = 0; k < kFusedPhases; ++k)
+      h->last_times.emplace_back(kFusedPhaseNames[k], (float)((after.ph_acc[k] - before.ph_acc[k]) * 1e-6));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->timer.events[0], h->timer.events[1]);
+    h->last_times.emplace_back("k_step_fused", ms);
+    h->time_next = false;
+    h->cur ^= 1;
+    return RD_OK;
+  }
   if (h->time_next) {
     h->timer.reset();
     launch_step(L, h->stream, &h->timer);
@@ -907,8 +988,12 @@ int rd_step(rd_handle* h) {
 static int capture_graph(rd_handle* h, int start) {
   cudaGraph_t g = nullptr;
   RD_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  launch_step(launch_for(h, start), h->stream, nullptr);
-  launch_step(launch_for(h, 1 - start), h->stream, nullptr);
+  if (h->L.fused) {
+    launch_fused_steps(launch_for(h, start), 2, h->stream);     // both steps in one launch
+  } else {
+    launch_step(launch_for(h, start), h->stream, nullptr);
+    launch_step(launch_for(h, 1 - start), h->stream, nullptr);
+  }
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaGraphInstantiate(&h->graph[start], g, 0);
@@ -965,6 +1050,20 @@ int rd_num_particles(rd_handle* h, int64_t* n) {
   return RD_OK;
 }
 
+// Device address of a page-locked host buffer (the kernels then read or write it directly over
+// the host link, without a staging copy); nullptr for pageable memory.  A null pointer counts as
+// page-locked (nothing to move).
+static void* pinned_device_ptr(const void* p, bool* ok) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
+  }
+  return a.devicePointer;
+}
+
 static bool ensure_staging(rd_handle* h) {
   if (h->st_x) return true;
   const int64_t cap = h->L.cap_particles;
@@ -994,13 +1093,23 @@ int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, ui
   *n_inout = n;
   if (step) *step = ctl.step;
   if (n > 0 && (x || species || replica)) {
-    if (!ensure_staging(h)) return RD_ENOMEM;
-    launch_get_state(h->L, h->xbuf[h->cur], n, x ? h->st_x : nullptr, species ? h->st_sp : nullptr,
-                     replica ? h->st_rep : nullptr, h->stream);
-    RD_CUDA(cudaGetLastError());
-    if (x) RD_CUDA(cudaMemcpyAsync(x, h->st_x, (size_t)n * 24, cudaMemcpyDeviceToHost, h->stream));
-    if (species) RD_CUDA(cudaMemcpyAsync(species, h->st_sp, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
-    if (replica) RD_CUDA(cudaMemcpyAsync(replica, h->st_rep, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    bool pinned = true;
+    double* dx = (double*)pinned_device_ptr(x, &pinned);
+    int32_t* dsp = (int32_t*)pinned_device_ptr(species, &pinned);
+    int32_t* drep = (int32_t*)pinned_device_ptr(replica, &pinned);
+    if (pinned) {
+      // page-locked caller buffers: the unpacking kernel writes them directly
+      launch_get_state(h->L, h->xbuf[h->cur], n, dx, dsp, drep, h->stream);
+      RD_CUDA(cudaGetLastError());
+    } else {
+      if (!ensure_staging(h)) return RD_ENOMEM;
+      launch_get_state(h->L, h->xbuf[h->cur], n, x ? h->st_x : nullptr, species ? h->st_sp : nullptr,
+                       replica ? h->st_rep : nullptr, h->stream);
+      RD_CUDA(cudaGetLastError());
+      if (x) RD_CUDA(cudaMemcpyAsync(x, h->st_x, (size_t)n * 24, cudaMemcpyDeviceToHost, h->stream));
+      if (species) RD_CUDA(cudaMemcpyAsync(species, h->st_sp, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+      if (replica) RD_CUDA(cudaMemcpyAsync(replica, h->st_rep, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   if (id && n > 0) RD_CUDA(cudaMemcpyAsync(id, h->idbuf[h->cur], (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
   std::vector<RepDev> reps;
@@ -1021,21 +1130,31 @@ int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* specie
   const rd_config& c = h->cfg;
   if (!ensure_staging(h)) return RD_ENOMEM;
   cudaStream_t s = h->stream;
-  // raw inputs to the device; validation and packing there, into the spare state buffer, so that
-  // a rejected state leaves the current one untouched
-  if (n > 0) {
+  // raw inputs to the device (page-locked caller buffers are read there directly); validation and
+  // packing there, into the spare state buffer, so that a rejected state leaves the current one
+  // untouched
+  bool pinned = true;
+  const double* dx = (const double*)pinned_device_ptr(x, &pinned);
+  const int32_t* dsp = (const int32_t*)pinned_device_ptr(species, &pinned);
+  const uint32_t* did = (const uint32_t*)pinned_device_ptr(id, &pinned);
+  const int32_t* drep = (const int32_t*)pinned_device_ptr(replica, &pinned);
+  if (!pinned && n > 0) {
     RD_CUDA(cudaMemcpyAsync(h->st_x, x, (size_t)n * 24, cudaMemcpyHostToDevice, s));
     RD_CUDA(cudaMemcpyAsync(h->st_sp, species, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     RD_CUDA(cudaMemcpyAsync(h->st_id, id, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     if (replica) RD_CUDA(cudaMemcpyAsync(h->st_rep, replica, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    dx = h->st_x;
+    dsp = h->st_sp;
+    did = h->st_id;
+    drep = replica ? h->st_rep : nullptr;
   }
   if (next_id) RD_CUDA(cudaMemcpyAsync(h->st_next, next_id, (size_t)c.n_replicas * 4, cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemsetAsync(h->st_cnt, 0, (size_t)c.n_replicas * 4, s));
   RD_CUDA(cudaMemsetAsync(h->st_maxid, 0, (size_t)c.n_replicas * 4, s));
   RD_CUDA(cudaMemsetAsync(h->st_err, 0, 4, s));
   const int spare = 1 - h->cur;
-  launch_set_state(h->L, n, h->st_x, h->st_sp, h->st_id, replica ? h->st_rep : nullptr, h->xbuf[spare],
-                   h->idbuf[spare], h->st_cnt, h->st_maxid, next_id ? h->st_next : nullptr, h->st_err, step, s);
+  launch_set_state(h->L, n, dx, dsp, did, drep, h->xbuf[spare], h->idbuf[spare], h->st_cnt, h->st_maxid,
+                   next_id ? h->st_next : nullptr, h->st_err, step, s);
   RD_CUDA(cudaGetLastError());
   int32_t err = 0;
   RD_CUDA(cudaMemcpyAsync(&err, h->st_err, 4, cudaMemcpyDeviceToHost, s));
@@ -1063,6 +1182,16 @@ int rd_resample(rd_handle* h, int32_t rule, const double* r0, const double* u, i
   if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
   if (n == 0) return RD_OK;
   launch_resample(h->L.P, rule, r0, u, n, r_new, h->L.max_grid, h->stream);
+  RD_CUDA(cudaGetLastError());
+  return RD_OK;
+}
+
+int rd_propagate(rd_handle* h, int32_t rule, const double* r0, const double* u, int64_t n, double* r_out) {
+  if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || (n > 0 && (!r0 || !u || !r_out))) return RD_EINVAL;
+  const int bc = h->cfg.pairs[rule].bc;
+  if (bc != RD_BC_REF && bc != RD_BC_RAD) return RD_EINVAL;
+  if (n == 0) return RD_OK;
+  launch_propagate(h->L.P, rule, r0, u, n, r_out, h->L.max_grid, h->stream);
   RD_CUDA(cudaGetLastError());
   return RD_OK;
 }
@@ -1181,10 +1310,11 @@ int rd_check_bounded_wait(rd_handle* h, uint32_t spin_limit, int32_t* status_out
 
 int rd_info(rd_handle* h, double* out, int32_t n) {
   if (!h || !out || n < 0) return RD_EINVAL;
-  const double v[9] = {h->factor, (double)h->L.total_cells, (double)h->L.block,
-                       (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
-                       max_cutoff(h->cfg), (double)h->L.sweep_split, (double)h->reach};
-  for (int k = 0; k < n && k < 9; ++k) out[k] = v[k];
+  const double v[11] = {h->factor, (double)h->L.total_cells, (double)h->L.block,
+                        (double)h->L.cap_particles, (double)h->L.cap_pairs, h->tuned_ms,
+                        max_cutoff(h->cfg), (double)h->L.sweep_split, (double)h->reach,
+                        (double)h->L.fused, (double)h->L.fused_grid};
+  for (int k = 0; k < n && k < 11; ++k) out[k] = v[k];
   return RD_OK;
 }
 
@@ -1443,6 +1573,9 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   L.fstate = (uint32_t*)b.take(pair_cap * 4);
   L.conflict = (uint32_t*)b.take(pair_cap * 4);
   L.crec = (ConflictRec*)b.take(pair_cap * sizeof(ConflictRec));
+  L.angles = c.angle_mode == 0;
+  L.ang_cap = RD_STATIC_MAX_PARTICLES;
+  L.ang_jobs = (AngJob*)b.take((size_t)L.ang_cap * sizeof(AngJob));
   L.counts = (unsigned long long*)b.take((size_t)L.n_counts * 8);
   L.P = (const DevParams*)b.take(sizeof(DevParams));
   L.ctl = (DevCtl*)b.take(sizeof(DevCtl));

@@ -12,6 +12,8 @@ namespace rd {
 constexpr int kMaxSpecies = RD_MAX_SPECIES;
 constexpr int kMaxPairs = RD_MAX_PAIRS;
 constexpr int kMaxDecays = RD_MAX_DECAYS;
+constexpr int kAngTabU = 64;       // intervals of the angle table's U axis
+constexpr int kAngTabStride = kAngTabU + 4;   // floats per (R0, R') node of the angle table
 constexpr uint32_t kNoCell = 0xFFFFFFFFu;
 constexpr uint32_t kOneParticle = 0xFFFFFFFFu;   // id_b of one-particle random streams
 constexpr int kSmemCounts = 6144;                // per-block histogram of (replica, species) counts
@@ -20,7 +22,7 @@ constexpr int kSmemCounts = 6144;                // per-block histogram of (repl
 enum Tag : uint32_t {
   TAG_INIT0 = 1, TAG_INIT1 = 2, TAG_UNI = 3, TAG_DISP0 = 4, TAG_DISP1 = 5, TAG_ENC = 6,
   TAG_RES = 7, TAG_DIR = 8, TAG_DISS0 = 9, TAG_DISS1 = 10, TAG_DISS2 = 11, TAG_DISS3 = 12,
-  TAG_FPT = 13
+  TAG_FPT = 13, TAG_ANG = 14
 };
 
 // Per-particle status word written every step.
@@ -51,6 +53,19 @@ struct Tab2 {
   float inv_h1, h1;           // second axis
 };
 
+// Tabulated conditional angle law of one pair rule (mixed step): for start and new separations
+// R0 = 1 + (a - 1) h, R' = 1 + (b - 1) h (a < n0, b < n1; node 0 a ghost) and CDF values
+// U = sin^2(pi w / 2), w = (k - 1) / kAngTabU (k < kAngTabU + 3, first and last ghosts), the
+// CDF value s(U) of the exact angle under the reference law, then (k = kAngTabU + 3) the reference
+// law's concentration (Catmull-Rom in all three axes); d0max, d1max: the largest R0 - 1 and R' - 1
+// inside the table.
+struct AngTab {
+  const float* v;             // n0 x n1 x kAngTabStride values, null when not built
+  int32_t n0, n1;
+  float h, inv_h, d0max, d1max;
+  float inv_2tau, pad;
+};
+
 struct PairDev {
   int32_t bc, product, s1, s2;
   double sigma, tau, inv_tau, s, h, alpha, rcut2, Drel;
@@ -64,6 +79,7 @@ struct PairDev {
   // mixed step: FP32 tables of p_reac (2D and 3D), F = p_enc e^{d d0/tau} and -ln(tail) (2D)
   Tab2 tab_preac, tab_penc, tab_tail;
   Tab2 tab_inv;               // propagator sample V = R - 1 at (R0 - 1, sqrt(-ln U))
+  AngTab tab_ang;             // conditional angle law of the exact propagation
 };
 
 struct DecayDev {
@@ -74,6 +90,10 @@ struct DecayDev {
 struct DevParams {
   int32_t dim, n_species, precision, n_replicas;
   int32_t n_pairs, n_decays, match_max_rounds, pad0;
+  uint32_t match_single_max;   // conflict pairs matched by one block (more: the whole grid)
+  uint32_t match_smem_max;     // conflict pairs matched in shared memory by that block
+  int32_t angle_mode;          // 0: exact propagator direction; 1: free-step direction
+  int32_t pad_angle;
   double dt;
   uint32_t seed_lo, seed_hi;
   uint32_t binned_mask;        // species that appear in an interacting pair rule
@@ -114,7 +134,9 @@ struct DevCtl {
   uint32_t fired;          // fired pairs this step
   uint32_t n_conflict;     // pairs left to the iterative matching
   uint32_t n_decay;        // decays this step
-  uint32_t n_accept;       // accepted pairs this step
+  uint32_t n_accept;       // trivially accepted pairs this step (final once the matching phase starts)
+  uint32_t n_round_acc;    // pairs accepted by the conflict rounds (appended after the trivial ones)
+  uint32_t n_ang;          // angle jobs of this step
   uint32_t epoch;          // incremented every step; tags the scan flags
   uint32_t tile_ctr[2];    // tile tickets of the two scans
   uint32_t done_blocks;    // blocks of the compaction that finished
@@ -125,6 +147,9 @@ struct DevCtl {
   uint32_t done_res;       // blocks of the matching / resolution kernel that finished
   uint32_t n_new;          // particles after this step (set with the replica table)
   uint32_t spin_limit;     // bound of the device waits in polls (0: the built-in bounds)
+  uint32_t ph_steps;       // steps timed by the fused step's phase clock
+  unsigned long long ph_t[8];    // fused step: global-timer stamp at the start of each phase
+  unsigned long long ph_acc[8];  // fused step: accumulated ns per phase
   double t;
   unsigned long long stats[RD_NSTATS];
 };
@@ -141,6 +166,22 @@ struct RepX {
 struct ConflictRec {
   uint32_t e, ia, ib, st;
   unsigned long long key, pid;
+};
+
+// An encountered pair (kind 0) or a decay's product pair (kind 1) whose new separation direction is
+// drawn from the full propagator in the angle pass (one warp per job); the resolution pass has
+// already decided everything else (length, reaction, products).
+struct AngJob {
+  double c[3];              // centre of diffusion
+  double u[3];              // axis: the start separation's direction (decay: the contact direction)
+  double fb[3];             // direction kept if the law needs more partial waves than the device holds
+  double len;               // new separation length R' sigma
+  double Rn, R0, tau;       // scaled lengths and time of the law
+  double ca, cb;            // D_a / D_rel, D_b / D_rel
+  double U_ang, U_azi;      // the angle's CDF value and the azimuth (2D: the sign) uniform
+  uint32_t kind, ia, ib;    // kind (low byte) 0: particles ia, ib -> x1; 1: parent ia -> prodpos[2 ia ..
+                            // 2 ia + 1]; the pair rule in the bits above
+  uint32_t wa, wb, r;       // species/replica bits of the two particles, replica
 };
 
 struct FiredPair {          // 32 B

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 
+#include "rd_angle.cuh"
 #include "rd_gf2d.cuh"
 #include "rd_kernels.h"
 
@@ -89,17 +90,15 @@ __device__ __forceinline__ double resample_dim(const DevParams& P, const PairDev
 // cell (start-of-step positions).
 // ================================================================================================
 template <class T>
-__global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                          const RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
-                          const uint32_t* __restrict__ id, typename V4<T>::type* __restrict__ x1,
-                          uint32_t* __restrict__ status, int32_t* __restrict__ matched,
-                          uint32_t* __restrict__ deg, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
-                          uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list,
-                          unsigned long long* __restrict__ counts, int n_counts,
-                          typename V4<T>::type* __restrict__ x0d) {
-  pdl_enter();
+__device__ __forceinline__ void ph_prepare(const DevParams* Pp, DevCtl* ctl,
+                          const RepDev* reps, const typename V4<T>::type* x0,
+                          const uint32_t* id, typename V4<T>::type* x1,
+                          uint32_t* status, uint32_t* cell_of, uint32_t* slot,
+                          uint32_t* cell_count, uint32_t* decay_list,
+                          unsigned long long* counts, int n_counts,
+                          typename V4<T>::type* x0d, const uint32_t bid, const uint32_t nblk) {
   const DevParams& P = *Pp;
-  if (blockIdx.x == 0) {
+  if (bid == 0) {
     // counters of the step's later kernels (the counters used by this kernel were reset at the
     // end of the previous step)
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x) counts[k] = 0ull;
@@ -112,7 +111,7 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
   if (ctl->status) return;
   const uint32_t n = ctl->n, step = ctl->step;
   const int dim = P.dim;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     auto p = x0[i];
     const uint32_t wb = w_bits(p.w);
     const uint32_t sp = wb & 0xFFu, r = wb >> 8;
@@ -200,6 +199,19 @@ __global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__
   }
 }
 
+template <class T>
+__global__ void k_prepare(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          const RepDev* __restrict__ reps, const typename V4<T>::type* __restrict__ x0,
+                          const uint32_t* __restrict__ id, typename V4<T>::type* __restrict__ x1,
+                          uint32_t* __restrict__ status, uint32_t* __restrict__ cell_of, uint32_t* __restrict__ slot,
+                          uint32_t* __restrict__ cell_count, uint32_t* __restrict__ decay_list,
+                          unsigned long long* __restrict__ counts, int n_counts,
+                          typename V4<T>::type* __restrict__ x0d) {
+  pdl_enter();
+  ph_prepare<T>(Pp, ctl, reps, x0, id, x1, status, cell_of, slot, cell_count, decay_list, counts, n_counts, x0d,
+                blockIdx.x, gridDim.x);
+}
+
 // ================================================================================================
 // Block-level exclusive scan and the per-element loaders of the two scans of a step.
 // ================================================================================================
@@ -275,8 +287,8 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 // the tile's inclusive prefix and returns the exclusive prefix (in every lane).  Flags carry an
 // epoch that changes every scan, so nothing needs clearing.
 template <class U>
-__device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch, U* __restrict__ agg,
-                                           U* __restrict__ incl, uint32_t* __restrict__ flag, DevCtl* ctl) {
+__device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch, U* agg,
+                                           U* incl, uint32_t* flag, DevCtl* ctl) {
   const int lane = threadIdx.x & 31;
   U prefix = 0;
   if (tile > 0) {
@@ -325,22 +337,23 @@ __device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch,
 // RD_ETIMEOUT).  Flags carry an epoch that changes every scan, so nothing needs clearing.
 // out[i] = exclusive prefix for i < n, out[n] = total; zero_after (optional) is cleared behind.
 
+// One tile of the scan, taken by ticket (tile < ntiles).  Returns false when the tickets are used up.
 template <class U, class Load>
-__global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const uint32_t* __restrict__ n_ptr,
-                                               U* __restrict__ out, uint32_t* __restrict__ zero_after,
-                                               U* __restrict__ agg, U* __restrict__ incl,
-                                               uint32_t* __restrict__ flag, DevCtl* __restrict__ ctl, int which) {
-  pdl_enter();
+__device__ __forceinline__ bool ph_scan_tile(Load load, int64_t n_const, const uint32_t* n_ptr,
+                                             U* out, uint32_t* zero_after,
+                                             U* agg, U* incl,
+                                             uint32_t* flag, DevCtl* ctl, int which) {
   __shared__ U sm[32];
   __shared__ uint32_t s_tile;
   __shared__ U s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[which], 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
+  __syncthreads();
   const int64_t n = n_ptr ? (int64_t)*n_ptr : n_const;
   const int64_t tile_elems = (int64_t)blockDim.x * kScanItems;
   const int64_t ntiles = n > 0 ? (n + tile_elems - 1) / tile_elems : 1;
-  if ((int64_t)tile >= ntiles) return;
+  if ((int64_t)tile >= ntiles) return false;
   const uint32_t epoch = (ctl->epoch * 2u + (uint32_t)which) & 0x3FFFFFFFu;
   const int64_t base = (int64_t)tile * tile_elems + (int64_t)threadIdx.x * kScanItems;
   // blocked arrangement: each thread owns kScanItems consecutive elements
@@ -385,6 +398,17 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
     }
   }
   if (threadIdx.x == 0 && (int64_t)tile == ntiles - 1) out[n > 0 ? n : 0] = s_prefix + tot;
+  __syncthreads();
+  return true;
+}
+
+template <class U, class Load>
+__global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const uint32_t* __restrict__ n_ptr,
+                                               U* __restrict__ out, uint32_t* __restrict__ zero_after,
+                                               U* __restrict__ agg, U* __restrict__ incl,
+                                               uint32_t* __restrict__ flag, DevCtl* __restrict__ ctl, int which) {
+  pdl_enter();
+  ph_scan_tile<U, Load>(load, n_const, n_ptr, out, zero_after, agg, incl, flag, ctl, which);
 }
 
 // ================================================================================================
@@ -392,16 +416,15 @@ __global__ void __launch_bounds__(256) k_scan1(Load load, int64_t n_const, const
 // end-of-free-step position (w = id bits) and the particle index.
 // ================================================================================================
 template <class T>
-__global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V4<T>::type* __restrict__ x0,
-                                const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
-                                const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ slot,
-                                const uint32_t* __restrict__ cell_start,
-                                typename V4<T>::type* __restrict__ sx0, typename V4<T>::type* __restrict__ sx1,
-                                uint32_t* __restrict__ sidx) {
-  pdl_enter();
+__device__ __forceinline__ void ph_scatter(const DevCtl* ctl, const typename V4<T>::type* x0,
+                                const typename V4<T>::type* x1, const uint32_t* id,
+                                const uint32_t* cell_of, const uint32_t* slot,
+                                const uint32_t* cell_start,
+                                typename V4<T>::type* sx0, typename V4<T>::type* sx1,
+                                uint32_t* sidx, const uint32_t bid, const uint32_t nblk) {
   if (ctl->status) return;
   const uint32_t n = ctl->n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (uint32_t i = bid * blockDim.x + threadIdx.x; i < n; i += nblk * blockDim.x) {
     const uint32_t c = cell_of[i];
     if (c == kNoCell) continue;
     const uint32_t k = cell_start[c] + slot[i];
@@ -416,6 +439,17 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
   }
 }
 
+template <class T>
+__global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V4<T>::type* __restrict__ x0,
+                                const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
+                                const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ slot,
+                                const uint32_t* __restrict__ cell_start,
+                                typename V4<T>::type* __restrict__ sx0, typename V4<T>::type* __restrict__ sx1,
+                                uint32_t* __restrict__ sidx) {
+  pdl_enter();
+  ph_scatter<T>(ctl, x0, x1, id, cell_of, slot, cell_start, sx0, sx1, sidx, blockIdx.x, gridDim.x);
+}
+
 // ================================================================================================
 // K3: cell sweep.  One thread per binned particle (cell order) walks the forward half of the
 // 27-cell (3D) / 9-cell (2D) neighbourhood; every pair (k, j > k) of an interacting species pair
@@ -428,19 +462,18 @@ __global__ void k_scatter_cells(const DevCtl* __restrict__ ctl, const typename V
 constexpr int kSweepRanges = 10;
 
 template <class T, bool kSplit, int kReach>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                                                  const RepDev* __restrict__ reps,
-                                                  const typename V4<T>::type* __restrict__ sx0,
-                                                  const typename V4<T>::type* __restrict__ sx1,
-                                                  const uint32_t* __restrict__ sidx,
-                                                  const uint32_t* __restrict__ cell_start,
-                                                  const int64_t total_cells, FiredPair* __restrict__ fired,
-                                                  uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
-                                                  int32_t* __restrict__ matched, const uint32_t cap_pairs,
-                                                  const uint32_t split) {
-  pdl_enter();
+__device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
+                                         const RepDev* reps,
+                                         const typename V4<T>::type* sx0,
+                                         const typename V4<T>::type* sx1,
+                                         const uint32_t* sidx,
+                                         const uint32_t* cell_start,
+                                         const int64_t total_cells, FiredPair* fired,
+                                         uint32_t* fstate, uint32_t* deg,
+                                         int32_t* matched, const uint32_t cap_pairs,
+                                         const uint32_t split, uint2 (*ranges)[256],
+                                         const uint32_t bid, const uint32_t nblk) {
   const DevParams& P = *Pp;
-  __shared__ uint2 ranges[kSweepRanges][256];
   if (ctl->status) return;
   const uint32_t nb = cell_start[total_cells];
   const uint32_t step = ctl->step;
@@ -449,10 +482,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
   // split = 1: one thread walks all rows of a particle; split = number of rows: one thread per
   // (particle, row), more independent chains for small systems (the host keeps nb * split < 2^32)
   const uint32_t work = kSplit ? nb * split : nb;
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride = nblk * blockDim.x;
   const uint32_t n_iter = (work + stride - 1) / stride;
   for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t t = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t t = it * stride + bid * blockDim.x + threadIdx.x;
     if (t < work) {
       const uint32_t k = kSplit ? t / split : t;
       const int row_lo = kSplit ? (int)(t - k * split) : 0;
@@ -625,6 +658,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const Dev
   warp_sum_add(&ctl->stats[RD_STAT_OVERLAPS], n_overlap);
 }
 
+template <class T, bool kSplit, int kReach>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 5) k_sweep(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                  const RepDev* __restrict__ reps,
+                                                  const typename V4<T>::type* __restrict__ sx0,
+                                                  const typename V4<T>::type* __restrict__ sx1,
+                                                  const uint32_t* __restrict__ sidx,
+                                                  const uint32_t* __restrict__ cell_start,
+                                                  const int64_t total_cells, FiredPair* __restrict__ fired,
+                                                  uint32_t* __restrict__ fstate, uint32_t* __restrict__ deg,
+                                                  int32_t* __restrict__ matched, const uint32_t cap_pairs,
+                                                  const uint32_t split) {
+  pdl_enter();
+  __shared__ uint2 ranges[kSweepRanges][256];
+  ph_sweep<T, kSplit, kReach>(Pp, ctl, reps, sx0, sx1, sidx, cell_start, total_cells, fired, fstate, deg, matched,
+                              cap_pairs, split, ranges, blockIdx.x, gridDim.x);
+}
+
 // ================================================================================================
 // K4: conflict resolution.  Pairs whose two particles fired with nobody else are accepted at once;
 // the rest go through rounds of locally-dominant matching (a pair is accepted when its
@@ -641,21 +691,20 @@ __device__ __forceinline__ void append_accepted(DevCtl* ctl, uint32_t* accepted,
   accepted[base + __popc(m & ((1u << lane) - 1u))] = e;
 }
 
-__global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
-                                uint32_t* __restrict__ fstate, const uint32_t* __restrict__ deg,
-                                int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
-                                uint32_t* __restrict__ accepted,
-                                unsigned long long* __restrict__ best_key,
-                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs,
-                                ConflictRec* __restrict__ crec) {
-  pdl_enter();
+__device__ __forceinline__ void ph_match_trivial(DevCtl* ctl, const FiredPair* fired,
+                                uint32_t* fstate, const uint32_t* deg,
+                                int32_t* matched, uint32_t* conflict,
+                                uint32_t* accepted,
+                                unsigned long long* best_key,
+                                unsigned long long* best_pid, uint32_t cap_pairs,
+                                ConflictRec* crec, const uint32_t bid, const uint32_t nblk) {
   if (ctl->status) return;
   const uint32_t nf = min(ctl->fired, cap_pairs);
   unsigned long long acc = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride = nblk * blockDim.x;
   const uint32_t n_iter = (nf + stride - 1) / stride;
   for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t e = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t e = it * stride + bid * blockDim.x + threadIdx.x;
     if (e < nf) {
       const FiredPair f = fired[e];
       if (deg[f.ia] == 1u && deg[f.ib] == 1u) {
@@ -691,12 +740,26 @@ __global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __res
   warp_sum_add(&ctl->stats[RD_STAT_MATCHED], acc);
 }
 
+__global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
+                                uint32_t* __restrict__ fstate, const uint32_t* __restrict__ deg,
+                                int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
+                                uint32_t* __restrict__ accepted,
+                                unsigned long long* __restrict__ best_key,
+                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs,
+                                ConflictRec* __restrict__ crec) {
+  pdl_enter();
+  ph_match_trivial(ctl, fired, fstate, deg, matched, conflict, accepted, best_key, best_pid, cap_pairs, crec,
+                   blockIdx.x, gridDim.x);
+}
+
 // Grid-wide barrier of the cooperative matching launch (every block resident).  Bounded: a block
 // that waits longer than kBarrierSpin polls sets RD_ETIMEOUT and leaves; the caller then stops.
 constexpr uint32_t kBarrierSpin = 1u << 22;
-constexpr uint32_t kMatchSingleMax = 2048;   // conflict pairs handled by one block without barriers
 
-__device__ __forceinline__ bool grid_barrier(DevCtl* ctl) {
+// check_status: also report a status latched by any block (the matching rounds stop on it); the
+// fused step's barriers between phases report only their own timeout (a latched error still lets
+// the step reach its compaction, which then keeps the old state).
+__device__ __forceinline__ bool grid_barrier(DevCtl* ctl, bool check_status = true) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -721,7 +784,7 @@ __device__ __forceinline__ bool grid_barrier(DevCtl* ctl) {
       }
     }
     __threadfence();
-    s_ok = ok && *(volatile int32_t*)&ctl->status == 0;
+    s_ok = ok && (!check_status || *(volatile int32_t*)&ctl->status == 0);
   }
   __syncthreads();
   return s_ok != 0;
@@ -757,21 +820,39 @@ __device__ __forceinline__ void load3(const typename V4<T>::type& v, double o[3]
   o[0] = (double)v.x; o[1] = (double)v.y; o[2] = (double)v.z;
 }
 
+// Stores one position record (x, y, z and the species/replica bits).  An FP64 record goes out as
+// two 16-byte halves: built with nvcc 13.0 for sm_103a, a whole 32-byte record assignment in the
+// out-of-line resolver kept only its x component in the separately launched resolution kernel
+// (the same code inside the cooperative step launch stored all four).
 template <class T>
-__device__ __forceinline__ typename V4<T>::type store4(const double p[3], uint32_t wb) {
-  if constexpr (sizeof(T) == 8)
-    return make_v4(p[0], p[1], p[2], wb);
+__device__ __forceinline__ void put4(typename V4<T>::type* p, const double a[3], uint32_t wb) {
+  if constexpr (sizeof(T) == 8) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(a[0], a[1]);
+    q[1] = make_double2(a[2], w_from_bits_d(wb));
+  } else {
+    *p = make_v4f((float)a[0], (float)a[1], (float)a[2], wb);
+  }
+}
+
+// Appends an angle job: the angle pass draws the pair's new direction and places its particles.
+__device__ __forceinline__ void push_ang_job(DevCtl* ctl, AngJob* jobs, uint32_t cap,
+                                             const AngJob& job) {
+  const uint32_t k = atomicAdd(&ctl->n_ang, 1u);
+  if (k < cap)
+    jobs[k] = job;
   else
-    return make_v4f((float)p[0], (float)p[1], (float)p[2], wb);
+    set_status(ctl, RD_ECAPACITY);
 }
 
 template <class T>
-__device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* __restrict__ reps,
-                                             const FiredPair* __restrict__ fired, const uint32_t* __restrict__ fstate,
-                                             uint32_t e, uint32_t step, const typename V4<T>::type* __restrict__ x0,
-                                             typename V4<T>::type* __restrict__ x1, uint32_t* __restrict__ status,
-                                             typename V4<T>::type* __restrict__ prodpos, unsigned long long& n_react,
-                                             unsigned long long& n_res, unsigned long long& n_near) {
+__device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* reps,
+                                             const FiredPair* fired, const uint32_t* fstate,
+                                             uint32_t e, uint32_t step, const typename V4<T>::type* x0,
+                                             typename V4<T>::type* x1, uint32_t* status,
+                                             typename V4<T>::type* prodpos, unsigned long long& n_react,
+                                             unsigned long long& n_res, unsigned long long& n_near,
+                                             DevCtl* ctl, AngJob* jobs, uint32_t job_cap) {
   const int dim = P.dim;
     const uint32_t fs = fstate[e];
     const FiredPair f = fired[e];
@@ -793,7 +874,8 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
       r0v[d] = min_image(b0[d] - a0[d], rep.L, rep.half_L);
       c[d] = a1[d] + ca * rv[d];
     }
-    bool react = false;
+    bool react = false, job = false;
+    AngJob aj;
     if (pr.bc == RD_BC_ABS) {
       react = true;
     } else {
@@ -803,20 +885,49 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
       if (R0 < 1.0) R0 = 1.0;
       const double Rn = resample_dim_ni(P, pr, u_res, R0);
       const double len = sqrt(norm2_rn(rv[0], rv[1], rv[2], dim));
+      const double l0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim));
+      // the free step's direction: the new direction itself (angle mode 1), or the one kept when
+      // the exact law needs more partial waves than the device holds
       double dir[3] = {0, 0, 0};
       if (len > 0.0) {
         for (int d = 0; d < dim; ++d) dir[d] = rv[d] / len;
+      } else if (l0 > 0.0) {
+        for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
       } else {
-        const double l0 = sqrt(norm2_rn(r0v[0], r0v[1], r0v[2], dim));
-        if (l0 > 0.0)
-          for (int d = 0; d < dim; ++d) dir[d] = r0v[d] / l0;
-        else
-          dir[0] = 1.0;
+        dir[0] = 1.0;
       }
-      for (int d = 0; d < dim; ++d) {
-        const double nr = Rn * pr.sigma * dir[d];
-        a1[d] = wrap(c[d] - ca * nr, rep.L);
-        b1[d] = wrap(c[d] + cb * nr, rep.L);
+      if (P.angle_mode == 0) {
+        // exact direction from the full propagator about the start separation (x axis if zero):
+        // drawn in the angle pass
+        job = true;
+        const uint4 wg = draw_ni(P, step, f.ida, f.idb, TAG_ANG, r);
+        for (int d = 0; d < 3; ++d) {
+          aj.c[d] = c[d];
+          aj.fb[d] = dir[d];
+          aj.u[d] = d == 0 ? 1.0 : 0.0;
+        }
+        if (l0 > 0.0)
+          for (int d = 0; d < 3; ++d) aj.u[d] = d < dim ? r0v[d] / l0 : 0.0;
+        aj.len = Rn * pr.sigma;
+        aj.Rn = Rn;
+        aj.R0 = R0;
+        aj.tau = pr.tau;
+        aj.ca = ca;
+        aj.cb = cb;
+        aj.U_ang = u52(wg.x, wg.y);
+        aj.U_azi = u52(wg.z, wg.w);
+        aj.kind = 0u | ((uint32_t)rule << 8);
+        aj.ia = f.ia;
+        aj.ib = f.ib;
+        aj.wa = wa;
+        aj.wb = wb;
+        aj.r = r;
+      } else {
+        for (int d = 0; d < dim; ++d) {
+          const double nr = Rn * pr.sigma * dir[d];
+          a1[d] = wrap(c[d] - ca * nr, rep.L);
+          b1[d] = wrap(c[d] + cb * nr, rep.L);
+        }
       }
       ++n_res;
       if (pr.bc == RD_BC_RAD) {
@@ -836,14 +947,16 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
       if (pr.product >= 0) {
         double cw[3] = {0, 0, 0};
         for (int d = 0; d < dim; ++d) cw[d] = wrap(c[d], rep.L);
-        prodpos[2 * (size_t)f.ia] = store4<T>(cw, pack_sp((uint32_t)pr.product, r));
+        put4<T>(&prodpos[2 * (size_t)f.ia], cw, pack_sp((uint32_t)pr.product, r));
         np = 1;
       }
       status[f.ia] |= ST_CONSUMED | (np << ST_NPROD_SHIFT);
       status[f.ib] |= ST_CONSUMED;
+    } else if (job) {
+      push_ang_job(ctl, jobs, job_cap, aj);
     } else {
-      x1[f.ia] = store4<T>(a1, wa);
-      x1[f.ib] = store4<T>(b1, wb);
+      put4<T>(&x1[f.ia], a1, wa);
+      put4<T>(&x1[f.ib], b1, wb);
     }
 }
 
@@ -854,11 +967,12 @@ __device__ __forceinline__ void resolve_pair(const DevParams& P, const RepDev* _
 // p_reac(R', 1); non-interacting products start sigma_place apart and separate freely.
 // ================================================================================================
 template <class T>
-__device__ __forceinline__ void decay_products(const DevParams& P, const RepDev* __restrict__ reps, uint32_t i,
-                                               uint32_t step, const typename V4<T>::type* __restrict__ x0,
-                                               const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-                                               typename V4<T>::type* __restrict__ prodpos, unsigned long long& n_rec,
-                                               unsigned long long& n_near) {
+__device__ __forceinline__ void decay_products(const DevParams& P, const RepDev* reps, uint32_t i,
+                                               uint32_t step, const typename V4<T>::type* x0,
+                                               const uint32_t* id, uint32_t* status,
+                                               typename V4<T>::type* prodpos, unsigned long long& n_rec,
+                                               unsigned long long& n_near, DevCtl* ctl,
+                                               AngJob* jobs, uint32_t job_cap) {
   const int dim = P.dim;
     const uint32_t st = status[i];
     const DecayDev& dc = P.decays[(st >> ST_CHANNEL_SHIFT) & 15u];
@@ -875,7 +989,7 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
       const double ell = sqrt(2.0 * P.D[dc.p0] * P.dt);
       double q3[3] = {0, 0, 0};
       for (int d = 0; d < dim; ++d) q3[d] = wrap(xp[d] + ell * nr[d], rep.L);
-      prodpos[2 * (size_t)i] = store4<T>(q3, pack_sp((uint32_t)dc.p0, r));
+      put4<T>(&prodpos[2 * (size_t)i], q3, pack_sp((uint32_t)dc.p0, r));
       np = 1;
     } else if (dc.n_products == 2) {
       const int sa = dc.p0, sb = dc.p1;
@@ -901,13 +1015,14 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
       double c[3] = {0, 0, 0}, rv[3] = {0, 0, 0};
       for (int d = 0; d < dim; ++d) c[d] = xp[d] + ellc * nc[d];
       const int rule = P.pair_of[sa][sb];
-      bool recombine = false;
+      bool recombine = false, job = false;
       int product = -1;
+      double Rn = 0.0;
       if (rule >= 0) {
         const PairDev& pr = P.pairs[rule];
         w = draw_ni(P, step, pid, kOneParticle, TAG_RES, r);
         const double u_res = u52(w.x, w.y), u_reac = u52(w.z, w.w);
-        const double Rn = resample_dim_ni(P, pr, u_res, 1.0);
+        Rn = resample_dim_ni(P, pr, u_res, 1.0);
         for (int d = 0; d < dim; ++d) rv[d] = Rn * pr.sigma * dir[d];
         if (pr.bc == RD_BC_ABS) {
           recombine = true;
@@ -922,6 +1037,32 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
           }
         }
         product = pr.product;
+        if (!recombine && P.angle_mode == 0) {
+          // from contact along dir: the new direction from the full propagator, in the angle pass
+          job = true;
+          const uint4 wg = draw_ni(P, step, pid, kOneParticle, TAG_ANG, r);
+          AngJob aj;
+          for (int d = 0; d < 3; ++d) {
+            aj.c[d] = c[d];
+            aj.u[d] = dir[d];
+            aj.fb[d] = dir[d];
+          }
+          aj.len = Rn * pr.sigma;
+          aj.Rn = Rn;
+          aj.R0 = 1.0;
+          aj.tau = pr.tau;
+          aj.ca = ca;
+          aj.cb = cb;
+          aj.U_ang = u52(wg.x, wg.y);
+          aj.U_azi = u52(wg.z, wg.w);
+          aj.kind = 1u | ((uint32_t)rule << 8);
+          aj.ia = i;
+          aj.ib = i;
+          aj.wa = pack_sp((uint32_t)sa, r);
+          aj.wb = pack_sp((uint32_t)sb, r);
+          aj.r = r;
+          push_ang_job(ctl, jobs, job_cap, aj);
+        }
       } else {
         double nr[4];
         normals64_ni(P, step, pid, TAG_DISS2, r, dim, nr);
@@ -933,17 +1074,19 @@ __device__ __forceinline__ void decay_products(const DevParams& P, const RepDev*
         if (product >= 0) {
           double cw[3] = {0, 0, 0};
           for (int d = 0; d < dim; ++d) cw[d] = wrap(c[d], rep.L);
-          prodpos[2 * (size_t)i] = store4<T>(cw, pack_sp((uint32_t)product, r));
+          put4<T>(&prodpos[2 * (size_t)i], cw, pack_sp((uint32_t)product, r));
           np = 1;
         }
       } else {
-        double qa[3] = {0, 0, 0}, qb[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-          qa[d] = wrap(c[d] - ca * rv[d], rep.L);
-          qb[d] = wrap(c[d] + cb * rv[d], rep.L);
+        if (!job) {
+          double qa[3] = {0, 0, 0}, qb[3] = {0, 0, 0};
+          for (int d = 0; d < dim; ++d) {
+            qa[d] = wrap(c[d] - ca * rv[d], rep.L);
+            qb[d] = wrap(c[d] + cb * rv[d], rep.L);
+          }
+          put4<T>(&prodpos[2 * (size_t)i], qa, pack_sp((uint32_t)sa, r));
+          put4<T>(&prodpos[2 * (size_t)i + 1], qb, pack_sp((uint32_t)sb, r));
         }
-        prodpos[2 * (size_t)i] = store4<T>(qa, pack_sp((uint32_t)sa, r));
-        prodpos[2 * (size_t)i + 1] = store4<T>(qb, pack_sp((uint32_t)sb, r));
         np = 2;
       }
     }
@@ -981,12 +1124,13 @@ __device__ __noinline__ float resample_tab_ni(const PairDev& pr, bool d3, float 
   return d3 ? resample3_tab(pr, U, R0) : resample2_tab(pr, U, R0);
 }
 
-__device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev* __restrict__ reps,
-                                               const FiredPair* __restrict__ fired,
-                                               const uint32_t* __restrict__ fstate, uint32_t e, uint32_t step,
-                                               const float4* __restrict__ x0, float4* __restrict__ x1,
-                                               uint32_t* __restrict__ status, float4* __restrict__ prodpos,
-                                               unsigned long long& n_react, unsigned long long& n_res) {
+__device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev* reps,
+                                               const FiredPair* fired,
+                                               const uint32_t* fstate, uint32_t e, uint32_t step,
+                                               const float4* x0, float4* x1,
+                                               uint32_t* status, float4* prodpos,
+                                               unsigned long long& n_react, unsigned long long& n_res,
+                                               DevCtl* ctl, AngJob* jobs, uint32_t job_cap) {
   const bool d3 = P.dim == 3;
   const uint32_t fs = fstate[e];
   const FiredPair f = fired[e];
@@ -1010,21 +1154,46 @@ __device__ __forceinline__ void resolve_pair_f(const DevParams& P, const RepDev*
     R0 = fmaxf(R0, 1.0f);
     const float Rn = resample_tab_ni(pr, d3, u23(w.x), R0);
     const float len = sqrtf(rx * rx + ry * ry + rz * rz);
+    const float l0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z);
     float dx, dy, dz;
     if (len > 0.0f) {
       dx = rx / len; dy = ry / len; dz = rz / len;
+    } else if (l0 > 0.0f) {
+      dx = r0x / l0; dy = r0y / l0; dz = r0z / l0;
     } else {
-      const float l0 = sqrtf(r0x * r0x + r0y * r0y + r0z * r0z);
-      if (l0 > 0.0f) {
-        dx = r0x / l0; dy = r0y / l0; dz = r0z / l0;
-      } else {
-        dx = 1.0f; dy = 0.0f; dz = 0.0f;
-      }
+      dx = 1.0f; dy = 0.0f; dz = 0.0f;
     }
     const float ln = Rn * pr.sigma_f;
     ++n_res;
     react = pr.bc == RD_BC_RAD && u23(w.z) < p_reac_tab_ni(pr, Rn - 1.0f, R0 - 1.0f);
     if (!react) {
+      if (P.angle_mode == 0) {
+        // exact direction from the full propagator about the start separation, in the angle pass
+        const uint4 wg = draw_ni(P, step, f.ida, f.idb, TAG_ANG, r);
+        AngJob aj;
+        aj.c[0] = cx; aj.c[1] = cy; aj.c[2] = cz;
+        aj.fb[0] = dx; aj.fb[1] = dy; aj.fb[2] = dz;
+        aj.u[0] = 1.0; aj.u[1] = 0.0; aj.u[2] = 0.0;
+        if (l0 > 0.0f) {
+          aj.u[0] = r0x / l0; aj.u[1] = r0y / l0; aj.u[2] = r0z / l0;
+        }
+        aj.len = ln;
+        aj.Rn = Rn;
+        aj.R0 = R0;
+        aj.tau = pr.tau;
+        aj.ca = ca;
+        aj.cb = cb;
+        aj.U_ang = u23(wg.x);
+        aj.U_azi = u23(wg.z);
+        aj.kind = 0u | ((uint32_t)rule << 8);
+        aj.ia = f.ia;
+        aj.ib = f.ib;
+        aj.wa = wa;
+        aj.wb = wb;
+        aj.r = r;
+        push_ang_job(ctl, jobs, job_cap, aj);
+        return;
+      }
       x1[f.ia] = make_float4(wrap_f(cx - ca * ln * dx, rep.Lf), wrap_f(cy - ca * ln * dy, rep.Lf),
                              d3 ? wrap_f(cz - ca * ln * dz, rep.Lf) : 0.0f, a1.w);
       x1[f.ib] = make_float4(wrap_f(cx + cb * ln * dx, rep.Lf), wrap_f(cy + cb * ln * dy, rep.Lf),
@@ -1051,10 +1220,12 @@ __device__ __forceinline__ void normals_f(const DevParams& P, uint32_t c0, uint3
   if (d3) box_muller_f(u23(w.z), u23(w.w), n[2], n[3]);
 }
 
-__device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDev* __restrict__ reps, uint32_t i,
-                                                 uint32_t step, const float4* __restrict__ x0,
-                                                 const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-                                                 float4* __restrict__ prodpos, unsigned long long& n_rec) {
+__device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDev* reps, uint32_t i,
+                                                 uint32_t step, const float4* x0,
+                                                 const uint32_t* id, uint32_t* status,
+                                                 float4* prodpos, unsigned long long& n_rec,
+                                                 DevCtl* ctl, AngJob* jobs,
+                                                 uint32_t job_cap) {
   const bool d3 = P.dim == 3;
   const uint32_t st = status[i];
   const DecayDev& dc = P.decays[(st >> ST_CHANNEL_SHIFT) & 15u];
@@ -1093,7 +1264,7 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
     const float ellc = sqrtf(2.0f * DR * dt);
     const float cx = p0.x + ellc * nc[0], cy = p0.y + ellc * nc[1], cz = p0.z + ellc * nc[2];
     const int rule = P.pair_of[sa][sb];
-    bool recombine = false;
+    bool recombine = false, job = false;
     int product = -1;
     float rx, ry, rz;
     if (rule >= 0) {
@@ -1107,6 +1278,30 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
       else if (pr.bc == RD_BC_RAD)
         recombine = u23(w.z) < p_reac_tab_ni(pr, Rn - 1.0f, 0.0f);
       product = pr.product;
+      if (!recombine && P.angle_mode == 0) {
+        // from contact along the drawn direction: the new direction in the angle pass
+        job = true;
+        const uint4 wg = draw_ni(P, step, pid, kOneParticle, TAG_ANG, r);
+        AngJob aj;
+        aj.c[0] = cx; aj.c[1] = cy; aj.c[2] = cz;
+        aj.u[0] = dx; aj.u[1] = dy; aj.u[2] = dz;
+        aj.fb[0] = dx; aj.fb[1] = dy; aj.fb[2] = dz;
+        aj.len = ln;
+        aj.Rn = Rn;
+        aj.R0 = 1.0;
+        aj.tau = pr.tau;
+        aj.ca = ca;
+        aj.cb = cb;
+        aj.U_ang = u23(wg.x);
+        aj.U_azi = u23(wg.z);
+        aj.kind = 1u | ((uint32_t)rule << 8);
+        aj.ia = i;
+        aj.ib = i;
+        aj.wa = pack_sp((uint32_t)sa, r);
+        aj.wb = pack_sp((uint32_t)sb, r);
+        aj.r = r;
+        push_ang_job(ctl, jobs, job_cap, aj);
+      }
     } else {
       float nr[4];
       normals_f(P, step, pid, TAG_DISS2, r, d3, nr);
@@ -1122,12 +1317,14 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
         np = 1;
       }
     } else {
-      prodpos[2 * (size_t)i] = make_float4(wrap_f(cx - ca * rx, rep.Lf), wrap_f(cy - ca * ry, rep.Lf),
-                                           d3 ? wrap_f(cz - ca * rz, rep.Lf) : 0.0f,
-                                           w_from_bits_f(pack_sp((uint32_t)sa, r)));
-      prodpos[2 * (size_t)i + 1] = make_float4(wrap_f(cx + cb * rx, rep.Lf), wrap_f(cy + cb * ry, rep.Lf),
-                                               d3 ? wrap_f(cz + cb * rz, rep.Lf) : 0.0f,
-                                               w_from_bits_f(pack_sp((uint32_t)sb, r)));
+      if (!job) {
+        prodpos[2 * (size_t)i] = make_float4(wrap_f(cx - ca * rx, rep.Lf), wrap_f(cy - ca * ry, rep.Lf),
+                                             d3 ? wrap_f(cz - ca * rz, rep.Lf) : 0.0f,
+                                             w_from_bits_f(pack_sp((uint32_t)sa, r)));
+        prodpos[2 * (size_t)i + 1] = make_float4(wrap_f(cx + cb * rx, rep.Lf), wrap_f(cy + cb * ry, rep.Lf),
+                                                 d3 ? wrap_f(cz + cb * rz, rep.Lf) : 0.0f,
+                                                 w_from_bits_f(pack_sp((uint32_t)sb, r)));
+      }
       np = 2;
     }
   }
@@ -1141,10 +1338,10 @@ __device__ __forceinline__ void decay_products_f(const DevParams& P, const RepDe
 // particles among the live pairs.  Returns false if the round bound ran out.
 constexpr int kMatchSmemPairs = 256, kMatchSmemSlots = 1024;
 
-__device__ __noinline__ bool match_rounds_smem(const DevParams& P, DevCtl* __restrict__ ctl,
-                                               const FiredPair* __restrict__ fired, uint32_t* __restrict__ fstate,
-                                               int32_t* __restrict__ matched, const uint32_t* __restrict__ conflict,
-                                               uint32_t* __restrict__ accepted, uint32_t nc) {
+__device__ __noinline__ bool match_rounds_smem(const DevParams& P, DevCtl* ctl,
+                                               const FiredPair* fired, uint32_t* fstate,
+                                               int32_t* matched, const uint32_t* conflict,
+                                               uint32_t* accepted, uint32_t nc, uint32_t n_triv) {
   __shared__ uint32_t s_e[kMatchSmemPairs];
   __shared__ unsigned long long s_key[kMatchSmemPairs], s_pid[kMatchSmemPairs];
   __shared__ uint16_t s_sa[kMatchSmemPairs], s_sb[kMatchSmemPairs];
@@ -1214,7 +1411,7 @@ __device__ __noinline__ bool match_rounds_smem(const DevParams& P, DevCtl* __res
         matched[f.ia] = (int32_t)f.ib;
         matched[f.ib] = (int32_t)f.ia;
         fstate[e] = (fstate[e] & ~3u) | FS_ACCEPTED;
-        accepted[atomicAdd(&ctl->n_accept, 1u)] = e;
+        accepted[n_triv + atomicAdd(&ctl->n_round_acc, 1u)] = e;
         atomicAdd(&s_acc, 1ull);
       }
     }
@@ -1254,10 +1451,10 @@ __device__ __noinline__ bool match_rounds_smem(const DevParams& P, DevCtl* __res
 // Compaction table over replicas, by one block: survivors = particles - consumed; exclusive
 // prefixes of products and inclusive prefixes of survivors over the replicas; the new particle
 // count.
-__device__ __forceinline__ void replica_table(int n_replicas, const RepDev* __restrict__ reps,
-                                              const uint32_t* __restrict__ rep_cons,
-                                              const uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx,
-                                              DevCtl* __restrict__ ctl) {
+__device__ __forceinline__ void replica_table(int n_replicas, const RepDev* reps,
+                                              const uint32_t* rep_cons,
+                                              const uint32_t* rep_prod, RepX* repx,
+                                              DevCtl* ctl) {
   __shared__ unsigned long long sm[32];
   unsigned long long carry = 0;      // survivors << 32 | products of the replicas done so far
   for (int base = 0; base < n_replicas; base += blockDim.x) {
@@ -1284,26 +1481,29 @@ __device__ __forceinline__ void replica_table(int n_replicas, const RepDev* __re
 }
 
 // One accepted pair or one decay of this step (item q of the combined list).
+// One accepted pair or one decay of this step (item q of the combined list).
 template <class T>
-__device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __restrict__ reps,
-                                             const FiredPair* __restrict__ fired, const uint32_t* __restrict__ fstate,
+__device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* reps,
+                                             const FiredPair* fired, const uint32_t* fstate,
                                              bool pair, uint32_t idx, uint32_t step,
-                                             const typename V4<T>::type* __restrict__ x0,
-                                             typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
-                                             uint32_t* __restrict__ status, typename V4<T>::type* __restrict__ prodpos,
-                                             uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod,
+                                             const typename V4<T>::type* x0,
+                                             typename V4<T>::type* x1, const uint32_t* id,
+                                             uint32_t* status, typename V4<T>::type* prodpos,
+                                             uint32_t* rep_cons, uint32_t* rep_prod,
                                              unsigned long long& n_react, unsigned long long& n_res,
-                                             unsigned long long& n_rec, unsigned long long& n_near) {
+                                             unsigned long long& n_rec, unsigned long long& n_near,
+                                             DevCtl* ctl, AngJob* jobs, uint32_t job_cap) {
   if constexpr (sizeof(T) == 8) {
     if (pair)
-      resolve_pair<T>(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res, n_near);
+      resolve_pair<T>(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res, n_near, ctl, jobs,
+                      job_cap);
     else
-      decay_products<T>(P, reps, idx, step, x0, id, status, prodpos, n_rec, n_near);
+      decay_products<T>(P, reps, idx, step, x0, id, status, prodpos, n_rec, n_near, ctl, jobs, job_cap);
   } else {
     if (pair)
-      resolve_pair_f(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res);
+      resolve_pair_f(P, reps, fired, fstate, idx, step, x0, x1, status, prodpos, n_react, n_res, ctl, jobs, job_cap);
     else
-      decay_products_f(P, reps, idx, step, x0, id, status, prodpos, n_rec);
+      decay_products_f(P, reps, idx, step, x0, id, status, prodpos, n_rec, ctl, jobs, job_cap);
   }
   // per-replica tallies for the compaction: a reacting pair consumes both particles, a decay its
   // parent; the owner's status carries the number of products
@@ -1328,17 +1528,16 @@ __device__ __noinline__ void resolve_item(const DevParams& P, const RepDev* __re
 //    pairs touching an accepted particle die, the rest stay live.  The pairs accepted in the
 //    rounds are resolved after the last round.
 template <class T>
-__global__ void __launch_bounds__(256, 2) k_match_resolve(
-    const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl, const RepDev* __restrict__ reps,
-    const FiredPair* __restrict__ fired, uint32_t* __restrict__ fstate, int32_t* __restrict__ matched,
-    const uint32_t* __restrict__ conflict, uint32_t* __restrict__ accepted,
-    unsigned long long* __restrict__ best_key, unsigned long long* __restrict__ best_pid,
-    const uint32_t* __restrict__ decay_list, const typename V4<T>::type* __restrict__ x0,
-    typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
-    typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs,
-    uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx,
-    ConflictRec* __restrict__ crec) {
-  pdl_enter();
+__device__ __forceinline__ void ph_match_resolve(
+    const DevParams* Pp, DevCtl* ctl, const RepDev* reps,
+    const FiredPair* fired, uint32_t* fstate, int32_t* matched,
+    const uint32_t* conflict, uint32_t* accepted,
+    unsigned long long* best_key, unsigned long long* best_pid,
+    const uint32_t* decay_list, const typename V4<T>::type* x0,
+    typename V4<T>::type* x1, const uint32_t* id, uint32_t* status,
+    typename V4<T>::type* prodpos, uint32_t* deg, uint32_t cap_pairs,
+    uint32_t* rep_cons, uint32_t* rep_prod, RepX* repx,
+    ConflictRec* crec, AngJob* jobs, uint32_t job_cap) {
   __shared__ unsigned long long acc_s;
   __shared__ uint32_t live_s;
   const DevParams& P = *Pp;
@@ -1350,8 +1549,10 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
     deg[fired[e].ib] = 0u;
   }
   if (ctl->status) return;
+  // n_accept holds the trivially accepted pairs only: the rounds count theirs in n_round_acc, so
+  // every block reads the same n_triv whenever it starts
   const uint32_t nc = ctl->n_conflict, n_triv = ctl->n_accept, nd = ctl->n_decay, step = ctl->step;
-  const bool multi = nc > kMatchSingleMax && gridDim.x > 1;
+  const bool multi = nc > P.match_single_max && gridDim.x > 1;
   unsigned long long n_react = 0, n_res = 0, n_near = 0, n_rec = 0;
   if (!multi) {
     // block 0 runs the (short) rounds alone, the other blocks resolve meanwhile
@@ -1362,17 +1563,17 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
       for (uint32_t q = b * blockDim.x + threadIdx.x; q < n_triv + nd; q += nblk * blockDim.x) {
         const bool pair = q < n_triv;
         resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_triv], step, x0, x1, id,
-                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near);
+                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near, ctl, jobs, job_cap);
       }
     }
   }
-  if (nc > 0 && !multi && nc <= (uint32_t)kMatchSmemPairs && blockIdx.x == 0) {
+  if (nc > 0 && !multi && nc <= min(P.match_smem_max, (uint32_t)kMatchSmemPairs) && blockIdx.x == 0) {
     // short list: block 0 matches in shared memory, then resolves the pairs it accepted
-    if (match_rounds_smem(P, ctl, fired, fstate, matched, conflict, accepted, nc)) {
-      const uint32_t n_acc = *(volatile uint32_t*)&ctl->n_accept;
+    if (match_rounds_smem(P, ctl, fired, fstate, matched, conflict, accepted, nc, n_triv)) {
+      const uint32_t n_acc = n_triv + *(volatile uint32_t*)&ctl->n_round_acc;
       for (uint32_t q = n_triv + threadIdx.x; q < n_acc; q += blockDim.x)
         resolve_item<T>(P, reps, fired, fstate, true, accepted[q], step, x0, x1, id, status, prodpos, rep_cons,
-                        rep_prod, n_react, n_res, n_rec, n_near);
+                        rep_prod, n_react, n_res, n_rec, n_near, ctl, jobs, job_cap);
     }
   } else if (nc > 0 && (multi || blockIdx.x == 0)) {
     const uint32_t nthr = multi ? gridDim.x * blockDim.x : blockDim.x;
@@ -1432,7 +1633,7 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
           matched[c.ib] = (int32_t)c.ia;
           fstate[c.e] = (fstate[c.e] & ~3u) | FS_ACCEPTED;
           crec[q].st = FS_ACCEPTED;
-          accepted[atomicAdd(&ctl->n_accept, 1u)] = c.e;
+          accepted[n_triv + atomicAdd(&ctl->n_round_acc, 1u)] = c.e;
           atomicAdd(&acc_s, 1ull);
         }
       }
@@ -1475,12 +1676,12 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
     // rounds; with the whole grid in the rounds also the trivially accepted pairs and the decays,
     // kept out of the barrier-separated phases because a resolution can take long (FP64 2D)
     if (ok) {
-      const uint32_t n_acc = *(volatile uint32_t*)&ctl->n_accept;
+      const uint32_t n_acc = n_triv + *(volatile uint32_t*)&ctl->n_round_acc;
       const uint32_t first = multi ? 0u : n_triv, last = multi ? n_acc + nd : n_acc;
       for (uint32_t q = first + tid; q < last; q += nthr) {
         const bool pair = q < n_acc;
         resolve_item<T>(P, reps, fired, fstate, pair, pair ? accepted[q] : decay_list[q - n_acc], step, x0, x1, id,
-                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near);
+                        status, prodpos, rep_cons, rep_prod, n_react, n_res, n_rec, n_near, ctl, jobs, job_cap);
       }
     }
   }
@@ -1501,6 +1702,106 @@ __global__ void __launch_bounds__(256, 2) k_match_resolve(
   replica_table(P.n_replicas, reps, rep_cons, rep_prod, repx, ctl);
 }
 
+template <class T>
+__global__ void __launch_bounds__(256, 2) k_match_resolve(
+    const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl, const RepDev* __restrict__ reps,
+    const FiredPair* __restrict__ fired, uint32_t* __restrict__ fstate, int32_t* __restrict__ matched,
+    const uint32_t* __restrict__ conflict, uint32_t* __restrict__ accepted,
+    unsigned long long* __restrict__ best_key, unsigned long long* __restrict__ best_pid,
+    const uint32_t* __restrict__ decay_list, const typename V4<T>::type* __restrict__ x0,
+    typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id, uint32_t* __restrict__ status,
+    typename V4<T>::type* __restrict__ prodpos, uint32_t* __restrict__ deg, uint32_t cap_pairs,
+    uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod, RepX* __restrict__ repx,
+    ConflictRec* __restrict__ crec, AngJob* __restrict__ jobs, uint32_t job_cap) {
+  pdl_enter();
+  ph_match_resolve<T>(Pp, ctl, reps, fired, fstate, matched, conflict, accepted, best_key, best_pid, decay_list, x0,
+                      x1, id, status, prodpos, deg, cap_pairs, rep_cons, rep_prod, repx, crec, jobs, job_cap);
+}
+
+// Places the two particles of angle job j along dir (the new separation direction).
+template <class T>
+__device__ __forceinline__ void ang_job_place(const AngJob& j, const RepDev& rep, int dim, const T* dir,
+                                              typename V4<T>::type* x1, typename V4<T>::type* prodpos) {
+  double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+  if constexpr (sizeof(T) == 8) {
+    for (int d = 0; d < dim; ++d) {
+      const double nr = j.len * dir[d];
+      a[d] = wrap(j.c[d] - j.ca * nr, rep.L);
+      b[d] = wrap(j.c[d] + j.cb * nr, rep.L);
+    }
+  } else {
+    const float ln = (float)j.len, caf = (float)j.ca, cbf = (float)j.cb;
+    for (int d = 0; d < dim; ++d) {
+      const float cf = (float)j.c[d];
+      a[d] = wrap_f(cf - caf * ln * dir[d], rep.Lf);
+      b[d] = wrap_f(cf + cbf * ln * dir[d], rep.Lf);
+    }
+  }
+  if ((j.kind & 0xFFu) == 0) {
+    put4<T>(&x1[j.ia], a, j.wa);
+    put4<T>(&x1[j.ib], b, j.wb);
+  } else {
+    put4<T>(&prodpos[2 * (size_t)j.ia], a, j.wa);
+    put4<T>(&prodpos[2 * (size_t)j.ia + 1], b, j.wb);
+  }
+}
+
+// Angle pass: the new separation direction of every encountered pair and every decay's product
+// pair that the resolution left to it (angle mode 0), then the particles placed.  Mixed step: one
+// thread per job from the rule's tabulated law; jobs of rules without a table (and every job of the
+// FP64 step) one warp per job from the full propagator (the partial-wave evaluation is
+// warp-collective).
+template <class T>
+__device__ __forceinline__ void ph_angles(const DevParams* Pp, DevCtl* ctl,
+                                          const RepDev* reps, const AngJob* jobs,
+                                          uint32_t job_cap, typename V4<T>::type* x1,
+                                          typename V4<T>::type* prodpos, const uint32_t bid,
+                                          const uint32_t nblk) {
+  const DevParams& P = *Pp;
+  if (ctl->status) return;
+  const uint32_t nj = min(ctl->n_ang, job_cap);
+  const int dim = P.dim;
+  unsigned long long n_fb = 0;
+  if constexpr (sizeof(T) == 4) {
+    for (uint32_t q = bid * blockDim.x + threadIdx.x; q < nj; q += nblk * blockDim.x) {
+      const AngJob& j = jobs[q];
+      const AngTab& A = P.pairs[j.kind >> 8].tab_ang;
+      if (!A.v) continue;
+      float u[3] = {(float)j.u[0], (float)j.u[1], (float)j.u[2]}, dir[3];
+      const float v = ang_table_sample(A, dim, (float)j.U_ang, (float)j.Rn, (float)j.R0);
+      if (v == v) {
+        ang_place<float>(dim, u, v, (float)j.U_azi, dir);
+      } else {
+        for (int d = 0; d < 3; ++d) dir[d] = (float)j.fb[d];
+        ++n_fb;
+      }
+      ang_job_place<T>(j, reps[j.r], dim, dir, x1, prodpos);
+    }
+  }
+  const uint32_t wpb = blockDim.x >> 5, nw = nblk * wpb;
+  const bool lane0 = (threadIdx.x & 31) == 0;
+  for (uint32_t q = bid * wpb + (threadIdx.x >> 5); q < nj; q += nw) {
+    const AngJob& j = jobs[q];
+    if (sizeof(T) == 4 && P.pairs[j.kind >> 8].tab_ang.v) continue;
+    T u[3] = {(T)j.u[0], (T)j.u[1], (T)j.u[2]}, dir[3];
+    if (!ang_direction_warp<T>(dim, u, (T)j.U_ang, (T)j.U_azi, (T)j.Rn, (T)j.R0, (T)j.tau, P.gl16, dir)) {
+      for (int d = 0; d < 3; ++d) dir[d] = (T)j.fb[d];
+      n_fb += lane0;
+    }
+    if (lane0) ang_job_place<T>(j, reps[j.r], dim, dir, x1, prodpos);
+  }
+  if (n_fb) atomicAdd(&ctl->stats[RD_STAT_ANGLE_FALLBACK], n_fb);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, 2) k_angles(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                                                   const RepDev* __restrict__ reps, const AngJob* __restrict__ jobs,
+                                                   uint32_t job_cap, typename V4<T>::type* __restrict__ x1,
+                                                   typename V4<T>::type* __restrict__ prodpos) {
+  pdl_enter();
+  ph_angles<T>(Pp, ctl, reps, jobs, job_cap, x1, prodpos, blockIdx.x, gridDim.x);
+}
+
 // Per-warp aggregated count: lanes holding the same (replica, species) key add once.  Called by all
 // 32 lanes of a converged warp; key kNoKey is skipped.
 constexpr uint32_t kNoKey = 0xFFFFFFFFu;
@@ -1515,8 +1816,8 @@ __device__ __forceinline__ void count_key(uint32_t key, bool smem, uint32_t* his
 }
 
 // Species totals over all replicas of the (replica, species) counts, by one whole block.
-__device__ __forceinline__ void species_totals(const unsigned long long* __restrict__ counts, int n_replicas, int ns,
-                                               long long* __restrict__ out) {
+__device__ __forceinline__ void species_totals(const unsigned long long* counts, int n_replicas, int ns,
+                                               long long* out) {
   __shared__ unsigned long long tot[RD_MAX_SPECIES];
   for (int k = threadIdx.x; k < ns; k += blockDim.x) tot[k] = 0ull;
   __syncthreads();
@@ -1543,20 +1844,20 @@ __device__ __forceinline__ void species_totals(const unsigned long long* __restr
 constexpr int kCompactTile = 2048;   // particles per tile (the look-back buffers are sized for it)
 
 template <class T, int kCompactThreads>
-__global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
-                          RepDev* __restrict__ reps, const RepX* __restrict__ repx,
-                          uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod,
-                          const typename V4<T>::type* __restrict__ x0,
-                          const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
-                          const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
-                          unsigned long long* __restrict__ agg, unsigned long long* __restrict__ incl,
-                          uint32_t* __restrict__ flag, typename V4<T>::type* __restrict__ xo,
-                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts,
-                          long long* __restrict__ history, int history_len) {
-  pdl_enter();
-  extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
+__device__ __forceinline__ void ph_compact(const DevParams* Pp, DevCtl* ctl,
+                          RepDev* reps, const RepX* repx,
+                          uint32_t* rep_cons, uint32_t* rep_prod,
+                          const typename V4<T>::type* x0,
+                          const typename V4<T>::type* x1, const uint32_t* id,
+                          const uint32_t* status, const typename V4<T>::type* prodpos,
+                          unsigned long long* agg, unsigned long long* incl,
+                          uint32_t* flag, typename V4<T>::type* xo,
+                          uint32_t* ido, unsigned long long* counts, int n_counts,
+                          long long* history, int history_len,
+                          uint32_t* hist /* n_counts entries when n_counts <= kSmemCounts */,
+                          unsigned long long* s_pre /* kCompactTile entries */,
+                          const int stamp_phase = -1) {
   constexpr int kTile = kCompactTile, kCompactItems = kCompactTile / kCompactThreads;
-  __shared__ unsigned long long s_pre[kTile];
   __shared__ unsigned long long sm[32];
   __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_prefix;
@@ -1564,11 +1865,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __
   const DevParams& P = *Pp;
   const int ns = P.n_species;
   const bool use_smem = n_counts <= kSmemCounts;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[1], 1u);
   if (use_smem)
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x) hist[k] = 0u;
-  __syncthreads();
-  const uint32_t tile = s_tile;
   const uint32_t n = ctl->n;
   // a single replica: its placement follows from the step's tallies directly
   const bool one = P.n_replicas == 1;
@@ -1582,7 +1880,13 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __
   const bool fail = ctl->status != 0 || (unsigned long long)n_new > (unsigned long long)P.cap_particles;
   const uint32_t ntiles = (uint32_t)(((int64_t)n + kTile - 1) / kTile);
   auto key_of = [&](uint32_t wb) { return (wb >> 8) * ns + (wb & 0xFFu); };
-  if (tile < ntiles) {
+  // tiles by ticket, so that every tile's predecessors are taken before it (look-back order)
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[1], 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) break;
     const int64_t t0 = (int64_t)tile * kTile;
     if (!fail) {
       // blocked arrangement for the scan: each thread owns kCompactItems consecutive particles
@@ -1656,6 +1960,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __
     for (int k = threadIdx.x; k < n_counts; k += blockDim.x)
       if (hist[k]) atomicAdd(&counts[k], (unsigned long long)hist[k]);
   }
+  __syncthreads();
   // the last block to finish commits the step: replica segments, ids, count, step, time
   __threadfence();
   __syncthreads();
@@ -1679,6 +1984,13 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __
     species_totals(counts, P.n_replicas, ns, history + (size_t)((ctl->step + 1u) % (uint32_t)history_len) * ns);
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (stamp_phase >= 0) {
+      // fused step: the compaction phase ends with this commit
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      ctl->ph_acc[stamp_phase] += now - ctl->ph_t[stamp_phase];
+      ctl->ph_steps += 1;
+    }
     if (!fail) {
       ctl->stats[RD_STAT_PARTICLE_STEPS] += n;
       ctl->stats[RD_STAT_DECAYS] += ctl->n_decay;
@@ -1694,10 +2006,30 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __
     ctl->fired = 0;
     ctl->n_conflict = 0;
     ctl->n_accept = 0;
+    ctl->n_round_acc = 0;
+    ctl->n_ang = 0;
     ctl->n_decay = 0;
     ctl->done_blocks = 0;
     ctl->done_res = 0;
   }
+}
+
+template <class T, int kCompactThreads>
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const DevParams* __restrict__ Pp, DevCtl* __restrict__ ctl,
+                          RepDev* __restrict__ reps, const RepX* __restrict__ repx,
+                          uint32_t* __restrict__ rep_cons, uint32_t* __restrict__ rep_prod,
+                          const typename V4<T>::type* __restrict__ x0,
+                          const typename V4<T>::type* __restrict__ x1, const uint32_t* __restrict__ id,
+                          const uint32_t* __restrict__ status, const typename V4<T>::type* __restrict__ prodpos,
+                          unsigned long long* __restrict__ agg, unsigned long long* __restrict__ incl,
+                          uint32_t* __restrict__ flag, typename V4<T>::type* __restrict__ xo,
+                          uint32_t* __restrict__ ido, unsigned long long* __restrict__ counts, int n_counts,
+                          long long* __restrict__ history, int history_len) {
+  pdl_enter();
+  extern __shared__ uint32_t hist[];   // n_counts entries when n_counts <= kSmemCounts
+  __shared__ unsigned long long s_pre[kCompactTile];
+  ph_compact<T, kCompactThreads>(Pp, ctl, reps, repx, rep_cons, rep_prod, x0, x1, id, status, prodpos, agg, incl,
+                                 flag, xo, ido, counts, n_counts, history, history_len, hist, s_pre);
 }
 
 // ================================================================================================
@@ -1760,12 +2092,13 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
                              double* __restrict__ p_reac) {
   const DevParams& P = *Pp;
   const PairDev& pr = P.pairs[rule];
-  const double inv_sigma = 1.0 / pr.sigma;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double a = r0[k], b = r[k];
+    // mixed: the separations rounded once to FP32 and scaled there (FP64 arithmetic runs at 1/64 of
+    // the FP32 rate on this part)
+    const float d0 = fmaf((float)a, pr.inv_sigma_f, -1.0f), d = fmaf((float)b, pr.inv_sigma_f, -1.0f);
     if (p_enc) {
       if (P.precision == RD_MIXED) {
-        const float d0 = (float)((a - pr.sigma) * inv_sigma), d = (float)((b - pr.sigma) * inv_sigma);
         float pf;
         if (P.dim == 3) {
           pf = p_enc3_f(d, d0, pr.inv_tau_f);
@@ -1783,10 +2116,58 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
     if (p_reac) {
       double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
       if (pr.bc == RD_BC_RAD)
-        v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, (float)(b * inv_sigma - 1.0), (float)(a * inv_sigma - 1.0))
-                                    : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
+        v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
       p_reac[k] = v;
     }
+  }
+}
+
+// Standalone propagation of encountered pairs (rd_propagate): one warp per pair, the same device
+// functions as the step (length from the radial law, direction from the partial-wave law).
+__global__ void k_propagate(const DevParams* __restrict__ Pp, int rule, const double* __restrict__ r0,
+                            const double* __restrict__ u, int64_t n, double* __restrict__ out) {
+  const DevParams& P = *Pp;
+  const PairDev& pr = P.pairs[rule];
+  const int dim = P.dim;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += nw) {
+    const double a0 = r0[3 * k] / pr.sigma, a1 = r0[3 * k + 1] / pr.sigma, a2 = dim == 3 ? r0[3 * k + 2] / pr.sigma : 0.0;
+    const double l0 = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+    const double R0 = l0 < 1.0 ? 1.0 : l0;
+    double res[3] = {0.0, 0.0, 0.0};
+    if (P.precision == RD_MIXED) {
+      const float Rn = resample_tab_ni(pr, dim == 3, (float)u[4 * k], (float)R0);
+      float uu[3] = {1.0f, 0.0f, 0.0f}, dir[3];
+      if (l0 > 0.0) {
+        uu[0] = (float)(a0 / l0); uu[1] = (float)(a1 / l0); uu[2] = (float)(a2 / l0);
+      }
+      bool ok;
+      if (pr.tab_ang.v) {
+        // the mixed step's tabulated law
+        const float v = ang_table_sample(pr.tab_ang, dim, (float)u[4 * k + 1], Rn, (float)R0);
+        ok = v == v;
+        if (ok) ang_place<float>(dim, uu, v, (float)u[4 * k + 2], dir);
+      } else {
+        ok = ang_direction_warp<float>(dim, uu, (float)u[4 * k + 1], (float)u[4 * k + 2], Rn, (float)R0,
+                                       (float)pr.tau, P.gl16, dir);
+      }
+      if (!ok) {
+        dir[0] = uu[0]; dir[1] = uu[1]; dir[2] = uu[2];
+      }
+      for (int d = 0; d < dim; ++d) res[d] = (double)(Rn * dir[d]);
+    } else {
+      const double Rn = resample_dim_ni(P, pr, u[4 * k], R0);
+      double uu[3] = {1.0, 0.0, 0.0}, dir[3];
+      if (l0 > 0.0) {
+        uu[0] = a0 / l0; uu[1] = a1 / l0; uu[2] = a2 / l0;
+      }
+      if (!ang_direction_warp<double>(dim, uu, u[4 * k + 1], u[4 * k + 2], Rn, R0, pr.tau, P.gl16, dir)) {
+        dir[0] = uu[0]; dir[1] = uu[1]; dir[2] = uu[2];
+      }
+      for (int d = 0; d < dim; ++d) res[d] = Rn * dir[d];
+    }
+    if ((threadIdx.x & 31) == 0)
+      for (int d = 0; d < 3; ++d) out[3 * k + d] = res[d] * pr.sigma;
   }
 }
 
@@ -1902,6 +2283,135 @@ void launch_build_table(const DevParams* P, int rule, int kind, float* out, floa
 }
 
 // ================================================================================================
+// The whole step as one cooperative launch (every block resident): the phases of the separate
+// kernels above, in the same order and with the same device code, separated by bounded grid
+// barriers instead of kernel boundaries; nsteps steps per launch with the state buffers
+// alternating.  Block 0 stamps the global timer at each phase start (per-phase times).
+// ================================================================================================
+const char* const kFusedPhaseNames[kFusedPhases] = {"ph_prepare", "ph_scan_cells", "ph_scatter_cells", "ph_sweep",
+                                                     "ph_match_trivial", "ph_match_resolve", "ph_angles",
+                                                     "ph_compact"};
+
+__device__ __forceinline__ void phase_stamp(DevCtl* ctl, int k) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (k > 0) ctl->ph_acc[k - 1] += now - ctl->ph_t[k - 1];
+    ctl->ph_t[k] = now;
+  }
+}
+
+constexpr size_t kFusedSmemSweep = sizeof(uint2) * kSweepRanges * 256;
+
+template <class T, bool kSplit, int kReach>
+__global__ void __launch_bounds__(256, 2) k_step_fused(const StepLaunch L, const int nsteps) {
+  using V = typename V4<T>::type;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  DevCtl* ctl = L.ctl;
+  const uint32_t split = L.sweep_split > 1 ? (uint32_t)L.sweep_split : 1u;
+  for (int st = 0; st < nsteps; ++st) {
+    const bool odd = st & 1;
+    V* x0 = (V*)(odd ? L.x_next : L.x_cur);
+    V* xo = (V*)(odd ? L.x_cur : L.x_next);
+    uint32_t* id0 = odd ? L.id_next : L.id_cur;
+    uint32_t* ido = odd ? L.id_cur : L.id_next;
+    V* x0s = L.x0d ? (V*)L.x0d : x0;
+    V* x1 = (V*)L.x1;
+    V* sx0 = (V*)L.sx0;
+    V* sx1 = (V*)L.sx1;
+    V* prod = (V*)L.prodpos;
+    phase_stamp(ctl, 0);
+    ph_prepare<T>(L.P, ctl, L.reps, x0, id0, x1, L.status, L.cell_of, L.slot, L.cell_count, L.decay_list, L.counts,
+                  L.n_counts, L.x0d ? x0s : (V*)nullptr, blockIdx.x, gridDim.x);
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 1);
+    while (ph_scan_tile<uint32_t, LoadCellCount>(LoadCellCount{L.cell_count}, L.total_cells, nullptr, L.cell_start,
+                                                 L.cell_count, L.agg32, L.incl32, L.flags, ctl, 0)) {
+    }
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 2);
+    ph_scatter<T>(ctl, x0s, x1, id0, L.cell_of, L.slot, L.cell_start, sx0, sx1, L.sidx, blockIdx.x, gridDim.x);
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 3);
+    ph_sweep<T, kSplit, kReach>(L.P, ctl, L.reps, sx0, sx1, L.sidx, L.cell_start, L.total_cells, L.fired, L.fstate,
+                                L.deg, L.matched, (uint32_t)L.cap_pairs, split, (uint2(*)[256])dsm, blockIdx.x,
+                                gridDim.x);
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 4);
+    ph_match_trivial(ctl, L.fired, L.fstate, L.deg, L.matched, L.conflict, L.accepted, L.best_key, L.best_pid,
+                     (uint32_t)L.cap_pairs, L.crec, blockIdx.x, gridDim.x);
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 5);
+    ph_match_resolve<T>(L.P, ctl, L.reps, L.fired, L.fstate, L.matched, L.conflict, L.accepted, L.best_key,
+                        L.best_pid, L.decay_list, x0s, x1, id0, L.status, prod, L.deg, (uint32_t)L.cap_pairs,
+                        L.rep_cons, L.rep_prod, L.repx, L.crec, L.ang_jobs, L.ang_cap);
+    if (!grid_barrier(ctl, false)) return;
+    phase_stamp(ctl, 6);
+    if (L.angles) {
+      ph_angles<T>(L.P, ctl, L.reps, L.ang_jobs, L.ang_cap, x1, prod, blockIdx.x, gridDim.x);
+      if (!grid_barrier(ctl, false)) return;
+    }
+    phase_stamp(ctl, 7);
+    ph_compact<T, 256>(L.P, ctl, L.reps, (const RepX*)L.repx, L.rep_cons, L.rep_prod, x0, x1, id0, L.status, prod,
+                       L.agg64, L.incl64, L.flags + L.flag_stride, xo, ido, L.counts, L.n_counts, L.history,
+                       L.history_len, (uint32_t*)(dsm + sizeof(unsigned long long) * kCompactTile),
+                       (unsigned long long*)dsm, 7);
+    if (st + 1 < nsteps) {
+      // the next step starts from the committed state; after an error the state is kept and the
+      // remaining steps are not taken
+      if (!grid_barrier(ctl, false)) return;
+      if (*(volatile int32_t*)&ctl->status != 0) return;
+    }
+  }
+}
+
+static size_t fused_smem_bytes(const StepLaunch& L) {
+  const size_t hist = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
+  return std::max(kFusedSmemSweep, sizeof(unsigned long long) * kCompactTile + hist);
+}
+
+template <class T>
+static void* fused_kernel_for(const StepLaunch& L) {
+  const bool split = L.sweep_split > 1;
+  if (L.reach == 2)
+    return split ? (void*)k_step_fused<T, true, 2> : (void*)k_step_fused<T, false, 2>;
+  return split ? (void*)k_step_fused<T, true, 1> : (void*)k_step_fused<T, false, 1>;
+}
+
+static void* fused_kernel(const StepLaunch& L) {
+  return L.precision == RD_MIXED ? fused_kernel_for<float>(L) : fused_kernel_for<double>(L);
+}
+
+int fused_grid_size(const StepLaunch& L, int device_sms) {
+  int per_sm = 0;
+  // static (conflict rounds, ~28 KB) plus dynamic shared memory exceeds the default 48 KB per
+  // block: opt in to the larger dynamic size (per kernel, per device)
+  if (cudaFuncSetAttribute(fused_kernel(L), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes(L)) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(L), 256, fused_smem_bytes(L)) !=
+      cudaSuccess)
+    return 0;
+  per_sm = std::min(per_sm, 2);
+  return per_sm >= 1 ? device_sms * per_sm : 0;
+}
+
+void launch_fused_steps(const StepLaunch& L, int nsteps, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::max(L.fused_grid, 1));
+  cfg.blockDim = dim3(256u);
+  cfg.dynamicSmemBytes = fused_smem_bytes(L);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&L, (void*)&nsteps};
+  cudaLaunchKernelExC(&cfg, fused_kernel(L), args);
+}
+
+// ================================================================================================
 // host-side launchers
 // ================================================================================================
 static inline int grid_for(int64_t n, int block, int max_grid) {
@@ -1977,8 +2487,8 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   const bool pdl = L.pdl;
   // start-of-step positions of the step proper: drifted copies when there is a drift step
   V* x0s = L.x0d ? (V*)L.x0d : x0;
-  launch_k(pdl, k_prepare<T>, Gp, B, 0, s, L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.matched, L.deg,
-           L.cell_of, L.slot, L.cell_count, L.decay_list, L.counts, L.n_counts, L.x0d ? x0s : (V*)nullptr);
+  launch_k(pdl, k_prepare<T>, Gp, B, 0, s, L.P, L.ctl, L.reps, x0, L.id_cur, x1, L.status, L.cell_of, L.slot,
+           L.cell_count, L.decay_list, L.counts, L.n_counts, L.x0d ? x0s : (V*)nullptr);
   mark("k_prepare");
   const int nbc = (int)((L.total_cells + tile - 1) / tile);
   launch_k(pdl, k_scan1<uint32_t, LoadCellCount>, nbc, 256, 0, s, LoadCellCount{L.cell_count}, L.total_cells,
@@ -2004,8 +2514,13 @@ static void step_impl(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
   mark("k_match_trivial");
   launch_coop(pdl, k_match_resolve<T>, L.match_grid > 0 ? L.match_grid : 1, 256, s, L.P, L.ctl, L.reps, L.fired, L.fstate,
               L.matched, L.conflict, L.accepted, L.best_key, L.best_pid, L.decay_list, x0s, x1, L.id_cur, L.status,
-              prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx, L.crec);
+              prod, L.deg, (uint32_t)L.cap_pairs, L.rep_cons, L.rep_prod, L.repx, L.crec, L.ang_jobs, L.ang_cap);
   mark("k_match_resolve");
+  if (L.angles) {
+    launch_k(pdl, k_angles<T>, L.match_grid > 0 ? L.match_grid : 1, 256, 0, s, L.P, L.ctl, (const RepDev*)L.reps,
+             (const AngJob*)L.ang_jobs, L.ang_cap, x1, prod);
+    mark("k_angles");
+  }
   const int nbp = (int)((L.cap_particles + kCompactTile - 1) / kCompactTile);
   const size_t hist_bytes = L.n_counts <= kSmemCounts ? (size_t)L.n_counts * 4 : 0;
   // small systems: 1024 threads per tile (more independent placements per tile); large ones 256
@@ -2160,6 +2675,10 @@ void launch_cell_scan(const StepLaunch& L, cudaStream_t s) {
 }
 
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer) {
+  if (L.fused && !timer) {
+    launch_fused_steps(L, 1, s);
+    return;
+  }
   if (L.precision == RD_MIXED)
     step_impl<float>(L, s, timer);
   else
@@ -2202,9 +2721,56 @@ void launch_pair_probs(const DevParams* P, int rule, const double* r0, const dou
   k_pair_probs<<<grid_for(n, 256, max_grid), 256, 0, s>>>(P, rule, r0, r, n, pe, pr);
 }
 
+void launch_propagate(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
+                      int max_grid, cudaStream_t s) {
+  k_propagate<<<grid_for(n * 32, 128, max_grid), 128, 0, s>>>(P, rule, r0, u, n, out);
+}
+
 void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
                      int max_grid, cudaStream_t s) {
   k_resample<<<grid_for(n, 128, max_grid), 128, 0, s>>>(P, rule, r0, u, n, out);
+}
+
+// Angle table of one pair rule (mixed step): one warp per node (a, b >= 1) of the law at
+// R0 = 1 + (a - 1) h, R' = 1 + (b - 1) h, FP64; then the ghost row a = 0 and column b = 0 by linear
+// extrapolation.
+__global__ void __launch_bounds__(128) k_ang_table(const DevParams* __restrict__ Pp, int dim, double tau, double h,
+                                                   int n0, int n1, float* __restrict__ out) {
+  __shared__ double dn[4][32 * kAngBuildSlots];
+  const int w = threadIdx.x >> 5;
+  const int64_t nodes = (int64_t)(n0 - 1) * (n1 - 1);
+  for (int64_t q = (int64_t)blockIdx.x * 4 + w; q < nodes; q += (int64_t)gridDim.x * 4) {
+    const int a = 1 + (int)(q / (n1 - 1)), b = 1 + (int)(q % (n1 - 1));
+    ang_table_node(dim, 1.0 + (b - 1) * h, 1.0 + (a - 1) * h, tau, Pp->gl16, dn[w],
+                   out + ((size_t)a * n1 + b) * kAngTabStride);
+  }
+}
+
+__global__ void k_ang_table_ghosts(int n0, int n1, int pass, float* __restrict__ out) {
+  constexpr int nu = kAngTabStride;
+  const int64_t m = pass == 0 ? (int64_t)(n1 - 1) * nu : (int64_t)n0 * nu;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % nu);
+    if (pass == 0) {
+      // row a = 0 (R0 = 1 - h) for b >= 1
+      const int b = 1 + (int)(i / nu);
+      out[(size_t)b * nu + k] = 2.0f * out[((size_t)n1 + b) * nu + k] - out[((size_t)2 * n1 + b) * nu + k];
+    } else {
+      // column b = 0 (R' = 1 - h) for every a
+      const int a = (int)(i / nu);
+      out[(size_t)a * n1 * nu + k] = 2.0f * out[((size_t)a * n1 + 1) * nu + k] - out[((size_t)a * n1 + 2) * nu + k];
+    }
+  }
+}
+
+void launch_build_ang_table(const DevParams* P, int dim, double tau, double h, int n0, int n1, float* out,
+                            int device_sms, cudaStream_t s) {
+  const int64_t nodes = (int64_t)(n0 - 1) * (n1 - 1);
+  const int G = (int)std::min<int64_t>((nodes + 3) / 4, (int64_t)device_sms * 16);
+  k_ang_table<<<G, 128, 0, s>>>(P, dim, tau, h, n0, n1, out);
+  constexpr int nu = kAngTabStride;
+  k_ang_table_ghosts<<<(int)(((int64_t)(n1 - 1) * nu + 255) / 256), 256, 0, s>>>(n0, n1, 0, out);
+  k_ang_table_ghosts<<<(int)(((int64_t)n0 * nu + 255) / 256), 256, 0, s>>>(n0, n1, 1, out);
 }
 
 }  // namespace rd

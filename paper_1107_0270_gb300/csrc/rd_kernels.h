@@ -19,6 +19,11 @@ struct StepLaunch {
   int scan_items;
   bool pdl;                    // programmatic dependent launch between the step kernels
   int match_grid;              // blocks of the cooperative matching launch (all resident)
+  int fused;                   // 1: the whole step as one cooperative launch (k_step_fused)
+  int fused_grid;              // blocks of that launch (all resident)
+  int angles;                  // 1: exact directions of encountered pairs (angle pass after the resolution)
+  AngJob* ang_jobs;            // angle jobs of a step (ang_cap entries)
+  uint32_t ang_cap;
   void* x0d;                   // drifted start positions (drift step only; nullptr without drift)
   ConflictRec* crec;           // conflict pairs of the matching rounds (fired-pair capacity)
   RepX* repx;                  // per-replica placement of the compaction
@@ -90,7 +95,18 @@ struct KernelTimer {
 
 // blocks of the cooperative matching launch that fit on the device at once (>= 1)
 int match_grid_size(int device_sms);
+// blocks of the fused step launch for L's precision, sweep split and reach that fit on the device
+// at once (at most 2 per SM); 0 if the kernel cannot be made resident (the step then uses separate
+// kernels)
+int fused_grid_size(const StepLaunch& L, int device_sms);
+// one step; with L.fused and no timer, the fused single-launch step
 void launch_step(const StepLaunch& L, cudaStream_t s, KernelTimer* timer);
+// nsteps steps as ONE fused cooperative launch (buffers alternate inside; L.x_cur holds the state
+// at the start and, for even nsteps, at the end)
+void launch_fused_steps(const StepLaunch& L, int nsteps, cudaStream_t s);
+// names of the fused step's phases (index k of DevCtl::ph_acc)
+constexpr int kFusedPhases = 8;
+extern const char* const kFusedPhaseNames[kFusedPhases];
 // device-side state transfer (validation + packing into out / ido; unpacking)
 void launch_set_state(const StepLaunch& L, int64_t n, const double* x, const int32_t* sp, const uint32_t* id,
                       const int32_t* rep, void* out, uint32_t* ido, uint32_t* cnt, uint32_t* maxid,
@@ -109,6 +125,11 @@ void launch_build_table(const DevParams* P, int rule, int kind, float* out, floa
                         double h1, double* tot, const Tab2* fwd, int device_sms, cudaStream_t s);
 void launch_resample(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
                      int max_grid, cudaStream_t s);
+// Angle table of one pair rule into out (n0 x n1 x (kAngTabU + 3) floats), on stream s.
+void launch_build_ang_table(const DevParams* P, int dim, double tau, double h, int n0, int n1, float* out,
+                            int device_sms, cudaStream_t s);
+void launch_propagate(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,
+                      int max_grid, cudaStream_t s);
 
 // First-passage refinement of encountered pairs (one pair rule, one step length).
 constexpr int kFptMaxLevels = 24;

@@ -179,3 +179,19 @@ def test_openmp_build_gives_the_serial_result():
     assert sa == sb
     assert np.array_equal(a.ids, b.ids) and np.array_equal(a.species, b.species)
     assert np.array_equal(a.x, b.x)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_angle_cdf_is_the_integral_of_the_density_and_inverts_the_sampler(dim):
+    # the CDF (summed from the integrated Legendre / cosine terms) against the density (summed from
+    # the terms themselves) by finite differences, its end values, and the sampler's round trip
+    R, R0, tau = 1.35, 1.15, 0.5
+    lo, hi = (-1.0, 1.0) if dim == 3 else (0.0, math.pi)
+    assert abs(O.ang_cdf(dim, lo, R, R0, tau)) < 1e-12
+    assert abs(O.ang_cdf(dim, hi, R, R0, tau) - 1.0) < 1e-12
+    eps = 1e-5
+    for v in np.linspace(lo + 0.05, hi - 0.05, 9):
+        fd = (O.ang_cdf(dim, v + eps, R, R0, tau) - O.ang_cdf(dim, v - eps, R, R0, tau)) / (2 * eps)
+        assert abs(fd - O.ang_density(dim, v, R, R0, tau)) < 1e-7
+    for U in (0.02, 0.4, 0.93):
+        assert abs(O.ang_cdf(dim, O.ang_sample(dim, U, R, R0, tau), R, R0, tau) - U) < 1e-12
