@@ -51,6 +51,8 @@ def parse(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--dt", type=float, default=1e-5)
     ap.add_argument("--n-each", type=int, default=100_000)
+    ap.add_argument("--step-launch", default="auto", choices=["auto", "fused", "separate"],
+                    help="one cooperative launch per step, one launch per kernel, or the autotuner's pick")
     ap.add_argument("--angle", default="free_step", choices=["free_step", "exact"],
                     help="direction of a resampled pair: the free step's (the step as specified) or "
                          "drawn from the full propagator (measured beside it in any case)")
@@ -179,8 +181,9 @@ def algorithmic_bytes(kernel, precision, w):
         # degrees cleared; per accepted pair or decay: record, state, 2x2 positions read, 2
         # positions + statuses written (conflict rounds add re-reads of the conflict pairs)
         "k_match_resolve": fired * 16 + (acc + dec) * (48 + 6 * v),
-        # one 160-B job per resolved pair or decay pair left to it; write two positions
-        "k_angles": (acc + dec) * (160 + 2 * v),
+        # one 160-B job per resolved pair or decay pair left to it; write two positions (only
+        # when directions come from the full propagator)
+        "k_angles": (acc + dec) * (160 + 2 * v) if w.get("angles") else 0,
         # read status, end position, id; write position + id (the scan stays on chip)
         "k_compact": n * (2 * v + 12),
     }
@@ -360,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
 
     system = workload(args, seed=1 + rank)
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    sim = pkg.Simulation(system, precision=args.precision, cell_factor="tune")
+    sim = pkg.Simulation(system, precision=args.precision, cell_factor="tune", step_launch=args.step_launch)
     layout = sim.info()
     sim.run(max(args.warmup, 3))
     sim.sync()
@@ -403,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
         per = max(steps_done, 1)
         work = {"n": n_now, "nb": int(np.sum(np.isin(st["species"], [0, 1]))), "cells": layout["cells"],
                 "fired": d_stats["fired"] / per, "accepted": d_stats["matched"] / per,
-                "decays": d_stats["decays"] / per}
+                "decays": d_stats["decays"] / per, "angles": args.angle == "exact"}
         cand_per_step = cand_local / per
         peak, peak_kind = measured_peaks()
         ab = algorithmic_bytes(dominant, args.precision, work)

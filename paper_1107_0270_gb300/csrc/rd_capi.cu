@@ -452,11 +452,19 @@ static cudaError_t build_tables(rd_handle* h, Alloc alloc) {
     if (e == cudaSuccess && c.pairs[k].bc != RD_BC_ABS)
       e = make(3, q.tab_inv, ninv, hinv, c.dim == 2 ? &q.tab_tail : nullptr);
     if (e == cudaSuccess && c.angle_mode == 0 && c.pairs[k].bc != RD_BC_ABS) {
-      // conditional angle law of the exact propagation: spacing s / 10 in R0 and R'; R0 up to the
-      // cut-off, R' up to 10 s beyond it (the radial law's tail at U = 2^-24 reaches about 8.2 s)
-      const double ha = 0.1 * q.s;
+      // conditional angle law of the exact propagation: spacing min(s, 1) / 10 in R0 and R' (the
+      // law varies on the scale s, and near contact on the contact radius); R0 up to the cut-off,
+      // R' up to 10 s beyond it (the radial law's tail at U = 2^-24 reaches about 8.2 s); at most
+      // 150 000 nodes
       const double a0max = std::sqrt(q.rcut2) / q.sigma - 1.0, a1max = a0max + 10.0 * q.s;
-      const int m0 = (int)std::ceil(a0max / ha) + 3, m1 = (int)std::ceil(a1max / ha) + 3;
+      double ha = 0.1 * std::min(q.s, 1.0);
+      int m0 = 0, m1 = 0;
+      for (;;) {
+        m0 = (int)std::ceil(a0max / ha) + 3;
+        m1 = (int)std::ceil(a1max / ha) + 3;
+        if ((int64_t)m0 * m1 <= 150000) break;
+        ha *= 1.25;
+      }
       float* t = (float*)alloc((size_t)m0 * m1 * kAngTabStride * sizeof(float));
       if (!t) return cudaErrorMemoryAllocation;
       launch_build_ang_table(h->L.P, c.dim, q.tau, ha, m0, m1, t, device_sms(), h->stream);
@@ -1050,20 +1058,6 @@ int rd_num_particles(rd_handle* h, int64_t* n) {
   return RD_OK;
 }
 
-// Device address of a page-locked host buffer (the kernels then read or write it directly over
-// the host link, without a staging copy); nullptr for pageable memory.  A null pointer counts as
-// page-locked (nothing to move).
-static void* pinned_device_ptr(const void* p, bool* ok) {
-  if (!p) return nullptr;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer) {
-    cudaGetLastError();
-    *ok = false;
-    return nullptr;
-  }
-  return a.devicePointer;
-}
-
 static bool ensure_staging(rd_handle* h) {
   if (h->st_x) return true;
   const int64_t cap = h->L.cap_particles;
@@ -1093,23 +1087,15 @@ int rd_get_state(rd_handle* h, int64_t* n_inout, double* x, int32_t* species, ui
   *n_inout = n;
   if (step) *step = ctl.step;
   if (n > 0 && (x || species || replica)) {
-    bool pinned = true;
-    double* dx = (double*)pinned_device_ptr(x, &pinned);
-    int32_t* dsp = (int32_t*)pinned_device_ptr(species, &pinned);
-    int32_t* drep = (int32_t*)pinned_device_ptr(replica, &pinned);
-    if (pinned) {
-      // page-locked caller buffers: the unpacking kernel writes them directly
-      launch_get_state(h->L, h->xbuf[h->cur], n, dx, dsp, drep, h->stream);
-      RD_CUDA(cudaGetLastError());
-    } else {
-      if (!ensure_staging(h)) return RD_ENOMEM;
-      launch_get_state(h->L, h->xbuf[h->cur], n, x ? h->st_x : nullptr, species ? h->st_sp : nullptr,
-                       replica ? h->st_rep : nullptr, h->stream);
-      RD_CUDA(cudaGetLastError());
-      if (x) RD_CUDA(cudaMemcpyAsync(x, h->st_x, (size_t)n * 24, cudaMemcpyDeviceToHost, h->stream));
-      if (species) RD_CUDA(cudaMemcpyAsync(species, h->st_sp, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
-      if (replica) RD_CUDA(cudaMemcpyAsync(replica, h->st_rep, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
-    }
+    // unpacked on the device, then one copy per array (page-locked caller buffers take the copy
+    // engines' direct path; a kernel writing host memory itself measured slower)
+    if (!ensure_staging(h)) return RD_ENOMEM;
+    launch_get_state(h->L, h->xbuf[h->cur], n, x ? h->st_x : nullptr, species ? h->st_sp : nullptr,
+                     replica ? h->st_rep : nullptr, h->stream);
+    RD_CUDA(cudaGetLastError());
+    if (x) RD_CUDA(cudaMemcpyAsync(x, h->st_x, (size_t)n * 24, cudaMemcpyDeviceToHost, h->stream));
+    if (species) RD_CUDA(cudaMemcpyAsync(species, h->st_sp, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (replica) RD_CUDA(cudaMemcpyAsync(replica, h->st_rep, (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
   }
   if (id && n > 0) RD_CUDA(cudaMemcpyAsync(id, h->idbuf[h->cur], (size_t)n * 4, cudaMemcpyDeviceToHost, h->stream));
   std::vector<RepDev> reps;
@@ -1130,24 +1116,18 @@ int rd_set_state(rd_handle* h, int64_t n, const double* x, const int32_t* specie
   const rd_config& c = h->cfg;
   if (!ensure_staging(h)) return RD_ENOMEM;
   cudaStream_t s = h->stream;
-  // raw inputs to the device (page-locked caller buffers are read there directly); validation and
-  // packing there, into the spare state buffer, so that a rejected state leaves the current one
-  // untouched
-  bool pinned = true;
-  const double* dx = (const double*)pinned_device_ptr(x, &pinned);
-  const int32_t* dsp = (const int32_t*)pinned_device_ptr(species, &pinned);
-  const uint32_t* did = (const uint32_t*)pinned_device_ptr(id, &pinned);
-  const int32_t* drep = (const int32_t*)pinned_device_ptr(replica, &pinned);
-  if (!pinned && n > 0) {
+  // raw inputs to the device, one copy per array; validation and packing there, into the spare
+  // state buffer, so that a rejected state leaves the current one untouched
+  if (n > 0) {
     RD_CUDA(cudaMemcpyAsync(h->st_x, x, (size_t)n * 24, cudaMemcpyHostToDevice, s));
     RD_CUDA(cudaMemcpyAsync(h->st_sp, species, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     RD_CUDA(cudaMemcpyAsync(h->st_id, id, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     if (replica) RD_CUDA(cudaMemcpyAsync(h->st_rep, replica, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    dx = h->st_x;
-    dsp = h->st_sp;
-    did = h->st_id;
-    drep = replica ? h->st_rep : nullptr;
   }
+  const double* dx = h->st_x;
+  const int32_t* dsp = h->st_sp;
+  const uint32_t* did = h->st_id;
+  const int32_t* drep = replica ? h->st_rep : nullptr;
   if (next_id) RD_CUDA(cudaMemcpyAsync(h->st_next, next_id, (size_t)c.n_replicas * 4, cudaMemcpyHostToDevice, s));
   RD_CUDA(cudaMemsetAsync(h->st_cnt, 0, (size_t)c.n_replicas * 4, s));
   RD_CUDA(cudaMemsetAsync(h->st_maxid, 0, (size_t)c.n_replicas * 4, s));

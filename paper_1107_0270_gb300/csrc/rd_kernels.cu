@@ -759,31 +759,45 @@ constexpr uint32_t kBarrierSpin = 1u << 22;
 // check_status: also report a status latched by any block (the matching rounds stop on it); the
 // fused step's barriers between phases report only their own timeout (a latched error still lets
 // the step reach its compaction, which then keeps the old state).
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrival counts with acquire-release semantics instead of full fences: the __syncthreads before
+// thread 0's arrival orders the block's writes before it, the release publishes them, the last
+// arrival acquires every other block's arrival and releases the new generation, and each waiter
+// acquires the generation before the closing __syncthreads hands the data to its block.  Waiters
+// poll without sleeping for the first polls (the common wait is a few hundred nanoseconds).
 __device__ __forceinline__ bool grid_barrier(DevCtl* ctl, bool check_status = true) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t* gen = &ctl->bar_gen;
-    const uint32_t g = *gen;
-    __threadfence();
+    const uint32_t g = ld_acquire_gpu(&ctl->bar_gen);
     int ok = 1;
-    if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
-      ctl->bar_count = 0u;
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&ctl->bar_count) : "memory");
+    if (old == gridDim.x - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&ctl->bar_count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_gen) : "memory");
     } else {
       uint32_t spins = 0;
       const uint32_t limit = ctl->spin_limit ? ctl->spin_limit : kBarrierSpin;
-      while (*gen == g) {
+      while (ld_acquire_gpu(&ctl->bar_gen) == g) {
         if (++spins > limit) {
           set_status(ctl, RD_ETIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (spins > 64) __nanosleep(64);
+        // a block that gave up at an earlier barrier never arrives: leave as soon as it is known
+        if ((spins & 1023u) == 0 && *(volatile int32_t*)&ctl->status == RD_ETIMEOUT) {
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();
     s_ok = ok && (!check_status || *(volatile int32_t*)&ctl->status == 0);
   }
   __syncthreads();
@@ -2731,46 +2745,27 @@ void launch_resample(const DevParams* P, int rule, const double* r0, const doubl
   k_resample<<<grid_for(n, 128, max_grid), 128, 0, s>>>(P, rule, r0, u, n, out);
 }
 
-// Angle table of one pair rule (mixed step): one warp per node (a, b >= 1) of the law at
-// R0 = 1 + (a - 1) h, R' = 1 + (b - 1) h, FP64; then the ghost row a = 0 and column b = 0 by linear
-// extrapolation.
+// Angle table of one pair rule (mixed step): one warp per node (a, b) of the law at
+// R0 = 1 + (a - 1) h, R' = 1 + (b - 1) h, FP64.  The ghost row and column (a = 0, b = 0: R0 or R'
+// = 1 - h) hold the law's own continuation below contact, which keeps the interpolation's first
+// interval as accurate as the others (a linear extrapolation there cost a factor ten).
 __global__ void __launch_bounds__(128) k_ang_table(const DevParams* __restrict__ Pp, int dim, double tau, double h,
                                                    int n0, int n1, float* __restrict__ out) {
   __shared__ double dn[4][32 * kAngBuildSlots];
   const int w = threadIdx.x >> 5;
-  const int64_t nodes = (int64_t)(n0 - 1) * (n1 - 1);
+  const int64_t nodes = (int64_t)n0 * n1;
   for (int64_t q = (int64_t)blockIdx.x * 4 + w; q < nodes; q += (int64_t)gridDim.x * 4) {
-    const int a = 1 + (int)(q / (n1 - 1)), b = 1 + (int)(q % (n1 - 1));
+    const int a = (int)(q / n1), b = (int)(q % n1);
     ang_table_node(dim, 1.0 + (b - 1) * h, 1.0 + (a - 1) * h, tau, Pp->gl16, dn[w],
                    out + ((size_t)a * n1 + b) * kAngTabStride);
   }
 }
 
-__global__ void k_ang_table_ghosts(int n0, int n1, int pass, float* __restrict__ out) {
-  constexpr int nu = kAngTabStride;
-  const int64_t m = pass == 0 ? (int64_t)(n1 - 1) * nu : (int64_t)n0 * nu;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % nu);
-    if (pass == 0) {
-      // row a = 0 (R0 = 1 - h) for b >= 1
-      const int b = 1 + (int)(i / nu);
-      out[(size_t)b * nu + k] = 2.0f * out[((size_t)n1 + b) * nu + k] - out[((size_t)2 * n1 + b) * nu + k];
-    } else {
-      // column b = 0 (R' = 1 - h) for every a
-      const int a = (int)(i / nu);
-      out[(size_t)a * n1 * nu + k] = 2.0f * out[((size_t)a * n1 + 1) * nu + k] - out[((size_t)a * n1 + 2) * nu + k];
-    }
-  }
-}
-
 void launch_build_ang_table(const DevParams* P, int dim, double tau, double h, int n0, int n1, float* out,
                             int device_sms, cudaStream_t s) {
-  const int64_t nodes = (int64_t)(n0 - 1) * (n1 - 1);
+  const int64_t nodes = (int64_t)n0 * n1;
   const int G = (int)std::min<int64_t>((nodes + 3) / 4, (int64_t)device_sms * 16);
   k_ang_table<<<G, 128, 0, s>>>(P, dim, tau, h, n0, n1, out);
-  constexpr int nu = kAngTabStride;
-  k_ang_table_ghosts<<<(int)(((int64_t)(n1 - 1) * nu + 255) / 256), 256, 0, s>>>(n0, n1, 0, out);
-  k_ang_table_ghosts<<<(int)(((int64_t)n0 * nu + 255) / 256), 256, 0, s>>>(n0, n1, 1, out);
 }
 
 }  // namespace rd

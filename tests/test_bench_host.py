@@ -20,7 +20,9 @@ def test_every_step_kernel_has_algorithmic_bytes():
     # one timer mark after each kernel of the step (a launch that picks between two kernel
     # variants still launches one)
     assert len(marks) == len(set(marks)) == bench.KERNELS_PER_STEP
-    w = {"n": 1000, "nb": 800, "cells": 500, "fired": 10, "accepted": 8, "decays": 2}
+    w = {"n": 1000, "nb": 800, "cells": 500, "fired": 10, "accepted": 8, "decays": 2, "angles": True}
     for k in marks:
         for prec in ("mixed", "fp64"):
             assert bench.algorithmic_bytes(k, prec, w) > 0
+    # the angle pass moves nothing when directions are the free step's (it is not launched then)
+    assert bench.algorithmic_bytes("k_angles", "mixed", {**w, "angles": False}) == 0
