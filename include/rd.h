@@ -120,11 +120,12 @@ typedef struct {
                                          Brownian / reaction step runs from there with the pair
                                          probabilities taken from the Brownian end points.  All zero: no
                                          drift step */
-  int32_t step_launch;                /* how a step is launched: 0 automatic (one fused cooperative
-                                         launch per graph of steps up to 2^22 particles of capacity,
-                                         separate kernels above; with the autotuner, the faster of
-                                         the two), 1 always fused, 2 always separate kernels.  Both
-                                         give bit-identical results; RD_EINVAL outside 0..2 */
+  int32_t step_launch;                /* how a step is launched: 0 automatic (separate kernels under
+                                         programmatic dependent launch; with the autotuner, and up
+                                         to 2^22 particles of capacity, the faster of those and one
+                                         fused cooperative launch), 1 always fused, 2 always
+                                         separate kernels.  Both give bit-identical results;
+                                         RD_EINVAL outside 0..2 */
   int32_t force_paths;                /* 0 normally.  Bit 0: conflict rounds on the whole cooperative
                                          grid for any number of conflict pairs (normally only above
                                          2048); bit 1: short conflict lists in global memory instead

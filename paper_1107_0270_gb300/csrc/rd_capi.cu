@@ -31,8 +31,8 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 constexpr int kHistoryLen = 1 << 16;   // steps kept by the per-step count history
-// automatic step launch: fused up to this particle capacity (at 2 resident blocks per SM the
-// fused launch has fewer warps per SM than the separate sweep, which matters only far above it)
+// the autotuner tries the fused launch up to this particle capacity (at 2 resident blocks per SM
+// the fused launch has fewer warps per SM than the separate sweep)
 constexpr int64_t kFusedMaxCapacity = (int64_t)1 << 22;
 
 struct rd_handle {
@@ -663,7 +663,10 @@ static cudaError_t autotune(rd_handle* h) {
     }
   }
   // one fused launch per step or one launch per kernel (bit-identical results either way)
-  if (h->cfg.step_launch == 0 && h->L.fused_grid >= 1 && !(h->cfg.angle_mode == 0 && h->cfg.precision == RD_FP64)) {
+  // (not with the FP64 step's exact angle pass, which can take far longer than a grid barrier
+  // waits: about a millisecond of FP64 work per pair)
+  if (h->cfg.step_launch == 0 && h->L.fused_grid >= 1 && h->L.cap_particles <= kFusedMaxCapacity &&
+      !(h->cfg.angle_mode == 0 && h->cfg.precision == RD_FP64)) {
     h->L.fused = !h->L.fused;
     const float ms = std::min(trial(), trial());
     if (ms < best)
@@ -797,10 +800,10 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   L.precision = c.precision;
   L.block = c.block_size > 0 ? c.block_size : 256;
   L.max_grid = device_sms() * 16;
-  // the FP64 step's exact angle pass can take far longer than a grid barrier waits (about a
-  // millisecond of FP64 work per pair), so automatically it runs as separate kernels
-  const bool long_phase = c.angle_mode == 0 && c.precision == RD_FP64;
-  L.fused = c.step_launch == 1 || (c.step_launch == 0 && cap <= kFusedMaxCapacity && !long_phase);
+  // automatic: separate kernels under programmatic dependent launch, which measured faster than
+  // the fused launch on every workload timed (a grid barrier costs more than a kernel boundary the
+  // next launch already overlaps); the autotuner tries the fused launch as well
+  L.fused = c.step_launch == 1;
   L.scan_items = 8;
   L.cap_particles = cap;
   L.cap_pairs = pair_cap;

@@ -473,80 +473,28 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
                                          int32_t* matched, const uint32_t cap_pairs,
                                          const uint32_t split, uint2 (*ranges)[256],
                                          const uint32_t bid, const uint32_t nblk) {
+  using V = typename V4<T>::type;
+  // per-warp queue of (particle, candidate) pairs that passed the cut-off test
+  __shared__ uint2 s_queue[8][64];
   const DevParams& P = *Pp;
   if (ctl->status) return;
   const uint32_t nb = cell_start[total_cells];
   const uint32_t step = ctl->step;
   const int dim = P.dim;
+  const int lane = threadIdx.x & 31;
+  uint2* queue = s_queue[threadIdx.x >> 5];
+  uint32_t qc = 0;   // entries in this warp's queue (the same in every lane)
   unsigned long long n_cand = 0, n_near = 0, n_overlap = 0;
-  // split = 1: one thread walks all rows of a particle; split = number of rows: one thread per
-  // (particle, row), more independent chains for small systems (the host keeps nb * split < 2^32)
-  const uint32_t work = kSplit ? nb * split : nb;
-  const uint32_t stride = nblk * blockDim.x;
-  const uint32_t n_iter = (work + stride - 1) / stride;
-  for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t t = it * stride + bid * blockDim.x + threadIdx.x;
-    if (t < work) {
-      const uint32_t k = kSplit ? t / split : t;
-      const int row_lo = kSplit ? (int)(t - k * split) : 0;
-      // rows of the half stencil: reach 1 (cell edge >= r_cut): 5 in 3D, 2 in 2D; reach 2 (2D only,
-      // cell edge >= r_cut / 2): rows y, y+1, y+2, each x-2 .. x+2 (own row x .. x+2)
-      constexpr int kRows = kReach == 2 ? 3 : kSweepRanges / 2;
-      const int row_hi = kSplit ? row_lo + 1 : kRows;
-      const auto a0 = sx0[k];
-      const auto a1 = sx1[k];
-      const uint32_t wa = w_bits(a0.w);
-      const uint32_t spa = wa & 0xFFu, r = wa >> 8;
-      const uint32_t ida = w_bits(a1.w);
-      const RepDev& rep = reps[r];
-      int cx, cy, cz = 0;
-      if constexpr (sizeof(T) == 8) {
-        cx = cell_coord(a0.x, rep.inv_edge[0], rep.nc[0]);
-        cy = cell_coord(a0.y, rep.inv_edge[1], rep.nc[1]);
-        if (dim == 3) cz = cell_coord(a0.z, rep.inv_edge[2], rep.nc[2]);
-      } else {
-        cx = cell_coord_f(a0.x, rep.inv_edge_f[0], rep.nc[0]);
-        cy = cell_coord_f(a0.y, rep.inv_edge_f[1], rep.nc[1]);
-        if (dim == 3) cz = cell_coord_f(a0.z, rep.inv_edge_f[2], rep.nc[2]);
-      }
-      const int nc0 = rep.nc[0];
-      // the grid has 1 or >= 2 kReach + 1 cells along each axis; with 1 only the own cell counts
-      constexpr int kMinCells = 2 * kReach + 1;
-      const bool ox = nc0 >= kMinCells, oy = rep.nc[1] >= kMinCells, oz = dim == 3 && rep.nc[2] >= kMinCells;
-      // all row ranges first (independent loads in flight together), the non-empty ones kept in
-      // order, then one flattened walk over them
-      int nr = 0;
-#pragma unroll
-      for (int row = 0; row < kRows; ++row) {
-        const int dy = kReach == 2 ? row : (row == 0 ? 0 : (row == 1 ? 1 : row - 3));
-        const int dz = (kReach == 2 || row < 2) ? 0 : 1;
-        if (row >= row_lo && row < row_hi && (dy == 0 || oy) && (dz == 0 || oz)) {
-          int yy = cy + dy, zz = cz + dz;
-          yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
-          zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
-          const int64_t rowc = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * nc0;
-          const int xl = (row == 0 || !ox) ? cx : max(cx - kReach, 0);
-          const int xh = ox ? min(cx + kReach, nc0 - 1) : cx;
-          const uint2 main_rg = make_uint2(row == 0 ? k + 1 : cell_start[rowc + xl], cell_start[rowc + xh + 1]);
-          uint2 wrap_rg = make_uint2(0u, 0u);
-          if (ox && row != 0 && cx - kReach < 0)          // cells nc0 + cx - kReach .. nc0 - 1
-            wrap_rg = make_uint2(cell_start[rowc + nc0 + cx - kReach], cell_start[rowc + nc0]);
-          else if (ox && cx + kReach >= nc0)               // cells 0 .. cx + kReach - nc0
-            wrap_rg = make_uint2(cell_start[rowc], cell_start[rowc + cx + kReach - nc0 + 1]);
-          if (main_rg.y > main_rg.x) ranges[nr++][threadIdx.x] = main_rg;
-          if (wrap_rg.y > wrap_rg.x) ranges[nr++][threadIdx.x] = wrap_rg;
-        }
-      }
-      int rr = 0;
-      uint2 rg = nr > 0 ? ranges[0][threadIdx.x] : make_uint2(0u, 0u);
-      uint32_t j = rg.x;
-      while (rr < nr) {
-        const uint32_t jj = j++;
-        if (j >= rg.y && ++rr < nr) {
-          rg = ranges[rr][threadIdx.x];
-          j = rg.x;
-        }
-        const auto b0 = sx0[jj];
+
+  // One candidate pair (k, jj) within the cut-off: p_enc, the encounter draw, the append.
+  auto process = [&](const uint32_t k, const uint32_t jj) {
+    const auto a0 = sx0[k];
+    const auto a1 = sx1[k];
+    const uint32_t wa = w_bits(a0.w);
+    const uint32_t spa = wa & 0xFFu, r = wa >> 8;
+    const uint32_t ida = w_bits(a1.w);
+    const RepDev& rep = reps[r];
+    const auto b0 = sx0[jj];
         // start-of-step separation first (the norm does not depend on the pair's orientation),
         // against the largest cut-off; the species pair and its own cut-off after that
         double p, r02;
@@ -556,22 +504,22 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
           const double r0y = min_image(b0.y - a0.y, rep.L, rep.half_L);
           const double r0z = dim == 3 ? min_image(b0.z - a0.z, rep.L, rep.half_L) : 0.0;
           r02 = norm2_rn(r0x, r0y, r0z, dim);
-          if (!(r02 < P.rcut2_max)) continue;
+          if (!(r02 < P.rcut2_max)) return;
         } else {
           const float r0x = min_image_f(b0.x - a0.x, rep.Lf, rep.half_Lf);
           const float r0y = min_image_f(b0.y - a0.y, rep.Lf, rep.half_Lf);
           const float r0z = dim == 3 ? min_image_f(b0.z - a0.z, rep.Lf, rep.half_Lf) : 0.0f;
           r02f = r0x * r0x + r0y * r0y + r0z * r0z;
-          if (!(r02f < P.rcut2_max_f)) continue;
+          if (!(r02f < P.rcut2_max_f)) return;
         }
         const uint32_t spb = w_bits(b0.w) & 0xFFu;
         const int rule = P.pair_of[spa][spb];
-        if (rule < 0) continue;
+        if (rule < 0) return;
         const PairDev& pr = P.pairs[rule];
         if constexpr (sizeof(T) == 8) {
-          if (!(r02 < pr.rcut2)) continue;
+          if (!(r02 < pr.rcut2)) return;
         } else {
-          if (!(r02f < pr.rcut2_f)) continue;
+          if (!(r02f < pr.rcut2_f)) return;
         }
         const auto b1 = sx1[jj];
         const uint32_t idb = w_bits(b1.w);
@@ -609,7 +557,7 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
         // mixed step: FP32 draw and comparison; the smallest FP32 uniform is 2^-24, so a smaller
         // p_enc cannot fire and needs no draw
         if constexpr (sizeof(T) == 4) {
-          if (!(pf > 0x1p-24f)) continue;
+          if (!(pf > 0x1p-24f)) return;
         }
         const uint4 w = draw(P, step, id_lo, id_hi, TAG_ENC, r);
         bool fires;
@@ -650,8 +598,137 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
             set_status(ctl, RD_ECAPACITY);
           }
         }
+  };
+
+  // Walks one particle's candidates and queues those within the cut-off; whenever the warp's
+  // queue holds 32 pairs, all lanes process one each.  (Examining a candidate is cheap, processing
+  // one is not: processed where it is found, the expensive part would run once per loop iteration
+  // in which any lane found one.)
+  // split = 1: one thread walks all rows of a particle; split = number of rows: one thread per
+  // (particle, row), more independent chains for small systems (the host keeps nb * split < 2^32)
+  const uint32_t work = kSplit ? nb * split : nb;
+  const uint32_t stride = nblk * blockDim.x;
+  const uint32_t n_iter = (work + stride - 1) / stride;
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t t = it * stride + bid * blockDim.x + threadIdx.x;
+    int nr = 0;
+    uint32_t k = 0;
+    V a0{};
+    float4 cut{};   // (L, half L, largest squared cut-off) of the particle's replica, FP32 step
+    double Ld = 0.0, hLd = 0.0;
+    uint32_t spa = 0;
+    if (t < work) {
+      k = kSplit ? t / split : t;
+      const int row_lo = kSplit ? (int)(t - k * split) : 0;
+      // rows of the half stencil: reach 1 (cell edge >= r_cut): 5 in 3D, 2 in 2D; reach 2 (2D only,
+      // cell edge >= r_cut / 2): rows y, y+1, y+2, each x-2 .. x+2 (own row x .. x+2)
+      constexpr int kRows = kReach == 2 ? 3 : kSweepRanges / 2;
+      const int row_hi = kSplit ? row_lo + 1 : kRows;
+      a0 = sx0[k];
+      const uint32_t wa = w_bits(a0.w);
+      spa = wa & 0xFFu;
+      const uint32_t r = wa >> 8;
+      const RepDev& rep = reps[r];
+      int cx, cy, cz = 0;
+      if constexpr (sizeof(T) == 8) {
+        cx = cell_coord(a0.x, rep.inv_edge[0], rep.nc[0]);
+        cy = cell_coord(a0.y, rep.inv_edge[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord(a0.z, rep.inv_edge[2], rep.nc[2]);
+      } else {
+        cx = cell_coord_f(a0.x, rep.inv_edge_f[0], rep.nc[0]);
+        cy = cell_coord_f(a0.y, rep.inv_edge_f[1], rep.nc[1]);
+        if (dim == 3) cz = cell_coord_f(a0.z, rep.inv_edge_f[2], rep.nc[2]);
+      }
+      const int nc0 = rep.nc[0];
+      // the grid has 1 or >= 2 kReach + 1 cells along each axis; with 1 only the own cell counts
+      constexpr int kMinCells = 2 * kReach + 1;
+      const bool ox = nc0 >= kMinCells, oy = rep.nc[1] >= kMinCells, oz = dim == 3 && rep.nc[2] >= kMinCells;
+      // all row ranges first (independent loads in flight together), the non-empty ones kept in
+      // order, then one flattened walk over them
+#pragma unroll
+      for (int row = 0; row < kRows; ++row) {
+        const int dy = kReach == 2 ? row : (row == 0 ? 0 : (row == 1 ? 1 : row - 3));
+        const int dz = (kReach == 2 || row < 2) ? 0 : 1;
+        if (row >= row_lo && row < row_hi && (dy == 0 || oy) && (dz == 0 || oz)) {
+          int yy = cy + dy, zz = cz + dz;
+          yy = yy < 0 ? yy + rep.nc[1] : (yy >= rep.nc[1] ? yy - rep.nc[1] : yy);
+          zz = zz >= rep.nc[2] ? zz - rep.nc[2] : zz;
+          const int64_t rowc = rep.cell_base + ((int64_t)zz * rep.nc[1] + yy) * nc0;
+          const int xl = (row == 0 || !ox) ? cx : max(cx - kReach, 0);
+          const int xh = ox ? min(cx + kReach, nc0 - 1) : cx;
+          const uint2 main_rg = make_uint2(row == 0 ? k + 1 : cell_start[rowc + xl], cell_start[rowc + xh + 1]);
+          uint2 wrap_rg = make_uint2(0u, 0u);
+          if (ox && row != 0 && cx - kReach < 0)          // cells nc0 + cx - kReach .. nc0 - 1
+            wrap_rg = make_uint2(cell_start[rowc + nc0 + cx - kReach], cell_start[rowc + nc0]);
+          else if (ox && cx + kReach >= nc0)               // cells 0 .. cx + kReach - nc0
+            wrap_rg = make_uint2(cell_start[rowc], cell_start[rowc + cx + kReach - nc0 + 1]);
+          if (main_rg.y > main_rg.x) ranges[nr++][threadIdx.x] = main_rg;
+          if (wrap_rg.y > wrap_rg.x) ranges[nr++][threadIdx.x] = wrap_rg;
+        }
+      }
+      Ld = rep.L;
+      hLd = rep.half_L;
+      cut = make_float4(rep.Lf, rep.half_Lf, 0.0f, 0.0f);
+    }
+    int rr = 0;
+    uint2 rg = nr > 0 ? ranges[0][threadIdx.x] : make_uint2(0u, 0u);
+    uint32_t j = rg.x;
+    for (;;) {
+      const bool more = rr < nr;
+      if (!__any_sync(0xFFFFFFFFu, more)) break;
+      bool push = false;
+      uint32_t jj = 0;
+      if (more) {
+        jj = j++;
+        if (j >= rg.y && ++rr < nr) {
+          rg = ranges[rr][threadIdx.x];
+          j = rg.x;
+        }
+        // the cut-off tests of process(), which repeats them
+        const auto b0 = sx0[jj];
+        bool in;
+        if constexpr (sizeof(T) == 8) {
+          const double r0x = min_image(b0.x - a0.x, Ld, hLd);
+          const double r0y = min_image(b0.y - a0.y, Ld, hLd);
+          const double r0z = dim == 3 ? min_image(b0.z - a0.z, Ld, hLd) : 0.0;
+          const double r02 = norm2_rn(r0x, r0y, r0z, dim);
+          in = r02 < P.rcut2_max;
+          if (in) {
+            const int rule = P.pair_of[spa][w_bits(b0.w) & 0xFFu];
+            in = rule >= 0 && r02 < P.pairs[rule].rcut2;
+          }
+        } else {
+          const float r0x = min_image_f(b0.x - a0.x, cut.x, cut.y);
+          const float r0y = min_image_f(b0.y - a0.y, cut.x, cut.y);
+          const float r0z = dim == 3 ? min_image_f(b0.z - a0.z, cut.x, cut.y) : 0.0f;
+          const float r02f = r0x * r0x + r0y * r0y + r0z * r0z;
+          in = r02f < P.rcut2_max_f;
+          if (in) {
+            const int rule = P.pair_of[spa][w_bits(b0.w) & 0xFFu];
+            in = rule >= 0 && r02f < P.pairs[rule].rcut2_f;
+          }
+        }
+        push = in;
+      }
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, push);
+      if (push) queue[qc + __popc(bal & ((1u << lane) - 1u))] = make_uint2(k, jj);
+      qc += __popc(bal);
+      __syncwarp();
+      if (qc >= 32) {
+        const uint2 e = queue[lane];
+        __syncwarp();
+        if (lane + 32 < (int)qc) queue[lane] = queue[lane + 32];
+        qc -= 32;
+        __syncwarp();
+        process(e.x, e.y);
       }
     }
+  }
+  // the rest of the queue
+  __syncwarp();
+  if (lane < (int)qc) {
+    const uint2 e = queue[lane];
+    process(e.x, e.y);
   }
   warp_sum_add(&ctl->stats[RD_STAT_CANDIDATES], n_cand);
   warp_sum_add(&ctl->stats[RD_STAT_NEAR_THRESHOLD], n_near);
