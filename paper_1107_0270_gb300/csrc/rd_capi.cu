@@ -828,8 +828,9 @@ int rd_init(const rd_config* cfg, void* stream, rd_handle** out) {
   h->idbuf[0] = (uint32_t*)A(cap * 4);
   h->idbuf[1] = (uint32_t*)A(cap * 4);
   L.x1 = A(cap * vs);
-  L.sx0 = A(cap * vs);
-  L.sx1 = A(cap * vs);
+  // sorted start and end positions interleaved: record k's pair fills one 32-byte sector (mixed)
+  L.sx0 = A(2 * cap * vs);
+  L.sx1 = L.sx0 ? (void*)((char*)L.sx0 + vs) : nullptr;
   L.prodpos = A(2 * cap * vs);
   L.status = (uint32_t*)A(cap * 4);
   L.matched = (int32_t*)A(cap * 4);
@@ -1527,8 +1528,8 @@ extern "C" int rd_step_static(const rd_config* cfg, void* stream, int64_t n, con
   uint32_t* id0 = (uint32_t*)b.take(cap * 4);
   uint32_t* id1 = (uint32_t*)b.take(cap * 4);
   L.x1 = b.take(cap * vs);
-  L.sx0 = b.take(cap * vs);
-  L.sx1 = b.take(cap * vs);
+  L.sx0 = b.take(2 * cap * vs);
+  L.sx1 = (void*)((char*)L.sx0 + vs);
   L.prodpos = b.take(2 * cap * vs);
   L.status = (uint32_t*)b.take(cap * 4);
   L.matched = (int32_t*)b.take(cap * 4);

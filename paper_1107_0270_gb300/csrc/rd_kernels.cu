@@ -22,6 +22,18 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 
+// Acquire load / release store of a 32-bit flag at GPU scope (the look-back's and the grid
+// barrier's publication protocol: data written before a release store is visible to whoever
+// acquires the flag value it stored).
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <class T> struct V4;
 template <> struct V4<double> { using type = d4; };
 template <> struct V4<float> { using type = float4; };
@@ -294,15 +306,15 @@ __device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch,
   if (tile > 0) {
     if (lane == 0) {
       agg[tile] = tot;
-      __threadfence();
-      atomicExch(&flag[tile], (epoch << 2) | 1u);
+      st_release_gpu(&flag[tile], (epoch << 2) | 1u);
     }
     int64_t top = (int64_t)tile - 1;
     uint32_t spins = 0;
     const uint32_t limit = ctl->spin_limit ? ctl->spin_limit : kSpinLimit;
     for (;;) {
       const int64_t q = top - lane;
-      const uint32_t f = q >= 0 ? *(volatile uint32_t*)&flag[q] : ((epoch << 2) | 2u);
+      // acquire: a flag seen set makes the value published before it visible
+      const uint32_t f = q >= 0 ? ld_acquire_gpu(&flag[q]) : ((epoch << 2) | 2u);
       const bool ready = (f >> 2) == epoch && (f & 3u) != 0u;
       if (!__all_sync(0xFFFFFFFFu, ready)) {
         if (++spins > limit) {
@@ -311,7 +323,6 @@ __device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch,
         }
         continue;
       }
-      __threadfence();
       const unsigned incl_mask = __ballot_sync(0xFFFFFFFFu, q >= 0 && (f & 3u) == 2u);
       const int stop = incl_mask ? __ffs(incl_mask) - 1 : 32;   // nearest inclusive predecessor
       U vv = 0;
@@ -325,8 +336,7 @@ __device__ __forceinline__ U tile_lookback(U tot, uint32_t tile, uint32_t epoch,
   }
   if (lane == 0) {
     incl[tile] = prefix + tot;
-    __threadfence();
-    atomicExch(&flag[tile], (epoch << 2) | 2u);
+    st_release_gpu(&flag[tile], (epoch << 2) | 2u);
   }
   return prefix;
 }
@@ -428,13 +438,13 @@ __device__ __forceinline__ void ph_scatter(const DevCtl* ctl, const typename V4<
     const uint32_t c = cell_of[i];
     if (c == kNoCell) continue;
     const uint32_t k = cell_start[c] + slot[i];
-    sx0[k] = x0[i];
+    sx0[2 * (size_t)k] = x0[i];
     auto q = x1[i];
     if constexpr (sizeof(T) == 8)
       q.w = w_from_bits_d(id[i]);
     else
       q.w = w_from_bits_f(id[i]);
-    sx1[k] = q;
+    sx1[2 * (size_t)k] = q;
     sidx[k] = i;
   }
 }
@@ -488,13 +498,13 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
 
   // One candidate pair (k, jj) within the cut-off: p_enc, the encounter draw, the append.
   auto process = [&](const uint32_t k, const uint32_t jj) {
-    const auto a0 = sx0[k];
-    const auto a1 = sx1[k];
+    const auto a0 = sx0[2 * (size_t)k];
+    const auto a1 = sx1[2 * (size_t)k];
     const uint32_t wa = w_bits(a0.w);
     const uint32_t spa = wa & 0xFFu, r = wa >> 8;
     const uint32_t ida = w_bits(a1.w);
     const RepDev& rep = reps[r];
-    const auto b0 = sx0[jj];
+    const auto b0 = sx0[2 * (size_t)jj];
         // start-of-step separation first (the norm does not depend on the pair's orientation),
         // against the largest cut-off; the species pair and its own cut-off after that
         double p, r02;
@@ -521,7 +531,7 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
         } else {
           if (!(r02f < pr.rcut2_f)) return;
         }
-        const auto b1 = sx1[jj];
+        const auto b1 = sx1[2 * (size_t)jj];
         const uint32_t idb = w_bits(b1.w);
         // orient the pair from the lower id to the higher id
         const bool swap = idb < ida;
@@ -624,7 +634,7 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
       // cell edge >= r_cut / 2): rows y, y+1, y+2, each x-2 .. x+2 (own row x .. x+2)
       constexpr int kRows = kReach == 2 ? 3 : kSweepRanges / 2;
       const int row_hi = kSplit ? row_lo + 1 : kRows;
-      a0 = sx0[k];
+      a0 = sx0[2 * (size_t)k];
       const uint32_t wa = w_bits(a0.w);
       spa = wa & 0xFFu;
       const uint32_t r = wa >> 8;
@@ -685,7 +695,7 @@ __device__ __forceinline__ void ph_sweep(const DevParams* Pp, DevCtl* ctl,
           j = rg.x;
         }
         // the cut-off tests of process(), which repeats them
-        const auto b0 = sx0[jj];
+        const auto b0 = sx0[2 * (size_t)jj];
         bool in;
         if constexpr (sizeof(T) == 8) {
           const double r0x = min_image(b0.x - a0.x, Ld, hLd);
@@ -836,12 +846,6 @@ constexpr uint32_t kBarrierSpin = 1u << 22;
 // check_status: also report a status latched by any block (the matching rounds stop on it); the
 // fused step's barriers between phases report only their own timeout (a latched error still lets
 // the step reach its compaction, which then keeps the old state).
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Arrival counts with acquire-release semantics instead of full fences: the __syncthreads before
 // thread 0's arrival orders the block's writes before it, the release publishes them, the last
 // arrival acquires every other block's arrival and releases the new generation, and each waiter

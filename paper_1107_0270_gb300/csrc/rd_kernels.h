@@ -41,8 +41,8 @@ struct StepLaunch {
   uint32_t* id_cur;
   uint32_t* id_next;
   void* x1;
-  void* sx0;
-  void* sx1;
+  void* sx0;                 // cell-ordered start / end positions, interleaved: record k at sx0[2k],
+  void* sx1;                 // sx1[2k] (sx1 = sx0 + one record)
   void* prodpos;
   uint32_t* status;
   int32_t* matched;
