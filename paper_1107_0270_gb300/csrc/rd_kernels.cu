@@ -2182,38 +2182,76 @@ __global__ void k_count(const DevParams* __restrict__ Pp, const DevCtl* __restri
 }
 
 // Standalone per-pair probabilities (rd_pair_probs).
+// p_enc and p_reac of one pair at start / end separations a, b (um).
+__device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev& pr, double a, double b, double& pe,
+                                               double& prc, bool want_enc, bool want_reac) {
+  // mixed: the separations rounded once to FP32 and scaled there (FP64 arithmetic runs at 1/64 of
+  // the FP32 rate on this part)
+  const float d0 = fmaf((float)a, pr.inv_sigma_f, -1.0f), d = fmaf((float)b, pr.inv_sigma_f, -1.0f);
+  if (want_enc) {
+    if (P.precision == RD_MIXED) {
+      float pf;
+      if (P.dim == 3) {
+        pf = p_enc3_f(d, d0, pr.inv_tau_f);
+      } else if (d <= 0.0f || d0 <= 0.0f) {
+        pf = 1.0f;
+      } else {
+        const float xx = d * d0 * pr.inv_tau_f;
+        pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
+      }
+      pe = (double)pf;
+    } else {
+      pe = p_enc_dim(P, pr, b / pr.sigma, a / pr.sigma);
+    }
+  }
+  if (want_reac) {
+    double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
+    if (pr.bc == RD_BC_RAD)
+      v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
+    prc = v;
+  }
+}
+
+// Standalone pair probabilities (streaming).  With 16-byte aligned arrays each thread takes four
+// consecutive pairs per pass through 16-byte loads and stores (more bytes in flight per thread);
+// the remainder, or unaligned arrays, one pair per thread.
 __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const double* __restrict__ r0,
                              const double* __restrict__ r, int64_t n, double* __restrict__ p_enc,
                              double* __restrict__ p_reac) {
   const DevParams& P = *Pp;
   const PairDev& pr = P.pairs[rule];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const double a = r0[k], b = r[k];
-    // mixed: the separations rounded once to FP32 and scaled there (FP64 arithmetic runs at 1/64 of
-    // the FP32 rate on this part)
-    const float d0 = fmaf((float)a, pr.inv_sigma_f, -1.0f), d = fmaf((float)b, pr.inv_sigma_f, -1.0f);
-    if (p_enc) {
-      if (P.precision == RD_MIXED) {
-        float pf;
-        if (P.dim == 3) {
-          pf = p_enc3_f(d, d0, pr.inv_tau_f);
-        } else if (d <= 0.0f || d0 <= 0.0f) {
-          pf = 1.0f;
-        } else {
-          const float xx = d * d0 * pr.inv_tau_f;
-          pf = xx > 60.0f ? 0.0f : fminf(1.0f, fmaxf(0.0f, tab_eval(pr.tab_penc, d0, d) * expf(-xx)));
-        }
-        p_enc[k] = (double)pf;
-      } else {
-        p_enc[k] = p_enc_dim(P, pr, b / pr.sigma, a / pr.sigma);
+  const bool we = p_enc != nullptr, wr = p_reac != nullptr;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = (((uintptr_t)r0 | (uintptr_t)r | (uintptr_t)p_enc | (uintptr_t)p_reac) & 15u) == 0;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    for (int64_t q = tid; q < n4; q += stride) {
+      const double2 a01 = __ldcs(reinterpret_cast<const double2*>(r0) + 2 * q);
+      const double2 a23 = __ldcs(reinterpret_cast<const double2*>(r0) + 2 * q + 1);
+      const double2 b01 = __ldcs(reinterpret_cast<const double2*>(r) + 2 * q);
+      const double2 b23 = __ldcs(reinterpret_cast<const double2*>(r) + 2 * q + 1);
+      double e[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+      pair_probs_one(P, pr, a01.x, b01.x, e[0], c[0], we, wr);
+      pair_probs_one(P, pr, a01.y, b01.y, e[1], c[1], we, wr);
+      pair_probs_one(P, pr, a23.x, b23.x, e[2], c[2], we, wr);
+      pair_probs_one(P, pr, a23.y, b23.y, e[3], c[3], we, wr);
+      if (we) {
+        __stcs(reinterpret_cast<double2*>(p_enc) + 2 * q, make_double2(e[0], e[1]));
+        __stcs(reinterpret_cast<double2*>(p_enc) + 2 * q + 1, make_double2(e[2], e[3]));
+      }
+      if (wr) {
+        __stcs(reinterpret_cast<double2*>(p_reac) + 2 * q, make_double2(c[0], c[1]));
+        __stcs(reinterpret_cast<double2*>(p_reac) + 2 * q + 1, make_double2(c[2], c[3]));
       }
     }
-    if (p_reac) {
-      double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
-      if (pr.bc == RD_BC_RAD)
-        v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
-      p_reac[k] = v;
-    }
+    done = 4 * n4;
+  }
+  for (int64_t k = done + tid; k < n; k += stride) {
+    double e = 0.0, c = 0.0;
+    pair_probs_one(P, pr, r0[k], r[k], e, c, we, wr);
+    if (we) p_enc[k] = e;
+    if (wr) p_reac[k] = c;
   }
 }
 
