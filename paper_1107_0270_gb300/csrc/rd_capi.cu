@@ -1156,7 +1156,8 @@ int rd_pair_probs(rd_handle* h, int32_t rule, const double* r0, const double* r,
   if (!h || rule < 0 || rule >= h->cfg.n_pairs || n < 0 || (n > 0 && (!r0 || !r))) return RD_EINVAL;
   if (h->cfg.pairs[rule].bc == RD_BC_NONE) return RD_EINVAL;
   if (n == 0) return RD_OK;
-  launch_pair_probs(h->L.P, rule, r0, r, n, p_enc, p_reac, h->L.max_grid, h->stream);
+  launch_pair_probs(h->L.P, rule, r0, r, n, p_enc, p_reac, h->L.max_grid,
+                    h->cfg.precision == RD_MIXED && h->cfg.dim == 3, h->stream);
   RD_CUDA(cudaGetLastError());
   return RD_OK;
 }

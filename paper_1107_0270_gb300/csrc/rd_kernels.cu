@@ -2182,14 +2182,18 @@ __global__ void k_count(const DevParams* __restrict__ Pp, const DevCtl* __restri
 }
 
 // Standalone per-pair probabilities (rd_pair_probs).
-// p_enc and p_reac of one pair at start / end separations a, b (um).
+// p_enc and p_reac of one pair at start / end separations a, b (um); kMixed3D: the mixed step in
+// 3D (no FP64 or 2D branch compiled, which keeps the streaming kernel's register count low).
+template <bool kMixed3D>
 __device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev& pr, double a, double b, double& pe,
                                                double& prc, bool want_enc, bool want_reac) {
   // mixed: the separations rounded once to FP32 and scaled there (FP64 arithmetic runs at 1/64 of
   // the FP32 rate on this part)
   const float d0 = fmaf((float)a, pr.inv_sigma_f, -1.0f), d = fmaf((float)b, pr.inv_sigma_f, -1.0f);
   if (want_enc) {
-    if (P.precision == RD_MIXED) {
+    if (kMixed3D) {
+      pe = (double)p_enc3_f(d, d0, pr.inv_tau_f);
+    } else if (P.precision == RD_MIXED) {
       float pf;
       if (P.dim == 3) {
         pf = p_enc3_f(d, d0, pr.inv_tau_f);
@@ -2206,8 +2210,12 @@ __device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev
   }
   if (want_reac) {
     double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
-    if (pr.bc == RD_BC_RAD)
-      v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
+    if (pr.bc == RD_BC_RAD) {
+      if (kMixed3D)
+        v = (double)p_reac_tab(pr, d, d0);
+      else
+        v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
+    }
     prc = v;
   }
 }
@@ -2215,6 +2223,7 @@ __device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev
 // Standalone pair probabilities (streaming).  With 16-byte aligned arrays each thread takes four
 // consecutive pairs per pass through 16-byte loads and stores (more bytes in flight per thread);
 // the remainder, or unaligned arrays, one pair per thread.
+template <bool kMixed3D>
 __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const double* __restrict__ r0,
                              const double* __restrict__ r, int64_t n, double* __restrict__ p_enc,
                              double* __restrict__ p_reac) {
@@ -2232,10 +2241,10 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
       const double2 b01 = __ldcs(reinterpret_cast<const double2*>(r) + 2 * q);
       const double2 b23 = __ldcs(reinterpret_cast<const double2*>(r) + 2 * q + 1);
       double e[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
-      pair_probs_one(P, pr, a01.x, b01.x, e[0], c[0], we, wr);
-      pair_probs_one(P, pr, a01.y, b01.y, e[1], c[1], we, wr);
-      pair_probs_one(P, pr, a23.x, b23.x, e[2], c[2], we, wr);
-      pair_probs_one(P, pr, a23.y, b23.y, e[3], c[3], we, wr);
+      pair_probs_one<kMixed3D>(P, pr, a01.x, b01.x, e[0], c[0], we, wr);
+      pair_probs_one<kMixed3D>(P, pr, a01.y, b01.y, e[1], c[1], we, wr);
+      pair_probs_one<kMixed3D>(P, pr, a23.x, b23.x, e[2], c[2], we, wr);
+      pair_probs_one<kMixed3D>(P, pr, a23.y, b23.y, e[3], c[3], we, wr);
       if (we) {
         __stcs(reinterpret_cast<double2*>(p_enc) + 2 * q, make_double2(e[0], e[1]));
         __stcs(reinterpret_cast<double2*>(p_enc) + 2 * q + 1, make_double2(e[2], e[3]));
@@ -2249,7 +2258,7 @@ __global__ void k_pair_probs(const DevParams* __restrict__ Pp, int rule, const d
   }
   for (int64_t k = done + tid; k < n; k += stride) {
     double e = 0.0, c = 0.0;
-    pair_probs_one(P, pr, r0[k], r[k], e, c, we, wr);
+    pair_probs_one<kMixed3D>(P, pr, r0[k], r[k], e, c, we, wr);
     if (we) p_enc[k] = e;
     if (wr) p_reac[k] = c;
   }
@@ -2850,8 +2859,11 @@ void launch_count(const StepLaunch& L, cudaStream_t s) {
 }
 
 void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,
-                       double* pr, int max_grid, cudaStream_t s) {
-  k_pair_probs<<<grid_for(n, 256, max_grid), 256, 0, s>>>(P, rule, r0, r, n, pe, pr);
+                       double* pr, int max_grid, bool mixed3d, cudaStream_t s) {
+  if (mixed3d)
+    k_pair_probs<true><<<grid_for(n, 256, max_grid), 256, 0, s>>>(P, rule, r0, r, n, pe, pr);
+  else
+    k_pair_probs<false><<<grid_for(n, 256, max_grid), 256, 0, s>>>(P, rule, r0, r, n, pe, pr);
 }
 
 void launch_propagate(const DevParams* P, int rule, const double* r0, const double* u, int64_t n, double* out,

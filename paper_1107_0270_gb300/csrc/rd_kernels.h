@@ -119,7 +119,7 @@ void launch_init_positions(const StepLaunch& L, const int32_t* rep_of, const int
                            uint32_t n, cudaStream_t s);
 void launch_count(const StepLaunch& L, cudaStream_t s);
 void launch_pair_probs(const DevParams* P, int rule, const double* r0, const double* r, int64_t n, double* pe,
-                       double* pr, int max_grid, cudaStream_t s);
+                       double* pr, int max_grid, bool mixed3d, cudaStream_t s);
 // kind 3 with fwd != nullptr: the 2D inverse table from the forward -ln(tail) table fwd
 void launch_build_table(const DevParams* P, int rule, int kind, float* out, float4* quad, int n0, int n1, double h,
                         double h1, double* tot, const Tab2* fwd, int device_sms, cudaStream_t s);
