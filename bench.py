@@ -32,13 +32,12 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-KERNELS_PER_STEP = 8           # kernels of one step with separate launches: prepare, scan (cells),
-                               # scatter, sweep, trivial matching, matching rounds + resolution,
-                               # angle pass (exact directions), compaction (scan + placement)
-# the fused launch runs the same seven stages as phases of one cooperative kernel
+KERNELS_PER_STEP = 7           # kernels of one step with separate launches: prepare, scan (cells),
+                               # scatter, sweep, matching (trivial pairs, rounds, resolution), angle
+                               # pass (exact directions only), compaction (scan + placement)
+# the fused launch runs the same stages as phases of one cooperative kernel (the matching as two)
 KERNEL_OF_PHASE = {"ph_prepare": "k_prepare", "ph_scan_cells": "k_scan_cells", "ph_scatter_cells": "k_scatter_cells",
-                   "ph_sweep": "k_sweep", "ph_match_trivial": "k_match_trivial",
-                   "ph_match_resolve": "k_match_resolve", "ph_angles": "k_angles", "ph_compact": "k_compact"}
+                   "ph_sweep": "k_sweep", "ph_angles": "k_angles", "ph_compact": "k_compact"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -176,11 +175,10 @@ def algorithmic_bytes(kernel, precision, w):
         "k_scatter_cells": nb * (4 * v + 20),
         # both positions of every binned particle once, the cell starts once, the fired records
         "k_sweep": nb * 2 * v + 4 * cells + fired * 52,
-        # fired records and both degrees; accepted / conflict lists
-        "k_match_trivial": fired * 48,
-        # degrees cleared; per accepted pair or decay: record, state, 2x2 positions read, 2
-        # positions + statuses written (conflict rounds add re-reads of the conflict pairs)
-        "k_match_resolve": fired * 16 + (acc + dec) * (48 + 6 * v),
+        # trivial pairs: fired records and both degrees, accepted / conflict lists (48 B per fired
+        # pair); then degrees cleared, and per accepted pair or decay: record, state, 2x2 positions
+        # read, 2 positions + statuses written (conflict rounds add re-reads of the conflict pairs)
+        "k_match_resolve": fired * (48 + 16) + (acc + dec) * (48 + 6 * v),
         # one 160-B job per resolved pair or decay pair left to it; write two positions (only
         # when directions come from the full propagator)
         "k_angles": (acc + dec) * (160 + 2 * v) if w.get("angles") else 0,
@@ -188,6 +186,9 @@ def algorithmic_bytes(kernel, precision, w):
         "k_compact": n * (2 * v + 12),
     }
     table["k_step_fused"] = sum(table.values())      # the whole step in one launch
+    # the fused launch's two matching phases split the matching kernel's bytes
+    table["ph_match_trivial"] = fired * 48
+    table["ph_match_resolve"] = table["k_match_resolve"] - fired * 48
     kernel = KERNEL_OF_PHASE.get(kernel, kernel)     # a phase of the fused launch = its stage's kernel
     if kernel not in table:
         raise KeyError(f"no algorithmic byte count for step kernel {kernel}")
@@ -450,7 +451,8 @@ def run_ours(args, rank, world, local_rank):
                    "particles": int(obs1["counts"].sum()), "timing": "2-step CUDA graph launches, events on the library stream",
                    "l2": "flushed (512 MiB write) between timed graph launches",
                    "parallelism": f"replicas x{world} (one independent system per GPU)"},
-        "gpu_launches": steps_done // 2 if layout.get("fused") else KERNELS_PER_STEP * steps_done,
+        "gpu_launches": steps_done // 2 if layout.get("fused")
+        else (KERNELS_PER_STEP - (args.angle != "exact")) * steps_done,
         "layout": layout,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
     }
