@@ -2187,47 +2187,6 @@ __global__ void k_count(const DevParams* __restrict__ Pp, const DevCtl* __restri
 }
 
 // Standalone per-pair probabilities (rd_pair_probs).
-// double -> float (round to nearest, ties to even) and float -> double written out on the IEEE 754
-// bit patterns with integer operations.  The hardware conversions run on the FP64 pipe (1/64 of the
-// FP32 rate on this part): three per pair kept it 90% busy in the streaming mixed pair-probability
-// kernel.  All inputs handled (zeros, subnormals, overflow, infinities, NaNs).
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-  const int ed = (int)((b >> 52) & 0x7FFu);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  if (ed == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
-  const int e = ed - 1023 + 127;
-  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
-  if (e <= 0) {
-    // a float subnormal (or zero): the 53-bit significand shifted right by 30 - e bits
-    if (ed == 0 || e < -24) return __uint_as_float(sign);
-    const unsigned long long sig = m | (1ull << 52);
-    const int shift = 30 - e;
-    uint32_t r = (uint32_t)(sig >> shift);
-    const unsigned long long rem = sig & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
-    if (rem > half || (rem == half && (r & 1u))) r += 1u;
-    return __uint_as_float(sign | r);
-  }
-  uint32_t r = ((uint32_t)e << 23) | (uint32_t)(m >> 29);
-  const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);
-  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) r += 1u;   // a carry moves the exponent
-  return __uint_as_float(sign | r);
-}
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  if (e == 0u) {
-    if (m == 0u) return __longlong_as_double((long long)sign);
-    const int lz = __clz(m) - 8;    // shift that brings the leading one to bit 23
-    const unsigned long long en = (unsigned long long)(897 - lz);
-    return __longlong_as_double((long long)(sign | (en << 52) | ((unsigned long long)((m << lz) & 0x7FFFFFu) << 29)));
-  }
-  const unsigned long long eb = e == 255u ? 0x7FFull : (unsigned long long)(e - 127u + 1023u);
-  return __longlong_as_double((long long)(sign | (eb << 52) | ((unsigned long long)m << 29)));
-}
-
 // p_enc and p_reac of one pair at start / end separations a, b (um); kMixed3D: the mixed step in
 // 3D (no FP64 or 2D branch compiled, which keeps the streaming kernel's register count low).
 template <bool kMixed3D>
@@ -2235,11 +2194,10 @@ __device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev
                                                double& prc, bool want_enc, bool want_reac) {
   // mixed: the separations rounded once to FP32 and scaled there (FP64 arithmetic runs at 1/64 of
   // the FP32 rate on this part)
-  const float af = kMixed3D ? f64_to_f32_rn(a) : (float)a, bf = kMixed3D ? f64_to_f32_rn(b) : (float)b;
-  const float d0 = fmaf(af, pr.inv_sigma_f, -1.0f), d = fmaf(bf, pr.inv_sigma_f, -1.0f);
+  const float d0 = fmaf((float)a, pr.inv_sigma_f, -1.0f), d = fmaf((float)b, pr.inv_sigma_f, -1.0f);
   if (want_enc) {
     if (kMixed3D) {
-      pe = f32_to_f64(p_enc3_f(d, d0, pr.inv_tau_f));
+      pe = (double)p_enc3_f(d, d0, pr.inv_tau_f);
     } else if (P.precision == RD_MIXED) {
       float pf;
       if (P.dim == 3) {
@@ -2259,7 +2217,7 @@ __device__ __forceinline__ void pair_probs_one(const DevParams& P, const PairDev
     double v = pr.bc == RD_BC_ABS ? 1.0 : 0.0;
     if (pr.bc == RD_BC_RAD) {
       if (kMixed3D)
-        v = f32_to_f64(p_reac_tab(pr, d, d0));
+        v = (double)p_reac_tab(pr, d, d0);
       else
         v = P.precision == RD_MIXED ? (double)p_reac_tab(pr, d, d0) : p_reac_dim(P, pr, b / pr.sigma, a / pr.sigma);
     }
