@@ -135,10 +135,13 @@ typedef struct {
                                          passage_prob): 0 (default) drawn from the full propagator
                                          G_ref - G_abs, its angle to the start separation from the
                                          partial-wave series of Eqs. genericGF3D / genericGF (a draw
-                                         needing more than 128 partial waves, kappa = R' R0 / 2 tau
-                                         beyond ~40, keeps the free step's direction and is counted in
-                                         RD_STAT_ANGLE_FALLBACK); 1 the free step's direction kept, only
-                                         the length resampled */
+                                         needing more than 127 partial waves, kappa = R' R0 / 2 tau
+                                         beyond ~53, keeps the free step's direction and is counted in
+                                         RD_STAT_ANGLE_FALLBACK).  RD_FP64 evaluates the series per
+                                         pair (about a millisecond of FP64 work each); RD_MIXED reads a
+                                         per-rule table of the law built at rd_init (within 1e-4 in
+                                         the law's CDF); 1 the free step's direction kept, only the
+                                         length resampled */
   int32_t pad_angle;
   rd_allocator allocator;
 } rd_config;
@@ -317,8 +320,11 @@ int rd_kernel_times(rd_handle* h, int32_t cap, int32_t* n_out, char* names /* ca
  * millisecond); their size grows like (r_cut/sigma) (r_cut/sigma + 13 sqrt(tau)) / tau with
  * tau = (D_A + D_B) dt / sigma^2, so large steps do not fit: the 10 uM reversible system
  * (sigma = 0.005, D_A + D_B = 2) fits at dt = 1e-5 but not at dt = 1e-4 in RD_MIXED (RD_FP64 needs
- * no tables).  Inputs beyond any limit are rejected with RD_EINVAL before anything is enqueued, and
- * the outputs are left untouched.
+ * no tables).  No table of the angle law is built: with angle_mode 0 an RD_MIXED call evaluates
+ * that law per resampled pair in FP32 (about a millisecond of one warp each), where a handle reads
+ * its table, so the two agree within the FP32 angle tolerance, not bit for bit.  Inputs beyond any
+ * limit are rejected with RD_EINVAL before anything is enqueued, and the outputs are left
+ * untouched.
  *
  * Inputs (DEVICE pointers, caller-owned): x_in double[n*3] (positions in [0,L)),
  * species_in int32[n], id_in uint32[n] sorted ascending; next_id = first id for new products;
