@@ -1988,6 +1988,23 @@ __device__ __forceinline__ void ph_compact(const DevParams* Pp, DevCtl* ctl,
     const uint32_t tile = s_tile;
     if (tile >= ntiles) break;
     const int64_t t0 = (int64_t)tile * kTile;
+    // with at most two placement passes per thread, the placement's loads go out before the scan,
+    // so that their latency overlaps the scan and the look-back
+    constexpr int kPasses = kTile / kCompactThreads;
+    constexpr bool kEarly = kPasses <= 2;
+    typename V4<T>::type q_r[kEarly ? kPasses : 1];
+    uint32_t st_r[kEarly ? kPasses : 1], id_r[kEarly ? kPasses : 1];
+    if constexpr (kEarly) {
+#pragma unroll
+      for (int ps = 0; ps < kPasses; ++ps) {
+        const int64_t i = t0 + threadIdx.x + ps * kCompactThreads;
+        if (i < (int64_t)n) {
+          q_r[ps] = fail ? x0[i] : x1[i];
+          st_r[ps] = fail ? 0u : status[i];
+          id_r[ps] = id[i];
+        }
+      }
+    }
     if (!fail) {
       // blocked arrangement for the scan: each thread owns kCompactItems consecutive particles
       const int64_t base = t0 + (int64_t)threadIdx.x * kCompactItems;
@@ -2017,27 +2034,29 @@ __device__ __forceinline__ void ph_compact(const DevParams* Pp, DevCtl* ctl,
       __syncthreads();
     }
     // striped placement (coalesced), one particle per thread per pass, warp-converged counting
-    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+#pragma unroll
+    for (int ps = 0; ps < kPasses; ++ps) {
+      const int j = threadIdx.x + ps * kCompactThreads;
       const int64_t i = t0 + j;
       uint32_t k0 = kNoKey, k1 = kNoKey, k2 = kNoKey;
       if (i < (int64_t)n) {
         if (fail) {
-          const auto q0 = x0[i];
+          const auto q0 = kEarly ? q_r[kEarly ? ps : 0] : x0[i];
           xo[i] = q0;
-          ido[i] = id[i];
+          ido[i] = kEarly ? id_r[kEarly ? ps : 0] : id[i];
           k0 = key_of(w_bits(q0.w));
         } else {
           const unsigned long long e = s_pre[j];
           const uint32_t S_i = (uint32_t)(e >> 32), P_i = (uint32_t)e;
-          const uint32_t st = status[i];
-          const auto q = x1[i];
+          const uint32_t st = kEarly ? st_r[kEarly ? ps : 0] : status[i];
+          const auto q = kEarly ? q_r[kEarly ? ps : 0] : x1[i];
           const uint32_t wb = w_bits(q.w);
           const uint32_t r = wb >> 8;
           const RepX rx = one ? rx1 : repx[r];
           if (!(st & ST_CONSUMED)) {
             const uint32_t o = S_i + rx.p_beg;
             xo[o] = q;
-            ido[o] = id[i];
+            ido[o] = kEarly ? id_r[kEarly ? ps : 0] : id[i];
             k0 = key_of(wb);
           }
           const uint32_t np = (st >> ST_NPROD_SHIFT) & 3u;
