@@ -41,3 +41,43 @@ def test_two_gloo_ranks_reduce_like_the_benchmark(tmp_path):
         assert float(t) == 2.5                 # slowest rank
         assert float(ps) == 3000.0             # all ranks' particle-steps
         assert printed == "None"
+
+
+def _rank_systems(rank, world, port, out_dir):
+    # each rank steps its own seeded system (the benchmark's workload shape at a small size, on the
+    # CPU oracle) and the whole-job figure adds up both ranks' particle-steps
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import hashlib
+    import time
+
+    import bench
+    import oracle as O
+
+    args = bench.parse(["--n-each", "300", "--steps", "2", "--warmup", "0"])
+    system = bench.workload(args, seed=1 + rank)
+    st = O.init_state(system)
+    ps = 0
+    t0 = time.perf_counter()
+    for _ in range(2):
+        ps += st.n
+        st, _ = O.step(system, st)
+    el = time.perf_counter() - t0
+    t, total = bench.reduce_over_ranks(dist, torch, el, ps, "cpu")
+    digest = hashlib.sha256(st.x.tobytes() + st.ids.tobytes()).hexdigest()
+    with open(os.path.join(out_dir, f"s{rank}.txt"), "w") as f:
+        f.write(f"{system.seed} {ps} {total} {t >= el} {digest}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_step_independent_seeded_systems(tmp_path):
+    port = _free_port()
+    mp.start_processes(_rank_systems, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn")
+    rows = [open(tmp_path / f"s{r}.txt").read().split() for r in range(2)]
+    assert [int(r[0]) for r in rows] == [1, 2]                 # one seed per rank
+    assert rows[0][4] != rows[1][4]                            # different trajectories
+    ps = [int(r[1]) for r in rows]
+    assert all(float(r[2]) == float(sum(ps)) for r in rows)    # the job's particle-steps on every rank
+    assert all(r[3] == "True" for r in rows)                   # the job time is the slowest rank's
