@@ -1989,7 +1989,8 @@ __device__ __forceinline__ void ph_compact(const DevParams* Pp, DevCtl* ctl,
     if (tile >= ntiles) break;
     const int64_t t0 = (int64_t)tile * kTile;
     // with at most two placement passes per thread, the placement's loads go out before the scan,
-    // so that their latency overlaps the scan and the look-back
+    // so that their latency overlaps the scan and the look-back (more passes' worth of registers
+    // cost occupancy: 512-thread tiles with four early passes ran at half the speed)
     constexpr int kPasses = kTile / kCompactThreads;
     constexpr bool kEarly = kPasses <= 2;
     typename V4<T>::type q_r[kEarly ? kPasses : 1];
