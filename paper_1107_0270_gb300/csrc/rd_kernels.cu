@@ -827,18 +827,6 @@ __device__ __forceinline__ void ph_match_trivial(DevCtl* ctl, const FiredPair* f
   warp_sum_add(&ctl->stats[RD_STAT_MATCHED], acc);
 }
 
-__global__ void k_match_trivial(DevCtl* __restrict__ ctl, const FiredPair* __restrict__ fired,
-                                uint32_t* __restrict__ fstate, const uint32_t* __restrict__ deg,
-                                int32_t* __restrict__ matched, uint32_t* __restrict__ conflict,
-                                uint32_t* __restrict__ accepted,
-                                unsigned long long* __restrict__ best_key,
-                                unsigned long long* __restrict__ best_pid, uint32_t cap_pairs,
-                                ConflictRec* __restrict__ crec) {
-  pdl_enter();
-  ph_match_trivial(ctl, fired, fstate, deg, matched, conflict, accepted, best_key, best_pid, cap_pairs, crec,
-                   blockIdx.x, gridDim.x);
-}
-
 // Grid-wide barrier of the cooperative matching launch (every block resident).  Bounded: a block
 // that waits longer than kBarrierSpin polls sets RD_ETIMEOUT and leaves; the caller then stops.
 constexpr uint32_t kBarrierSpin = 1u << 22;
