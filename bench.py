@@ -506,7 +506,13 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b) * 1e-3)
         t = statistics.median(times)
-        res[prec] = {"evals_per_s": r0.numel() / t, "gbs": r0.numel() * 24 / t / 1e9, "pairs": r0.numel()}
+        gbs = r0.numel() * 24 / t / 1e9
+        peak, _ = measured_peaks()
+        res[prec] = {"evals_per_s": r0.numel() / t, "gbs": gbs, "pairs": r0.numel(),
+                     # 24 B per pair against the measured HBM copy rate; the FP64 batch is bound by
+                     # the FP64 pipe instead (profiles/k_pair_probs_fp64_2e25pairs.md)
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak}}
         sim.close()
     # error of the mixed probabilities at scale: the 2^20 distinct pairs of the batch, mixed against
     # the FP64 GPU values (which match the oracle to 1e-12)
