@@ -495,6 +495,7 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
         times = []
         for _ in range(10):
             flush.add_(1)
+            torch.cuda.synchronize()           # the flush has finished before the timed launch
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(sim.stream):
