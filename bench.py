@@ -329,6 +329,8 @@ def timed_graph_run(sim, torch, flush, steps):
     for k in range(launches):
         with torch.cuda.stream(s):
             flush.add_(1)                      # L2 flush, outside the timed events
+        s.synchronize()                        # finished before the timed launch starts
+        with torch.cuda.stream(s):
             starts[k].record(s)
         sim.run(2)
         with torch.cuda.stream(s):
