@@ -590,10 +590,58 @@ def extra_measurements(args, torch, pkg, flush, sim_main):
             d2h += st["ids"].shape[0] * (24 + 4 + 4) + 4
             n_e2e += 1
         rates.append(ps / (time.perf_counter() - t0))
+    binding_rate = statistics.median(rates)
+    # the same three calls made on the C ABI directly (what a C caller does): pointers and
+    # by-reference outputs prepared once, so the host's share per step is the three calls alone
+    import ctypes as C
+
+    lib, h = pkg._lib(), sim._h
+    ptrs = [(b["x"].ctypes.data_as(C.POINTER(C.c_double)), b["species"].ctypes.data_as(C.POINTER(C.c_int32)),
+             b["ids"].ctypes.data_as(C.POINTER(C.c_uint32)), b["next_id"].ctypes.data_as(C.POINTER(C.c_uint32)))
+            for b in bufs]
+    n_io, step_io = C.c_int64(), C.c_int64()
+    n_ref, step_ref = C.byref(n_io), C.byref(step_io)
+    n_cur, step_cur = int(st["ids"].shape[0]), int(st["step"])
+    if st["ids"].ctypes.data != bufs[0]["ids"].ctypes.data:     # the state must sit in buffer 0
+        for key in ("x", "species", "ids"):
+            bufs[0][key][:n_cur] = st[key]
+        bufs[0]["next_id"][:] = st["next_id"]
+
+    def capi_step(k, n, step):
+        xa, spa, ida, nxa = ptrs[k % 2]
+        xb, spb, idb, nxb = ptrs[(k + 1) % 2]
+        rc = lib.rd_set_state(h, n, xa, spa, ida, None, nxa, step)
+        if rc == 0:
+            rc = lib.rd_step(h)
+        if rc == 0:
+            n_io.value = cap
+            rc = lib.rd_get_state(h, n_ref, xb, spb, idb, None, nxb, step_ref)
+        if rc != 0:
+            raise pkg.RDError(rc, "C-ABI end-to-end step")
+        return n_io.value, step_io.value
+
+    for k in range(4):                                            # even count: the state is back in buffer 0
+        n_cur, step_cur = capi_step(k, n_cur, step_cur)
+    rates, h2d, d2h, n_e2e = [], 0, 0, 0
+    for _ in range(5):
+        t0 = time.perf_counter()
+        ps = 0
+        for k in range(20):
+            n_in = n_cur
+            n_cur, step_cur = capi_step(k, n_cur, step_cur)
+            ps += n_in
+            h2d += n_in * (24 + 4 + 4) + 4
+            d2h += n_cur * (24 + 4 + 4) + 4
+            n_e2e += 1
+        rates.append(ps / (time.perf_counter() - t0))
     out["e2e"] = {"value": statistics.median(rates), "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // n_e2e,
                   "d2h_bytes_per_step": d2h // n_e2e,
                   "path": "rd_set_state (page-locked host arrays: positions, species, ids, next id) + rd_step "
-                          "+ rd_get_state (the same arrays back), per step"}
+                          "+ rd_get_state (the same arrays back), per step, called on the C ABI with "
+                          "pointers prepared once",
+                  "binding_value": binding_rate,
+                  "binding_path": "the same three calls through the Python binding's Simulation.set_state / "
+                                  "step / get_state"}
     sim.close()
     return out
 
