@@ -6,6 +6,9 @@ and exits; the kernel of interest is then captured with `ncu -k regex:<kernel> -
   python profile_cases.py ensemble R        the first R replicas of the 4096-replica ensemble, mixed
   python profile_cases.py pairprob PREC     2^25 candidate-shaped pairs of the headline rule (PREC
                                             mixed or fp64), three batches
+  python profile_cases.py angles PREC       the headline 3D A+B<->C system (1e5 + 1e5, dt = 1e-5)
+                                            with directions drawn from the full propagator (PREC
+                                            mixed or fp64), six steps: the angle pass runs once a step
 """
 import argparse
 
@@ -16,8 +19,8 @@ import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["network", "ensemble", "pairprob"])
-    ap.add_argument("size", help="network: scale; ensemble: replicas; pairprob: precision")
+    ap.add_argument("case", choices=["network", "ensemble", "pairprob", "angles"])
+    ap.add_argument("size", help="network: scale; ensemble: replicas; pairprob, angles: precision")
     args = ap.parse_args()
 
     import torch
@@ -38,6 +41,15 @@ def main():
         sim.close()
         return
     system = W.reversible_3d(dt=1e-5, seed=2, n_each=100_000, L=2.55, equilibrium_start=True)
+    if args.case == "angles":
+        system.angle = "exact"
+        sim = pkg.Simulation(system, precision=args.size, step_launch="separate")
+        sim.run(4)
+        for _ in range(2):
+            print(dict(sim.timed_step()), flush=True)
+        print("particles", sim.num_particles(), "stats", sim.observables()["stats"], flush=True)
+        sim.close()
+        return
     pr = system.pairs[0]
     d_rel = system.D[pr.s1] + system.D[pr.s2]
     r0n, rn = W.pair_samples(1 << 20, pr.sigma, d_rel, system.dt, seed=11)
