@@ -6,9 +6,11 @@ and exits; the kernel of interest is then captured with `ncu -k regex:<kernel> -
   python profile_cases.py ensemble R        the first R replicas of the 4096-replica ensemble, mixed
   python profile_cases.py pairprob PREC     2^25 candidate-shaped pairs of the headline rule (PREC
                                             mixed or fp64), three batches
-  python profile_cases.py angles PREC       the headline 3D A+B<->C system (1e5 + 1e5, dt = 1e-5)
-                                            with directions drawn from the full propagator (PREC
-                                            mixed or fp64), six steps: the angle pass runs once a step
+  python profile_cases.py headline PREC     the headline 3D A+B<->C system (1e5 + 1e5, dt = 1e-5,
+                                            mass-action start), free-step directions (PREC mixed or
+                                            fp64), separate kernels, six steps
+  python profile_cases.py angles PREC       the same system with directions drawn from the full
+                                            propagator: the angle pass runs once a step
 """
 import argparse
 
@@ -19,8 +21,8 @@ import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["network", "ensemble", "pairprob", "angles"])
-    ap.add_argument("size", help="network: scale; ensemble: replicas; pairprob, angles: precision")
+    ap.add_argument("case", choices=["network", "ensemble", "pairprob", "headline", "angles"])
+    ap.add_argument("size", help="network: scale; ensemble: replicas; pairprob, headline, angles: precision")
     args = ap.parse_args()
 
     import torch
@@ -41,8 +43,8 @@ def main():
         sim.close()
         return
     system = W.reversible_3d(dt=1e-5, seed=2, n_each=100_000, L=2.55, equilibrium_start=True)
-    if args.case == "angles":
-        system.angle = "exact"
+    if args.case in ("headline", "angles"):
+        system.angle = "exact" if args.case == "angles" else "free_step"
         sim = pkg.Simulation(system, precision=args.size, step_launch="separate")
         sim.run(4)
         for _ in range(2):
